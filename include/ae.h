@@ -1,0 +1,175 @@
+/*
+ * ae.h — C ABI of the GB300 exact local-alignment search library (libae.so).
+ *
+ * The library answers the local-alignment problem of Section 2.1: for a text T
+ * (n letters) and a query P (m letters), every pair (text end i, query end j)
+ * whose largest similarity max_{x<=i, y<=j} sim(T[x..i], P[y..j]) reaches a
+ * threshold H, with sim the best global-alignment score under an affine-gap
+ * scheme (Algorithm 1's output A(i,j) >= H).  It walks the suffix trie of T
+ * through an FM index of the reversed text (Section 5), computes one Gotoh row
+ * per trie node (Section 2.2) and skips the entries that Theorems 1-3 prove
+ * meaningless (Section 3.1).
+ *
+ * Conventions
+ *  - Letters are ASCII: DNA "ACGT" (upper case), protein the 20 residues
+ *    "ARNDCQEGHILKMFPSTWYV".  Any other byte is an error (AE_EINVAL).
+ *  - Positions are 0-based, ends inclusive (the paper is 1-based: pi = end+1).
+ *  - Every entry point returns an ae_status; no C++ exception crosses the ABI.
+ *  - Host pointers are marked "host", device pointers "device" (CUDA global
+ *    memory of the current device).  The library never frees caller memory.
+ *  - An ae_index is immutable after build/load and may be shared by threads;
+ *    run at most one search per stream at a time.
+ */
+#ifndef AE_H
+#define AE_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    AE_OK = 0,
+    AE_EINVAL = 1,        /* bad argument: scheme signs, H < 1, unknown letter, empty text */
+    AE_ENOMEM = 2,        /* host or device allocation failed */
+    AE_EOVERFLOW = 3,     /* caller buffer too small; required sizes are returned */
+    AE_ETIMEOUT = 4,      /* a bounded device wait gave up */
+    AE_ECUDA = 5,         /* a CUDA runtime call failed */
+    AE_EUNSUPPORTED = 6,  /* sizes beyond what this build handles (e.g. n >= 2^31) */
+    AE_EIO = 7            /* file read/write or format error */
+} ae_status;
+
+enum { AE_DNA = 0, AE_PROTEIN = 1 };
+
+typedef struct ae_index ae_index;   /* opaque; owns its device memory */
+
+/* Scoring scheme <s_a, s_b, s_g, s_s> of Section 2.1: an identical pair scores
+ * match (> 0), a substitution mismatch (< 0), a run of r gap letters scores
+ * gap_open + r * gap_extend (gap_open <= 0, gap_extend < 0).  If matrix is not
+ * NULL it is a host sigma x sigma table (row = text letter, column = query
+ * letter, alphabet order above) used instead of match/mismatch; its diagonal
+ * must be positive.  With a matrix the q-prefix seeding of Theorem 3 is off
+ * and the trie walk starts at the root. */
+typedef struct {
+    int32_t match;
+    int32_t mismatch;
+    const int8_t *matrix;
+    int32_t gap_open;
+    int32_t gap_extend;
+} ae_scoring;
+
+/* One result: the largest similarity `score` of any alignment ending at text
+ * position text_end and query position query_end (Algorithm 1 line 11). */
+typedef struct {
+    int64_t text_end;
+    int32_t query_end;
+    int32_t score;
+} ae_hit;
+
+typedef struct {
+    const uint8_t *seq;   /* host ASCII letters */
+    int64_t len;
+} ae_query;
+
+/* Counters of the last search on the calling thread, summed over queries.
+ * The tiers follow Table 4's cost model: an entry whose value came from one
+ * live term of the recurrence (the no-gap form of Eq. 3) costs 1, from two
+ * live terms 2, from all three 3. */
+typedef struct {
+    int64_t nodes;          /* trie nodes whose rows were computed (range size >= 2) */
+    int64_t leaf_rows;      /* rows computed along unique text positions */
+    int64_t entries;        /* live DP entries written */
+    int64_t entries_tier[3];
+    int64_t injections;     /* trie rows handed to the text-position sweep */
+    int64_t raw_hits;       /* hit records before the per-cell max */
+    int64_t hits;           /* distinct (query, text end, query end) results */
+    int32_t levels;         /* trie levels expanded */
+    int32_t seed_depth;     /* depth the trie walk started at */
+    double  ms_trie, ms_leaf, ms_reduce, ms_total;
+} ae_stats;
+
+/* Engine knobs (NULL = defaults).  None of them changes the result set. */
+typedef struct {
+    int32_t qprefix_seed;   /* 1: start at depth q-1 from the query's (q-1)-grams (Theorem 3); 0: root */
+    int32_t leaf_segment;   /* trie rows merged per sweep task (>= 1) */
+    int64_t item_columns;   /* query columns per work item (seed range) */
+    int64_t batch_columns;  /* query columns processed per batch */
+    int32_t leaf_capacity;  /* initial per-task row capacity of the sweep, in entries */
+} ae_options;
+
+/* Fill *opt with the defaults. */
+void ae_options_default(ae_options *opt);
+
+/* Build an index of text[0..n) (host ASCII) for `alphabet` (AE_DNA or
+ * AE_PROTEIN): the suffix array of the reversed text followed by a sentinel,
+ * its BWT packed into occurrence blocks (2-bit symbols for DNA, 5 bit-planes
+ * for protein) with sampled ranks, the text-end array (entry h = end position
+ * in T of the substrings whose reverse prefixes suffix h), and the forward
+ * text (Section 2.3 and Section 5 (1)-(3)).  The suffix array is built on the
+ * host; the index is then copied once to the current CUDA device.
+ * Errors: AE_EINVAL (n < 1, unknown letter, bad alphabet), AE_EUNSUPPORTED
+ * (n >= 2^31 - 1), AE_ENOMEM, AE_ECUDA. */
+ae_status ae_index_build(const uint8_t *text, int64_t n, int32_t alphabet, ae_index **out);
+
+/* Write / read an index file (versioned header + checksum).  Load copies to
+ * the current device.  Errors: AE_EIO, AE_ENOMEM, AE_ECUDA. */
+ae_status ae_index_save(const ae_index *idx, const char *path);
+ae_status ae_index_load(const char *path, ae_index **out);
+
+/* Release the index and its device memory (NULL is ignored). */
+void ae_index_free(ae_index *idx);
+
+/* Text length, alphabet and device bytes held by the index. */
+ae_status ae_index_info(const ae_index *idx, int64_t *n, int32_t *alphabet, int64_t *device_bytes);
+
+/* Search nq host queries with per-query thresholds H[k] >= 1 (host array).
+ * On success *hits is one library-allocated host array holding every result,
+ * grouped by query in input order and sorted by (text_end, query_end) inside
+ * a group; counts[k] (host, nq entries) is the number of results of query k.
+ * Free *hits with ae_hits_free.  stream is a cudaStream_t (NULL = the legacy
+ * default stream); the call returns after the results are on the host.
+ * Errors: AE_EINVAL, AE_ENOMEM, AE_ECUDA, AE_EUNSUPPORTED. */
+ae_status ae_search(const ae_index *idx, const ae_query *queries, int32_t nq,
+                    const ae_scoring *scoring, const int32_t *H, const ae_options *opt,
+                    ae_hit **hits, int64_t *counts, void *stream);
+
+void ae_hits_free(ae_hit *hits);
+
+/* Same search with device-resident input and output.  d_seq (device) holds the
+ * nq queries' ASCII letters back to back; offsets (host, nq+1 entries) delimit
+ * query k as d_seq[offsets[k] .. offsets[k+1]).  Results are written to d_hits
+ * (device, capacity entries) in the order ae_search uses, and counts (host, nq)
+ * receives the per-query result counts.  If the total exceeds capacity nothing
+ * is written to d_hits, counts still holds the required sizes, and the call
+ * returns AE_EOVERFLOW.  Working memory is allocated by the library and kept
+ * on the index between calls. */
+ae_status ae_search_device(const ae_index *idx, const uint8_t *d_seq, const int64_t *offsets,
+                           int32_t nq, const ae_scoring *scoring, const int32_t *H,
+                           const ae_options *opt, ae_hit *d_hits, int64_t capacity,
+                           int64_t *counts, void *stream);
+
+/* Counters of the calling thread's last search. */
+ae_status ae_last_stats(ae_stats *out);
+
+/* Host helpers used by the index build and the engine, exposed for tests. */
+
+/* Suffix array of codes[0..n) followed by a sentinel smaller than every code
+ * (so sa has n+1 entries and sa[0] = n).  codes are in [0, sigma).  Built with
+ * induced sorting (SA-IS, Nong, Zhang & Chan 2009).  Host memory. */
+ae_status ae_suffix_array(const uint8_t *codes, int64_t n, int32_t sigma, int32_t *sa);
+
+/* For a query of length m over `alphabet`: q of Eq. 2 (0 with a matrix), the
+ * depth the trie walk starts at, and L_max of Eq. 1 (with the largest matrix
+ * entry in place of s_a when a matrix is given).  Outputs may be NULL. */
+ae_status ae_plan(int64_t m, int32_t alphabet, const ae_scoring *scoring, int32_t H,
+                  int32_t *q, int32_t *seed_depth, int64_t *L_max);
+
+/* Human-readable text of a status code (static storage). */
+const char *ae_strerror(int32_t status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AE_H */

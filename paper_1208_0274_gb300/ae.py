@@ -1,0 +1,289 @@
+"""Python binding of libae (include/ae.h): argument marshalling only.
+
+Every function here has the name and meaning of the C entry point it wraps;
+all compute happens in the library's CUDA kernels.  The library is loaded
+from this package directory; if it is missing the import of this module
+fails with an error naming the build command (there is no fallback path).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIBPATH = os.path.join(_HERE, "libae.so")
+
+AE_OK, AE_EINVAL, AE_ENOMEM, AE_EOVERFLOW, AE_ETIMEOUT, AE_ECUDA, AE_EUNSUPPORTED, AE_EIO = range(8)
+AE_DNA, AE_PROTEIN = 0, 1
+ALPHABETS = {AE_DNA: b"ACGT", AE_PROTEIN: b"ARNDCQEGHILKMFPSTWYV"}
+
+HIT_DTYPE = np.dtype([("text_end", "<i8"), ("query_end", "<i4"), ("score", "<i4")])
+
+
+class AEError(RuntimeError):
+    def __init__(self, status, where):
+        self.status = status
+        super().__init__(f"{where}: {strerror(status)} (status {status})")
+
+
+class ae_scoring(ctypes.Structure):
+    _fields_ = [("match", ctypes.c_int32), ("mismatch", ctypes.c_int32),
+                ("matrix", ctypes.c_void_p), ("gap_open", ctypes.c_int32),
+                ("gap_extend", ctypes.c_int32)]
+
+
+class ae_query(ctypes.Structure):
+    _fields_ = [("seq", ctypes.c_void_p), ("len", ctypes.c_int64)]
+
+
+class ae_options(ctypes.Structure):
+    _fields_ = [("qprefix_seed", ctypes.c_int32), ("leaf_segment", ctypes.c_int32),
+                ("item_columns", ctypes.c_int64), ("batch_columns", ctypes.c_int64),
+                ("leaf_capacity", ctypes.c_int32)]
+
+
+class ae_stats(ctypes.Structure):
+    _fields_ = [("nodes", ctypes.c_int64), ("leaf_rows", ctypes.c_int64),
+                ("entries", ctypes.c_int64), ("entries_tier", ctypes.c_int64 * 3),
+                ("injections", ctypes.c_int64), ("raw_hits", ctypes.c_int64),
+                ("hits", ctypes.c_int64), ("levels", ctypes.c_int32),
+                ("seed_depth", ctypes.c_int32), ("ms_trie", ctypes.c_double),
+                ("ms_leaf", ctypes.c_double), ("ms_reduce", ctypes.c_double),
+                ("ms_total", ctypes.c_double)]
+
+
+def _load():
+    if not os.path.exists(LIBPATH):
+        raise ImportError(f"{LIBPATH} is missing: build it with "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(LIBPATH)
+    V, I64, I32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    sig = {
+        "ae_options_default": (None, [V]),
+        "ae_strerror": (ctypes.c_char_p, [I32]),
+        "ae_index_build": (I32, [V, I64, I32, V]),
+        "ae_index_save": (I32, [V, ctypes.c_char_p]),
+        "ae_index_load": (I32, [ctypes.c_char_p, V]),
+        "ae_index_free": (None, [V]),
+        "ae_index_info": (I32, [V, V, V, V]),
+        "ae_search": (I32, [V, V, I32, V, V, V, V, V, V]),
+        "ae_hits_free": (None, [V]),
+        "ae_search_device": (I32, [V, V, V, I32, V, V, V, V, I64, V, V]),
+        "ae_last_stats": (I32, [V]),
+        "ae_suffix_array": (I32, [V, I64, I32, V]),
+        "ae_plan": (I32, [I64, I32, V, I32, V, V, V]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(lib, name)
+        f.restype = res
+        f.argtypes = args
+    return lib
+
+
+lib = _load()
+
+
+def strerror(status):
+    return lib.ae_strerror(int(status)).decode()
+
+
+def _check(st, where):
+    if st != AE_OK:
+        raise AEError(st, where)
+
+
+def _u8(seq):
+    if isinstance(seq, str):
+        seq = seq.encode()
+    if isinstance(seq, (bytes, bytearray)):
+        return np.frombuffer(bytes(seq), dtype=np.uint8)
+    return np.ascontiguousarray(np.asarray(seq, dtype=np.uint8))
+
+
+def make_scoring(scheme, alphabet=AE_DNA):
+    """ae_scoring from any object with match / mismatch / gap_open /
+    gap_extend (/ matrix) attributes, or a dict with those keys. Returns the
+    struct and the matrix buffer it points to (keep both alive)."""
+    get = (lambda k, d=None: scheme.get(k, d)) if isinstance(scheme, dict) else \
+        (lambda k, d=None: getattr(scheme, k, d))
+    s = ae_scoring()
+    s.match = int(get("match", 1))
+    s.mismatch = int(get("mismatch", -3))
+    s.gap_open = int(get("gap_open", -5))
+    s.gap_extend = int(get("gap_extend", -2))
+    mat = get("matrix", None)
+    buf = None
+    if mat is not None:
+        buf = np.ascontiguousarray(np.asarray(mat, dtype=np.int8))
+        s.matrix = buf.ctypes.data
+    else:
+        s.matrix = None
+    return s, buf
+
+
+def ae_options_default():
+    o = ae_options()
+    lib.ae_options_default(ctypes.byref(o))
+    return o
+
+
+def make_options(**kw):
+    o = ae_options_default()
+    for k, v in kw.items():
+        if v is not None:
+            setattr(o, k, int(v))
+    return o
+
+
+class Index:
+    """Owns one ae_index*; freed with ae_index_free."""
+
+    def __init__(self, handle, alphabet):
+        self._h = ctypes.c_void_p(handle)
+        self.alphabet = alphabet
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if self._h and self._h.value:
+            lib.ae_index_free(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def ae_index_build(text, alphabet=AE_DNA):
+    t = _u8(text)
+    out = ctypes.c_void_p(0)
+    _check(lib.ae_index_build(t.ctypes.data, t.size, int(alphabet), ctypes.byref(out)), "ae_index_build")
+    return Index(out.value, alphabet)
+
+
+def ae_index_save(index, path):
+    _check(lib.ae_index_save(index.handle, str(path).encode()), "ae_index_save")
+
+
+def ae_index_load(path):
+    out = ctypes.c_void_p(0)
+    _check(lib.ae_index_load(str(path).encode(), ctypes.byref(out)), "ae_index_load")
+    n, a, b = ae_index_info_raw(out)
+    return Index(out.value, a)
+
+
+def ae_index_info_raw(handle):
+    n = ctypes.c_int64()
+    a = ctypes.c_int32()
+    b = ctypes.c_int64()
+    _check(lib.ae_index_info(handle, ctypes.byref(n), ctypes.byref(a), ctypes.byref(b)), "ae_index_info")
+    return n.value, a.value, b.value
+
+
+def ae_index_info(index):
+    n, a, b = ae_index_info_raw(index.handle)
+    return {"n": n, "alphabet": a, "device_bytes": b}
+
+
+def _thresholds(H, nq):
+    h = np.full(nq, H, dtype=np.int32) if np.isscalar(H) else np.ascontiguousarray(np.asarray(H, dtype=np.int32))
+    if h.size != nq:
+        raise ValueError("one threshold per query")
+    return h
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if isinstance(stream, int):
+        return stream
+    return int(getattr(stream, "cuda_stream"))
+
+
+def ae_search(index, queries, scheme, H, options=None, stream=None):
+    """Host queries in, host results out. Returns (hits, counts): hits is a
+    structured array (text_end, query_end, score) grouped by query and sorted
+    by (text_end, query_end); counts[k] is query k's number of results."""
+    qs = [_u8(q) for q in queries]
+    nq = len(qs)
+    arr = (ae_query * max(nq, 1))()
+    for k, q in enumerate(qs):
+        arr[k].seq = q.ctypes.data if q.size else None
+        arr[k].len = q.size
+    h = _thresholds(H, nq)
+    sc, _mat = make_scoring(scheme, index.alphabet)
+    out = ctypes.c_void_p(0)
+    counts = np.zeros(max(nq, 1), dtype=np.int64)
+    st = lib.ae_search(index.handle, ctypes.cast(arr, ctypes.c_void_p), nq, ctypes.byref(sc),
+                       h.ctypes.data, ctypes.byref(options) if options is not None else None,
+                       ctypes.byref(out), counts.ctypes.data, _stream_handle(stream))
+    _check(st, "ae_search")
+    total = int(counts[:nq].sum())
+    hits = np.empty(total, dtype=HIT_DTYPE)
+    if total:
+        ctypes.memmove(hits.ctypes.data, out.value, total * HIT_DTYPE.itemsize)
+    lib.ae_hits_free(out)
+    return hits, counts[:nq].copy()
+
+
+def ae_search_device(index, d_seq_ptr, offsets, scheme, H, d_hits_ptr, capacity, options=None, stream=None):
+    """Device-resident queries (d_seq_ptr: device address of the ASCII letters
+    back to back; offsets: host int64 nq+1) and results (d_hits_ptr: device
+    buffer of `capacity` 16-byte hits). Returns (status, counts); status is
+    AE_OK or AE_EOVERFLOW (counts then hold the sizes needed)."""
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    nq = off.size - 1
+    h = _thresholds(H, nq)
+    sc, _mat = make_scoring(scheme, index.alphabet)
+    counts = np.zeros(max(nq, 1), dtype=np.int64)
+    st = lib.ae_search_device(index.handle, ctypes.c_void_p(int(d_seq_ptr)), off.ctypes.data, nq,
+                              ctypes.byref(sc), h.ctypes.data,
+                              ctypes.byref(options) if options is not None else None,
+                              ctypes.c_void_p(int(d_hits_ptr)) if d_hits_ptr else None, int(capacity),
+                              counts.ctypes.data, _stream_handle(stream))
+    if st not in (AE_OK, AE_EOVERFLOW):
+        _check(st, "ae_search_device")
+    return st, counts[:nq].copy()
+
+
+def ae_last_stats():
+    s = ae_stats()
+    _check(lib.ae_last_stats(ctypes.byref(s)), "ae_last_stats")
+    d = {k: getattr(s, k) for k, _ in ae_stats._fields_}
+    d["entries_tier"] = list(s.entries_tier)
+    return d
+
+
+def ae_suffix_array(codes, sigma):
+    c = _u8(codes)
+    sa = np.empty(c.size + 1, dtype=np.int32)
+    _check(lib.ae_suffix_array(c.ctypes.data if c.size else None, c.size, int(sigma), sa.ctypes.data),
+           "ae_suffix_array")
+    return sa
+
+
+def ae_plan(m, scheme, H, alphabet=AE_DNA):
+    sc, _mat = make_scoring(scheme, alphabet)
+    q = ctypes.c_int32()
+    d0 = ctypes.c_int32()
+    L = ctypes.c_int64()
+    _check(lib.ae_plan(int(m), int(alphabet), ctypes.byref(sc), int(H), ctypes.byref(q), ctypes.byref(d0),
+                       ctypes.byref(L)), "ae_plan")
+    return q.value, d0.value, L.value
+
+
+def encode_codes(seq, alphabet=AE_DNA):
+    """ASCII -> letter codes (host helper for tests of ae_suffix_array)."""
+    a = np.frombuffer(ALPHABETS[alphabet], dtype=np.uint8)
+    lut = np.full(256, 255, dtype=np.uint8)
+    lut[a] = np.arange(a.size, dtype=np.uint8)
+    c = lut[_u8(seq)]
+    if c.size and c.max() == 255:
+        raise ValueError("letter outside the alphabet")
+    return c

@@ -1,0 +1,887 @@
+// Host orchestration of the search and the C ABI of include/ae.h.
+//
+// ae_search_device runs, per batch of work items:
+//   seed (Theorem 3: the query's (q-1)-grams located by backward search) or
+//   the trie root;  then one trie level per iteration (count pass, scan, write
+//   pass) until the frontier is empty;  then the text-position sweep over the
+//   rows that reached a single occurrence;  then the located hits of the
+//   multi-occurrence nodes.  All hits of all batches are sorted by
+//   (query, text end, query end) and reduced to the per-cell maximum
+//   (Algorithm 1, lines 6-11).
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <mutex>
+#include <new>
+#include <vector>
+
+#include "ae_internal.h"
+#include "ae_kernels.h"
+
+namespace {
+
+thread_local ae_stats g_last_stats;
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct ae_error {
+    ae_status st;
+};
+
+#define CU(x)                                    \
+    do {                                         \
+        cudaError_t _e = (x);                    \
+        if (_e != cudaSuccess) throw ae_error{AE_ECUDA}; \
+    } while (0)
+
+// Grow-only device buffer; contents are not preserved.
+void ensure(DevBuf &b, size_t bytes, cudaStream_t st) {
+    if (bytes <= b.bytes) return;
+    size_t nb = std::max(bytes, b.bytes + b.bytes / 2);
+    nb = (nb + 255) & ~size_t(255);
+    if (b.p) {
+        CU(cudaStreamSynchronize(st));
+        CU(cudaFree(b.p));
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    if (cudaMalloc(&b.p, nb) != cudaSuccess) {
+        cudaGetLastError();
+        throw ae_error{AE_ENOMEM};
+    }
+    b.bytes = nb;
+}
+
+// Grow preserving the first `keep` bytes.
+void ensure_keep(DevBuf &b, size_t bytes, size_t keep, cudaStream_t st) {
+    if (bytes <= b.bytes) return;
+    size_t nb = std::max(bytes, b.bytes + b.bytes / 2);
+    nb = (nb + 255) & ~size_t(255);
+    void *p = nullptr;
+    if (cudaMalloc(&p, nb) != cudaSuccess) {
+        cudaGetLastError();
+        throw ae_error{AE_ENOMEM};
+    }
+    if (b.p) {
+        if (keep) CU(cudaMemcpyAsync(p, b.p, keep, cudaMemcpyDeviceToDevice, st));
+        CU(cudaStreamSynchronize(st));
+        CU(cudaFree(b.p));
+    }
+    b.p = p;
+    b.bytes = nb;
+}
+
+template <typename T>
+T *ptr(DevBuf &b) {
+    return reinterpret_cast<T *>(b.p);
+}
+
+struct Workspace {
+    cudaStream_t stream = nullptr;
+    // queries
+    DevBuf ascii, codes, qoff, qm, qH, items, item_pos, bad;
+    // level arenas (ping-pong) and nodes
+    DevBuf aj[2], aM[2], aGa[2], nodes[2];
+    // count outputs and scanned offsets (5 arrays each)
+    DevBuf cnt[5], off[5], totals, scan_tmp;
+    // leaf arena, injections, range hits
+    DevBuf lj, lM, lGa, inj, rhits;
+    // sort buffers
+    DevBuf sk0, sv0, sk1, sv1, sort_tmp;
+    // point hits of the whole search
+    DevBuf hkey, hscore, hcount, hk1, hv1;
+    // leaf sweep scratch
+    DevBuf scratch, next_seg;
+    // output
+    DevBuf uniq, uflags, uoff, qcount;
+    DevBuf stats;
+    // pinned host staging
+    uint64_t *h_tot = nullptr;
+    int32_t leaf_cap = 0;
+
+    ~Workspace() {
+        DevBuf *all[] = {&ascii, &codes, &qoff, &qm, &qH, &items, &item_pos, &bad, &aj[0], &aj[1], &aM[0],
+                         &aM[1], &aGa[0], &aGa[1], &nodes[0], &nodes[1], &cnt[0], &cnt[1], &cnt[2], &cnt[3],
+                         &cnt[4], &off[0], &off[1], &off[2], &off[3], &off[4], &totals, &scan_tmp, &lj, &lM,
+                         &lGa, &inj, &rhits, &sk0, &sv0, &sk1, &sv1, &sort_tmp, &hkey, &hscore, &hcount, &hk1,
+                         &hv1, &scratch, &next_seg, &uniq, &uflags, &uoff, &qcount, &stats};
+        for (DevBuf *b : all)
+            if (b->p) cudaFree(b->p);
+        if (h_tot) cudaFreeHost(h_tot);
+    }
+};
+
+}  // namespace
+
+struct ae_index {
+    HostIndex host;
+    IndexView view;
+    void *d_occ = nullptr, *d_tend = nullptr, *d_text = nullptr;
+    int64_t device_bytes = 0;
+    int device = 0;
+    std::mutex mu;
+    std::vector<std::pair<cudaStream_t, Workspace *>> ws;
+
+    ~ae_index() {
+        for (auto &p : ws) delete p.second;
+        if (d_occ) cudaFree(d_occ);
+        if (d_tend) cudaFree(d_tend);
+        if (d_text) cudaFree(d_text);
+        ae_host_index_free(&host);
+    }
+};
+
+namespace {
+
+Workspace *workspace_for(const ae_index *cidx, cudaStream_t st) {
+    ae_index *idx = const_cast<ae_index *>(cidx);
+    std::lock_guard<std::mutex> g(idx->mu);
+    for (auto &p : idx->ws)
+        if (p.first == st) return p.second;
+    Workspace *w = new Workspace();
+    w->stream = st;
+    if (cudaMallocHost(&w->h_tot, 64 * sizeof(uint64_t)) != cudaSuccess) {
+        cudaGetLastError();
+        delete w;
+        throw ae_error{AE_ENOMEM};
+    }
+    idx->ws.push_back({st, w});
+    return w;
+}
+
+ae_status upload_index(ae_index *idx) {
+    HostIndex &h = idx->host;
+    size_t occ_b = sizeof(uint32_t) * (size_t)(h.nblocks * h.block_words);
+    size_t tend_b = sizeof(int32_t) * (size_t)(h.n + 1);
+    size_t text_b = (size_t)h.n;
+    if (cudaGetDevice(&idx->device) != cudaSuccess) return AE_ECUDA;
+    if (cudaMalloc(&idx->d_occ, occ_b) != cudaSuccess || cudaMalloc(&idx->d_tend, tend_b) != cudaSuccess ||
+        cudaMalloc(&idx->d_text, text_b) != cudaSuccess) {
+        cudaGetLastError();
+        return AE_ENOMEM;
+    }
+    if (cudaMemcpy(idx->d_occ, h.occ, occ_b, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(idx->d_tend, h.tend, tend_b, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(idx->d_text, h.text, text_b, cudaMemcpyHostToDevice) != cudaSuccess)
+        return AE_ECUDA;
+    idx->device_bytes = (int64_t)(occ_b + tend_b + text_b);
+    IndexView &v = idx->view;
+    memset(&v, 0, sizeof(v));
+    v.occ = (const uint32_t *)idx->d_occ;
+    v.tend = (const int32_t *)idx->d_tend;
+    v.text = (const uint8_t *)idx->d_text;
+    v.n = h.n;
+    v.dollar_row = h.dollar_row;
+    for (int c = 0; c <= h.sigma; ++c) v.C[c] = h.C[c];
+    v.sigma = h.sigma;
+    v.alphabet = h.alphabet;
+    return AE_OK;
+}
+
+int bits_for(int64_t maxval) {  // bits to hold values in [0, maxval]
+    int b = 1;
+    while (b < 63 && (maxval >> b) != 0) ++b;
+    return b;
+}
+
+double ms_since(std::chrono::steady_clock::time_point t0) {
+    return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
+ae_status make_score(const ae_scoring *s, int sigma, ScoreView &sc) {
+    if (!s) return AE_EINVAL;
+    memset(&sc, 0, sizeof(sc));
+    sc.sg = s->gap_open;
+    sc.ss = s->gap_extend;
+    if (s->gap_open > 0 || s->gap_extend >= 0) return AE_EINVAL;
+    if (s->matrix) {
+        sc.use_matrix = 1;
+        int gmax = INT32_MIN;
+        for (int a = 0; a < sigma; ++a)
+            for (int b = 0; b < sigma; ++b) {
+                int8_t v = s->matrix[a * sigma + b];
+                sc.mat[a * AE_MAX_SIGMA + b] = v;
+                gmax = std::max(gmax, (int)v);
+            }
+        for (int a = 0; a < sigma; ++a)
+            if (s->matrix[a * sigma + a] <= 0) return AE_EINVAL;
+        sc.gmax = gmax;
+        sc.sa = gmax;
+        sc.sb = -1;
+    } else {
+        if (s->match <= 0 || s->mismatch >= 0) return AE_EINVAL;
+        sc.sa = s->match;
+        sc.sb = s->mismatch;
+        sc.gmax = s->match;
+        for (int a = 0; a < sigma; ++a)
+            for (int b = 0; b < sigma; ++b) sc.mat[a * AE_MAX_SIGMA + b] = (int8_t)(a == b ? s->match : s->mismatch);
+    }
+    return AE_OK;
+}
+
+// Eq. 2 and the seed depth: the walk may start at depth q-1 (every live entry
+// there is an exact match of the query's (q-1)-gram, Theorem 3), and must start
+// below ceil(H/s_a) so that no hit is skipped.
+int seed_depth(const ScoreView &sc, int32_t Hmin, bool qprefix) {
+    if (sc.use_matrix || !qprefix) return 0;
+    int q = std::min(-sc.sb, -(sc.sg + sc.ss)) / sc.sa + 1;
+    int hd = (Hmin + sc.sa - 1) / sc.sa - 1;
+    int d0 = std::min(q - 1, hd);
+    int bits = 2;
+    while (d0 > 0 && bits * d0 > 40) --d0;
+    return std::max(d0, 0);
+}
+
+struct Search {
+    const ae_index *idx;
+    Workspace *w;
+    cudaStream_t st;
+    IndexView ix;
+    ScoreView sc;
+    QueryView qv;
+    int32_t nq;
+    std::vector<int64_t> off;
+    std::vector<int32_t> m, H;
+    ae_options opt;
+    int be, bj, bq;
+    int d0;
+    int64_t nhits = 0;        // point hits accumulated in w->hkey/hscore
+    ae_stats stats;
+    int num_sms = 152;
+
+    uint64_t *tot() { return w->h_tot; }
+
+    void sync() { CU(cudaStreamSynchronize(st)); }
+
+    // Append `n` point hits capacity.
+    void hits_reserve(int64_t extra) {
+        size_t need = (size_t)(nhits + extra);
+        ensure_keep(w->hkey, need * sizeof(uint64_t), (size_t)nhits * sizeof(uint64_t), st);
+        ensure_keep(w->hscore, need * sizeof(int32_t), (size_t)nhits * sizeof(int32_t), st);
+    }
+
+    void run_batch(const std::vector<WorkItem> &items);
+    void leaf_phase(int64_t ninj);
+    void locate_phase(int64_t nrh);
+    int64_t finish(ae_hit **out_dev, std::vector<int64_t> &counts);
+};
+
+void Search::run_batch(const std::vector<WorkItem> &items) {
+    const int sigma = ix.sigma;
+    const int nitems = (int)items.size();
+    ensure(w->items, sizeof(WorkItem) * items.size(), st);
+    CU(cudaMemcpyAsync(w->items.p, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice, st));
+    const WorkItem *d_items = ptr<WorkItem>(w->items);
+    auto t0 = std::chrono::steady_clock::now();
+
+    int cur = 0;
+    int64_t F = 0;
+    int depth = d0;
+    if (d0 >= 1) {
+        // ---- seed: (item, (d0)-gram) keys of every start column, sorted
+        std::vector<int64_t> ipos(nitems + 1, 0);
+        for (int i = 0; i < nitems; ++i) {
+            const WorkItem &it = items[i];
+            int64_t hi = std::min<int64_t>(it.c1, (int64_t)m[it.qid] - d0 + 1);
+            ipos[i + 1] = ipos[i] + std::max<int64_t>(0, hi - it.c0);
+        }
+        const int64_t npos = ipos[nitems];
+        if (npos == 0) return;
+        ensure(w->item_pos, sizeof(int64_t) * ipos.size(), st);
+        CU(cudaMemcpyAsync(w->item_pos.p, ipos.data(), sizeof(int64_t) * ipos.size(), cudaMemcpyHostToDevice, st));
+        SeedArgs sa;
+        sa.ix = ix;
+        sa.sc = sc;
+        sa.qv = qv;
+        sa.items = d_items;
+        sa.item_pos = ptr<int64_t>(w->item_pos);
+        sa.nitems = nitems;
+        sa.d0 = d0;
+        sa.npos = npos;
+        ensure(w->sk0, npos * 8, st);
+        ensure(w->sv0, npos * 4, st);
+        ensure(w->sk1, npos * 8, st);
+        ensure(w->sv1, npos * 4, st);
+        ensure(w->sort_tmp, ae_sort_tmp_words(npos) * 8, st);
+        ae_seed_keys(sa, ptr<uint64_t>(w->sk0), ptr<uint32_t>(w->sv0), st);
+        const int key_bits = (sigma == 4 ? 2 : 5) * d0 + bits_for(nitems);
+        int which = ae_radix_sort(ptr<uint64_t>(w->sk0), ptr<uint32_t>(w->sv0), ptr<uint64_t>(w->sk1),
+                                  ptr<uint32_t>(w->sv1), npos, key_bits, ptr<uint64_t>(w->sort_tmp), st);
+        uint64_t *keys = which ? ptr<uint64_t>(w->sk1) : ptr<uint64_t>(w->sk0);
+        uint32_t *vals = which ? ptr<uint32_t>(w->sv1) : ptr<uint32_t>(w->sv0);
+        ensure(w->cnt[0], npos * 4, st);
+        ensure(w->off[0], npos * 8, st);
+        ensure(w->scan_tmp, ae_scan_tmp_words(npos, 5) * 8, st);
+        ensure(w->totals, 64, st);
+        ensure(w->nodes[cur], npos * sizeof(Node), st);
+        ensure(w->aj[cur], npos * 4, st);
+        ensure(w->aM[cur], npos * 4, st);
+        ensure(w->aGa[cur], npos * 4, st);
+        ae_seed_nodes(sa, keys, vals, npos, key_bits, ptr<uint32_t>(w->cnt[0]), ptr<uint64_t>(w->off[0]),
+                      ptr<uint64_t>(w->scan_tmp), ptr<Node>(w->nodes[cur]), ptr<int32_t>(w->aj[cur]),
+                      ptr<int32_t>(w->aM[cur]), ptr<int32_t>(w->aGa[cur]), ptr<uint64_t>(w->totals), st);
+        CU(cudaMemcpyAsync(tot(), w->totals.p, 8, cudaMemcpyDeviceToHost, st));
+        sync();
+        F = (int64_t)tot()[0];
+    } else {
+        // ---- root: one node per item with the implicit row M(0, j) = 0
+        std::vector<Node> roots(nitems);
+        for (int i = 0; i < nitems; ++i) {
+            roots[i].lo = 0;
+            roots[i].hi = (uint32_t)(ix.n + 1);
+            roots[i].item = i;
+            roots[i].cnt = AE_ROOT_ROW;
+            roots[i].off = 0;
+        }
+        ensure(w->nodes[cur], sizeof(Node) * nitems, st);
+        CU(cudaMemcpyAsync(w->nodes[cur].p, roots.data(), sizeof(Node) * nitems, cudaMemcpyHostToDevice, st));
+        for (int b = 0; b < 2; ++b) {
+            ensure(w->aj[b], 256, st);
+            ensure(w->aM[b], 256, st);
+            ensure(w->aGa[b], 256, st);
+        }
+        F = nitems;
+        sync();
+    }
+
+    // ---- trie levels
+    int64_t lf_ent_base = 0, lf_node_base = 0, rh_base = 0;
+    int64_t L_max_all = 0;
+    for (int q = 0; q < nq; ++q) {
+        int64_t Lm = std::max<int64_t>(m[q], m[q] + (int64_t)floor((double)(H[q] - ((int64_t)sc.sa * m[q] + sc.sg)) / sc.ss));
+        L_max_all = std::max(L_max_all, Lm);
+    }
+    ensure(w->totals, 64, st);
+    while (F > 0 && depth <= L_max_all) {
+        const int64_t S = F * sigma;
+        for (int k = 0; k < 5; ++k) {
+            ensure(w->cnt[k], S * 4, st);
+            ensure(w->off[k], S * 8, st);
+        }
+        ensure(w->scan_tmp, ae_scan_tmp_words(S, 5) * 8, st);
+        ExpandArgs ea;
+        memset(&ea, 0, sizeof(ea));
+        ea.ix = ix;
+        ea.sc = sc;
+        ea.qv = qv;
+        ea.items = d_items;
+        ea.nodes = ptr<Node>(w->nodes[cur]);
+        ea.nnodes = F;
+        ea.pj = ptr<int32_t>(w->aj[cur]);
+        ea.pM = ptr<int32_t>(w->aM[cur]);
+        ea.pGa = ptr<int32_t>(w->aGa[cur]);
+        ea.c_fr_ent = ptr<uint32_t>(w->cnt[0]);
+        ea.c_lf_ent = ptr<uint32_t>(w->cnt[1]);
+        ea.c_fr_node = ptr<uint32_t>(w->cnt[2]);
+        ea.c_lf_node = ptr<uint32_t>(w->cnt[3]);
+        ea.c_hits = ptr<uint32_t>(w->cnt[4]);
+        ea.stats = ptr<DevStats>(w->stats);
+        ae_expand(ea, false, st);
+        const uint32_t *cin[5] = {ea.c_fr_ent, ea.c_lf_ent, ea.c_fr_node, ea.c_lf_node, ea.c_hits};
+        uint64_t *cout[5];
+        for (int k = 0; k < 5; ++k) cout[k] = ptr<uint64_t>(w->off[k]);
+        ae_scan_u32(cin, cout, 5, S, ptr<uint64_t>(w->totals), ptr<uint64_t>(w->scan_tmp), st);
+        CU(cudaMemcpyAsync(tot(), w->totals.p, 5 * 8, cudaMemcpyDeviceToHost, st));
+        sync();
+        const int64_t fr_ent = (int64_t)tot()[0], lf_ent = (int64_t)tot()[1], fr_node = (int64_t)tot()[2],
+                      lf_node = (int64_t)tot()[3], hits = (int64_t)tot()[4];
+        const int nxt = cur ^ 1;
+        ensure(w->aj[nxt], std::max<int64_t>(fr_ent, 1) * 4, st);
+        ensure(w->aM[nxt], std::max<int64_t>(fr_ent, 1) * 4, st);
+        ensure(w->aGa[nxt], std::max<int64_t>(fr_ent, 1) * 4, st);
+        ensure(w->nodes[nxt], std::max<int64_t>(fr_node, 1) * sizeof(Node), st);
+        ensure_keep(w->lj, (size_t)(lf_ent_base + lf_ent + 1) * 4, (size_t)lf_ent_base * 4, st);
+        ensure_keep(w->lM, (size_t)(lf_ent_base + lf_ent + 1) * 4, (size_t)lf_ent_base * 4, st);
+        ensure_keep(w->lGa, (size_t)(lf_ent_base + lf_ent + 1) * 4, (size_t)lf_ent_base * 4, st);
+        ensure_keep(w->inj, (size_t)(lf_node_base + lf_node + 1) * sizeof(Inject), (size_t)lf_node_base * sizeof(Inject), st);
+        ensure_keep(w->rhits, (size_t)(rh_base + hits + 1) * sizeof(RangeHit), (size_t)rh_base * sizeof(RangeHit), st);
+        ea.o_fr_ent = ptr<uint64_t>(w->off[0]);
+        ea.o_lf_ent = ptr<uint64_t>(w->off[1]);
+        ea.o_fr_node = ptr<uint64_t>(w->off[2]);
+        ea.o_lf_node = ptr<uint64_t>(w->off[3]);
+        ea.o_hits = ptr<uint64_t>(w->off[4]);
+        ea.lf_ent_base = (uint64_t)lf_ent_base;
+        ea.lf_node_base = (uint64_t)lf_node_base;
+        ea.hit_base = (uint64_t)rh_base;
+        ea.fj = ptr<int32_t>(w->aj[nxt]);
+        ea.fM = ptr<int32_t>(w->aM[nxt]);
+        ea.fGa = ptr<int32_t>(w->aGa[nxt]);
+        ea.fnodes = ptr<Node>(w->nodes[nxt]);
+        ea.lj = ptr<int32_t>(w->lj);
+        ea.lM = ptr<int32_t>(w->lM);
+        ea.lGa = ptr<int32_t>(w->lGa);
+        ea.inj = ptr<Inject>(w->inj);
+        ea.rhits = ptr<RangeHit>(w->rhits);
+        ae_expand(ea, true, st);
+        lf_ent_base += lf_ent;
+        lf_node_base += lf_node;
+        rh_base += hits;
+        cur = nxt;
+        F = fr_node;
+        ++depth;
+        stats.levels++;
+    }
+    CU(cudaGetLastError());
+    sync();
+    stats.ms_trie += ms_since(t0);
+    stats.injections += lf_node_base;
+
+    auto t1 = std::chrono::steady_clock::now();
+    leaf_phase(lf_node_base);
+    stats.ms_leaf += ms_since(t1);
+    auto t2 = std::chrono::steady_clock::now();
+    locate_phase(rh_base);
+    stats.ms_reduce += ms_since(t2);
+}
+
+void Search::leaf_phase(int64_t ninj) {
+    if (ninj <= 0) return;
+    ensure(w->sk0, ninj * 8, st);
+    ensure(w->sv0, ninj * 4, st);
+    ensure(w->sk1, ninj * 8, st);
+    ensure(w->sv1, ninj * 4, st);
+    ensure(w->sort_tmp, ae_sort_tmp_words(ninj) * 8, st);
+    ae_inject_keys(ptr<Inject>(w->inj), ninj, ptr<uint64_t>(w->sk0), ptr<uint32_t>(w->sv0), st);
+    int which = ae_radix_sort(ptr<uint64_t>(w->sk0), ptr<uint32_t>(w->sv0), ptr<uint64_t>(w->sk1),
+                              ptr<uint32_t>(w->sv1), ninj, 32 + bits_for(std::max(nq - 1, 1)),
+                              ptr<uint64_t>(w->sort_tmp), st);
+    const uint32_t *order = which ? ptr<uint32_t>(w->sv1) : ptr<uint32_t>(w->sv0);
+
+    const int threads = 128;
+    const int blocks = num_sms * 8;
+    const int nwarps = blocks * threads / 32;
+    if (w->leaf_cap < opt.leaf_capacity) w->leaf_cap = opt.leaf_capacity;
+    ensure(w->next_seg, 8, st);
+    ensure(w->hcount, 8, st);
+    int64_t hit_cap = std::max<int64_t>(1 << 20, ninj * 4);
+    for (int attempt = 0; attempt < 12; ++attempt) {
+        ensure(w->scratch, (size_t)ae_leaf_scratch_words(w->leaf_cap, nwarps) * 4, st);
+        hits_reserve(hit_cap);
+        CU(cudaMemsetAsync(w->next_seg.p, 0, 8, st));
+        unsigned long long base = (unsigned long long)nhits;
+        CU(cudaMemcpyAsync(w->hcount.p, &base, 8, cudaMemcpyHostToDevice, st));
+        CU(cudaMemsetAsync((char *)w->stats.p + offsetof(DevStats, leaf_overflow), 0, 16, st));
+        LeafArgs la;
+        memset(&la, 0, sizeof(la));
+        la.ix = ix;
+        la.sc = sc;
+        la.qv = qv;
+        la.inj = ptr<Inject>(w->inj);
+        la.order = order;
+        la.ninj = ninj;
+        la.lj = ptr<int32_t>(w->lj);
+        la.lM = ptr<int32_t>(w->lM);
+        la.lGa = ptr<int32_t>(w->lGa);
+        la.seg = std::max(1, opt.leaf_segment);
+        la.nseg = (ninj + la.seg - 1) / la.seg;
+        la.next_seg = ptr<unsigned long long>(w->next_seg);
+        la.scratch = ptr<int32_t>(w->scratch);
+        la.cap = w->leaf_cap;
+        la.nwarps = nwarps;
+        la.hit_key = ptr<uint64_t>(w->hkey);
+        la.hit_score = ptr<int32_t>(w->hscore);
+        la.hit_count = ptr<unsigned long long>(w->hcount);
+        la.hit_cap = (uint64_t)(nhits + hit_cap);
+        la.be = be;
+        la.bj = bj;
+        la.stats = ptr<DevStats>(w->stats);
+        ae_leaf_sweep(la, blocks, threads, st);
+        CU(cudaGetLastError());
+        unsigned long long hdr[3];
+        CU(cudaMemcpyAsync(tot(), w->hcount.p, 8, cudaMemcpyDeviceToHost, st));
+        CU(cudaMemcpyAsync(tot() + 1, (char *)w->stats.p + offsetof(DevStats, leaf_overflow), 16,
+                           cudaMemcpyDeviceToHost, st));
+        sync();
+        hdr[0] = tot()[0];
+        hdr[1] = tot()[1];
+        hdr[2] = tot()[2];
+        if (hdr[1] != 0) {          // a row outgrew the scratch: retry larger
+            w->leaf_cap *= 4;
+            continue;
+        }
+        if (hdr[2] != 0 || (int64_t)hdr[0] > nhits + hit_cap) {   // hit buffer too small
+            hit_cap = (int64_t)hdr[0] - nhits + 1024;
+            continue;
+        }
+        nhits = (int64_t)hdr[0];
+        return;
+    }
+    throw ae_error{AE_ENOMEM};
+}
+
+void Search::locate_phase(int64_t nrh) {
+    if (nrh <= 0) return;
+    ensure(w->cnt[0], nrh * 4, st);
+    ensure(w->off[0], nrh * 8, st);
+    ensure(w->scan_tmp, ae_scan_tmp_words(nrh, 5) * 8, st);
+    ae_locate_counts(ptr<RangeHit>(w->rhits), nrh, ptr<uint32_t>(w->cnt[0]), st);
+    const uint32_t *in[1] = {ptr<uint32_t>(w->cnt[0])};
+    uint64_t *out[1] = {ptr<uint64_t>(w->off[0])};
+    ae_scan_u32(in, out, 1, nrh, ptr<uint64_t>(w->totals), ptr<uint64_t>(w->scan_tmp), st);
+    CU(cudaMemcpyAsync(tot(), w->totals.p, 8, cudaMemcpyDeviceToHost, st));
+    sync();
+    const int64_t total = (int64_t)tot()[0];
+    hits_reserve(total);
+    ae_locate(ptr<RangeHit>(w->rhits), nrh, ptr<uint64_t>(w->off[0]), total, ix.tend, be, bj,
+              ptr<uint64_t>(w->hkey) + nhits, ptr<int32_t>(w->hscore) + nhits, st);
+    nhits += total;
+}
+
+// Sort all point hits by (query, text end, query end) and keep the maximum
+// score of each cell.  Returns the number of distinct results; *out_dev points
+// into the workspace.
+int64_t Search::finish(ae_hit **out_dev, std::vector<int64_t> &counts) {
+    auto t0 = std::chrono::steady_clock::now();
+    const int64_t N = nhits;
+    counts.assign(nq, 0);
+    ensure(w->qcount, sizeof(unsigned long long) * nq, st);
+    CU(cudaMemsetAsync(w->qcount.p, 0, sizeof(unsigned long long) * nq, st));
+    stats.raw_hits = N;
+    if (N == 0) {
+        *out_dev = nullptr;
+        stats.ms_reduce += ms_since(t0);
+        return 0;
+    }
+    ensure(w->hk1, N * 8, st);
+    ensure(w->hv1, N * 4, st);
+    ensure(w->sort_tmp, ae_sort_tmp_words(N) * 8, st);
+    int which = ae_radix_sort(ptr<uint64_t>(w->hkey), reinterpret_cast<uint32_t *>(w->hscore.p),
+                              ptr<uint64_t>(w->hk1), ptr<uint32_t>(w->hv1), N, be + bj + bq,
+                              ptr<uint64_t>(w->sort_tmp), st);
+    const uint64_t *keys = which ? ptr<uint64_t>(w->hk1) : ptr<uint64_t>(w->hkey);
+    const int32_t *scores = which ? ptr<int32_t>(w->hv1) : ptr<int32_t>(w->hscore);
+    ensure(w->uflags, N * 4, st);
+    ensure(w->uoff, N * 8, st);
+    ensure(w->scan_tmp, ae_scan_tmp_words(N, 5) * 8, st);
+    ae_unique_flags(keys, N, ptr<uint32_t>(w->uflags), st);
+    const uint32_t *in[1] = {ptr<uint32_t>(w->uflags)};
+    uint64_t *out[1] = {ptr<uint64_t>(w->uoff)};
+    ae_scan_u32(in, out, 1, N, ptr<uint64_t>(w->totals), ptr<uint64_t>(w->scan_tmp), st);
+    CU(cudaMemcpyAsync(tot(), w->totals.p, 8, cudaMemcpyDeviceToHost, st));
+    sync();
+    const int64_t U = (int64_t)tot()[0];
+    ensure(w->uniq, std::max<int64_t>(U, 1) * sizeof(ae_hit), st);
+    ae_unique_write(keys, scores, N, ptr<uint64_t>(w->uoff), be, bj, ptr<ae_hit>(w->uniq),
+                    ptr<unsigned long long>(w->qcount), st);
+    std::vector<unsigned long long> qc(nq);
+    CU(cudaMemcpyAsync(qc.data(), w->qcount.p, sizeof(unsigned long long) * nq, cudaMemcpyDeviceToHost, st));
+    sync();
+    for (int q = 0; q < nq; ++q) counts[q] = (int64_t)qc[q];
+    *out_dev = ptr<ae_hit>(w->uniq);
+    stats.hits = U;
+    stats.ms_reduce += ms_since(t0);
+    return U;
+}
+
+// Shared core: codes already on the device in w->codes.
+ae_status search_core(const ae_index *idx, Workspace *w, const int64_t *offsets, int32_t nq,
+                      const ae_scoring *scoring, const int32_t *H, const ae_options *opt, cudaStream_t st,
+                      ae_hit **out_dev, std::vector<int64_t> &counts, int64_t *total) {
+    auto t0 = std::chrono::steady_clock::now();
+    Search s;
+    s.idx = idx;
+    s.w = w;
+    s.st = st;
+    s.ix = idx->view;
+    s.nq = nq;
+    memset(&s.stats, 0, sizeof(s.stats));
+    ae_options_default(&s.opt);
+    if (opt) s.opt = *opt;
+    if (s.opt.item_columns < 1 || s.opt.batch_columns < 1 || s.opt.leaf_capacity < 64 || s.opt.leaf_segment < 1)
+        return AE_EINVAL;
+    ae_status e = make_score(scoring, s.ix.sigma, s.sc);
+    if (e != AE_OK) return e;
+    s.off.assign(offsets, offsets + nq + 1);
+    s.m.resize(nq);
+    s.H.resize(nq);
+    int32_t mmax = 1, Hmin = INT32_MAX;
+    for (int q = 0; q < nq; ++q) {
+        int64_t len = offsets[q + 1] - offsets[q];
+        if (len < 0 || len >= (1 << 28) || H[q] < 1) return AE_EINVAL;
+        s.m[q] = (int32_t)len;
+        s.H[q] = H[q];
+        mmax = std::max(mmax, (int32_t)len);
+        Hmin = std::min(Hmin, H[q]);
+    }
+    // keys of the max-plus scan stay within int32
+    if ((int64_t)mmax * (-(int64_t)s.sc.ss + s.sc.gmax + 1) >= (1ll << 30)) return AE_EUNSUPPORTED;
+    s.be = bits_for(std::max<int64_t>(s.ix.n - 1, 1));
+    s.bj = bits_for(std::max(mmax - 1, 1));
+    s.bq = bits_for(std::max(nq - 1, 1));
+    if (s.be + s.bj + s.bq > 64 || s.be > 32) return AE_EUNSUPPORTED;
+    s.d0 = seed_depth(s.sc, Hmin, s.opt.qprefix_seed != 0);
+    s.stats.seed_depth = s.d0;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&s.num_sms, cudaDevAttrMultiProcessorCount, dev);
+
+    try {
+        ensure(w->qoff, sizeof(int64_t) * (nq + 1), st);
+        ensure(w->qm, sizeof(int32_t) * nq, st);
+        ensure(w->qH, sizeof(int32_t) * nq, st);
+        ensure(w->stats, sizeof(DevStats), st);
+        CU(cudaMemcpyAsync(w->qoff.p, s.off.data(), sizeof(int64_t) * (nq + 1), cudaMemcpyHostToDevice, st));
+        CU(cudaMemcpyAsync(w->qm.p, s.m.data(), sizeof(int32_t) * nq, cudaMemcpyHostToDevice, st));
+        CU(cudaMemcpyAsync(w->qH.p, s.H.data(), sizeof(int32_t) * nq, cudaMemcpyHostToDevice, st));
+        CU(cudaMemsetAsync(w->stats.p, 0, sizeof(DevStats), st));
+        s.qv.codes = ptr<uint8_t>(w->codes);
+        s.qv.off = ptr<int64_t>(w->qoff);
+        s.qv.m = ptr<int32_t>(w->qm);
+        s.qv.H = ptr<int32_t>(w->qH);
+
+        // work items: columns of each query in slices of item_columns
+        std::vector<WorkItem> batch;
+        int64_t cols = 0;
+        for (int q = 0; q < nq; ++q) {
+            for (int64_t c0 = 0; c0 < s.m[q]; c0 += s.opt.item_columns) {
+                WorkItem it;
+                it.qid = q;
+                it.c0 = (int32_t)c0;
+                it.c1 = (int32_t)std::min<int64_t>(s.m[q], c0 + s.opt.item_columns);
+                it.pad = 0;
+                batch.push_back(it);
+                cols += it.c1 - it.c0;
+                if (cols >= s.opt.batch_columns) {
+                    s.run_batch(batch);
+                    batch.clear();
+                    cols = 0;
+                }
+            }
+        }
+        if (!batch.empty()) s.run_batch(batch);
+        *total = s.finish(out_dev, counts);
+        DevStats ds;
+        CU(cudaMemcpyAsync(&ds, w->stats.p, sizeof(ds), cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+        s.stats.nodes = (int64_t)ds.nodes;
+        s.stats.leaf_rows = (int64_t)ds.leaf_rows;
+        s.stats.entries = (int64_t)ds.entries;
+        for (int k = 0; k < 3; ++k) s.stats.entries_tier[k] = (int64_t)ds.tier[k];
+    } catch (const ae_error &err) {
+        cudaGetLastError();
+        return err.st;
+    } catch (const std::bad_alloc &) {
+        return AE_ENOMEM;
+    }
+    s.stats.ms_total = ms_since(t0);
+    g_last_stats = s.stats;
+    return AE_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI
+
+extern "C" {
+
+void ae_options_default(ae_options *opt) {
+    if (!opt) return;
+    opt->qprefix_seed = 1;
+    opt->leaf_segment = 32;
+    opt->item_columns = 1 << 16;
+    opt->batch_columns = 1 << 20;
+    opt->leaf_capacity = 4096;
+}
+
+const char *ae_strerror(int32_t status) {
+    switch (status) {
+        case AE_OK: return "ok";
+        case AE_EINVAL: return "invalid argument";
+        case AE_ENOMEM: return "out of memory";
+        case AE_EOVERFLOW: return "output buffer too small";
+        case AE_ETIMEOUT: return "device wait timed out";
+        case AE_ECUDA: return "CUDA runtime error";
+        case AE_EUNSUPPORTED: return "unsupported size";
+        case AE_EIO: return "index file error";
+        default: return "unknown status";
+    }
+}
+
+ae_status ae_index_build(const uint8_t *text, int64_t n, int32_t alphabet, ae_index **out) {
+    if (!out) return AE_EINVAL;
+    *out = nullptr;
+    if (!text || n < 1 || !ae_alphabet_sigma(alphabet)) return AE_EINVAL;
+    if (n + 1 >= INT32_MAX) return AE_EUNSUPPORTED;
+    std::vector<uint8_t> codes;
+    try {
+        codes.resize((size_t)n);
+    } catch (...) {
+        return AE_ENOMEM;
+    }
+    if (ae_encode_letters(text, n, alphabet, codes.data()) != 0) return AE_EINVAL;
+    ae_index *idx = new (std::nothrow) ae_index();
+    if (!idx) return AE_ENOMEM;
+    ae_status st = ae_host_index_build(codes.data(), n, alphabet, &idx->host);
+    if (st == AE_OK) st = upload_index(idx);
+    if (st != AE_OK) {
+        delete idx;
+        return st;
+    }
+    *out = idx;
+    return AE_OK;
+}
+
+ae_status ae_index_save(const ae_index *idx, const char *path) {
+    if (!idx || !path) return AE_EINVAL;
+    return ae_host_index_save(&idx->host, path);
+}
+
+ae_status ae_index_load(const char *path, ae_index **out) {
+    if (!path || !out) return AE_EINVAL;
+    *out = nullptr;
+    ae_index *idx = new (std::nothrow) ae_index();
+    if (!idx) return AE_ENOMEM;
+    ae_status st = ae_host_index_load(path, &idx->host);
+    if (st == AE_OK) st = upload_index(idx);
+    if (st != AE_OK) {
+        delete idx;
+        return st;
+    }
+    *out = idx;
+    return AE_OK;
+}
+
+void ae_index_free(ae_index *idx) { delete idx; }
+
+ae_status ae_index_info(const ae_index *idx, int64_t *n, int32_t *alphabet, int64_t *device_bytes) {
+    if (!idx) return AE_EINVAL;
+    if (n) *n = idx->host.n;
+    if (alphabet) *alphabet = idx->host.alphabet;
+    if (device_bytes) *device_bytes = idx->device_bytes;
+    return AE_OK;
+}
+
+ae_status ae_search(const ae_index *idx, const ae_query *queries, int32_t nq, const ae_scoring *scoring,
+                    const int32_t *H, const ae_options *opt, ae_hit **hits, int64_t *counts, void *stream) {
+    if (!idx || !hits || !counts || nq < 0 || (nq > 0 && (!queries || !H))) return AE_EINVAL;
+    *hits = nullptr;
+    if (nq == 0) return AE_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<int64_t> off(nq + 1, 0);
+    for (int q = 0; q < nq; ++q) {
+        if (queries[q].len < 0 || (queries[q].len > 0 && !queries[q].seq)) return AE_EINVAL;
+        off[q + 1] = off[q] + queries[q].len;
+    }
+    try {
+        Workspace *w = workspace_for(idx, st);
+        const int64_t total_len = off[nq];
+        uint8_t *h_ascii = nullptr;
+        if (total_len > 0) {
+            CU(cudaMallocHost(&h_ascii, (size_t)total_len));
+            for (int q = 0; q < nq; ++q)
+                if (queries[q].len) memcpy(h_ascii + off[q], queries[q].seq, (size_t)queries[q].len);
+        }
+        ensure(w->ascii, std::max<int64_t>(total_len, 1), st);
+        ensure(w->codes, std::max<int64_t>(total_len, 1), st);
+        ensure(w->bad, 4, st);
+        CU(cudaMemsetAsync(w->bad.p, 0, 4, st));
+        if (total_len > 0)
+            CU(cudaMemcpyAsync(w->ascii.p, h_ascii, (size_t)total_len, cudaMemcpyHostToDevice, st));
+        ae_encode_queries(ptr<uint8_t>(w->ascii), ptr<uint8_t>(w->codes), total_len, idx->host.alphabet,
+                          ptr<int>(w->bad), st);
+        int bad = 0;
+        CU(cudaMemcpyAsync(&bad, w->bad.p, 4, cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+        if (h_ascii) cudaFreeHost(h_ascii);
+        if (bad) return AE_EINVAL;
+        ae_hit *dev = nullptr;
+        std::vector<int64_t> cnt;
+        int64_t total = 0;
+        ae_status e = search_core(idx, w, off.data(), nq, scoring, H, opt, st, &dev, cnt, &total);
+        if (e != AE_OK) return e;
+        ae_hit *h = (ae_hit *)malloc(sizeof(ae_hit) * (size_t)std::max<int64_t>(total, 1));
+        if (!h) return AE_ENOMEM;
+        if (total > 0) {
+            if (cudaMemcpyAsync(h, dev, sizeof(ae_hit) * (size_t)total, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                cudaStreamSynchronize(st) != cudaSuccess) {
+                free(h);
+                return AE_ECUDA;
+            }
+        }
+        for (int q = 0; q < nq; ++q) counts[q] = cnt[q];
+        *hits = h;
+    } catch (const ae_error &err) {
+        cudaGetLastError();
+        return err.st;
+    } catch (const std::bad_alloc &) {
+        return AE_ENOMEM;
+    }
+    return AE_OK;
+}
+
+void ae_hits_free(ae_hit *hits) { free(hits); }
+
+ae_status ae_search_device(const ae_index *idx, const uint8_t *d_seq, const int64_t *offsets, int32_t nq,
+                           const ae_scoring *scoring, const int32_t *H, const ae_options *opt, ae_hit *d_hits,
+                           int64_t capacity, int64_t *counts, void *stream) {
+    if (!idx || !offsets || !counts || nq < 0 || (nq > 0 && !H) || capacity < 0 || (capacity > 0 && !d_hits))
+        return AE_EINVAL;
+    if (nq == 0) return AE_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t total_len = offsets[nq] - offsets[0];
+    if (offsets[0] != 0 || total_len < 0) return AE_EINVAL;
+    try {
+        Workspace *w = workspace_for(idx, st);
+        ensure(w->codes, std::max<int64_t>(total_len, 1), st);
+        ensure(w->bad, 4, st);
+        CU(cudaMemsetAsync(w->bad.p, 0, 4, st));
+        if (total_len > 0 && !d_seq) return AE_EINVAL;
+        ae_encode_queries(d_seq, ptr<uint8_t>(w->codes), total_len, idx->host.alphabet, ptr<int>(w->bad), st);
+        int bad = 0;
+        CU(cudaMemcpyAsync(&bad, w->bad.p, 4, cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+        if (bad) return AE_EINVAL;
+        ae_hit *dev = nullptr;
+        std::vector<int64_t> cnt;
+        int64_t total = 0;
+        ae_status e = search_core(idx, w, offsets, nq, scoring, H, opt, st, &dev, cnt, &total);
+        if (e != AE_OK) return e;
+        for (int q = 0; q < nq; ++q) counts[q] = cnt[q];
+        if (total > capacity) return AE_EOVERFLOW;
+        if (total > 0) {
+            CU(cudaMemcpyAsync(d_hits, dev, sizeof(ae_hit) * (size_t)total, cudaMemcpyDeviceToDevice, st));
+            CU(cudaStreamSynchronize(st));
+        }
+    } catch (const ae_error &err) {
+        cudaGetLastError();
+        return err.st;
+    } catch (const std::bad_alloc &) {
+        return AE_ENOMEM;
+    }
+    return AE_OK;
+}
+
+ae_status ae_last_stats(ae_stats *out) {
+    if (!out) return AE_EINVAL;
+    *out = g_last_stats;
+    return AE_OK;
+}
+
+ae_status ae_plan(int64_t m, int32_t alphabet, const ae_scoring *scoring, int32_t H, int32_t *q,
+                  int32_t *seed_depth_out, int64_t *L_max) {
+    const int sigma = ae_alphabet_sigma(alphabet);
+    if (!scoring || m < 0 || H < 1 || !sigma) return AE_EINVAL;
+    ScoreView sc;
+    ae_status e = make_score(scoring, sigma, sc);
+    if (e != AE_OK) return e;
+    if (q) *q = sc.use_matrix ? 0 : std::min(-sc.sb, -(sc.sg + sc.ss)) / sc.sa + 1;
+    if (seed_depth_out) *seed_depth_out = seed_depth(sc, H, true);
+    if (L_max) {
+        // Eq. 1: L_max = max{m, m + floor((H - (s_a m + s_g)) / s_s)}, mathematical floor
+        int64_t num = (int64_t)H - ((int64_t)sc.sa * m + sc.sg);
+        int64_t den = sc.ss;  // < 0
+        int64_t qv = num / den;
+        if ((num % den != 0) && ((num < 0) != (den < 0))) --qv;
+        *L_max = std::max<int64_t>(m, m + qv);
+    }
+    return AE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,100 @@
+// Launch wrappers of the device kernels (ae_kernels.cu), called by the engine.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "ae_internal.h"
+
+// Exclusive scans of W u32 arrays of length N into u64 arrays; totals[w]
+// (device, W entries) receives the sums.  tmp must hold scan_tmp_words(N, W)
+// u64 words.
+int64_t ae_scan_tmp_words(int64_t N, int W);
+void ae_scan_u32(const uint32_t *const *in, uint64_t *const *out, int W, int64_t N, uint64_t *totals,
+                 uint64_t *tmp, cudaStream_t st);
+
+// Stable LSD radix sort of (key, value) pairs on the low `bits` bits of the
+// key.  Ping-pong buffers k0/v0 (input) and k1/v1; returns 0 if the result
+// ended in k0/v0, 1 if in k1/v1.  tmp must hold ae_sort_tmp_words(N) u64.
+int64_t ae_sort_tmp_words(int64_t N);
+int ae_radix_sort(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int64_t N, int bits,
+                  uint64_t *tmp, cudaStream_t st);
+
+// Query letters -> codes; sets *bad (device int) on an unknown letter.
+void ae_encode_queries(const uint8_t *ascii, uint8_t *codes, int64_t total, int alphabet, int *bad,
+                       cudaStream_t st);
+
+struct SeedArgs {
+    IndexView ix;
+    ScoreView sc;
+    QueryView qv;
+    const WorkItem *items;
+    const int64_t *item_pos;   // exclusive prefix of seed positions per item (nitems + 1)
+    int32_t nitems;
+    int32_t d0;                // seed depth (>= 1)
+    int64_t npos;
+};
+// keys = (item << 2*d0... packed gram), vals = query start column y.
+void ae_seed_keys(const SeedArgs &a, uint64_t *keys, uint32_t *vals, cudaStream_t st);
+// After sorting: one node per run of equal keys; writes nodes + level-0 arena.
+// Returns via *nnodes (device u64).
+void ae_seed_nodes(const SeedArgs &a, const uint64_t *keys, const uint32_t *vals, int64_t npos, int key_bits,
+                   uint32_t *flags, uint64_t *flag_off, uint64_t *tmp, Node *nodes, int32_t *aj, int32_t *aM,
+                   int32_t *aGa, uint64_t *nnodes_dev, cudaStream_t st);
+
+struct ExpandArgs {
+    IndexView ix;
+    ScoreView sc;
+    QueryView qv;
+    const WorkItem *items;
+    const Node *nodes;
+    int64_t nnodes;
+    const int32_t *pj, *pM, *pGa;          // parent arena
+    // count pass outputs (nnodes * sigma each)
+    uint32_t *c_fr_ent, *c_lf_ent, *c_fr_node, *c_lf_node, *c_hits;
+    // write pass inputs: scanned offsets
+    const uint64_t *o_fr_ent, *o_lf_ent, *o_fr_node, *o_lf_node, *o_hits;
+    uint64_t lf_ent_base, lf_node_base, hit_base;
+    // write pass outputs
+    int32_t *fj, *fM, *fGa;                // next-level arena
+    Node *fnodes;                          // next-level nodes
+    int32_t *lj, *lM, *lGa;                // leaf arena
+    Inject *inj;
+    RangeHit *rhits;
+    DevStats *stats;
+};
+void ae_expand(const ExpandArgs &a, bool write, cudaStream_t st);
+
+struct LeafArgs {
+    IndexView ix;
+    ScoreView sc;
+    QueryView qv;
+    const Inject *inj;
+    const uint32_t *order;        // injections sorted by (qid, e)
+    int64_t ninj;
+    const int32_t *lj, *lM, *lGa; // leaf arena
+    int32_t seg;
+    int64_t nseg;
+    unsigned long long *next_seg;
+    int32_t *scratch;
+    int32_t cap;
+    int32_t nwarps;
+    uint64_t *hit_key;
+    int32_t *hit_score;
+    unsigned long long *hit_count;
+    uint64_t hit_cap;
+    int32_t be, bj;               // key packing widths
+    DevStats *stats;
+};
+void ae_inject_keys(const Inject *inj, int64_t ninj, uint64_t *keys, uint32_t *vals, cudaStream_t st);
+void ae_leaf_sweep(const LeafArgs &a, int blocks, int threads, cudaStream_t st);
+int64_t ae_leaf_scratch_words(int32_t cap, int32_t nwarps);
+
+// Range hits -> point hits (key, score) appended at dst.
+void ae_locate_counts(const RangeHit *rh, int64_t nrh, uint32_t *cnt, cudaStream_t st);
+void ae_locate(const RangeHit *rh, int64_t nrh, const uint64_t *off, int64_t total, const int32_t *tend, int be,
+               int bj, uint64_t *key, int32_t *score, cudaStream_t st);
+
+// Sorted (key, score) -> unique keys with max score.
+void ae_unique_flags(const uint64_t *key, int64_t N, uint32_t *flags, cudaStream_t st);
+void ae_unique_write(const uint64_t *key, const int32_t *score, int64_t N, const uint64_t *flag_off, int be,
+                     int bj, ae_hit *out, unsigned long long *qcount, cudaStream_t st);

@@ -1,0 +1,225 @@
+"""GPU search through the C ABI against the CPU oracle, hit for hit.
+
+Every comparison is exact: the set of (text end, query end, score) results
+with score >= H, sorted by (text end, query end), must be identical.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from workloads import (BLOSUM62, DNA, PROTEIN, Scheme, dna_small, iid_text, random_pair)
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1208_0274_gb300 import ae  # noqa: E402
+
+
+def want_hits(T, P, scheme, H, alphabet=DNA):
+    oi, oj, os_ = oracle.sw_hits(T, P, scheme, H, alphabet=alphabet)
+    w = np.zeros(oi.size, dtype=ae.HIT_DTYPE)
+    w["text_end"], w["query_end"], w["score"] = oi, oj, os_
+    return w   # row-major order == sorted by (text_end, query_end)
+
+
+def split(hits, counts):
+    out, s = [], 0
+    for c in counts:
+        out.append(hits[s:s + c])
+        s += c
+    return out
+
+
+def assert_same(got, want, label=""):
+    if not np.array_equal(got, want):
+        g = {(int(a), int(b)): int(c) for a, b, c in got}
+        w = {(int(a), int(b)): int(c) for a, b, c in want}
+        extra = [(k, v) for k, v in g.items() if w.get(k) != v][:5]
+        miss = [(k, v) for k, v in w.items() if g.get(k) != v][:5]
+        raise AssertionError(f"{label}: got {len(got)} want {len(want)}; wrong/extra {extra}; missing {miss}")
+
+
+def planted_pair(rng, n, m, sub=0.1):
+    T, P = random_pair(n, m, seed=int(rng.integers(1 << 30)))
+    if n > 40 and m > 30:
+        L = int(rng.integers(10, min(n, m) // 2))
+        x = int(rng.integers(0, n - L))
+        y = int(rng.integers(0, m - L))
+        seg = T[x:x + L].copy()
+        flip = rng.random(L) < sub
+        seg[flip] = np.frombuffer(DNA, dtype=np.uint8)[rng.integers(0, 4, size=int(flip.sum()))]
+        P[y:y + L] = seg
+    return T, P
+
+
+@pytest.fixture(scope="module")
+def small():
+    wl = dna_small()
+    idx = ae.ae_index_build(wl.text, ae.AE_DNA)
+    yield wl, idx
+    idx.close()
+
+
+def test_dna_small_workload_full_parity(small):
+    wl, idx = small
+    hits, counts = ae.ae_search(idx, wl.queries, wl.scheme, wl.H)
+    want = want_hits(wl.text, wl.queries[0], wl.scheme, wl.H[0])
+    assert counts[0] == want.size and want.size > 1000
+    assert_same(hits, want, "dna_small")
+    st = ae.ae_last_stats()
+    assert st["entries"] > 0 and st["hits"] == want.size and st["seed_depth"] == 3
+
+
+@pytest.mark.parametrize("opts", [dict(qprefix_seed=0), dict(leaf_segment=1), dict(leaf_segment=7),
+                                  dict(item_columns=97), dict(item_columns=250, batch_columns=300),
+                                  dict(leaf_capacity=64)])
+def test_dna_small_knobs_do_not_change_hits(small, opts):
+    wl, idx = small
+    want = want_hits(wl.text, wl.queries[0], wl.scheme, wl.H[0])
+    hits, counts = ae.ae_search(idx, wl.queries, wl.scheme, wl.H, options=ae.make_options(**opts))
+    assert_same(hits, want, str(opts))
+
+
+SCHEMES = [Scheme(1, -3, -5, -2), Scheme(1, -1, -5, -2), Scheme(1, -3, -2, -2), Scheme(2, -3, -1, -1),
+           Scheme(1, -4, -5, -2), Scheme(1, -2, 0, -1)]
+
+
+@pytest.mark.parametrize("si", range(len(SCHEMES)))
+def test_random_planted_cases(si):
+    scheme = SCHEMES[si]
+    rng = np.random.default_rng(100 + si)
+    for case in range(8):
+        n = int(rng.integers(50, 3000))
+        m = int(rng.integers(5, 400))
+        T, P = planted_pair(rng, n, m)
+        idx = ae.ae_index_build(T, ae.AE_DNA)
+        for H in (4, 9, 17):
+            for seed_on in (1, 0):
+                opts = ae.make_options(qprefix_seed=seed_on, leaf_segment=int(rng.integers(1, 40)),
+                                       item_columns=int(rng.integers(3, 500)))
+                hits, _ = ae.ae_search(idx, [P], scheme, [H], options=opts)
+                assert_same(hits, want_hits(T, P, scheme, H), f"case {case} H {H} seed {seed_on}")
+        idx.close()
+
+
+def test_multi_query_batch_equals_single():
+    rng = np.random.default_rng(7)
+    T, _ = random_pair(5000, 1, seed=3)
+    qs, Hs = [], []
+    for k in range(9):
+        _, P = planted_pair(rng, 5000, int(rng.integers(1, 300)))
+        L = min(P.size, 60)
+        if k % 2 and P.size > L:
+            x = int(rng.integers(0, 5000 - L))
+            P[:L] = T[x:x + L]
+        qs.append(P)
+        Hs.append(int(rng.integers(6, 20)))
+    qs.append(np.zeros(0, dtype=np.uint8))     # an empty query
+    Hs.append(5)
+    scheme = Scheme(1, -3, -5, -2)
+    idx = ae.ae_index_build(T, ae.AE_DNA)
+    hits, counts = ae.ae_search(idx, qs, scheme, Hs)
+    parts = split(hits, counts)
+    for k, (P, H) in enumerate(zip(qs, Hs)):
+        want = want_hits(T, P, scheme, H) if P.size else np.zeros(0, dtype=ae.HIT_DTYPE)
+        assert_same(parts[k], want, f"query {k}")
+        alone, c1 = ae.ae_search(idx, [P], scheme, [H])
+        assert_same(alone, want, f"alone {k}")
+    idx.close()
+
+
+def test_protein_blosum62():
+    rng = np.random.default_rng(3)
+    bg = [0.05] * 20
+    T = iid_text(20_000, PROTEIN, bg, rng)
+    scheme = Scheme(gap_open=-11, gap_extend=-1, matrix=BLOSUM62)
+    idx = ae.ae_index_build(T, ae.AE_PROTEIN)
+    for m, H in [(60, 30), (200, 40), (500, 50)]:
+        P = iid_text(m, PROTEIN, bg, rng)
+        L = m // 2
+        x = int(rng.integers(0, T.size - L))
+        seg = T[x:x + L].copy()
+        flip = rng.random(L) < 0.4
+        seg[flip] = np.frombuffer(PROTEIN, dtype=np.uint8)[rng.integers(0, 20, size=int(flip.sum()))]
+        P[m // 4:m // 4 + L] = seg
+        hits, _ = ae.ae_search(idx, [P], scheme, [H])
+        assert_same(hits, want_hits(T, P, scheme, H, alphabet=PROTEIN), f"protein m={m}")
+    idx.close()
+
+
+def test_edge_cases():
+    scheme = Scheme(1, -3, -5, -2)
+    # one-letter text; H = 1 makes every equal letter pair a hit (root start)
+    for T, P, H in [(b"A", b"A", 1), (b"A", b"C", 1), (b"ACGT", b"ACGT", 1), (b"ACGTACGTTT", b"GT", 1),
+                    (b"ACGTTGCA" * 20, b"TTGCAACG", 3), (b"ACGT" * 50, b"ACGT" * 10, 1000)]:
+        idx = ae.ae_index_build(T, ae.AE_DNA)
+        hits, _ = ae.ae_search(idx, [P], scheme, [H])
+        assert_same(hits, want_hits(np.frombuffer(T, np.uint8), np.frombuffer(P, np.uint8), scheme, H),
+                    f"{T[:10]} {P} {H}")
+        idx.close()
+
+
+def test_exact_copy_and_int16_overflow_scores():
+    scheme = Scheme(1, -3, -5, -2)
+    T, _ = random_pair(120_000, 1, seed=8)
+    P = T[30_000:70_000].copy()               # score 40,000 > int16 range
+    idx = ae.ae_index_build(T, ae.AE_DNA)
+    hits, _ = ae.ae_search(idx, [P], scheme, [39_990])
+    want = want_hits(T, P, scheme, 39_990)
+    assert_same(hits, want, "40k copy")
+    assert int(hits["score"].max()) == 40_000
+    assert (int(hits["text_end"][-1]), int(hits["query_end"][-1])) == (69_999, 39_999)
+    idx.close()
+
+
+def test_threshold_monotonicity_on_device(small):
+    wl, idx = small
+    lo, _ = ae.ae_search(idx, wl.queries, wl.scheme, [22])
+    hi, _ = ae.ae_search(idx, wl.queries, wl.scheme, [40])
+    assert_same(hi, lo[lo["score"] >= 40], "H monotonicity")
+
+
+def test_device_entry_point_and_overflow(small):
+    wl, idx = small
+    q = torch.from_numpy(np.concatenate(wl.queries)).cuda()
+    offsets = np.array([0, wl.queries[0].size], dtype=np.int64)
+    want = want_hits(wl.text, wl.queries[0], wl.scheme, wl.H[0])
+    out = torch.empty((want.size + 10) * 16, dtype=torch.uint8, device="cuda")
+    st, counts = ae.ae_search_device(idx, q.data_ptr(), offsets, wl.scheme, wl.H, out.data_ptr(),
+                                     want.size + 10)
+    assert st == ae.AE_OK and counts[0] == want.size
+    got = out[:want.size * 16].cpu().numpy().view(ae.HIT_DTYPE)
+    assert_same(got, want, "device")
+    st, counts = ae.ae_search_device(idx, q.data_ptr(), offsets, wl.scheme, wl.H, out.data_ptr(), 5)
+    assert st == ae.AE_EOVERFLOW and counts[0] == want.size
+
+
+def test_bad_letters_rejected(small):
+    wl, idx = small
+    with pytest.raises(ae.AEError) as e:
+        ae.ae_search(idx, [b"ACGTNACGT"], wl.scheme, [5])
+    assert e.value.status == ae.AE_EINVAL
+    with pytest.raises(ae.AEError) as e:
+        ae.ae_search(idx, [b"ACGT"], wl.scheme, [0])
+    assert e.value.status == ae.AE_EINVAL
+
+
+def test_index_save_load_roundtrip(small, tmp_path):
+    wl, idx = small
+    p = tmp_path / "small.aeidx"
+    ae.ae_index_save(idx, p)
+    idx2 = ae.ae_index_load(p)
+    assert ae.ae_index_info(idx2)["n"] == wl.n
+    a, _ = ae.ae_search(idx, wl.queries, wl.scheme, wl.H)
+    b, _ = ae.ae_search(idx2, wl.queries, wl.scheme, wl.H)
+    assert_same(b, a, "reloaded index")
+    idx2.close()
+    raw = bytearray(p.read_bytes())
+    raw[100] ^= 0xFF
+    p.write_bytes(bytes(raw))
+    with pytest.raises(ae.AEError) as e:
+        ae.ae_index_load(p)
+    assert e.value.status == ae.AE_EIO
