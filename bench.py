@@ -1,0 +1,394 @@
+#!/usr/bin/env python
+"""Benchmark of exact local-alignment search (effective GCUPS = m*n/time).
+
+Workload (default): the 100 Mbp DNA text at 41% GC with 8 queries each of
+10 kbp, 100 kbp and 1 Mbp (1% of each planted from the text at 5-15%
+divergence), scheme <1,-3,-5,-2>, H = 19/21/23 from E = 10.  A step is one
+batched search of all of a rank's queries with the index and queries resident
+in HBM; `value` is sum(m) * n / step time over all ranks.  `plain` times the
+same queries one launch sequence per query; `e2e` goes through the host API
+(queries from host memory in, results to host memory out).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank takes every N-th query (queries are independent
+problems; no collective on the data path) and the job time is the max over
+ranks.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from workloads import DNA_SCALE_H, Scheme, dna_scale_query, dna_scale_text, dna_small  # noqa: E402
+
+METRIC = "effective GCUPS (m*n/time) at bit-exact hits, batched"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--workload", default="dna_scale", choices=["dna_scale", "dna_small"])
+    p.add_argument("--lengths", type=str, default="10000,100000,1000000")
+    p.add_argument("--per-length", type=int, default=8)
+    p.add_argument("--n", type=int, default=100_000_000)
+    p.add_argument("--no-plain", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--cpu-seconds", type=float, default=15.0)
+    p.add_argument("--leaf-segment", type=int, default=None)
+    p.add_argument("--item-columns", type=int, default=None)
+    p.add_argument("--batch-columns", type=int, default=None)
+    p.add_argument("--verbose", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def make_workload(args):
+    """(name, text, queries, H list, scheme, description) identical on every rank."""
+    scheme = Scheme(1, -3, -5, -2)
+    if args.workload == "dna_small":
+        wl = dna_small()
+        return ("dna_small", wl.text, wl.queries, wl.H, scheme,
+                {"workload": "dna_small: 100 kbp uniform ACGT text, one 1 kbp query with 5 planted "
+                             "150-300 bp copies (10% subs, 2% indels), <1,-3,-5,-2>, H=30",
+                 "n": int(wl.text.size), "queries": 1, "sum_m": int(wl.queries[0].size)})
+    lengths = [int(x) for x in args.lengths.split(",")]
+    seed = 20120802
+    text = dna_scale_text(seed, args.n)
+    rng = np.random.default_rng(seed + 1)
+    queries, H = [], []
+    for m in lengths:
+        for _ in range(args.per_length):
+            q, _ = dna_scale_query(text, m, rng)
+            queries.append(q)
+            H.append(DNA_SCALE_H.get(m, 21))
+    desc = {"workload": f"dna_scale: {args.n:,} bp i.i.d. text at 41% GC; {args.per_length} queries each of "
+                        f"{'/'.join(str(x) for x in lengths)} bp with 1% planted from the text at 5-15% "
+                        f"divergence; <1,-3,-5,-2>; H={'/'.join(str(DNA_SCALE_H.get(m, 21)) for m in lengths)} "
+                        f"(E=10)",
+            "n": int(args.n), "queries": len(queries), "sum_m": int(sum(q.size for q in queries)),
+            "l2": "flushed between timed steps (512 MiB write)"}
+    return args.workload, text, queries, H, scheme, desc
+
+
+class Clocks:
+    """nvidia-smi samples during the timed region."""
+
+    def __init__(self, gpu):
+        self.gpu = gpu
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        os.makedirs(os.path.dirname(self.path), exist_ok=True)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if parts[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        try:
+            os.remove(self.path)
+        except OSError:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def cpu_baseline(text, queries, scheme, H, seconds):
+    """The oracle (plain full-matrix Smith-Waterman, one thread) on a bounded
+    sample: the shortest query against a text slice sized for ~`seconds`."""
+    import oracle
+    q = min(queries, key=lambda x: x.size)[: 10_000]
+    h = H[int(np.argmin([x.size for x in queries]))]
+    probe = text[: max(1, 20_000_000 // max(q.size, 1))]
+    t0 = time.perf_counter()
+    oracle.sw_hits(probe, q, scheme, h)
+    rate = probe.size * q.size / max(time.perf_counter() - t0, 1e-6)
+    L = int(min(text.size, max(1000, rate * seconds / q.size)))
+    t0 = time.perf_counter()
+    oracle.sw_hits(text[:L], q, scheme, h)
+    dt = time.perf_counter() - t0
+    return {"value": round(L * q.size / dt / 1e9, 4), "unit": "GCUPS", "cores": 1, "kind": "oracle",
+            "sample": f"one {q.size} bp query against the first {L:,} bp of the text "
+                      f"({L * q.size:.3g} cells, {dt:.1f} s, single thread)"}
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    name, text, queries, H, scheme, desc = make_workload(args)
+    import oracle
+    oracle.build()
+    q = min(queries, key=lambda x: x.size)[: 10_000]
+    h = H[int(np.argmin([x.size for x in queries]))]
+    # size one step at ~10 s of oracle work
+    probe = text[: max(1, 20_000_000 // max(q.size, 1))]
+    t0 = time.perf_counter()
+    oracle.sw_hits(probe, q, scheme, h)
+    rate = probe.size * q.size / max(time.perf_counter() - t0, 1e-6)
+    L = int(min(text.size, max(1000, rate * 10.0 / q.size)))
+    for _ in range(max(args.warmup, 0) if L * q.size < 2e9 else 0):
+        oracle.sw_hits(text[: L // 10], q, scheme, h)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.sw_hits(text[:L], q, scheme, h)
+        times.append(time.perf_counter() - t0)
+    tot = sum(times)
+    v = args.steps * L * q.size / tot / 1e9
+    sample = f"each step: one {q.size} bp query against the first {L:,} bp of the text, single thread"
+    line = {"metric": METRIC, "value": round(v, 4), "unit": "GCUPS", "impl": "reference", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000 * tot / args.steps, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+            "data": "synthetic", "config": desc,
+            "cpu_baseline": {"value": round(v, 4), "unit": "GCUPS", "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": round(v, 4), "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    from paper_1208_0274_gb300 import ae
+
+    name, text, queries, H, scheme, desc = make_workload(args)
+    mine = list(range(rank, len(queries), ws))
+    qs = [queries[k] for k in mine]
+    hs = [H[k] for k in mine]
+    t0 = time.perf_counter()
+    idx = ae.ae_index_build(text, ae.AE_DNA)
+    log(f"[rank {rank}] index of {text.size:,} bp built in {time.perf_counter() - t0:.1f} s")
+    n = text.size
+    stream = torch.cuda.Stream()
+    opts = ae.make_options(leaf_segment=args.leaf_segment, item_columns=args.item_columns,
+                           batch_columns=args.batch_columns, profile=1)
+    seq = np.concatenate(qs) if qs else np.zeros(0, np.uint8)
+    offsets = np.concatenate([[0], np.cumsum([q.size for q in qs])]).astype(np.int64)
+    d_seq = torch.from_numpy(seq).to(f"cuda:{local}")
+    cap = 1 << 20
+    d_hits = torch.empty(cap * 16, dtype=torch.uint8, device=f"cuda:{local}")
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=f"cuda:{local}")
+
+    def step():
+        nonlocal cap, d_hits
+        while True:
+            st, counts = ae.ae_search_device(idx, d_seq.data_ptr(), offsets, scheme, hs, d_hits.data_ptr(), cap,
+                                             options=opts, stream=stream)
+            if st == ae.AE_OK:
+                return counts
+            cap = int(counts.sum() * 1.25) + 1024
+            d_hits = torch.empty(cap * 16, dtype=torch.uint8, device=f"cuda:{local}")
+
+    cells = sum(q.size for q in qs) * n
+    for w in range(args.warmup):
+        t1 = time.perf_counter()
+        counts = step()
+        st = ae.ae_last_stats()
+        log(f"[rank {rank}] warmup {w}: {time.perf_counter() - t1:.3f} s, hits {int(counts.sum())}, "
+            f"entries {st['entries']:,} (leaf {st['entries_leaf']:,}), nodes {st['nodes']:,}, "
+            f"k_expand {st['ms_k_expand']:.1f} ms, k_leaf {st['ms_k_leaf']:.1f} ms, "
+            f"k_sort {st['ms_k_sort']:.1f} ms, k_other {st['ms_k_other']:.1f} ms, launches {st['launches']}")
+
+    clocks = Clocks(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    ev = []
+    kstats = {"ms_k_expand": 0.0, "ms_k_leaf": 0.0, "ms_k_sort": 0.0, "ms_k_other": 0.0, "launches": 0,
+              "entries": 0, "entries_leaf": 0, "nodes": 0, "hits": 0, "raw_hits": 0}
+    for s in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(s & 0xFF)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+        counts = step()
+        with torch.cuda.stream(stream):
+            b.record(stream)
+        ev.append((a, b))
+        st = ae.ae_last_stats()
+        for k in kstats:
+            kstats[k] += st[k]
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clk = clocks.stop()
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    tot_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([tot_ms], device=f"cuda:{local}", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        tot_ms = float(t.item())
+        c = torch.tensor([cells], device=f"cuda:{local}", dtype=torch.float64)
+        dist.all_reduce(c, op=dist.ReduceOp.SUM)
+        cells_all = float(c.item())
+    else:
+        cells_all = float(cells)
+    value = args.steps * cells_all / (tot_ms / 1000.0) / 1e9
+    qps = args.steps * (len(queries) if ws > 1 else len(qs)) / (tot_ms / 1000.0)
+
+    # plain: one launch sequence per query (the static single-query form)
+    plain = None
+    if not args.no_plain and rank == 0:
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(stream):
+            flush.fill_(7)
+            a.record(stream)
+        for k, q in enumerate(qs):
+            off1 = np.array([0, q.size], dtype=np.int64)
+            dq = d_seq[offsets[k]:offsets[k + 1]]
+            st_, c_ = ae.ae_search_device(idx, dq.data_ptr(), off1, scheme, [hs[k]], d_hits.data_ptr(), cap,
+                                          stream=stream)
+        with torch.cuda.stream(stream):
+            b.record(stream)
+        torch.cuda.synchronize()
+        pms = a.elapsed_time(b)
+        plain = {"value": round(cells / (pms / 1000.0) / 1e9, 3), "unit": "GCUPS", "ms_per_step": round(pms, 3),
+                 "queries_per_s": round(len(qs) / (pms / 1000.0), 3)}
+
+    # e2e: host queries in, host results out, through ae_search
+    e2e = None
+    if not args.no_e2e:
+        hbytes = 0
+        t_e = []
+        for s in range(max(1, min(args.steps, 3))):
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            hits, counts = ae.ae_search(idx, qs, scheme, hs, stream=stream)
+            t_e.append(time.perf_counter() - t1)
+            hbytes = hits.nbytes + counts.nbytes
+        et = sum(t_e) / len(t_e)
+        if dist:
+            t = torch.tensor([et], device=f"cuda:{local}", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            et = float(t.item())
+        e2e = {"value": round(cells_all / et / 1e9, 3), "unit": "GCUPS",
+               "h2d_bytes_per_step": int(seq.nbytes), "d2h_bytes_per_step": int(hbytes),
+               "ms_per_step": round(et * 1000, 3)}
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    # roofline of the dominant kernel group (device time from CUDA events
+    # recorded by the library on the search stream during the timed steps)
+    groups = {"k_leaf": kstats["ms_k_leaf"], "k_expand": kstats["ms_k_expand"],
+              "k_sort": kstats["ms_k_sort"], "k_other": kstats["ms_k_other"]}
+    dom = max(groups, key=groups.get)
+    peak, src = peaks()
+    # algorithmic bytes: a DP entry is read once as a parent (12 B: column,
+    # M, G_a) and written once as a child (12 B); an expanded trie node reads
+    # two 32-byte occurrence blocks and its 24-byte record
+    ent_leaf = kstats["entries_leaf"]
+    ent_trie = kstats["entries"] - ent_leaf
+    if dom == "k_leaf":
+        alg = 24.0 * ent_leaf
+    elif dom == "k_expand":
+        alg = 24.0 * ent_trie + 88.0 * kstats["nodes"]
+    else:
+        alg = 16.0 * kstats["raw_hits"] * 2
+    achieved = alg / (groups[dom] / 1000.0) / 1e9 if groups[dom] > 0 else 0.0
+    roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "traffic": None, "peak_source": src,
+            "group_ms_per_step": {k: round(v / args.steps, 3) for k, v in groups.items()}}
+    cpu = None
+    if not args.no_cpu:
+        import oracle
+        oracle.build()
+        cpu = cpu_baseline(text, queries, scheme, H, args.cpu_seconds)
+    line = {"metric": METRIC, "value": round(value, 3), "unit": "GCUPS", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(tot_ms / args.steps, 3), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic", "config": desc,
+            "queries_per_s": round(qps, 3), "hits_per_step": int(kstats["hits"] / max(args.steps, 1)),
+            "entries_per_step": int(kstats["entries"] / max(args.steps, 1)),
+            "gpu_launches": int(kstats["launches"]), "plain": plain, "e2e": e2e, "roofline": roof,
+            "cpu_baseline": cpu, "clocks": clk}
+    print(json.dumps(line), flush=True)
+    idx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -84,9 +84,14 @@ typedef struct {
     int64_t injections;     /* trie rows handed to the text-position sweep */
     int64_t raw_hits;       /* hit records before the per-cell max */
     int64_t hits;           /* distinct (query, text end, query end) results */
+    int64_t entries_leaf;   /* of `entries`, those written by the text-position sweep */
+    int64_t launches;       /* kernel launches issued by the search */
     int32_t levels;         /* trie levels expanded */
     int32_t seed_depth;     /* depth the trie walk started at */
-    double  ms_trie, ms_leaf, ms_reduce, ms_total;
+    double  ms_trie, ms_leaf, ms_reduce, ms_total;   /* host wall time per phase */
+    /* with ae_options.profile: device time of the kernels, by kind, from CUDA
+     * events recorded on the search's stream around each launch group */
+    double  ms_k_expand, ms_k_leaf, ms_k_sort, ms_k_other;
 } ae_stats;
 
 /* Engine knobs (NULL = defaults).  None of them changes the result set. */
@@ -96,6 +101,7 @@ typedef struct {
     int64_t item_columns;   /* query columns per work item (seed range) */
     int64_t batch_columns;  /* query columns processed per batch */
     int32_t leaf_capacity;  /* initial per-task row capacity of the sweep, in entries */
+    int32_t profile;        /* 1: time kernel groups with CUDA events (ae_stats.ms_k_*) */
 } ae_options;
 
 /* Fill *opt with the defaults. */

@@ -41,17 +41,20 @@ class ae_query(ctypes.Structure):
 class ae_options(ctypes.Structure):
     _fields_ = [("qprefix_seed", ctypes.c_int32), ("leaf_segment", ctypes.c_int32),
                 ("item_columns", ctypes.c_int64), ("batch_columns", ctypes.c_int64),
-                ("leaf_capacity", ctypes.c_int32)]
+                ("leaf_capacity", ctypes.c_int32), ("profile", ctypes.c_int32)]
 
 
 class ae_stats(ctypes.Structure):
     _fields_ = [("nodes", ctypes.c_int64), ("leaf_rows", ctypes.c_int64),
                 ("entries", ctypes.c_int64), ("entries_tier", ctypes.c_int64 * 3),
                 ("injections", ctypes.c_int64), ("raw_hits", ctypes.c_int64),
-                ("hits", ctypes.c_int64), ("levels", ctypes.c_int32),
+                ("hits", ctypes.c_int64), ("entries_leaf", ctypes.c_int64),
+                ("launches", ctypes.c_int64), ("levels", ctypes.c_int32),
                 ("seed_depth", ctypes.c_int32), ("ms_trie", ctypes.c_double),
                 ("ms_leaf", ctypes.c_double), ("ms_reduce", ctypes.c_double),
-                ("ms_total", ctypes.c_double)]
+                ("ms_total", ctypes.c_double), ("ms_k_expand", ctypes.c_double),
+                ("ms_k_leaf", ctypes.c_double), ("ms_k_sort", ctypes.c_double),
+                ("ms_k_other", ctypes.c_double)]
 
 
 def _load():

@@ -239,6 +239,35 @@ int seed_depth(const ScoreView &sc, int32_t Hmin, bool qprefix) {
     return std::max(d0, 0);
 }
 
+// Device time of kernel groups, from CUDA events recorded on the search's
+// stream around each launch group (only with ae_options.profile).
+struct Prof {
+    bool on = false;
+    cudaStream_t st = nullptr;
+    std::vector<cudaEvent_t> ev[4];
+    void mark(int k) {
+        if (!on) return;
+        cudaEvent_t e;
+        CU(cudaEventCreate(&e));
+        CU(cudaEventRecord(e, st));
+        ev[k].push_back(e);
+    }
+    double ms(int k) {
+        double t = 0;
+        for (size_t i = 0; i + 1 < ev[k].size(); i += 2) {
+            float f = 0;
+            cudaEventElapsedTime(&f, ev[k][i], ev[k][i + 1]);
+            t += f;
+        }
+        return t;
+    }
+    ~Prof() {
+        for (auto &v : ev)
+            for (cudaEvent_t e : v) cudaEventDestroy(e);
+    }
+};
+enum { K_EXPAND = 0, K_LEAF = 1, K_SORT = 2, K_OTHER = 3 };
+
 struct Search {
     const ae_index *idx;
     Workspace *w;
@@ -255,6 +284,7 @@ struct Search {
     int64_t nhits = 0;        // point hits accumulated in w->hkey/hscore
     ae_stats stats;
     int num_sms = 152;
+    Prof prof;
 
     uint64_t *tot() { return w->h_tot; }
 
@@ -310,10 +340,14 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
         ensure(w->sk1, npos * 8, st);
         ensure(w->sv1, npos * 4, st);
         ensure(w->sort_tmp, ae_sort_tmp_words(npos) * 8, st);
+        prof.mark(K_OTHER);
         ae_seed_keys(sa, ptr<uint64_t>(w->sk0), ptr<uint32_t>(w->sv0), st);
+        prof.mark(K_OTHER);
         const int key_bits = (sigma == 4 ? 2 : 5) * d0 + bits_for(nitems);
+        prof.mark(K_SORT);
         int which = ae_radix_sort(ptr<uint64_t>(w->sk0), ptr<uint32_t>(w->sv0), ptr<uint64_t>(w->sk1),
                                   ptr<uint32_t>(w->sv1), npos, key_bits, ptr<uint64_t>(w->sort_tmp), st);
+        prof.mark(K_SORT);
         uint64_t *keys = which ? ptr<uint64_t>(w->sk1) : ptr<uint64_t>(w->sk0);
         uint32_t *vals = which ? ptr<uint32_t>(w->sv1) : ptr<uint32_t>(w->sv0);
         ensure(w->cnt[0], npos * 4, st);
@@ -324,9 +358,11 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
         ensure(w->aj[cur], npos * 4, st);
         ensure(w->aM[cur], npos * 4, st);
         ensure(w->aGa[cur], npos * 4, st);
+        prof.mark(K_OTHER);
         ae_seed_nodes(sa, keys, vals, npos, key_bits, ptr<uint32_t>(w->cnt[0]), ptr<uint64_t>(w->off[0]),
                       ptr<uint64_t>(w->scan_tmp), ptr<Node>(w->nodes[cur]), ptr<int32_t>(w->aj[cur]),
                       ptr<int32_t>(w->aM[cur]), ptr<int32_t>(w->aGa[cur]), ptr<uint64_t>(w->totals), st);
+        prof.mark(K_OTHER);
         CU(cudaMemcpyAsync(tot(), w->totals.p, 8, cudaMemcpyDeviceToHost, st));
         sync();
         F = (int64_t)tot()[0];
@@ -383,11 +419,15 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
         ea.c_lf_node = ptr<uint32_t>(w->cnt[3]);
         ea.c_hits = ptr<uint32_t>(w->cnt[4]);
         ea.stats = ptr<DevStats>(w->stats);
+        prof.mark(K_EXPAND);
         ae_expand(ea, false, st);
+        prof.mark(K_EXPAND);
         const uint32_t *cin[5] = {ea.c_fr_ent, ea.c_lf_ent, ea.c_fr_node, ea.c_lf_node, ea.c_hits};
         uint64_t *cout[5];
         for (int k = 0; k < 5; ++k) cout[k] = ptr<uint64_t>(w->off[k]);
+        prof.mark(K_OTHER);
         ae_scan_u32(cin, cout, 5, S, ptr<uint64_t>(w->totals), ptr<uint64_t>(w->scan_tmp), st);
+        prof.mark(K_OTHER);
         CU(cudaMemcpyAsync(tot(), w->totals.p, 5 * 8, cudaMemcpyDeviceToHost, st));
         sync();
         const int64_t fr_ent = (int64_t)tot()[0], lf_ent = (int64_t)tot()[1], fr_node = (int64_t)tot()[2],
@@ -419,7 +459,9 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
         ea.lGa = ptr<int32_t>(w->lGa);
         ea.inj = ptr<Inject>(w->inj);
         ea.rhits = ptr<RangeHit>(w->rhits);
+        prof.mark(K_EXPAND);
         ae_expand(ea, true, st);
+        prof.mark(K_EXPAND);
         lf_ent_base += lf_ent;
         lf_node_base += lf_node;
         rh_base += hits;
@@ -448,10 +490,12 @@ void Search::leaf_phase(int64_t ninj) {
     ensure(w->sk1, ninj * 8, st);
     ensure(w->sv1, ninj * 4, st);
     ensure(w->sort_tmp, ae_sort_tmp_words(ninj) * 8, st);
+    prof.mark(K_SORT);
     ae_inject_keys(ptr<Inject>(w->inj), ninj, ptr<uint64_t>(w->sk0), ptr<uint32_t>(w->sv0), st);
     int which = ae_radix_sort(ptr<uint64_t>(w->sk0), ptr<uint32_t>(w->sv0), ptr<uint64_t>(w->sk1),
                               ptr<uint32_t>(w->sv1), ninj, 32 + bits_for(std::max(nq - 1, 1)),
                               ptr<uint64_t>(w->sort_tmp), st);
+    prof.mark(K_SORT);
     const uint32_t *order = which ? ptr<uint32_t>(w->sv1) : ptr<uint32_t>(w->sv0);
 
     const int threads = 128;
@@ -492,7 +536,9 @@ void Search::leaf_phase(int64_t ninj) {
         la.be = be;
         la.bj = bj;
         la.stats = ptr<DevStats>(w->stats);
+        prof.mark(K_LEAF);
         ae_leaf_sweep(la, blocks, threads, st);
+        prof.mark(K_LEAF);
         CU(cudaGetLastError());
         unsigned long long hdr[3];
         CU(cudaMemcpyAsync(tot(), w->hcount.p, 8, cudaMemcpyDeviceToHost, st));
@@ -521,16 +567,20 @@ void Search::locate_phase(int64_t nrh) {
     ensure(w->cnt[0], nrh * 4, st);
     ensure(w->off[0], nrh * 8, st);
     ensure(w->scan_tmp, ae_scan_tmp_words(nrh, 5) * 8, st);
+    prof.mark(K_OTHER);
     ae_locate_counts(ptr<RangeHit>(w->rhits), nrh, ptr<uint32_t>(w->cnt[0]), st);
     const uint32_t *in[1] = {ptr<uint32_t>(w->cnt[0])};
     uint64_t *out[1] = {ptr<uint64_t>(w->off[0])};
     ae_scan_u32(in, out, 1, nrh, ptr<uint64_t>(w->totals), ptr<uint64_t>(w->scan_tmp), st);
+    prof.mark(K_OTHER);
     CU(cudaMemcpyAsync(tot(), w->totals.p, 8, cudaMemcpyDeviceToHost, st));
     sync();
     const int64_t total = (int64_t)tot()[0];
     hits_reserve(total);
+    prof.mark(K_OTHER);
     ae_locate(ptr<RangeHit>(w->rhits), nrh, ptr<uint64_t>(w->off[0]), total, ix.tend, be, bj,
               ptr<uint64_t>(w->hkey) + nhits, ptr<int32_t>(w->hscore) + nhits, st);
+    prof.mark(K_OTHER);
     nhits += total;
 }
 
@@ -552,24 +602,30 @@ int64_t Search::finish(ae_hit **out_dev, std::vector<int64_t> &counts) {
     ensure(w->hk1, N * 8, st);
     ensure(w->hv1, N * 4, st);
     ensure(w->sort_tmp, ae_sort_tmp_words(N) * 8, st);
+    prof.mark(K_SORT);
     int which = ae_radix_sort(ptr<uint64_t>(w->hkey), reinterpret_cast<uint32_t *>(w->hscore.p),
                               ptr<uint64_t>(w->hk1), ptr<uint32_t>(w->hv1), N, be + bj + bq,
                               ptr<uint64_t>(w->sort_tmp), st);
+    prof.mark(K_SORT);
     const uint64_t *keys = which ? ptr<uint64_t>(w->hk1) : ptr<uint64_t>(w->hkey);
     const int32_t *scores = which ? ptr<int32_t>(w->hv1) : ptr<int32_t>(w->hscore);
     ensure(w->uflags, N * 4, st);
     ensure(w->uoff, N * 8, st);
     ensure(w->scan_tmp, ae_scan_tmp_words(N, 5) * 8, st);
+    prof.mark(K_OTHER);
     ae_unique_flags(keys, N, ptr<uint32_t>(w->uflags), st);
     const uint32_t *in[1] = {ptr<uint32_t>(w->uflags)};
     uint64_t *out[1] = {ptr<uint64_t>(w->uoff)};
     ae_scan_u32(in, out, 1, N, ptr<uint64_t>(w->totals), ptr<uint64_t>(w->scan_tmp), st);
+    prof.mark(K_OTHER);
     CU(cudaMemcpyAsync(tot(), w->totals.p, 8, cudaMemcpyDeviceToHost, st));
     sync();
     const int64_t U = (int64_t)tot()[0];
     ensure(w->uniq, std::max<int64_t>(U, 1) * sizeof(ae_hit), st);
+    prof.mark(K_OTHER);
     ae_unique_write(keys, scores, N, ptr<uint64_t>(w->uoff), be, bj, ptr<ae_hit>(w->uniq),
                     ptr<unsigned long long>(w->qcount), st);
+    prof.mark(K_OTHER);
     std::vector<unsigned long long> qc(nq);
     CU(cudaMemcpyAsync(qc.data(), w->qcount.p, sizeof(unsigned long long) * nq, cudaMemcpyDeviceToHost, st));
     sync();
@@ -618,6 +674,9 @@ ae_status search_core(const ae_index *idx, Workspace *w, const int64_t *offsets,
     if (s.be + s.bj + s.bq > 64 || s.be > 32) return AE_EUNSUPPORTED;
     s.d0 = seed_depth(s.sc, Hmin, s.opt.qprefix_seed != 0);
     s.stats.seed_depth = s.d0;
+    s.prof.on = s.opt.profile != 0;
+    s.prof.st = st;
+    const int64_t launches0 = ae_launches_read();
     int dev = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&s.num_sms, cudaDevAttrMultiProcessorCount, dev);
@@ -664,6 +723,11 @@ ae_status search_core(const ae_index *idx, Workspace *w, const int64_t *offsets,
         s.stats.leaf_rows = (int64_t)ds.leaf_rows;
         s.stats.entries = (int64_t)ds.entries;
         for (int k = 0; k < 3; ++k) s.stats.entries_tier[k] = (int64_t)ds.tier[k];
+        s.stats.entries_leaf = (int64_t)ds.entries_leaf;
+        s.stats.ms_k_expand = s.prof.ms(K_EXPAND);
+        s.stats.ms_k_leaf = s.prof.ms(K_LEAF);
+        s.stats.ms_k_sort = s.prof.ms(K_SORT);
+        s.stats.ms_k_other = s.prof.ms(K_OTHER);
     } catch (const ae_error &err) {
         cudaGetLastError();
         return err.st;
@@ -671,6 +735,7 @@ ae_status search_core(const ae_index *idx, Workspace *w, const int64_t *offsets,
         return AE_ENOMEM;
     }
     s.stats.ms_total = ms_since(t0);
+    s.stats.launches = ae_launches_read() - launches0;
     g_last_stats = s.stats;
     return AE_OK;
 }
@@ -688,6 +753,7 @@ void ae_options_default(ae_options *opt) {
     opt->item_columns = 1 << 16;
     opt->batch_columns = 1 << 20;
     opt->leaf_capacity = 4096;
+    opt->profile = 0;
 }
 
 const char *ae_strerror(int32_t status) {

@@ -100,7 +100,8 @@ struct RangeHit {
 struct DevStats {
     unsigned long long nodes, leaf_rows, entries, tier[3], raw_hits;
     unsigned long long leaf_overflow, hit_overflow;
-    unsigned long long pad[6];
+    unsigned long long entries_leaf;
+    unsigned long long pad[5];
 };
 
 // ---------------------------------------------------------------- host index

@@ -29,6 +29,9 @@
 
 #define FULL 0xffffffffu
 
+// Kernel launches issued by the calling thread (reported as ae_stats.launches).
+thread_local int64_t g_launches = 0;
+
 namespace {
 
 // ------------------------------------------------------------------ helpers
@@ -266,10 +269,12 @@ void scan_rec(const In *const *inp, uint64_t *const *outp, int64_t N, uint64_t *
     }
     int64_t nb = (N + SC_TILE - 1) / SC_TILE;
     if (nb == 1) {
+        ++g_launches;
         k_scan_down<In, W><<<1, SC_T, 0, st>>>(in, out, N, nullptr, 1, totals);
         return;
     }
     uint64_t *bsum = tmp, *boff = tmp + nb * W, *rest = tmp + 2 * nb * W;
+    g_launches += 2;
     k_scan_reduce<In, W><<<(unsigned)nb, SC_T, 0, st>>>(in, N, bsum, nb);
     const uint64_t *bin[W];
     uint64_t *bout[W];
@@ -974,7 +979,10 @@ __global__ void __launch_bounds__(128) k_leaf(LeafArgs a) {
     }
     if (lane == 0) {
         if (st_rows) atomicAdd(&a.stats->leaf_rows, st_rows);
-        if (st_ent) atomicAdd(&a.stats->entries, st_ent);
+        if (st_ent) {
+            atomicAdd(&a.stats->entries, st_ent);
+            atomicAdd(&a.stats->entries_leaf, st_ent);
+        }
         if (t0) atomicAdd(&a.stats->tier[0], t0);
         if (t1) atomicAdd(&a.stats->tier[1], t1);
         if (t2) atomicAdd(&a.stats->tier[2], t2);
@@ -1038,6 +1046,9 @@ inline unsigned grid_for(int64_t n, int threads, int64_t cap = 152 * 64) {
 
 // ------------------------------------------------------------------ launch wrappers
 
+int64_t ae_launches_read() { return g_launches; }
+
+
 int64_t ae_scan_tmp_words(int64_t N, int W) {
     int64_t words = 0;
     while (N > SC_TILE) {
@@ -1077,10 +1088,12 @@ int ae_radix_sort(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int64_
     for (int shift = 0; shift < bits; shift += 8) {
         uint64_t *ki = which ? k1 : k0, *ko = which ? k0 : k1;
         uint32_t *vi = which ? v1 : v0, *vo = which ? v0 : v1;
+        ++g_launches;
         k_rs_hist<<<(unsigned)ntiles, RS_T, 0, st>>>(ki, N, shift, hist, ntiles);
         const uint32_t *in[1] = {hist};
         uint64_t *out[1] = {offs};
         scan_rec<uint32_t, 1>(in, out, h, nullptr, stmp, st);
+        ++g_launches;
         k_rs_scatter<<<(unsigned)ntiles, RS_T, 0, st>>>(ki, vi, ko, vo, N, shift, offs, ntiles);
         which ^= 1;
     }
@@ -1090,11 +1103,13 @@ int ae_radix_sort(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int64_
 void ae_encode_queries(const uint8_t *ascii, uint8_t *codes, int64_t total, int alphabet, int *bad,
                        cudaStream_t st) {
     if (total <= 0) return;
+    ++g_launches;
     k_encode<<<grid_for(total, 256), 256, 0, st>>>(ascii, codes, total, alphabet, bad);
 }
 
 void ae_seed_keys(const SeedArgs &a, uint64_t *keys, uint32_t *vals, cudaStream_t st) {
     if (a.npos <= 0) return;
+    ++g_launches;
     k_seed_keys<<<grid_for(a.npos, 256), 256, 0, st>>>(a, keys, vals);
 }
 
@@ -1106,14 +1121,17 @@ void ae_seed_nodes(const SeedArgs &a, const uint64_t *keys, const uint32_t *vals
         cudaMemsetAsync(nnodes_dev, 0, sizeof(uint64_t), st);
         return;
     }
+    ++g_launches;
     k_seed_flags<<<grid_for(npos, 256), 256, 0, st>>>(keys, npos, flags);
     const uint32_t *in[1] = {flags};
     uint64_t *out[1] = {flag_off};
     scan_rec<uint32_t, 1>(in, out, npos, nnodes_dev, tmp, st);
+    ++g_launches;
     if (a.ix.sigma == 4)
         k_seed_nodes<4><<<grid_for(npos, 256), 256, 0, st>>>(a, keys, vals, npos, flags, flag_off, nodes, aj, aM, aGa);
     else
         k_seed_nodes<20><<<grid_for(npos, 256), 256, 0, st>>>(a, keys, vals, npos, flags, flag_off, nodes, aj, aM, aGa);
+    ++g_launches;
     k_seed_fix<<<grid_for(npos, 256), 256, 0, st>>>(nodes, nnodes_dev, npos);
 }
 
@@ -1122,16 +1140,17 @@ void ae_expand(const ExpandArgs &a, bool write, cudaStream_t st) {
     const int threads = 256;
     const unsigned blocks = grid_for(a.nnodes * 32, threads, 152 * 16);
     if (a.ix.sigma == 4) {
-        if (write) k_expand<4, true><<<blocks, threads, 0, st>>>(a);
-        else k_expand<4, false><<<blocks, threads, 0, st>>>(a);
+        if (write) { ++g_launches; k_expand<4, true><<<blocks, threads, 0, st>>>(a); }
+        else { ++g_launches; k_expand<4, false><<<blocks, threads, 0, st>>>(a); }
     } else {
-        if (write) k_expand<20, true><<<blocks, threads, 0, st>>>(a);
-        else k_expand<20, false><<<blocks, threads, 0, st>>>(a);
+        if (write) { ++g_launches; k_expand<20, true><<<blocks, threads, 0, st>>>(a); }
+        else { ++g_launches; k_expand<20, false><<<blocks, threads, 0, st>>>(a); }
     }
 }
 
 void ae_inject_keys(const Inject *inj, int64_t ninj, uint64_t *keys, uint32_t *vals, cudaStream_t st) {
     if (ninj <= 0) return;
+    ++g_launches;
     k_inject_keys<<<grid_for(ninj, 256), 256, 0, st>>>(inj, ninj, keys, vals);
 }
 
@@ -1139,27 +1158,32 @@ int64_t ae_leaf_scratch_words(int32_t cap, int32_t nwarps) { return (int64_t)12 
 
 void ae_leaf_sweep(const LeafArgs &a, int blocks, int threads, cudaStream_t st) {
     if (a.nseg <= 0) return;
+    ++g_launches;
     k_leaf<<<blocks, threads, 0, st>>>(a);
 }
 
 void ae_locate_counts(const RangeHit *rh, int64_t nrh, uint32_t *cnt, cudaStream_t st) {
     if (nrh <= 0) return;
+    ++g_launches;
     k_locate_counts<<<grid_for(nrh, 256), 256, 0, st>>>(rh, nrh, cnt);
 }
 
 void ae_locate(const RangeHit *rh, int64_t nrh, const uint64_t *off, int64_t total, const int32_t *tend, int be,
                  int bj, uint64_t *key, int32_t *score, cudaStream_t st) {
     if (total <= 0) return;
+    ++g_launches;
     k_locate<<<grid_for(total, 256), 256, 0, st>>>(rh, nrh, off, total, tend, be, bj, key, score);
 }
 
 void ae_unique_flags(const uint64_t *key, int64_t N, uint32_t *flags, cudaStream_t st) {
     if (N <= 0) return;
+    ++g_launches;
     k_unique_flags<<<grid_for(N, 256), 256, 0, st>>>(key, N, flags);
 }
 
 void ae_unique_write(const uint64_t *key, const int32_t *score, int64_t N, const uint64_t *flag_off, int be, int bj,
                      ae_hit *out, unsigned long long *qcount, cudaStream_t st) {
     if (N <= 0) return;
+    ++g_launches;
     k_unique_write<<<grid_for(N, 256), 256, 0, st>>>(key, score, N, flag_off, be, bj, out, qcount);
 }

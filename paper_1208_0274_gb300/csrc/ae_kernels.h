@@ -5,6 +5,9 @@
 
 #include "ae_internal.h"
 
+// Number of kernel launches issued so far by the calling thread.
+int64_t ae_launches_read();
+
 // Exclusive scans of W u32 arrays of length N into u64 arrays; totals[w]
 // (device, W entries) receives the sums.  tmp must hold scan_tmp_words(N, W)
 // u64 words.
