@@ -256,7 +256,9 @@ def run_ours(args):
         log(f"[rank {rank}] warmup {w}: {time.perf_counter() - t1:.3f} s, hits {int(counts.sum())}, "
             f"entries {st['entries']:,} (leaf {st['entries_leaf']:,}), nodes {st['nodes']:,}, "
             f"k_expand {st['ms_k_expand']:.1f} ms, k_leaf {st['ms_k_leaf']:.1f} ms, "
-            f"k_sort {st['ms_k_sort']:.1f} ms, k_other {st['ms_k_other']:.1f} ms, launches {st['launches']}")
+            f"k_sort {st['ms_k_sort']:.1f} ms, k_other {st['ms_k_other']:.1f} ms, launches {st['launches']}, "
+            f"leaf rows {st['leaf_rows']:,} max steps {st['leaf_max_steps']:,} max width {st['leaf_max_width']:,}, "
+            f"injections {st['injections']:,}, levels {st['levels']}, ws {st['ws_bytes'] / 1e9:.1f} GB")
 
     clocks = Clocks(local)
     if dist:

@@ -92,12 +92,15 @@ typedef struct {
     /* with ae_options.profile: device time of the kernels, by kind, from CUDA
      * events recorded on the search's stream around each launch group */
     double  ms_k_expand, ms_k_leaf, ms_k_sort, ms_k_other;
+    int64_t leaf_max_steps;   /* longest text walk of one sweep task (positions) */
+    int64_t leaf_max_width;   /* widest row met by the sweep (entries) */
+    int64_t ws_bytes;         /* device bytes held by the library's working buffers */
 } ae_stats;
 
 /* Engine knobs (NULL = defaults).  None of them changes the result set. */
 typedef struct {
     int32_t qprefix_seed;   /* 1: start at depth q-1 from the query's (q-1)-grams (Theorem 3); 0: root */
-    int32_t leaf_segment;   /* trie rows merged per sweep task (>= 1) */
+    int32_t leaf_segment;   /* injected rows per sweep task (0 = chosen from the load) */
     int64_t item_columns;   /* query columns per work item (seed range) */
     int64_t batch_columns;  /* query columns processed per batch */
     int32_t leaf_capacity;  /* initial per-task row capacity of the sweep, in entries */

@@ -54,7 +54,8 @@ class ae_stats(ctypes.Structure):
                 ("ms_leaf", ctypes.c_double), ("ms_reduce", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("ms_k_expand", ctypes.c_double),
                 ("ms_k_leaf", ctypes.c_double), ("ms_k_sort", ctypes.c_double),
-                ("ms_k_other", ctypes.c_double)]
+                ("ms_k_other", ctypes.c_double), ("leaf_max_steps", ctypes.c_int64),
+                ("leaf_max_width", ctypes.c_int64), ("ws_bytes", ctypes.c_int64)]
 
 
 def _load():

@@ -13,8 +13,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libae.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["ae_index.cpp", "ae_kernels.cu", "ae_engine.cu"]
-HEADERS = ["ae_internal.h", "ae_kernels.h"]
+SOURCES = ["ae_index.cpp", "ae_kernels.cu", "ae_trie.cu", "ae_engine.cu"]
+HEADERS = ["ae_internal.h", "ae_kernels.h", "ae_device.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -10,6 +10,7 @@
 //   (Algorithm 1, lines 6-11).
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -41,38 +42,65 @@ struct ae_error {
         if (_e != cudaSuccess) throw ae_error{AE_ECUDA}; \
     } while (0)
 
+int64_t g_ws_bytes = 0;   // device bytes held by all workspaces of the process
+bool mem_trace() {
+    static int on = -1;
+    if (on < 0) on = getenv("AE_TRACE_MEM") != nullptr;
+    return on == 1;
+}
+bool trace() {
+    static int on = -1;
+    if (on < 0) on = getenv("AE_TRACE") != nullptr;
+    return on == 1;
+}
+void trace_alloc(size_t nb, bool ok) {
+    if (!mem_trace()) return;
+    size_t fr = 0, tot = 0;
+    cudaMemGetInfo(&fr, &tot);
+    fprintf(stderr, "[ae mem] alloc %.3f GB %s; workspaces hold %.3f GB; device free %.3f of %.3f GB\n", nb / 1e9,
+            ok ? "ok" : "FAILED", g_ws_bytes / 1e9, fr / 1e9, tot / 1e9);
+}
+
 // Grow-only device buffer; contents are not preserved.
 void ensure(DevBuf &b, size_t bytes, cudaStream_t st) {
     if (bytes <= b.bytes) return;
-    size_t nb = std::max(bytes, b.bytes + b.bytes / 2);
+    size_t nb = std::max(bytes, b.bytes + b.bytes / 4);
     nb = (nb + 255) & ~size_t(255);
     if (b.p) {
         CU(cudaStreamSynchronize(st));
         CU(cudaFree(b.p));
+        g_ws_bytes -= (int64_t)b.bytes;
         b.p = nullptr;
         b.bytes = 0;
     }
     if (cudaMalloc(&b.p, nb) != cudaSuccess) {
         cudaGetLastError();
+        trace_alloc(nb, false);
         throw ae_error{AE_ENOMEM};
     }
+    g_ws_bytes += (int64_t)nb;
+    trace_alloc(nb, true);
     b.bytes = nb;
 }
 
 // Grow preserving the first `keep` bytes.
 void ensure_keep(DevBuf &b, size_t bytes, size_t keep, cudaStream_t st) {
     if (bytes <= b.bytes) return;
-    size_t nb = std::max(bytes, b.bytes + b.bytes / 2);
+    size_t nb = std::max(bytes, b.bytes + b.bytes / 4);
     nb = (nb + 255) & ~size_t(255);
     void *p = nullptr;
     if (cudaMalloc(&p, nb) != cudaSuccess) {
         cudaGetLastError();
+        trace_alloc(nb, false);
         throw ae_error{AE_ENOMEM};
     }
+    g_ws_bytes += (int64_t)nb;
+    trace_alloc(nb, true);
     if (b.p) {
         if (keep) CU(cudaMemcpyAsync(p, b.p, keep, cudaMemcpyDeviceToDevice, st));
         CU(cudaStreamSynchronize(st));
         CU(cudaFree(b.p));
+        g_ws_bytes -= (int64_t)b.bytes;
     }
     b.p = p;
     b.bytes = nb;
@@ -101,7 +129,8 @@ struct Workspace {
     DevBuf scratch, next_seg;
     // output
     DevBuf uniq, uflags, uoff, qcount;
-    DevBuf stats;
+    DevBuf stats, segs, ctr;
+    double fr_ratio = 0.5, lf_ratio = 0.25, hit_ratio = 0.5;
     // pinned host staging
     uint64_t *h_tot = nullptr;
     int32_t leaf_cap = 0;
@@ -111,9 +140,12 @@ struct Workspace {
                          &aM[1], &aGa[0], &aGa[1], &nodes[0], &nodes[1], &cnt[0], &cnt[1], &cnt[2], &cnt[3],
                          &cnt[4], &off[0], &off[1], &off[2], &off[3], &off[4], &totals, &scan_tmp, &lj, &lM,
                          &lGa, &inj, &rhits, &sk0, &sv0, &sk1, &sv1, &sort_tmp, &hkey, &hscore, &hcount, &hk1,
-                         &hv1, &scratch, &next_seg, &uniq, &uflags, &uoff, &qcount, &stats};
+                         &hv1, &scratch, &next_seg, &uniq, &uflags, &uoff, &qcount, &stats, &segs, &ctr};
         for (DevBuf *b : all)
-            if (b->p) cudaFree(b->p);
+            if (b->p) {
+                cudaFree(b->p);
+                g_ws_bytes -= (int64_t)b->bytes;
+            }
         if (h_tot) cudaFreeHost(h_tot);
     }
 };
@@ -298,6 +330,7 @@ struct Search {
     }
 
     void run_batch(const std::vector<WorkItem> &items);
+    void compact_hits(int64_t from);
     void leaf_phase(int64_t ninj);
     void locate_phase(int64_t nrh);
     int64_t finish(ae_hit **out_dev, std::vector<int64_t> &counts);
@@ -305,6 +338,7 @@ struct Search {
 
 void Search::run_batch(const std::vector<WorkItem> &items) {
     const int sigma = ix.sigma;
+    const int64_t batch_hits0 = nhits;
     const int nitems = (int)items.size();
     ensure(w->items, sizeof(WorkItem) * items.size(), st);
     CU(cudaMemcpyAsync(w->items.p, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice, st));
@@ -395,78 +429,120 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
         L_max_all = std::max(L_max_all, Lm);
     }
     ensure(w->totals, 64, st);
+    ensure(w->ctr, sizeof(LevelCounters), st);
     while (F > 0 && depth <= L_max_all) {
         const int64_t S = F * sigma;
-        for (int k = 0; k < 5; ++k) {
-            ensure(w->cnt[k], S * 4, st);
-            ensure(w->off[k], S * 8, st);
-        }
+        // children ranges (backward-search step per letter)
+        for (int k = 0; k < 4; ++k) ensure(w->cnt[k], S * 4, st);
+        for (int k = 0; k < 2; ++k) ensure(w->off[k], S * 8, st);
         ensure(w->scan_tmp, ae_scan_tmp_words(S, 5) * 8, st);
-        ExpandArgs ea;
-        memset(&ea, 0, sizeof(ea));
-        ea.ix = ix;
-        ea.sc = sc;
-        ea.qv = qv;
-        ea.items = d_items;
-        ea.nodes = ptr<Node>(w->nodes[cur]);
-        ea.nnodes = F;
-        ea.pj = ptr<int32_t>(w->aj[cur]);
-        ea.pM = ptr<int32_t>(w->aM[cur]);
-        ea.pGa = ptr<int32_t>(w->aGa[cur]);
-        ea.c_fr_ent = ptr<uint32_t>(w->cnt[0]);
-        ea.c_lf_ent = ptr<uint32_t>(w->cnt[1]);
-        ea.c_fr_node = ptr<uint32_t>(w->cnt[2]);
-        ea.c_lf_node = ptr<uint32_t>(w->cnt[3]);
-        ea.c_hits = ptr<uint32_t>(w->cnt[4]);
-        ea.stats = ptr<DevStats>(w->stats);
+        ChildrenArgs ca;
+        ca.ix = ix;
+        ca.items = d_items;
+        ca.nodes = ptr<Node>(w->nodes[cur]);
+        ca.nnodes = F;
+        ca.clo = ptr<uint32_t>(w->cnt[0]);
+        ca.chi = ptr<uint32_t>(w->cnt[1]);
+        ca.flag = ptr<uint32_t>(w->cnt[2]);
+        ca.len = ptr<uint32_t>(w->cnt[3]);
+        ca.stats = ptr<DevStats>(w->stats);
         prof.mark(K_EXPAND);
-        ae_expand(ea, false, st);
+        ae_children(ca, st);
+        const uint32_t *cin[2] = {ca.flag, ca.len};
+        uint64_t *cout[2] = {ptr<uint64_t>(w->off[0]), ptr<uint64_t>(w->off[1])};
+        ae_scan_u32(cin, cout, 2, S, ptr<uint64_t>(w->totals), ptr<uint64_t>(w->scan_tmp), st);
         prof.mark(K_EXPAND);
-        const uint32_t *cin[5] = {ea.c_fr_ent, ea.c_lf_ent, ea.c_fr_node, ea.c_lf_node, ea.c_hits};
-        uint64_t *cout[5];
-        for (int k = 0; k < 5; ++k) cout[k] = ptr<uint64_t>(w->off[k]);
-        prof.mark(K_OTHER);
-        ae_scan_u32(cin, cout, 5, S, ptr<uint64_t>(w->totals), ptr<uint64_t>(w->scan_tmp), st);
-        prof.mark(K_OTHER);
-        CU(cudaMemcpyAsync(tot(), w->totals.p, 5 * 8, cudaMemcpyDeviceToHost, st));
+        CU(cudaMemcpyAsync(tot(), w->totals.p, 16, cudaMemcpyDeviceToHost, st));
         sync();
-        const int64_t fr_ent = (int64_t)tot()[0], lf_ent = (int64_t)tot()[1], fr_node = (int64_t)tot()[2],
-                      lf_node = (int64_t)tot()[3], hits = (int64_t)tot()[4];
+        const int64_t nseg = (int64_t)tot()[0], ntrip = (int64_t)tot()[1];
+        if (nseg == 0) break;
+        ensure(w->segs, nseg * sizeof(Seg), st);
+        prof.mark(K_EXPAND);
+        ae_compact_segs(ca.clo, ca.chi, ca.flag, ca.len, cout[0], cout[1], S, sigma, ca.nodes, d_items, qv,
+                        ptr<Seg>(w->segs), st);
+        prof.mark(K_EXPAND);
         const int nxt = cur ^ 1;
-        ensure(w->aj[nxt], std::max<int64_t>(fr_ent, 1) * 4, st);
-        ensure(w->aM[nxt], std::max<int64_t>(fr_ent, 1) * 4, st);
-        ensure(w->aGa[nxt], std::max<int64_t>(fr_ent, 1) * 4, st);
-        ensure(w->nodes[nxt], std::max<int64_t>(fr_node, 1) * sizeof(Node), st);
-        ensure_keep(w->lj, (size_t)(lf_ent_base + lf_ent + 1) * 4, (size_t)lf_ent_base * 4, st);
-        ensure_keep(w->lM, (size_t)(lf_ent_base + lf_ent + 1) * 4, (size_t)lf_ent_base * 4, st);
-        ensure_keep(w->lGa, (size_t)(lf_ent_base + lf_ent + 1) * 4, (size_t)lf_ent_base * 4, st);
-        ensure_keep(w->inj, (size_t)(lf_node_base + lf_node + 1) * sizeof(Inject), (size_t)lf_node_base * sizeof(Inject), st);
-        ensure_keep(w->rhits, (size_t)(rh_base + hits + 1) * sizeof(RangeHit), (size_t)rh_base * sizeof(RangeHit), st);
-        ea.o_fr_ent = ptr<uint64_t>(w->off[0]);
-        ea.o_lf_ent = ptr<uint64_t>(w->off[1]);
-        ea.o_fr_node = ptr<uint64_t>(w->off[2]);
-        ea.o_lf_node = ptr<uint64_t>(w->off[3]);
-        ea.o_hits = ptr<uint64_t>(w->off[4]);
-        ea.lf_ent_base = (uint64_t)lf_ent_base;
-        ea.lf_node_base = (uint64_t)lf_node_base;
-        ea.hit_base = (uint64_t)rh_base;
-        ea.fj = ptr<int32_t>(w->aj[nxt]);
-        ea.fM = ptr<int32_t>(w->aM[nxt]);
-        ea.fGa = ptr<int32_t>(w->aGa[nxt]);
-        ea.fnodes = ptr<Node>(w->nodes[nxt]);
-        ea.lj = ptr<int32_t>(w->lj);
-        ea.lM = ptr<int32_t>(w->lM);
-        ea.lGa = ptr<int32_t>(w->lGa);
-        ea.inj = ptr<Inject>(w->inj);
-        ea.rhits = ptr<RangeHit>(w->rhits);
-        prof.mark(K_EXPAND);
-        ae_expand(ea, true, st);
-        prof.mark(K_EXPAND);
-        lf_ent_base += lf_ent;
-        lf_node_base += lf_node;
-        rh_base += hits;
+        // output capacities (grown and the level rerun if a reservation overflows)
+        // outputs per triple seen so far (each parent entry is one triple per
+        // non-empty child), with headroom; a reservation past these reruns the level
+        int64_t fr_cap = (int64_t)(ntrip * w->fr_ratio) + 4096;
+        int64_t lf_cap = lf_ent_base + (int64_t)(ntrip * w->lf_ratio) + 4096;
+        int64_t hit_cap = rh_base + ntrip / 64 + 4096;
+        LevelCounters h0;
+        memset(&h0, 0, sizeof(h0));
+        h0.lf_ent = (unsigned long long)lf_ent_base;
+        h0.lf_node = (unsigned long long)lf_node_base;
+        h0.hits = (unsigned long long)rh_base;
+        for (int attempt = 0;; ++attempt) {
+            if (attempt > 8) throw ae_error{AE_ENOMEM};
+            ensure(w->aj[nxt], fr_cap * 4, st);
+            ensure(w->aM[nxt], fr_cap * 4, st);
+            ensure(w->aGa[nxt], fr_cap * 4, st);
+            ensure(w->nodes[nxt], std::max<int64_t>(nseg, 1) * sizeof(Node), st);
+            ensure_keep(w->lj, (size_t)lf_cap * 4, (size_t)lf_ent_base * 4, st);
+            ensure_keep(w->lM, (size_t)lf_cap * 4, (size_t)lf_ent_base * 4, st);
+            ensure_keep(w->lGa, (size_t)lf_cap * 4, (size_t)lf_ent_base * 4, st);
+            ensure_keep(w->inj, (size_t)(lf_node_base + nseg + 1) * sizeof(Inject),
+                        (size_t)lf_node_base * sizeof(Inject), st);
+            ensure_keep(w->rhits, (size_t)hit_cap * sizeof(RangeHit), (size_t)rh_base * sizeof(RangeHit), st);
+            CU(cudaMemcpyAsync(w->ctr.p, &h0, sizeof(h0), cudaMemcpyHostToDevice, st));
+            RowsArgs ra;
+            memset(&ra, 0, sizeof(ra));
+            ra.ix = ix;
+            ra.sc = sc;
+            ra.qv = qv;
+            ra.items = d_items;
+            ra.nodes = ptr<Node>(w->nodes[cur]);
+            ra.pj = ptr<int32_t>(w->aj[cur]);
+            ra.pM = ptr<int32_t>(w->aM[cur]);
+            ra.pGa = ptr<int32_t>(w->aGa[cur]);
+            ra.segs = ptr<Seg>(w->segs);
+            ra.nseg_dev = ptr<uint64_t>(w->totals);
+            ra.ntrip_dev = ptr<uint64_t>(w->totals) + 1;
+            ra.fj = ptr<int32_t>(w->aj[nxt]);
+            ra.fM = ptr<int32_t>(w->aM[nxt]);
+            ra.fGa = ptr<int32_t>(w->aGa[nxt]);
+            ra.fnodes = ptr<Node>(w->nodes[nxt]);
+            ra.fr_ent_cap = (uint64_t)fr_cap;
+            ra.fr_node_cap = (uint64_t)nseg;
+            ra.lj = ptr<int32_t>(w->lj);
+            ra.lM = ptr<int32_t>(w->lM);
+            ra.lGa = ptr<int32_t>(w->lGa);
+            ra.inj = ptr<Inject>(w->inj);
+            ra.lf_ent_cap = (uint64_t)lf_cap;
+            ra.lf_node_cap = (uint64_t)(lf_node_base + nseg);
+            ra.rhits = ptr<RangeHit>(w->rhits);
+            ra.hit_cap = (uint64_t)hit_cap;
+            ra.ctr = ptr<LevelCounters>(w->ctr);
+            ra.stats = attempt == 0 ? ptr<DevStats>(w->stats) : nullptr;
+            prof.mark(K_EXPAND);
+            ae_rows(ra, num_sms * 4, st);
+            prof.mark(K_EXPAND);
+            LevelCounters hc;
+            const int64_t lf_ent_prev = lf_ent_base;
+            CU(cudaMemcpyAsync(tot(), w->ctr.p, sizeof(hc), cudaMemcpyDeviceToHost, st));
+            sync();
+            memcpy(&hc, tot(), sizeof(hc));
+            if (!hc.overflow) {
+                F = (int64_t)hc.fr_node;
+                lf_ent_base = (int64_t)hc.lf_ent;
+                lf_node_base = (int64_t)hc.lf_node;
+                rh_base = (int64_t)hc.hits;
+                const double fr_r = (double)hc.fr_ent / (double)ntrip;
+                const double lf_r = (double)((int64_t)hc.lf_ent - lf_ent_prev) / (double)ntrip;
+                w->fr_ratio = std::max(w->fr_ratio * 0.9, std::min(2.0, fr_r * 1.2 + 0.02));
+                w->lf_ratio = std::max(w->lf_ratio * 0.9, std::min(2.0, lf_r * 1.2 + 0.02));
+                if (trace())
+                    fprintf(stderr, "[ae level] depth %d nodes %lld segs %lld triples %lld -> frontier %lld, leaf %lld entries, attempts %d\n",
+                            depth, (long long)F, (long long)nseg, (long long)ntrip, (long long)hc.fr_ent,
+                            (long long)((int64_t)hc.lf_ent - lf_ent_prev), attempt + 1);
+                break;
+            }
+            fr_cap = std::max<int64_t>(fr_cap, (int64_t)hc.fr_ent + 1024);
+            lf_cap = std::max<int64_t>(lf_cap, (int64_t)hc.lf_ent + 1024);
+            hit_cap = std::max<int64_t>(hit_cap, (int64_t)hc.hits + 1024);
+        }
         cur = nxt;
-        F = fr_node;
         ++depth;
         stats.levels++;
     }
@@ -480,7 +556,50 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
     stats.ms_leaf += ms_since(t1);
     auto t2 = std::chrono::steady_clock::now();
     locate_phase(rh_base);
+    compact_hits(batch_hits0);
     stats.ms_reduce += ms_since(t2);
+}
+
+// Reduce the hits [from, nhits) of the batch just finished to one record per
+// (query, text end, query end) with the maximum score, in place.  Queries are
+// whole inside a batch by default, so the final pass then sorts far fewer
+// records; it stays exact either way.
+void Search::compact_hits(int64_t from) {
+    const int64_t N = nhits - from;
+    if (N <= 1) return;
+    ensure(w->hk1, N * 8, st);
+    ensure(w->hv1, N * 4, st);
+    ensure(w->sort_tmp, ae_sort_tmp_words(N) * 8, st);
+    uint64_t *k0 = ptr<uint64_t>(w->hkey) + from;
+    uint32_t *v0 = reinterpret_cast<uint32_t *>(ptr<int32_t>(w->hscore) + from);
+    prof.mark(K_SORT);
+    int which = ae_radix_sort(k0, v0, ptr<uint64_t>(w->hk1), ptr<uint32_t>(w->hv1), N, be + bj + bq,
+                              ptr<uint64_t>(w->sort_tmp), st);
+    prof.mark(K_SORT);
+    const uint64_t *keys = which ? ptr<uint64_t>(w->hk1) : k0;
+    const int32_t *scores = which ? ptr<int32_t>(w->hv1) : reinterpret_cast<int32_t *>(v0);
+    ensure(w->uflags, N * 4, st);
+    ensure(w->uoff, N * 8, st);
+    ensure(w->scan_tmp, ae_scan_tmp_words(N, 5) * 8, st);
+    prof.mark(K_OTHER);
+    ae_unique_flags(keys, N, ptr<uint32_t>(w->uflags), st);
+    const uint32_t *in[1] = {ptr<uint32_t>(w->uflags)};
+    uint64_t *out[1] = {ptr<uint64_t>(w->uoff)};
+    ae_scan_u32(in, out, 1, N, ptr<uint64_t>(w->totals), ptr<uint64_t>(w->scan_tmp), st);
+    CU(cudaMemcpyAsync(tot(), w->totals.p, 8, cudaMemcpyDeviceToHost, st));
+    sync();
+    const int64_t U = (int64_t)tot()[0];
+    // compacted records go to the other buffer, then back in place
+    uint64_t *dk = which ? k0 : ptr<uint64_t>(w->hk1);
+    int32_t *ds = which ? reinterpret_cast<int32_t *>(v0) : ptr<int32_t>(w->hv1);
+    ae_unique_compact(keys, scores, N, ptr<uint64_t>(w->uoff), dk, ds, st);
+    if (!which) {
+        CU(cudaMemcpyAsync(k0, dk, U * 8, cudaMemcpyDeviceToDevice, st));
+        CU(cudaMemcpyAsync(v0, ds, U * 4, cudaMemcpyDeviceToDevice, st));
+    }
+    prof.mark(K_OTHER);
+    if (trace()) fprintf(stderr, "[ae hits] batch raw %lld -> unique %lld\n", (long long)N, (long long)U);
+    nhits = from + U;
 }
 
 void Search::leaf_phase(int64_t ninj) {
@@ -499,12 +618,12 @@ void Search::leaf_phase(int64_t ninj) {
     const uint32_t *order = which ? ptr<uint32_t>(w->sv1) : ptr<uint32_t>(w->sv0);
 
     const int threads = 128;
-    const int blocks = num_sms * 8;
+    const int blocks = num_sms * 12;
     const int nwarps = blocks * threads / 32;
     if (w->leaf_cap < opt.leaf_capacity) w->leaf_cap = opt.leaf_capacity;
     ensure(w->next_seg, 8, st);
     ensure(w->hcount, 8, st);
-    int64_t hit_cap = std::max<int64_t>(1 << 20, ninj * 4);
+    int64_t hit_cap = std::max<int64_t>(1 << 20, (int64_t)(ninj * w->hit_ratio) + 4096);
     for (int attempt = 0; attempt < 12; ++attempt) {
         ensure(w->scratch, (size_t)ae_leaf_scratch_words(w->leaf_cap, nwarps) * 4, st);
         hits_reserve(hit_cap);
@@ -523,7 +642,12 @@ void Search::leaf_phase(int64_t ninj) {
         la.lj = ptr<int32_t>(w->lj);
         la.lM = ptr<int32_t>(w->lM);
         la.lGa = ptr<int32_t>(w->lGa);
-        la.seg = std::max(1, opt.leaf_segment);
+        // injections per sweep task: the option, or (0 = auto) enough for about
+        // eight tasks per warp -- longer tasks merge more rows that meet inside
+        // homologous regions, fewer tasks balance worse
+        la.seg = opt.leaf_segment > 0
+                     ? opt.leaf_segment
+                     : (int32_t)std::min<int64_t>(4096, std::max<int64_t>(32, ninj / ((int64_t)nwarps * 8)));
         la.nseg = (ninj + la.seg - 1) / la.seg;
         la.next_seg = ptr<unsigned long long>(w->next_seg);
         la.scratch = ptr<int32_t>(w->scratch);
@@ -548,6 +672,10 @@ void Search::leaf_phase(int64_t ninj) {
         hdr[0] = tot()[0];
         hdr[1] = tot()[1];
         hdr[2] = tot()[2];
+        if (trace())
+            fprintf(stderr, "[ae leaf] injections %lld attempt %d: hits %llu (cap %lld), row overflow %llu, hit overflow %llu, cap %d\n",
+                    (long long)ninj, attempt, hdr[0] - (unsigned long long)nhits, (long long)hit_cap, hdr[1], hdr[2],
+                    w->leaf_cap);
         if (hdr[1] != 0) {          // a row outgrew the scratch: retry larger
             w->leaf_cap *= 4;
             continue;
@@ -556,6 +684,8 @@ void Search::leaf_phase(int64_t ninj) {
             hit_cap = (int64_t)hdr[0] - nhits + 1024;
             continue;
         }
+        w->hit_ratio = std::max(w->hit_ratio * 0.9,
+                                std::min(64.0, 1.3 * (double)((int64_t)hdr[0] - nhits) / (double)ninj + 0.01));
         nhits = (int64_t)hdr[0];
         return;
     }
@@ -650,7 +780,7 @@ ae_status search_core(const ae_index *idx, Workspace *w, const int64_t *offsets,
     memset(&s.stats, 0, sizeof(s.stats));
     ae_options_default(&s.opt);
     if (opt) s.opt = *opt;
-    if (s.opt.item_columns < 1 || s.opt.batch_columns < 1 || s.opt.leaf_capacity < 64 || s.opt.leaf_segment < 1)
+    if (s.opt.item_columns < 1 || s.opt.batch_columns < 1 || s.opt.leaf_capacity < 64 || s.opt.leaf_segment < 0)
         return AE_EINVAL;
     ae_status e = make_score(scoring, s.ix.sigma, s.sc);
     if (e != AE_OK) return e;
@@ -724,6 +854,9 @@ ae_status search_core(const ae_index *idx, Workspace *w, const int64_t *offsets,
         s.stats.entries = (int64_t)ds.entries;
         for (int k = 0; k < 3; ++k) s.stats.entries_tier[k] = (int64_t)ds.tier[k];
         s.stats.entries_leaf = (int64_t)ds.entries_leaf;
+        s.stats.leaf_max_steps = (int64_t)ds.leaf_max_steps;
+        s.stats.leaf_max_width = (int64_t)ds.leaf_max_width;
+        s.stats.ws_bytes = g_ws_bytes;
         s.stats.ms_k_expand = s.prof.ms(K_EXPAND);
         s.stats.ms_k_leaf = s.prof.ms(K_LEAF);
         s.stats.ms_k_sort = s.prof.ms(K_SORT);
@@ -749,8 +882,8 @@ extern "C" {
 void ae_options_default(ae_options *opt) {
     if (!opt) return;
     opt->qprefix_seed = 1;
-    opt->leaf_segment = 32;
-    opt->item_columns = 1 << 16;
+    opt->leaf_segment = 0;
+    opt->item_columns = 1 << 24;
     opt->batch_columns = 1 << 20;
     opt->leaf_capacity = 4096;
     opt->profile = 0;

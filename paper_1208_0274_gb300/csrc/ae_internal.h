@@ -101,7 +101,8 @@ struct DevStats {
     unsigned long long nodes, leaf_rows, entries, tier[3], raw_hits;
     unsigned long long leaf_overflow, hit_overflow;
     unsigned long long entries_leaf;
-    unsigned long long pad[5];
+    unsigned long long leaf_max_steps, leaf_max_width;
+    unsigned long long pad[3];
 };
 
 // ---------------------------------------------------------------- host index

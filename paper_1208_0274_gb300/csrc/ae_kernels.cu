@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "ae_device.cuh"
 #include "ae_kernels.h"
 
 #define FULL 0xffffffffu
@@ -33,139 +34,7 @@
 thread_local int64_t g_launches = 0;
 
 namespace {
-
-// ------------------------------------------------------------------ helpers
-
-__device__ __forceinline__ int32_t warp_incl_max(int32_t v) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        int32_t o = __shfl_up_sync(FULL, v, d);
-        if (lane >= d) v = max(v, o);
-    }
-    return v;
-}
-
-__device__ __forceinline__ uint32_t warp_incl_sum(uint32_t v) {
-    const int lane = threadIdx.x & 31;
-#pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-        uint32_t o = __shfl_up_sync(FULL, v, d);
-        if (lane >= d) v += o;
-    }
-    return v;
-}
-
-__device__ __forceinline__ int64_t floordiv(int64_t a, int64_t b) {  // b > 0
-    int64_t q = a / b;
-    if ((a % b != 0) && (a < 0)) --q;
-    return q;
-}
-
-// Theorem 2 threshold of query column j (0-based): an entry lives iff > thr.
-__device__ __forceinline__ int32_t thr_of(int32_t j, int32_t m, int32_t H, int32_t g) {
-    int64_t t = (int64_t)H - 1 - (int64_t)(m - 1 - j) * g;
-    return t > 0 ? (int32_t)t : 0;
-}
-
-__device__ __forceinline__ int32_t delta_of(const ScoreView &sc, const int8_t *smat, int c, int q) {
-    return sc.use_matrix ? (int32_t)smat[c * AE_MAX_SIGMA + q] : (c == q ? sc.sa : sc.sb);
-}
-
-// Occ(c, k): occurrences of letter c in BWT rows [0, k).
-__device__ __forceinline__ uint32_t occ_dna(const IndexView &ix, int c, uint32_t k) {
-    const uint32_t *blk = ix.occ + (size_t)(k >> 6) * AE_DNA_BLOCK_WORDS;
-    const uint4 bits = __ldg(reinterpret_cast<const uint4 *>(blk + 4));
-    uint32_t acc = __ldg(blk + c);
-    const int r = k & 63;
-    const uint32_t w[4] = {bits.x, bits.y, bits.z, bits.w};
-#pragma unroll
-    for (int t = 0; t < 4; ++t) {
-        int take = r - 16 * t;
-        take = take < 0 ? 0 : (take > 16 ? 16 : take);
-        uint32_t mask = take == 16 ? 0x55555555u : (((1u << (2 * take)) - 1u) & 0x55555555u);
-        uint32_t lo = w[t] & 0x55555555u, hi = (w[t] >> 1) & 0x55555555u;
-        uint32_t eq = ((c & 1) ? lo : ~lo) & ((c & 2) ? hi : ~hi);
-        acc += __popc(eq & mask);
-    }
-    if (c == 0 && (int64_t)(k >> 6) == (ix.dollar_row >> 6) && (ix.dollar_row & 63) < r) acc -= 1;
-    return acc;
-}
-
-__device__ __forceinline__ uint32_t occ_prot(const IndexView &ix, int c, uint32_t k) {
-    const uint32_t *blk = ix.occ + (size_t)(k >> 6) * AE_PROT_BLOCK_WORDS;
-    const uint64_t *pl = reinterpret_cast<const uint64_t *>(blk + 22);
-    uint32_t acc = __ldg(blk + c);
-    const int r = k & 63;
-    const uint64_t mask = r ? (~0ull >> (64 - r)) : 0ull;
-    uint64_t eq = ~0ull;
-#pragma unroll
-    for (int t = 0; t < 5; ++t) {
-        uint64_t p = __ldg(pl + t);
-        eq &= ((c >> t) & 1) ? p : ~p;
-    }
-    acc += __popcll(eq & mask);
-    if (c == 0 && (int64_t)(k >> 6) == (ix.dollar_row >> 6) && (ix.dollar_row & 63) < r) acc -= 1;
-    return acc;
-}
-
-template <int SIGMA>
-__device__ __forceinline__ uint32_t occ_of(const IndexView &ix, int c, uint32_t k) {
-    return SIGMA == 4 ? occ_dna(ix, c, k) : occ_prot(ix, c, k);
-}
-
-__device__ __forceinline__ void load_matrix(const ScoreView &sc, int8_t *smat) {
-    for (int t = threadIdx.x; t < AE_MAX_SIGMA * AE_MAX_SIGMA; t += blockDim.x) smat[t] = sc.mat[t];
-    __syncthreads();
-}
-
-// Horizontal-gap finish of one lane's slots (see file comment).  Slot A is at
-// column colA with pre-G_b value MpA (already thresholded, AE_NEG if dead);
-// optional slot B at colA+1 with MpB.  excl/incl are the exclusive/inclusive
-// prefix maxima of the keys M'(k) + k*u over earlier slots (carry included).
-// The run covers the columns after the lane's last slot up to next_col - 1,
-// where only G_b can be live.
-struct SlotOut {
-    int32_t MA, MB, GbA, GbB;
-    bool aliveA, aliveB;
-    int32_t run_start, run_len, run_hits;
-};
-
-__device__ __forceinline__ void slot_finish(int32_t colA, int32_t MpA, bool hasB, int32_t MpB,
-                                            int32_t next_col, int32_t excl, int32_t incl,
-                                            const ScoreView &sc, int32_t m, int32_t H, int32_t u,
-                                            bool valid, SlotOut &o) {
-    const int32_t g = sc.gmax;
-    o.GbA = excl > AE_KNEG / 2 ? sc.sg - colA * u + excl : AE_NEG;
-    o.MA = max(MpA, o.GbA);
-    o.aliveA = valid && o.MA > thr_of(colA, m, H, g);
-    o.aliveB = false;
-    o.MB = AE_NEG;
-    o.GbB = AE_NEG;
-    if (valid && hasB) {
-        int32_t keyA = MpA > AE_NEG ? MpA + colA * u : AE_KNEG;
-        int32_t KB = max(excl, keyA);
-        o.GbB = KB > AE_KNEG / 2 ? sc.sg - (colA + 1) * u + KB : AE_NEG;
-        o.MB = max(MpB, o.GbB);
-        o.aliveB = o.MB > thr_of(colA + 1, m, H, g);
-    }
-    o.run_start = hasB ? colA + 2 : colA + 1;
-    o.run_len = 0;
-    o.run_hits = 0;
-    if (valid && incl > AE_KNEG / 2 && o.run_start < next_col) {
-        const int64_t K = incl;
-        int64_t x1 = floordiv(sc.sg + K - 1, u);
-        int64_t x2 = floordiv(sc.sg + K - H + (int64_t)(m - 1) * g, u + g);
-        int64_t xm = min(min(x1, x2), (int64_t)next_col - 1);
-        int64_t r = xm - o.run_start + 1;
-        if (r > 0) {
-            o.run_len = (int32_t)r;
-            int64_t xh = floordiv(sc.sg + K - H, u);
-            int64_t rh = min(xh, (int64_t)o.run_start + r - 1) - o.run_start + 1;
-            o.run_hits = rh > 0 ? (int32_t)rh : 0;
-        }
-    }
-}
+using namespace aedev;
 
 // ------------------------------------------------------------------ scan
 
@@ -439,239 +308,6 @@ __global__ void k_seed_fix(Node *nodes, const uint64_t *nn_dev, int64_t N) {
     }
 }
 
-// ------------------------------------------------------------------ trie expansion
-
-// One warp per frontier node; for each letter c the child's SA range and its
-// row.  The count pass sizes every child's output; the write pass recomputes
-// the same row and stores it at the scanned offsets (deterministic layout).
-template <int SIGMA, bool WRITE>
-__global__ void __launch_bounds__(256) k_expand(ExpandArgs a) {
-    __shared__ int8_t smat[AE_MAX_SIGMA * AE_MAX_SIGMA];
-    load_matrix(a.sc, smat);
-    const int lane = threadIdx.x & 31;
-    const int64_t gw = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    const ScoreView &sc = a.sc;
-    const int32_t u = -sc.ss, oe = sc.sg + sc.ss;
-    unsigned long long st_nodes = 0, st_ent = 0, st_t[3] = {0, 0, 0};
-
-    for (int64_t node = gw; node < a.nnodes; node += nw) {
-        const Node nd = a.nodes[node];
-        const WorkItem it = a.items[nd.item];
-        const int qid = it.qid;
-        const int32_t m = a.qv.m[qid], H = a.qv.H[qid];
-        const uint8_t *P = a.qv.codes + a.qv.off[qid];
-        uint32_t clo = 0, chi = 0;
-        if (lane < SIGMA) {
-            clo = a.ix.C[lane] + occ_of<SIGMA>(a.ix, lane, nd.lo);
-            chi = a.ix.C[lane] + occ_of<SIGMA>(a.ix, lane, nd.hi);
-        }
-        const bool root = nd.cnt == AE_ROOT_ROW;
-        const int64_t len = root ? (int64_t)(it.c1 - it.c0) : (int64_t)nd.cnt;
-        if (WRITE) ++st_nodes;
-        for (int c = 0; c < SIGMA; ++c) {
-            const uint32_t lo_c = __shfl_sync(FULL, clo, c), hi_c = __shfl_sync(FULL, chi, c);
-            const int64_t slot = node * SIGMA + c;
-            if (hi_c <= lo_c || len == 0) {
-                if (!WRITE && lane == 0) {
-                    a.c_fr_ent[slot] = 0;
-                    a.c_lf_ent[slot] = 0;
-                    a.c_fr_node[slot] = 0;
-                    a.c_lf_node[slot] = 0;
-                    a.c_hits[slot] = 0;
-                }
-                continue;
-            }
-            const int kind = (hi_c - lo_c >= 2) ? 1 : 2;
-            int32_t *oj = nullptr, *oM = nullptr, *oGa = nullptr;
-            RangeHit *orh = nullptr;
-            if (WRITE) {
-                if (kind == 1) {
-                    uint64_t o = a.o_fr_ent[slot];
-                    oj = a.fj + o; oM = a.fM + o; oGa = a.fGa + o;
-                    orh = a.rhits + a.hit_base + a.o_hits[slot];
-                } else {
-                    uint64_t o = a.lf_ent_base + a.o_lf_ent[slot];
-                    oj = a.lj + o; oM = a.lM + o; oGa = a.lGa + o;
-                }
-            }
-            uint32_t ent_run = 0, hit_run = 0;
-            int32_t carry = AE_KNEG, prev_j = -2, prev_M = AE_NEG;
-            for (int64_t base = 0; base < len; base += 32) {
-                const int64_t idx = base + lane;
-                const bool valid = idx < len;
-                int32_t colA = m, MpA = AE_NEG, GaA = AE_NEG, MpB = AE_NEG, next_col = m;
-                bool hasB = false;
-                int tierA = 0, tierB = 0;
-                int32_t Dprev = AE_NEG, Gap = AE_NEG, Dk = AE_NEG;
-                if (root) {
-                    if (valid) {
-                        colA = it.c0 + (int32_t)idx;
-                        int32_t D = delta_of(sc, smat, c, P[colA]);
-                        int32_t t = thr_of(colA, m, H, sc.gmax);
-                        Dprev = D > t ? D : AE_NEG;
-                        MpA = Dprev;
-                        next_col = (colA + 1 < it.c1) ? colA + 1 : m;
-                    }
-                } else {
-                    int32_t j = m, M = AE_NEG, Ga = AE_NEG;
-                    if (valid) {
-                        j = a.pj[nd.off + idx];
-                        M = a.pM[nd.off + idx];
-                        Ga = a.pGa[nd.off + idx];
-                    }
-                    int32_t jn = __shfl_down_sync(FULL, j, 1);
-                    if (lane == 31 && idx + 1 < len) jn = a.pj[nd.off + idx + 1];
-                    if (idx + 1 >= len) jn = m;
-                    int32_t pjv = __shfl_up_sync(FULL, j, 1), pMv = __shfl_up_sync(FULL, M, 1);
-                    if (lane == 0) {
-                        pjv = prev_j;
-                        pMv = prev_M;
-                    }
-                    if (valid) {
-                        colA = j;
-                        const int32_t tA = thr_of(j, m, H, sc.gmax);
-                        if (pjv + 1 == j && pMv > AE_NEG) {
-                            int32_t D = pMv + delta_of(sc, smat, c, P[j]);
-                            Dprev = D > tA ? D : AE_NEG;
-                        }
-                        int32_t g1 = Ga > AE_NEG ? Ga + sc.ss : AE_NEG;
-                        int32_t g2 = M + oe;
-                        int32_t gap = max(g1, g2);
-                        Gap = gap > tA ? gap : AE_NEG;
-                        MpA = max(Dprev, Gap);
-                        GaA = Gap;
-                        hasB = (j + 1 < m) && (j + 1 != jn);
-                        if (hasB) {
-                            int32_t D = M + delta_of(sc, smat, c, P[j + 1]);
-                            Dk = D > thr_of(j + 1, m, H, sc.gmax) ? D : AE_NEG;
-                            MpB = Dk;
-                        }
-                        next_col = jn;
-                    }
-                    prev_j = __shfl_sync(FULL, j, 31);
-                    prev_M = __shfl_sync(FULL, M, 31);
-                }
-                // horizontal gaps: max-plus scan of keys over the slots
-                int32_t keyA = MpA > AE_NEG ? MpA + colA * u : AE_KNEG;
-                int32_t keyB = MpB > AE_NEG ? MpB + (colA + 1) * u : AE_KNEG;
-                int32_t incl = warp_incl_max(max(keyA, keyB));
-                int32_t excl = __shfl_up_sync(FULL, incl, 1);
-                if (lane == 0) excl = AE_KNEG;
-                incl = max(incl, carry);
-                excl = max(excl, carry);
-                SlotOut o;
-                slot_finish(colA, MpA, hasB, MpB, next_col, excl, incl, sc, m, H, u, valid, o);
-                carry = __shfl_sync(FULL, incl, 31);
-
-                const uint32_t nA = o.aliveA, nB = o.aliveB, nR = (uint32_t)o.run_len;
-                const uint32_t cnt = nA + nB + nR;
-                const uint32_t hA = o.aliveA && o.MA >= H, hB = o.aliveB && o.MB >= H;
-                const uint32_t hcnt = kind == 1 ? (hA + hB + (uint32_t)o.run_hits) : 0u;
-                const uint32_t ci = warp_incl_sum(cnt), hi = warp_incl_sum(hcnt);
-                const uint32_t ctot = __shfl_sync(FULL, ci, 31), htot = __shfl_sync(FULL, hi, 31);
-                if (WRITE) {
-                    const uint32_t e0 = ent_run + ci - cnt, h0 = hit_run + hi - hcnt;
-                    if (o.aliveA) {
-                        oj[e0] = colA;
-                        oM[e0] = o.MA;
-                        oGa[e0] = GaA;
-                        tierA = (Dprev > AE_NEG) + (Gap > AE_NEG) + (o.GbA > thr_of(colA, m, H, sc.gmax));
-                        st_t[max(tierA, 1) - 1]++;
-                    }
-                    if (o.aliveB) {
-                        oj[e0 + nA] = colA + 1;
-                        oM[e0 + nA] = o.MB;
-                        oGa[e0 + nA] = AE_NEG;
-                        tierB = (Dk > AE_NEG) + (o.GbB > thr_of(colA + 1, m, H, sc.gmax));
-                        st_t[max(tierB, 1) - 1]++;
-                    }
-                    st_t[0] += nR;
-                    if (kind == 1) {
-                        uint32_t hp = h0;
-                        if (hA) {
-                            RangeHit r = {lo_c, hi_c, qid, colA, o.MA, 0};
-                            orh[hp++] = r;
-                        }
-                        if (hB) {
-                            RangeHit r = {lo_c, hi_c, qid, colA + 1, o.MB, 0};
-                            orh[hp++] = r;
-                        }
-                    }
-                    unsigned rmask = __ballot_sync(FULL, nR > 0);
-                    while (rmask) {
-                        const int L = __ffs(rmask) - 1;
-                        rmask &= rmask - 1;
-                        const int32_t s0 = __shfl_sync(FULL, o.run_start, L);
-                        const int32_t rl = __shfl_sync(FULL, o.run_len, L);
-                        const int32_t rh = __shfl_sync(FULL, o.run_hits, L);
-                        const int32_t K = __shfl_sync(FULL, incl, L);
-                        const uint32_t d0 = __shfl_sync(FULL, e0 + nA + nB, L);
-                        const uint32_t hd = __shfl_sync(FULL, h0 + hA + hB, L);
-                        for (int32_t t = lane; t < rl; t += 32) {
-                            const int32_t col = s0 + t;
-                            const int32_t v = sc.sg - col * u + K;
-                            oj[d0 + t] = col;
-                            oM[d0 + t] = v;
-                            oGa[d0 + t] = AE_NEG;
-                            if (kind == 1 && t < rh) {
-                                RangeHit r = {lo_c, hi_c, qid, col, v, 0};
-                                orh[hd + t] = r;
-                            }
-                        }
-                    }
-                }
-                ent_run += ctot;
-                hit_run += htot;
-            }
-            if (WRITE) {
-                st_ent += ent_run;
-                if (lane == 0 && ent_run > 0) {
-                    if (kind == 1) {
-                        Node cn;
-                        cn.lo = lo_c;
-                        cn.hi = hi_c;
-                        cn.item = nd.item;
-                        cn.cnt = ent_run;
-                        cn.off = a.o_fr_ent[slot];
-                        a.fnodes[a.o_fr_node[slot]] = cn;
-                    } else {
-                        Inject in;
-                        in.qid = qid;
-                        in.e = a.ix.tend[lo_c];
-                        in.cnt = ent_run;
-                        in.pad = 0;
-                        in.off = a.lf_ent_base + a.o_lf_ent[slot];
-                        a.inj[a.lf_node_base + a.o_lf_node[slot]] = in;
-                    }
-                }
-            } else if (lane == 0) {
-                a.c_fr_ent[slot] = kind == 1 ? ent_run : 0u;
-                a.c_lf_ent[slot] = kind == 2 ? ent_run : 0u;
-                a.c_fr_node[slot] = (kind == 1 && ent_run > 0) ? 1u : 0u;
-                a.c_lf_node[slot] = (kind == 2 && ent_run > 0) ? 1u : 0u;
-                a.c_hits[slot] = hit_run;
-            }
-        }
-    }
-    if (WRITE && a.stats) {
-        // per-lane tier counts, lane 0 holds node/entry counts (warp-uniform)
-        unsigned long long t0 = st_t[0], t1 = st_t[1], t2 = st_t[2];
-        for (int d = 16; d > 0; d >>= 1) {
-            t0 += __shfl_down_sync(FULL, t0, d);
-            t1 += __shfl_down_sync(FULL, t1, d);
-            t2 += __shfl_down_sync(FULL, t2, d);
-        }
-        if (lane == 0) {
-            if (st_nodes) atomicAdd(&a.stats->nodes, st_nodes);
-            if (st_ent) atomicAdd(&a.stats->entries, st_ent);
-            if (t0) atomicAdd(&a.stats->tier[0], t0);
-            if (t1) atomicAdd(&a.stats->tier[1], t1);
-            if (t2) atomicAdd(&a.stats->tier[2], t2);
-        }
-    }
-}
-
 // ------------------------------------------------------------------ text-position sweep
 
 __global__ void k_inject_keys(const Inject *inj, int64_t ninj, uint64_t *keys, uint32_t *vals) {
@@ -739,8 +375,184 @@ __global__ void __launch_bounds__(128) k_leaf(LeafArgs a) {
         int64_t rlen = 0;
         int32_t p = -1, qid = -1, m = 0, H = 0;
         const uint8_t *P = nullptr;
+        unsigned long long seg_steps = 0, seg_width = 0;
+        // R lives in registers (lane i holds entry i) while it has <= 32 entries
+        bool inreg = false;
+        int32_t rj = 0, rM = AE_NEG, rGa = AE_NEG;
         while (true) {
             int64_t clen = 0;
+            if (rlen > 0 && inreg && p + 1 < a.ix.n) {
+                bool inj_next = false;
+                if (k < kend) {
+                    const Inject In = a.inj[a.order[k]];
+                    inj_next = In.qid == qid && In.e == p + 1;
+                }
+                if (!inj_next) {
+                    // ---- fast step: gen + horizontal finish in registers
+                    ++p;
+                    const int c = a.ix.text[p];
+                    const bool valid = lane < rlen;
+                    int32_t j = valid ? rj : m, M = valid ? rM : AE_NEG, Ga = valid ? rGa : AE_NEG;
+                    int32_t jn = __shfl_down_sync(FULL, j, 1);
+                    if (lane + 1 >= rlen) jn = m;
+                    int32_t pjv = __shfl_up_sync(FULL, j, 1), pMv = __shfl_up_sync(FULL, M, 1);
+                    if (lane == 0) {
+                        pjv = -2;
+                        pMv = AE_NEG;
+                    }
+                    int32_t colA = m, MpA = AE_NEG, GaA = AE_NEG, MpB = AE_NEG, next_col = m;
+                    int32_t Dp = AE_NEG, Dk = AE_NEG;
+                    bool hasB = false;
+                    if (valid) {
+                        colA = j;
+                        const int32_t tA = thr_of(j, m, H, g);
+                        if (pjv + 1 == j && pMv > AE_NEG) {
+                            const int32_t D = pMv + delta_of(sc, smat, c, P[j]);
+                            Dp = D > tA ? D : AE_NEG;
+                        }
+                        const int32_t gap = max(Ga > AE_NEG ? Ga + sc.ss : AE_NEG, M + oe);
+                        GaA = gap > tA ? gap : AE_NEG;
+                        MpA = max(Dp, GaA);
+                        hasB = (j + 1 < m) && (j + 1 != jn);
+                        if (hasB) {
+                            const int32_t D = M + delta_of(sc, smat, c, P[j + 1]);
+                            Dk = D > thr_of(j + 1, m, H, g) ? D : AE_NEG;
+                            MpB = Dk;
+                        }
+                        next_col = jn;
+                    }
+                    const int32_t keyA = MpA > AE_NEG ? MpA + colA * u : AE_KNEG;
+                    const int32_t keyB = MpB > AE_NEG ? MpB + (colA + 1) * u : AE_KNEG;
+                    const int32_t incl = warp_incl_max(max(keyA, keyB));
+                    int32_t excl = __shfl_up_sync(FULL, incl, 1);
+                    if (lane == 0) excl = AE_KNEG;
+                    SlotOut o;
+                    slot_finish(colA, MpA, hasB, MpB, next_col, excl, incl, sc, m, H, u, valid, o);
+                    const uint32_t nA = o.aliveA, nB = o.aliveB, nR = (uint32_t)o.run_len;
+                    const uint32_t cn = nA + nB + nR;
+                    const uint32_t ci = warp_incl_sum(cn);
+                    const uint32_t tot = __shfl_sync(FULL, ci, 31);
+                    // hits
+                    const uint32_t hA = o.aliveA && o.MA >= H, hB = o.aliveB && o.MB >= H;
+                    const uint32_t hc = hA + hB + (uint32_t)o.run_hits;
+                    const uint32_t hi = warp_incl_sum(hc);
+                    const uint32_t htot = __shfl_sync(FULL, hi, 31);
+                    unsigned long long hbase = 0;
+                    if (htot) {
+                        if (lane == 0) hbase = atomicAdd(a.hit_count, (unsigned long long)htot);
+                        hbase = __shfl_sync(FULL, hbase, 0);
+                    }
+                    const bool hok = hbase + htot <= a.hit_cap;
+                    const uint64_t kq = ((uint64_t)qid << (a.be + a.bj)) | ((uint64_t)(uint32_t)p << a.bj);
+                    const uint64_t h0 = hbase + hi - hc;
+                    if (hok) {
+                        if (hA) {
+                            a.hit_key[h0] = kq | ((uint64_t)colA & jmask);
+                            a.hit_score[h0] = o.MA;
+                        }
+                        if (hB) {
+                            a.hit_key[h0 + hA] = kq | ((uint64_t)(colA + 1) & jmask);
+                            a.hit_score[h0 + hA] = o.MB;
+                        }
+                    } else if (htot && lane == 0) {
+                        atomicAdd(&a.stats->hit_overflow, 1ull);
+                    }
+                    if (o.aliveA) {
+                        const int tier = (Dp > AE_NEG) + (GaA > AE_NEG) + (o.GbA > thr_of(colA, m, H, g));
+                        st_t[min(max(tier, 1), 3) - 1]++;
+                    }
+                    if (o.aliveB) st_t[((Dk > AE_NEG) && (o.GbB > thr_of(colA + 1, m, H, g))) ? 1 : 0]++;
+                    st_t[0] += nR;
+                    const int64_t e0 = (int64_t)(ci - cn);
+                    if (tot > cap) {
+                        overflow = true;
+                        break;
+                    }
+                    // run hits and (for rows wider than a warp) run entries, cooperatively
+                    unsigned rmask = __ballot_sync(FULL, nR > 0);
+                    const bool spill = tot > 32;
+                    while (rmask) {
+                        const int L = __ffs(rmask) - 1;
+                        rmask &= rmask - 1;
+                        const int32_t s0 = __shfl_sync(FULL, o.run_start, L);
+                        const int32_t rl = __shfl_sync(FULL, o.run_len, L);
+                        const int32_t rh = __shfl_sync(FULL, o.run_hits, L);
+                        const int32_t K = __shfl_sync(FULL, incl, L);
+                        const int64_t d0 = __shfl_sync(FULL, e0 + nA + nB, L);
+                        const uint64_t hd = __shfl_sync(FULL, h0 + hA + hB, L);
+                        for (int32_t t = lane; t < rl; t += 32) {
+                            const int32_t cc = s0 + t;
+                            const int32_t v = sc.sg - cc * u + K;
+                            if (spill) {
+                                R.j[d0 + t] = cc;
+                                R.M[d0 + t] = v;
+                                R.Ga[d0 + t] = AE_NEG;
+                            }
+                            if (t < rh && hok) {
+                                a.hit_key[hd + t] = kq | ((uint64_t)cc & jmask);
+                                a.hit_score[hd + t] = v;
+                            }
+                        }
+                    }
+                    if (spill) {
+                        if (o.aliveA) {
+                            R.j[e0] = colA;
+                            R.M[e0] = o.MA;
+                            R.Ga[e0] = GaA;
+                        }
+                        if (o.aliveB) {
+                            R.j[e0 + nA] = colA + 1;
+                            R.M[e0 + nA] = o.MB;
+                            R.Ga[e0 + nA] = AE_NEG;
+                        }
+                        inreg = false;
+                    } else {
+                        // output lane <- the lane whose slots/run produced output number `lane`
+                        int s = 0;
+#pragma unroll
+                        for (int step = 16; step > 0; step >>= 1) {
+                            const uint32_t v = __shfl_sync(FULL, ci, s + step - 1);
+                            if (v <= (uint32_t)lane) s += step;
+                        }
+                        const uint32_t ex_s = __shfl_sync(FULL, ci - cn, s);
+                        const uint32_t nA_s = __shfl_sync(FULL, nA, s), nB_s = __shfl_sync(FULL, nB, s);
+                        const int32_t col_s = __shfl_sync(FULL, colA, s), MA_s = __shfl_sync(FULL, o.MA, s);
+                        const int32_t GaA_s = __shfl_sync(FULL, GaA, s), MB_s = __shfl_sync(FULL, o.MB, s);
+                        const int32_t rs_s = __shfl_sync(FULL, o.run_start, s), K_s = __shfl_sync(FULL, incl, s);
+                        const uint32_t r = (uint32_t)lane - ex_s;
+                        if ((uint32_t)lane < tot) {
+                            if (r < nA_s) {
+                                rj = col_s;
+                                rM = MA_s;
+                                rGa = GaA_s;
+                            } else if (r < nA_s + nB_s) {
+                                rj = col_s + 1;
+                                rM = MB_s;
+                                rGa = AE_NEG;
+                            } else {
+                                rj = rs_s + (int32_t)(r - nA_s - nB_s);
+                                rM = sc.sg - rj * u + K_s;
+                                rGa = AE_NEG;
+                            }
+                        }
+                    }
+                    __syncwarp();
+                    rlen = tot;
+                    ++st_rows;
+                    ++seg_steps;
+                    st_ent += (unsigned long long)tot;
+                    continue;
+                }
+            }
+            if (inreg && rlen > 0) {   // the slow path reads R from scratch
+                if (lane < rlen) {
+                    R.j[lane] = rj;
+                    R.M[lane] = rM;
+                    R.Ga[lane] = rGa;
+                }
+                __syncwarp();
+            }
+            inreg = false;
             if (rlen == 0) {
                 if (k >= kend) break;
                 const Inject I0 = a.inj[a.order[k]];
@@ -967,9 +779,23 @@ __global__ void __launch_bounds__(128) k_leaf(LeafArgs a) {
             Rn = t;
             rlen = nlen;
             ++st_rows;
+            ++seg_steps;
+            seg_width = max(seg_width, (unsigned long long)nlen);
             st_ent += (unsigned long long)nlen;
+            if (rlen <= 32) {
+                if (lane < rlen) {
+                    rj = R.j[lane];
+                    rM = R.M[lane];
+                    rGa = R.Ga[lane];
+                }
+                inreg = true;
+            }
         }
         if (overflow && lane == 0) atomicAdd(&a.stats->leaf_overflow, 1ull);
+        if (lane == 0) {
+            atomicMax(&a.stats->leaf_max_steps, seg_steps);
+            atomicMax(&a.stats->leaf_max_width, seg_width);
+        }
     }
     unsigned long long t0 = st_t[0], t1 = st_t[1], t2 = st_t[2];
     for (int d = 16; d > 0; d >>= 1) {
@@ -1032,6 +858,18 @@ __global__ void k_unique_write(const uint64_t *key, const int32_t *score, int64_
         h.score = best;
         out[off[t]] = h;
         atomicAdd(&qcount[k >> (be + bj)], 1ull);
+    }
+}
+
+__global__ void k_unique_compact(const uint64_t *key, const int32_t *score, int64_t N, const uint64_t *off,
+                                 uint64_t *okey, int32_t *oscore) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t k = key[t];
+        if (t > 0 && key[t - 1] == k) continue;
+        int32_t best = score[t];
+        for (int64_t u = t + 1; u < N && key[u] == k; ++u) best = max(best, score[u]);
+        okey[off[t]] = k;
+        oscore[off[t]] = best;
     }
 }
 
@@ -1135,19 +973,6 @@ void ae_seed_nodes(const SeedArgs &a, const uint64_t *keys, const uint32_t *vals
     k_seed_fix<<<grid_for(npos, 256), 256, 0, st>>>(nodes, nnodes_dev, npos);
 }
 
-void ae_expand(const ExpandArgs &a, bool write, cudaStream_t st) {
-    if (a.nnodes <= 0) return;
-    const int threads = 256;
-    const unsigned blocks = grid_for(a.nnodes * 32, threads, 152 * 16);
-    if (a.ix.sigma == 4) {
-        if (write) { ++g_launches; k_expand<4, true><<<blocks, threads, 0, st>>>(a); }
-        else { ++g_launches; k_expand<4, false><<<blocks, threads, 0, st>>>(a); }
-    } else {
-        if (write) { ++g_launches; k_expand<20, true><<<blocks, threads, 0, st>>>(a); }
-        else { ++g_launches; k_expand<20, false><<<blocks, threads, 0, st>>>(a); }
-    }
-}
-
 void ae_inject_keys(const Inject *inj, int64_t ninj, uint64_t *keys, uint32_t *vals, cudaStream_t st) {
     if (ninj <= 0) return;
     ++g_launches;
@@ -1179,6 +1004,13 @@ void ae_unique_flags(const uint64_t *key, int64_t N, uint32_t *flags, cudaStream
     if (N <= 0) return;
     ++g_launches;
     k_unique_flags<<<grid_for(N, 256), 256, 0, st>>>(key, N, flags);
+}
+
+void ae_unique_compact(const uint64_t *key, const int32_t *score, int64_t N, const uint64_t *flag_off, uint64_t *okey,
+                       int32_t *oscore, cudaStream_t st) {
+    if (N <= 0) return;
+    ++g_launches;
+    k_unique_compact<<<grid_for(N, 256), 256, 0, st>>>(key, score, N, flag_off, okey, oscore);
 }
 
 void ae_unique_write(const uint64_t *key, const int32_t *score, int64_t N, const uint64_t *flag_off, int be, int bj,

@@ -7,6 +7,7 @@
 
 // Number of kernel launches issued so far by the calling thread.
 int64_t ae_launches_read();
+extern thread_local int64_t g_launches;
 
 // Exclusive scans of W u32 arrays of length N into u64 arrays; totals[w]
 // (device, W entries) receives the sums.  tmp must hold scan_tmp_words(N, W)
@@ -44,28 +45,60 @@ void ae_seed_nodes(const SeedArgs &a, const uint64_t *keys, const uint32_t *vals
                    uint32_t *flags, uint64_t *flag_off, uint64_t *tmp, Node *nodes, int32_t *aj, int32_t *aM,
                    int32_t *aGa, uint64_t *nnodes_dev, cudaStream_t st);
 
-struct ExpandArgs {
+// ---- one trie level (ae_trie.cu)
+struct ChildrenArgs {
+    IndexView ix;
+    const WorkItem *items;
+    const Node *nodes;
+    int64_t nnodes;
+    uint32_t *clo, *chi, *flag, *len;     // nnodes * sigma each
+    DevStats *stats;
+};
+void ae_children(const ChildrenArgs &a, cudaStream_t st);
+
+// A non-empty child with everything its row computation needs (so a lane
+// reads one record instead of following node -> item -> query pointers):
+// SA range, letter, row length (= parent entries), first triple, parent row
+// offset (root rows: the work item's columns), query id, length, threshold
+// and letter offset.
+struct Seg {
+    uint32_t lo, hi;
+    uint32_t len, c;
+    uint64_t toff;
+    uint64_t poff;
+    int32_t qid, m, H, item;
+    int64_t qoff;
+    int32_t c0, c1;     // c0 < 0: a regular row; else the implicit root row over [c0, c1)
+};
+void ae_compact_segs(const uint32_t *clo, const uint32_t *chi, const uint32_t *flag, const uint32_t *len,
+                     const uint64_t *fpos, const uint64_t *toff, int64_t N, int sigma, const Node *nodes,
+                     const WorkItem *items, QueryView qv, Seg *segs, cudaStream_t st);
+
+struct LevelCounters {
+    unsigned long long fr_ent, fr_node, lf_ent, lf_node, hits, overflow, task, pad;
+};
+
+struct RowsArgs {
     IndexView ix;
     ScoreView sc;
     QueryView qv;
     const WorkItem *items;
     const Node *nodes;
-    int64_t nnodes;
-    const int32_t *pj, *pM, *pGa;          // parent arena
-    // count pass outputs (nnodes * sigma each)
-    uint32_t *c_fr_ent, *c_lf_ent, *c_fr_node, *c_lf_node, *c_hits;
-    // write pass inputs: scanned offsets
-    const uint64_t *o_fr_ent, *o_lf_ent, *o_fr_node, *o_lf_node, *o_hits;
-    uint64_t lf_ent_base, lf_node_base, hit_base;
-    // write pass outputs
-    int32_t *fj, *fM, *fGa;                // next-level arena
-    Node *fnodes;                          // next-level nodes
-    int32_t *lj, *lM, *lGa;                // leaf arena
+    const int32_t *pj, *pM, *pGa;         // parent arena
+    const Seg *segs;
+    const uint64_t *nseg_dev, *ntrip_dev; // scan totals (device)
+    int32_t *fj, *fM, *fGa;               // next-level arena
+    Node *fnodes;
+    uint64_t fr_ent_cap, fr_node_cap;
+    int32_t *lj, *lM, *lGa;               // leaf arena (accumulates over levels)
     Inject *inj;
+    uint64_t lf_ent_cap, lf_node_cap;
     RangeHit *rhits;
+    uint64_t hit_cap;
+    LevelCounters *ctr;
     DevStats *stats;
 };
-void ae_expand(const ExpandArgs &a, bool write, cudaStream_t st);
+void ae_rows(const RowsArgs &a, int blocks, cudaStream_t st);
 
 struct LeafArgs {
     IndexView ix;
@@ -99,5 +132,7 @@ void ae_locate(const RangeHit *rh, int64_t nrh, const uint64_t *off, int64_t tot
 
 // Sorted (key, score) -> unique keys with max score.
 void ae_unique_flags(const uint64_t *key, int64_t N, uint32_t *flags, cudaStream_t st);
+void ae_unique_compact(const uint64_t *key, const int32_t *score, int64_t N, const uint64_t *flag_off, uint64_t *okey,
+                       int32_t *oscore, cudaStream_t st);
 void ae_unique_write(const uint64_t *key, const int32_t *score, int64_t N, const uint64_t *flag_off, int be,
                      int bj, ae_hit *out, unsigned long long *qcount, cudaStream_t st);

@@ -1,0 +1,505 @@
+// One level of the breadth-wise suffix-trie walk (Section 5 (3)) with the
+// Gotoh rows of Section 2.2, on sm_103a.
+//
+//   k_children   every (node, letter c) pair: the child's SA range by one
+//                backward-search step, lo' = C[c] + Occ(c, lo), hi' = C[c] +
+//                Occ(c, hi); a non-empty child inherits its parent's row length
+//                as the number of "triples" (child, parent entry) to compute.
+//   scan+compact the non-empty children become segments laid end to end.
+//   k_rows       the triples are packed densely into warp lanes (many small
+//                rows share one warp); horizontal gaps use segmented max-plus
+//                scans.  Each warp task counts its outputs, reserves space with
+//                one atomic per arena, then recomputes and writes them.
+//
+// Children with one occurrence leave the trie: their rows go to the leaf
+// arena as injections for the text-position sweep.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ae_device.cuh"
+#include "ae_kernels.h"
+
+namespace {
+using namespace aedev;
+
+template <int SIGMA>
+__global__ void k_children(ChildrenArgs a) {
+    const int64_t N = a.nnodes * SIGMA;
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t v = t / SIGMA;
+        const int c = (int)(t - v * SIGMA);
+        const Node nd = a.nodes[v];
+        const uint32_t lo = a.ix.C[c] + occ_of<SIGMA>(a.ix, c, nd.lo);
+        const uint32_t hi = a.ix.C[c] + occ_of<SIGMA>(a.ix, c, nd.hi);
+        uint32_t len = 0;
+        if (hi > lo) {
+            if (nd.cnt == AE_ROOT_ROW) {
+                const WorkItem it = a.items[nd.item];
+                len = (uint32_t)(it.c1 - it.c0);
+            } else {
+                len = nd.cnt;
+            }
+        }
+        a.clo[t] = lo;
+        a.chi[t] = hi;
+        a.len[t] = len;
+        a.flag[t] = len > 0 ? 1u : 0u;
+    }
+    if (a.stats && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&a.stats->nodes, (unsigned long long)a.nnodes);
+}
+
+template <int SIGMA>
+__global__ void k_compact(const uint32_t *clo, const uint32_t *chi, const uint32_t *flag, const uint32_t *len,
+                          const uint64_t *fpos, const uint64_t *toff, int64_t N, const Node *nodes,
+                          const WorkItem *items, QueryView qv, Seg *segs) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
+        if (!flag[t]) continue;
+        const Node nd = nodes[t / SIGMA];
+        const WorkItem it = items[nd.item];
+        Seg s;
+        s.lo = clo[t];
+        s.hi = chi[t];
+        s.len = len[t];
+        s.c = (uint32_t)(t % SIGMA);
+        s.toff = toff[t];
+        s.poff = nd.cnt == AE_ROOT_ROW ? 0 : nd.off;
+        s.qid = it.qid;
+        s.m = qv.m[it.qid];
+        s.H = qv.H[it.qid];
+        s.item = nd.item;
+        s.qoff = qv.off[it.qid];
+        s.c0 = nd.cnt == AE_ROOT_ROW ? it.c0 : -1;
+        s.c1 = it.c1;
+        segs[fpos[t]] = s;
+    }
+}
+
+constexpr int RW_WARPS = 8;
+constexpr int RW_TASK = 128;   // triples per task window = max segments per task
+
+struct TaskSmem {
+    uint32_t cnt[RW_TASK];
+    uint32_t hit[RW_TASK];
+    uint64_t base[RW_TASK];
+    uint64_t hbase[RW_TASK];
+};
+
+__device__ __forceinline__ uint64_t lower_bound_toff(const Seg *segs, uint64_t n, uint64_t t) {
+    uint64_t lo = 0, hi = n;
+    while (lo < hi) {
+        uint64_t mid = (lo + hi) >> 1;
+        if (segs[mid].toff < t) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+// Process the triples [t_beg, t_end) of one task, whose segments are
+// [s_first, s_last).  Pass 1 (WRITE = false) adds each segment's output and
+// hit counts into sm; pass 2 writes entries and hits at sm.base/hbase plus
+// the running counts.
+template <int SIGMA, bool WRITE>
+__device__ void run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, uint64_t s_first, uint64_t s_last,
+                         uint64_t t_beg, uint64_t t_end, unsigned long long &st0, unsigned long long &st1,
+                         unsigned long long &st2) {
+    const int lane = threadIdx.x & 31;
+    const unsigned le = (lane == 31) ? 0xffffffffu : ((1u << (lane + 1)) - 1u);
+    const ScoreView &sc = a.sc;
+    const int32_t u = -sc.ss, oe = sc.sg + sc.ss, g = sc.gmax;
+    uint64_t sbase = s_first;
+    int32_t carry = AE_KNEG;
+    for (uint64_t t0 = t_beg; t0 < t_end; t0 += 32) {
+        const uint64_t t = t0 + lane;
+        const bool valid = t < t_end;
+        const uint64_t woff = (sbase + lane < s_last) ? a.segs[sbase + lane].toff : ~0ull;
+        int i = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const uint64_t o = __shfl_sync(FULL, woff, i + step);
+            if (o <= t) i += step;
+        }
+        const uint64_t sid = sbase + i;
+        Seg sg;
+        sg.len = 0;
+        sg.toff = 0;
+        sg.poff = 0;
+        sg.lo = sg.hi = 0;
+        sg.c = 0;
+        sg.qid = 0;
+        sg.m = 1;
+        sg.H = 1;
+        sg.qoff = 0;
+        sg.c0 = -1;
+        sg.c1 = 0;
+        if (valid) sg = a.segs[sid];
+        const int64_t k = valid ? (int64_t)(t - sg.toff) : 0;
+        const int32_t m = sg.m, H = sg.H;
+        const uint8_t *P = a.qv.codes + sg.qoff;
+        const int c = (int)sg.c;
+        const bool root = sg.c0 >= 0;
+        // ---- slots of this lane (see slot_finish)
+        int32_t colA = m, MpA = AE_NEG, GaA = AE_NEG, MpB = AE_NEG, next_col = m;
+        int32_t Dprev = AE_NEG, Gap = AE_NEG, Dk = AE_NEG;
+        bool hasB = false;
+        const unsigned heads = __ballot_sync(FULL, !valid || k == 0 || lane == 0);
+        const int first_lane = 31 - __clz(heads & le);
+        // neighbours inside the segment
+        int32_t j = m, M = AE_NEG, Ga = AE_NEG;
+        if (valid && !root) {
+            j = a.pj[sg.poff + k];
+            M = a.pM[sg.poff + k];
+            Ga = a.pGa[sg.poff + k];
+        }
+        int32_t jn = __shfl_down_sync(FULL, j, 1);
+        int32_t pjv = __shfl_up_sync(FULL, j, 1), pMv = __shfl_up_sync(FULL, M, 1);
+        if (valid && !root) {
+            const bool next_in = (lane < 31) && (((heads >> (lane + 1)) & 1u) == 0);
+            if (!next_in) jn = (k + 1 < (int64_t)sg.len) ? a.pj[sg.poff + k + 1] : m;
+            if (lane == first_lane) {   // first lane of its segment in this chunk
+                if (k > 0) {
+                    pjv = a.pj[sg.poff + k - 1];
+                    pMv = a.pM[sg.poff + k - 1];
+                } else {
+                    pjv = -2;
+                    pMv = AE_NEG;
+                }
+            }
+        }
+        if (valid) {
+            if (root) {
+                colA = sg.c0 + (int32_t)k;
+                const int32_t D = delta_of(sc, smat, c, P[colA]);
+                Dprev = D > thr_of(colA, m, H, g) ? D : AE_NEG;
+                MpA = Dprev;
+                next_col = (colA + 1 < sg.c1) ? colA + 1 : m;
+            } else {
+                colA = j;
+                const int32_t tA = thr_of(j, m, H, g);
+                if (pjv + 1 == j && pMv > AE_NEG) {
+                    const int32_t D = pMv + delta_of(sc, smat, c, P[j]);
+                    Dprev = D > tA ? D : AE_NEG;
+                }
+                const int32_t gap = max(Ga > AE_NEG ? Ga + sc.ss : AE_NEG, M + oe);
+                Gap = gap > tA ? gap : AE_NEG;
+                MpA = max(Dprev, Gap);
+                GaA = Gap;
+                hasB = (j + 1 < m) && (j + 1 != jn);
+                if (hasB) {
+                    const int32_t D = M + delta_of(sc, smat, c, P[j + 1]);
+                    Dk = D > thr_of(j + 1, m, H, g) ? D : AE_NEG;
+                    MpB = Dk;
+                }
+                next_col = jn;
+            }
+        }
+        // ---- segmented max-plus scan of the keys M'(k) + k*u
+        const int32_t keyA = MpA > AE_NEG ? MpA + colA * u : AE_KNEG;
+        const int32_t keyB = MpB > AE_NEG ? MpB + (colA + 1) * u : AE_KNEG;
+        int32_t incl = max(keyA, keyB);
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int32_t o = __shfl_up_sync(FULL, incl, d);
+            if (lane - d >= first_lane) incl = max(incl, o);
+        }
+        const int64_t k0 = __shfl_sync(FULL, k, 0);
+        const bool cont = (first_lane == 0) && valid && k0 > 0;   // segment continues from the last chunk
+        if (cont) incl = max(incl, carry);
+        int32_t excl = __shfl_up_sync(FULL, incl, 1);
+        if (lane - 1 < first_lane) excl = cont ? carry : AE_KNEG;
+        SlotOut o;
+        slot_finish(colA, MpA, hasB, MpB, next_col, excl, incl, sc, m, H, u, valid, o);
+        {
+            const int64_t k31 = __shfl_sync(FULL, k, 31);
+            const bool v31 = __shfl_sync(FULL, valid, 31);
+            const uint32_t len31 = __shfl_sync(FULL, sg.len, 31);
+            const int32_t inc31 = __shfl_sync(FULL, incl, 31);
+            const bool goes_on = v31 && (k31 + 1 < (int64_t)len31);
+            carry = goes_on ? inc31 : AE_KNEG;
+            const uint64_t sid31 = __shfl_sync(FULL, sid, 31);
+            sbase = goes_on ? sid31 : sid31 + 1;
+        }
+
+        // ---- counts, segmented sums
+        const bool kind1 = valid && (sg.hi - sg.lo >= 2);
+        const uint32_t nA = o.aliveA, nB = o.aliveB, nR = (uint32_t)o.run_len;
+        const uint32_t cnt = nA + nB + nR;
+        const uint32_t hA = o.aliveA && o.MA >= H, hB = o.aliveB && o.MB >= H;
+        const uint32_t hcnt = kind1 ? (hA + hB + (uint32_t)o.run_hits) : 0u;
+        uint32_t ci = cnt, hi = hcnt;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t oc = __shfl_up_sync(FULL, ci, d), oh = __shfl_up_sync(FULL, hi, d);
+            if (lane - d >= first_lane) {
+                ci += oc;
+                hi += oh;
+            }
+        }
+        const bool is_last = valid && (lane == 31 || ((heads >> (lane + 1)) & 1u));
+        const uint64_t rel = sid - s_first;
+        if (!WRITE) {
+            if (is_last) {
+                sm.cnt[rel] += ci;
+                sm.hit[rel] += hi;
+            }
+            __syncwarp();
+            continue;
+        }
+        // ---- write entries (and hits of multi-occurrence children)
+        const bool overflow_task = false;
+        (void)overflow_task;
+        uint64_t e0 = 0, h0 = 0;
+        int32_t *oj = nullptr, *oM = nullptr, *oGa = nullptr;
+        if (valid) {
+            e0 = sm.base[rel] + sm.cnt[rel] + (ci - cnt);
+            h0 = sm.hbase[rel] + sm.hit[rel] + (hi - hcnt);
+            if (kind1) {
+                oj = a.fj;
+                oM = a.fM;
+                oGa = a.fGa;
+            } else {
+                oj = a.lj;
+                oM = a.lM;
+                oGa = a.lGa;
+            }
+        }
+        __syncwarp();
+        if (is_last) {
+            sm.cnt[rel] += ci;
+            sm.hit[rel] += hi;
+        }
+        if (o.aliveA) {
+            oj[e0] = colA;
+            oM[e0] = o.MA;
+            oGa[e0] = GaA;
+            const int tier = (Dprev > AE_NEG) + (Gap > AE_NEG) + (o.GbA > thr_of(colA, m, H, g));
+            st0 += tier <= 1;
+            st1 += tier == 2;
+            st2 += tier == 3;
+        }
+        if (o.aliveB) {
+            oj[e0 + nA] = colA + 1;
+            oM[e0 + nA] = o.MB;
+            oGa[e0 + nA] = AE_NEG;
+            const int tier = (Dk > AE_NEG) + (o.GbB > thr_of(colA + 1, m, H, g));
+            st0 += tier <= 1;
+            st1 += tier == 2;
+        }
+        st0 += nR;
+        if (kind1) {
+            uint64_t hp = h0;
+            if (hA) {
+                RangeHit r = {sg.lo, sg.hi, sg.qid, colA, o.MA, 0};
+                a.rhits[hp++] = r;
+            }
+            if (hB) {
+                RangeHit r = {sg.lo, sg.hi, sg.qid, colA + 1, o.MB, 0};
+                a.rhits[hp++] = r;
+            }
+        }
+        unsigned rmask = __ballot_sync(FULL, nR > 0);
+        while (rmask) {
+            const int L = __ffs(rmask) - 1;
+            rmask &= rmask - 1;
+            const int32_t s0 = __shfl_sync(FULL, o.run_start, L);
+            const int32_t rl = __shfl_sync(FULL, o.run_len, L);
+            const int32_t rh = __shfl_sync(FULL, o.run_hits, L);
+            const int32_t K = __shfl_sync(FULL, incl, L);
+            const uint64_t d0 = __shfl_sync(FULL, e0 + nA + nB, L);
+            const uint64_t hd = __shfl_sync(FULL, h0 + hA + hB, L);
+            const bool k1 = __shfl_sync(FULL, kind1, L);
+            int32_t *rj = (int32_t *)__shfl_sync(FULL, (unsigned long long)oj, L);
+            int32_t *rM = (int32_t *)__shfl_sync(FULL, (unsigned long long)oM, L);
+            int32_t *rG = (int32_t *)__shfl_sync(FULL, (unsigned long long)oGa, L);
+            const uint32_t rlo = __shfl_sync(FULL, sg.lo, L), rhi = __shfl_sync(FULL, sg.hi, L);
+            const int32_t rq = __shfl_sync(FULL, sg.qid, L);
+            for (int32_t tt = lane; tt < rl; tt += 32) {
+                const int32_t col = s0 + tt;
+                const int32_t v = sc.sg - col * u + K;
+                rj[d0 + tt] = col;
+                rM[d0 + tt] = v;
+                rG[d0 + tt] = AE_NEG;
+                if (k1 && tt < rh) {
+                    RangeHit r = {rlo, rhi, rq, col, v, 0};
+                    a.rhits[hd + tt] = r;
+                }
+            }
+        }
+        __syncwarp();
+    }
+}
+
+template <int SIGMA>
+__global__ void __launch_bounds__(RW_WARPS * 32, 4) k_rows(RowsArgs a) {
+    __shared__ int8_t smat[AE_MAX_SIGMA * AE_MAX_SIGMA];
+    __shared__ TaskSmem smem[RW_WARPS];
+    load_matrix(a.sc, smat);
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    TaskSmem &sm = smem[wib];
+    const uint64_t S = *a.nseg_dev, T = *a.ntrip_dev;
+    const uint64_t W = RW_TASK;
+    const uint64_t ntask = (T + W - 1) / W;
+    unsigned long long st0 = 0, st1 = 0, st2 = 0;
+    unsigned long long st_ent = 0;
+    while (true) {
+        unsigned long long task = 0;
+        if (lane == 0) task = atomicAdd(&a.ctr->task, 1ull);
+        task = __shfl_sync(FULL, task, 0);
+        if (task >= ntask) break;
+        const uint64_t w_lo = task * W, w_hi = min(T, w_lo + W);
+        uint64_t s_first = 0, s_last = 0;
+        if (lane == 0) {
+            s_first = lower_bound_toff(a.segs, S, w_lo);
+            s_last = lower_bound_toff(a.segs, S, w_hi);
+        }
+        s_first = __shfl_sync(FULL, s_first, 0);
+        s_last = __shfl_sync(FULL, s_last, 0);
+        if (s_first >= s_last) continue;
+        const uint64_t nsg = s_last - s_first;
+        const Seg lastseg = a.segs[s_last - 1];
+        const uint64_t t_beg = a.segs[s_first].toff, t_end = lastseg.toff + lastseg.len;
+        for (uint64_t r = lane; r < nsg; r += 32) {
+            sm.cnt[r] = 0;
+            sm.hit[r] = 0;
+        }
+        __syncwarp();
+        run_task<SIGMA, false>(a, smat, sm, s_first, s_last, t_beg, t_end, st0, st1, st2);
+        __syncwarp();
+        // ---- exclusive prefixes per kind, one reservation per arena
+        uint64_t acc[5] = {0, 0, 0, 0, 0};   // fr_ent, lf_ent, fr_node, lf_node, hits
+        for (uint64_t r0 = 0; r0 < nsg; r0 += 32) {
+            const uint64_t r = r0 + lane;
+            uint32_t v[5] = {0, 0, 0, 0, 0};
+            if (r < nsg) {
+                const Seg sg = a.segs[s_first + r];
+                const bool k1 = sg.hi - sg.lo >= 2;
+                const uint32_t cn = sm.cnt[r];
+                v[0] = k1 ? cn : 0u;
+                v[1] = k1 ? 0u : cn;
+                v[2] = (k1 && cn) ? 1u : 0u;
+                v[3] = (!k1 && cn) ? 1u : 0u;
+                v[4] = sm.hit[r];
+            }
+            uint64_t ex[5];
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                uint64_t x = v[q];
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const uint64_t y = __shfl_up_sync(FULL, x, d);
+                    if (lane >= d) x += y;
+                }
+                ex[q] = acc[q] + x - v[q];
+                acc[q] += __shfl_sync(FULL, x, 31);
+            }
+            if (r < nsg) {
+                // temporarily keep the in-task prefixes
+                const Seg sg = a.segs[s_first + r];
+                const bool k1 = sg.hi - sg.lo >= 2;
+                sm.base[r] = k1 ? ex[0] : ex[1];
+                sm.hbase[r] = ex[4] | ((uint64_t)(k1 ? ex[2] : ex[3]) << 40);
+            }
+        }
+        unsigned long long b[5] = {0, 0, 0, 0, 0};
+        if (lane == 0) {
+            b[0] = atomicAdd(&a.ctr->fr_ent, (unsigned long long)acc[0]);
+            b[1] = atomicAdd(&a.ctr->lf_ent, (unsigned long long)acc[1]);
+            b[2] = atomicAdd(&a.ctr->fr_node, (unsigned long long)acc[2]);
+            b[3] = atomicAdd(&a.ctr->lf_node, (unsigned long long)acc[3]);
+            b[4] = atomicAdd(&a.ctr->hits, (unsigned long long)acc[4]);
+        }
+#pragma unroll
+        for (int q = 0; q < 5; ++q) b[q] = __shfl_sync(FULL, b[q], 0);
+        st_ent += acc[0] + acc[1];
+        const bool ovf = b[0] + acc[0] > a.fr_ent_cap || b[1] + acc[1] > a.lf_ent_cap ||
+                         b[2] + acc[2] > a.fr_node_cap || b[3] + acc[3] > a.lf_node_cap || b[4] + acc[4] > a.hit_cap;
+        if (ovf) {
+            if (lane == 0) atomicExch(&a.ctr->overflow, 1ull);
+            continue;
+        }
+        __syncwarp();
+        for (uint64_t r = lane; r < nsg; r += 32) {
+            const Seg sg = a.segs[s_first + r];
+            const bool k1 = sg.hi - sg.lo >= 2;
+            const uint32_t cn = sm.cnt[r];
+            const uint64_t nodeix = sm.hbase[r] >> 40;
+            const uint64_t hx = sm.hbase[r] & ((1ull << 40) - 1);
+            const uint64_t base = (k1 ? b[0] : b[1]) + sm.base[r];
+            sm.base[r] = base;
+            sm.hbase[r] = b[4] + hx;
+            if (cn) {
+                if (k1) {
+                    Node cn_;
+                    cn_.lo = sg.lo;
+                    cn_.hi = sg.hi;
+                    cn_.item = sg.item;
+                    cn_.cnt = cn;
+                    cn_.off = base;
+                    a.fnodes[b[2] + nodeix] = cn_;
+                } else {
+                    Inject in;
+                    in.qid = sg.qid;
+                    in.e = a.ix.tend[sg.lo];
+                    in.cnt = cn;
+                    in.pad = 0;
+                    in.off = base;
+                    a.inj[b[3] + nodeix] = in;
+                }
+            }
+            sm.cnt[r] = 0;
+            sm.hit[r] = 0;
+        }
+        __syncwarp();
+        run_task<SIGMA, true>(a, smat, sm, s_first, s_last, t_beg, t_end, st0, st1, st2);
+        __syncwarp();
+    }
+    if (a.stats) {
+        unsigned long long t0 = st0, t1 = st1, t2 = st2;
+        for (int d = 16; d > 0; d >>= 1) {
+            t0 += __shfl_down_sync(FULL, t0, d);
+            t1 += __shfl_down_sync(FULL, t1, d);
+            t2 += __shfl_down_sync(FULL, t2, d);
+        }
+        if (lane == 0) {
+            if (st_ent) atomicAdd(&a.stats->entries, st_ent);
+            if (t0) atomicAdd(&a.stats->tier[0], t0);
+            if (t1) atomicAdd(&a.stats->tier[1], t1);
+            if (t2) atomicAdd(&a.stats->tier[2], t2);
+        }
+    }
+}
+
+inline unsigned grid_for(int64_t n, int threads, int64_t cap = 152 * 64) {
+    int64_t b = (n + threads - 1) / threads;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (unsigned)b;
+}
+
+}  // namespace
+
+void ae_children(const ChildrenArgs &a, cudaStream_t st) {
+    if (a.nnodes <= 0) return;
+    ++g_launches;
+    if (a.ix.sigma == 4)
+        k_children<4><<<grid_for(a.nnodes * 4, 256), 256, 0, st>>>(a);
+    else
+        k_children<20><<<grid_for(a.nnodes * 20, 256), 256, 0, st>>>(a);
+}
+
+void ae_compact_segs(const uint32_t *clo, const uint32_t *chi, const uint32_t *flag, const uint32_t *len,
+                     const uint64_t *fpos, const uint64_t *toff, int64_t N, int sigma, const Node *nodes,
+                     const WorkItem *items, QueryView qv, Seg *segs, cudaStream_t st) {
+    if (N <= 0) return;
+    ++g_launches;
+    if (sigma == 4)
+        k_compact<4><<<grid_for(N, 256), 256, 0, st>>>(clo, chi, flag, len, fpos, toff, N, nodes, items, qv, segs);
+    else
+        k_compact<20><<<grid_for(N, 256), 256, 0, st>>>(clo, chi, flag, len, fpos, toff, N, nodes, items, qv, segs);
+}
+
+void ae_rows(const RowsArgs &a, int blocks, cudaStream_t st) {
+    ++g_launches;
+    if (a.ix.sigma == 4)
+        k_rows<4><<<blocks, RW_WARPS * 32, 0, st>>>(a);
+    else
+        k_rows<20><<<blocks, RW_WARPS * 32, 0, st>>>(a);
+}

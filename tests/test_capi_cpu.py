@@ -92,4 +92,4 @@ def test_argument_errors_without_device():
 
 def test_options_default():
     o = ae.ae_options_default()
-    assert o.qprefix_seed == 1 and o.leaf_segment >= 1 and o.item_columns > 0
+    assert o.qprefix_seed == 1 and o.leaf_segment >= 0 and o.item_columns > 0
