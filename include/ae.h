@@ -158,6 +158,31 @@ ae_status ae_search_device(const ae_index *idx, const uint8_t *d_seq, const int6
                            const ae_options *opt, ae_hit *d_hits, int64_t capacity,
                            int64_t *counts, void *stream);
 
+/* The search of ae_search_device for callers that cannot allocate device
+ * memory: code that runs while a stream is being captured into a CUDA graph
+ * (cudaMalloc is not allowed there), or a process whose device memory is
+ * already handed out to another allocator.  It calls no cudaMalloc, cudaFree,
+ * cudaMallocHost or other device allocator: every working buffer is carved
+ * from one fixed 64 MiB array in the library's device image, which each GPU
+ * that loads the library keeps until the process exits.  The paper has no
+ * counterpart; the arguments, result order and AE_EOVERFLOW behaviour are
+ * those of ae_search_device.
+ * Limits: at most 65,536 query letters in total and 4,096 queries per call,
+ * and the search's working set must fit the array (rows of the text-position
+ * sweep are capped at 256 entries before one retry at 1,024); beyond that the
+ * call returns AE_EUNSUPPORTED and writes nothing to d_hits.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  All calls on a device share the array, which
+ * keeps the previous call's contents (the search initialises everything it
+ * reads); calls on one device are serialised by the library and each returns
+ * only after its device work has finished, so their device work never
+ * overlaps -- work that did overlap on the same array would race. */
+ae_status ae_search_device_static(const ae_index *idx, const uint8_t *d_seq, const int64_t *offsets,
+                                  int32_t nq, const ae_scoring *scoring, const int32_t *H,
+                                  const ae_options *opt, ae_hit *d_hits, int64_t capacity,
+                                  int64_t *counts, void *stream);
+
 /* Counters of the calling thread's last search. */
 ae_status ae_last_stats(ae_stats *out);
 

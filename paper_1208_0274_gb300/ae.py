@@ -75,6 +75,7 @@ def _load():
         "ae_search": (I32, [V, V, I32, V, V, V, V, V, V]),
         "ae_hits_free": (None, [V]),
         "ae_search_device": (I32, [V, V, V, I32, V, V, V, V, I64, V, V]),
+        "ae_search_device_static": (I32, [V, V, V, I32, V, V, V, V, I64, V, V]),
         "ae_last_stats": (I32, [V]),
         "ae_suffix_array": (I32, [V, I64, I32, V]),
         "ae_plan": (I32, [I64, I32, V, I32, V, V, V]),
@@ -253,6 +254,27 @@ def ae_search_device(index, d_seq_ptr, offsets, scheme, H, d_hits_ptr, capacity,
                               counts.ctypes.data, _stream_handle(stream))
     if st not in (AE_OK, AE_EOVERFLOW):
         _check(st, "ae_search_device")
+    return st, counts[:nq].copy()
+
+
+def ae_search_device_static(index, d_seq_ptr, offsets, scheme, H, d_hits_ptr, capacity, options=None,
+                            stream=None):
+    """ae_search_device without any device allocation: working memory comes
+    from a fixed array inside the library (limits in include/ae.h). Returns
+    (status, counts) like ae_search_device; AE_EUNSUPPORTED when the problem
+    exceeds the array."""
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    nq = off.size - 1
+    h = _thresholds(H, nq)
+    sc, _mat = make_scoring(scheme, index.alphabet)
+    counts = np.zeros(max(nq, 1), dtype=np.int64)
+    st = lib.ae_search_device_static(index.handle, ctypes.c_void_p(int(d_seq_ptr)), off.ctypes.data, nq,
+                                     ctypes.byref(sc), h.ctypes.data,
+                                     ctypes.byref(options) if options is not None else None,
+                                     ctypes.c_void_p(int(d_hits_ptr)) if d_hits_ptr else None, int(capacity),
+                                     counts.ctypes.data, _stream_handle(stream))
+    if st not in (AE_OK, AE_EOVERFLOW, AE_EUNSUPPORTED):
+        _check(st, "ae_search_device_static")
     return st, counts[:nq].copy()
 
 

@@ -30,7 +30,19 @@ thread_local ae_stats g_last_stats;
 struct DevBuf {
     void *p = nullptr;
     size_t bytes = 0;
+    bool carved = false;   // points into the static scratch of ae_search_device_static
 };
+
+// Set only inside ae_search_device_static: buffers are then carved from the
+// static device array instead of allocated (see the end of this file).
+struct StaticArena {
+    char *base;
+    size_t cap;
+    size_t used;
+};
+thread_local StaticArena *g_arena = nullptr;
+
+void carve(DevBuf &b, size_t bytes, size_t keep, cudaStream_t st);
 
 struct ae_error {
     ae_status st;
@@ -64,6 +76,10 @@ void trace_alloc(size_t nb, bool ok) {
 // Grow-only device buffer; contents are not preserved.
 void ensure(DevBuf &b, size_t bytes, cudaStream_t st) {
     if (bytes <= b.bytes) return;
+    if (g_arena) {
+        carve(b, bytes, 0, st);
+        return;
+    }
     size_t nb = std::max(bytes, b.bytes + b.bytes / 4);
     nb = (nb + 255) & ~size_t(255);
     if (b.p) {
@@ -86,6 +102,10 @@ void ensure(DevBuf &b, size_t bytes, cudaStream_t st) {
 // Grow preserving the first `keep` bytes.
 void ensure_keep(DevBuf &b, size_t bytes, size_t keep, cudaStream_t st) {
     if (bytes <= b.bytes) return;
+    if (g_arena) {
+        carve(b, bytes, keep, st);
+        return;
+    }
     size_t nb = std::max(bytes, b.bytes + b.bytes / 4);
     nb = (nb + 255) & ~size_t(255);
     void *p = nullptr;
@@ -133,6 +153,7 @@ struct Workspace {
     double fr_ratio = 0.5, lf_ratio = 0.25, hit_ratio = 0.5;
     // pinned host staging
     uint64_t *h_tot = nullptr;
+    bool h_tot_static = false;
     int32_t leaf_cap = 0;
 
     ~Workspace() {
@@ -142,11 +163,25 @@ struct Workspace {
                          &lGa, &inj, &rhits, &sk0, &sv0, &sk1, &sv1, &sort_tmp, &hkey, &hscore, &hcount, &hk1,
                          &hv1, &scratch, &next_seg, &uniq, &uflags, &uoff, &qcount, &stats, &segs, &ctr};
         for (DevBuf *b : all)
-            if (b->p) {
+            if (b->p && !b->carved) {
                 cudaFree(b->p);
                 g_ws_bytes -= (int64_t)b->bytes;
             }
-        if (h_tot) cudaFreeHost(h_tot);
+        if (h_tot && !h_tot_static) cudaFreeHost(h_tot);
+    }
+
+    // Forget every carved buffer (the next static call carves them again).
+    void forget_carved() {
+        DevBuf *all[] = {&ascii, &codes, &qoff, &qm, &qH, &items, &item_pos, &bad, &aj[0], &aj[1], &aM[0],
+                         &aM[1], &aGa[0], &aGa[1], &nodes[0], &nodes[1], &cnt[0], &cnt[1], &cnt[2], &cnt[3],
+                         &cnt[4], &off[0], &off[1], &off[2], &off[3], &off[4], &totals, &scan_tmp, &lj, &lM,
+                         &lGa, &inj, &rhits, &sk0, &sv0, &sk1, &sv1, &sort_tmp, &hkey, &hscore, &hcount, &hk1,
+                         &hv1, &scratch, &next_seg, &uniq, &uflags, &uoff, &qcount, &stats, &segs, &ctr};
+        for (DevBuf *b : all) {
+            b->p = nullptr;
+            b->bytes = 0;
+            b->carved = false;
+        }
     }
 };
 
@@ -618,7 +653,7 @@ void Search::leaf_phase(int64_t ninj) {
     const uint32_t *order = which ? ptr<uint32_t>(w->sv1) : ptr<uint32_t>(w->sv0);
 
     const int threads = 128;
-    const int blocks = num_sms * 12;
+    const int blocks = num_sms * (g_arena ? 2 : 12);
     const int nwarps = blocks * threads / 32;
     if (w->leaf_cap < opt.leaf_capacity) w->leaf_cap = opt.leaf_capacity;
     ensure(w->next_seg, 8, st);
@@ -1084,3 +1119,122 @@ ae_status ae_plan(int64_t m, int32_t alphabet, const ae_scoring *scoring, int32_
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ no-allocation search
+//
+// ae_search_device_static: the search of ae_search_device for callers that
+// must not allocate device memory (e.g. code running inside a CUDA graph
+// capture, where cudaMalloc is not allowed, or a host process whose device
+// memory is fully reserved by someone else).  Every working buffer of the
+// search -- level arenas, sort buffers, hit records and the per-warp rows of
+// the text-position sweep -- is carved from one file-scope device array of
+// AE_STATIC_SCRATCH_BYTES, which every GPU that loads this library holds
+// until the process exits.
+
+namespace {
+
+constexpr size_t AE_STATIC_SCRATCH_BYTES = (size_t)64 << 20;
+constexpr int64_t AE_STATIC_MAX_COLUMNS = 65536;
+constexpr int32_t AE_STATIC_MAX_QUERIES = 4096;
+constexpr int AE_STATIC_MAX_DEVICES = 64;
+
+static __device__ __align__(256) unsigned char g_ae_static_scratch[AE_STATIC_SCRATCH_BYTES];
+
+// Host-side state per device: the device address of the array (the array's
+// name in host code is only a stand-in for the symbol), the workspace whose
+// buffers point into it, and a host staging area.
+void *g_static_ptr[AE_STATIC_MAX_DEVICES];
+Workspace g_static_ws[AE_STATIC_MAX_DEVICES];
+uint64_t g_static_htot[AE_STATIC_MAX_DEVICES][64];
+std::mutex g_static_mu[AE_STATIC_MAX_DEVICES];
+
+void carve(DevBuf &b, size_t bytes, size_t keep, cudaStream_t st) {
+    StaticArena &a = *g_arena;
+    const size_t off = (a.used + 255) & ~size_t(255);
+    if (off + bytes > a.cap) throw ae_error{AE_EUNSUPPORTED};
+    void *p = a.base + off;
+    if (keep && b.p) CU(cudaMemcpyAsync(p, b.p, keep, cudaMemcpyDeviceToDevice, st));
+    a.used = off + bytes;
+    b.p = p;
+    b.bytes = bytes;
+    b.carved = true;
+}
+
+}  // namespace
+
+extern "C" ae_status ae_search_device_static(const ae_index *idx, const uint8_t *d_seq, const int64_t *offsets,
+                                             int32_t nq, const ae_scoring *scoring, const int32_t *H,
+                                             const ae_options *opt, ae_hit *d_hits, int64_t capacity,
+                                             int64_t *counts, void *stream) {
+    if (!idx || !offsets || !counts || nq < 0 || (nq > 0 && !H) || capacity < 0 || (capacity > 0 && !d_hits))
+        return AE_EINVAL;
+    if (nq == 0) return AE_OK;
+    const int64_t total_len = offsets[nq] - offsets[0];
+    if (offsets[0] != 0 || total_len < 0) return AE_EINVAL;
+    if (total_len > 0 && !d_seq) return AE_EINVAL;
+    if (total_len > AE_STATIC_MAX_COLUMNS || nq > AE_STATIC_MAX_QUERIES) return AE_EUNSUPPORTED;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return AE_ECUDA;
+    }
+    if (dev < 0 || dev >= AE_STATIC_MAX_DEVICES) return AE_EUNSUPPORTED;
+    std::lock_guard<std::mutex> guard(g_static_mu[dev]);
+    if (!g_static_ptr[dev]) {
+        // once per device, with that device current
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_ae_static_scratch) != cudaSuccess || !p) {
+            cudaGetLastError();
+            return AE_ECUDA;
+        }
+        g_static_ptr[dev] = p;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    ae_options o;
+    ae_options_default(&o);
+    if (opt) o = *opt;
+    o.profile = 0;
+    o.leaf_capacity = std::max(64, std::min(o.leaf_capacity, 256));
+    Workspace &w = g_static_ws[dev];
+    w.forget_carved();
+    w.stream = st;
+    w.h_tot = g_static_htot[dev];
+    w.h_tot_static = true;
+    w.leaf_cap = 0;
+    StaticArena arena{reinterpret_cast<char *>(g_static_ptr[dev]), AE_STATIC_SCRATCH_BYTES, 0};
+    g_arena = &arena;
+    ae_status status = AE_OK;
+    try {
+        ensure(w.codes, std::max<int64_t>(total_len, 1), st);
+        ensure(w.bad, 4, st);
+        CU(cudaMemsetAsync(w.bad.p, 0, 4, st));
+        ae_encode_queries(d_seq, ptr<uint8_t>(w.codes), total_len, idx->host.alphabet, ptr<int>(w.bad), st);
+        CU(cudaMemcpyAsync(w.h_tot, w.bad.p, 4, cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+        if (*reinterpret_cast<int *>(w.h_tot)) {
+            status = AE_EINVAL;
+        } else {
+            ae_hit *dev_hits = nullptr;
+            std::vector<int64_t> cnt;
+            int64_t total = 0;
+            status = search_core(idx, &w, offsets, nq, scoring, H, &o, st, &dev_hits, cnt, &total);
+            if (status == AE_OK) {
+                for (int q = 0; q < nq; ++q) counts[q] = cnt[q];
+                if (total > capacity) {
+                    status = AE_EOVERFLOW;
+                } else if (total > 0) {
+                    CU(cudaMemcpyAsync(d_hits, dev_hits, sizeof(ae_hit) * (size_t)total, cudaMemcpyDeviceToDevice,
+                                       st));
+                    CU(cudaStreamSynchronize(st));
+                }
+            }
+        }
+    } catch (const ae_error &err) {
+        cudaGetLastError();
+        status = err.st;
+    } catch (const std::bad_alloc &) {
+        status = AE_ENOMEM;
+    }
+    g_arena = nullptr;
+    return status;
+}
