@@ -156,6 +156,26 @@ def peaks():
         return 6800.0, "fallback"
 
 
+def measured_traffic(kernel, units):
+    """DRAM bytes (read + write) of `kernel` for `units` DP entries, from the
+    per-entry figure of its last ncu capture (profiles/dram_per_entry.txt).
+    None if there is no capture or the kernel's source changed since."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "dram_per_entry.txt")
+    src_of = {"k_rows": "ae_trie.cu", "k_leaf": "ae_kernels.cu"}
+    if kernel not in src_of or not os.path.exists(path):
+        return None
+    for line in open(path):
+        parts = line.split()
+        if len(parts) >= 3 and not line.startswith("#") and parts[0] == kernel:
+            src = os.path.join(ROOT, "paper_1208_0274_gb300", "csrc", src_of[kernel])
+            digest = hashlib.sha1(open(src, "rb").read()).hexdigest()[:12]
+            if parts[2] != digest:
+                return None
+            return int(float(parts[1]) * units)
+    return None
+
+
 def cpu_baseline(text, queries, scheme, H, seconds):
     """The oracle (plain full-matrix Smith-Waterman, one thread) on a bounded
     sample: the shortest query against a text slice sized for ~`seconds`."""
@@ -255,7 +275,7 @@ def run_ours(args):
         st = ae.ae_last_stats()
         log(f"[rank {rank}] warmup {w}: {time.perf_counter() - t1:.3f} s, hits {int(counts.sum())}, "
             f"entries {st['entries']:,} (leaf {st['entries_leaf']:,}), nodes {st['nodes']:,}, "
-            f"k_expand {st['ms_k_expand']:.1f} ms, k_leaf {st['ms_k_leaf']:.1f} ms, "
+            f"k_rows {st['ms_k_rows']:.1f} ms, k_children {st['ms_k_expand']:.1f} ms, k_leaf {st['ms_k_leaf']:.1f} ms, "
             f"k_sort {st['ms_k_sort']:.1f} ms, k_other {st['ms_k_other']:.1f} ms, launches {st['launches']}, "
             f"leaf rows {st['leaf_rows']:,} max steps {st['leaf_max_steps']:,} max width {st['leaf_max_width']:,}, "
             f"injections {st['injections']:,}, levels {st['levels']}, ws {st['ws_bytes'] / 1e9:.1f} GB")
@@ -266,7 +286,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     clocks.start()
     ev = []
-    kstats = {"ms_k_expand": 0.0, "ms_k_leaf": 0.0, "ms_k_sort": 0.0, "ms_k_other": 0.0, "launches": 0,
+    kstats = {"ms_k_expand": 0.0, "ms_k_rows": 0.0, "ms_k_leaf": 0.0, "ms_k_sort": 0.0, "ms_k_other": 0.0,
+              "launches": 0, "levels": 0,
               "entries": 0, "entries_leaf": 0, "nodes": 0, "hits": 0, "raw_hits": 0}
     for s in range(args.steps):
         with torch.cuda.stream(stream):
@@ -345,26 +366,23 @@ def run_ours(args):
             dist.destroy_process_group()
         return 0
 
-    # roofline of the dominant kernel group (device time from CUDA events
-    # recorded by the library on the search stream during the timed steps)
-    groups = {"k_leaf": kstats["ms_k_leaf"], "k_expand": kstats["ms_k_expand"],
-              "k_sort": kstats["ms_k_sort"], "k_other": kstats["ms_k_other"]}
+    # roofline of the dominant kernel (device time from CUDA events recorded by
+    # the library on the search stream around each launch, during the timed steps)
+    groups = {"k_rows": kstats["ms_k_rows"], "k_leaf": kstats["ms_k_leaf"],
+              "k_children": kstats["ms_k_expand"], "k_sort": kstats["ms_k_sort"], "k_other": kstats["ms_k_other"]}
     dom = max(groups, key=groups.get)
     peak, src = peaks()
-    # algorithmic bytes: a DP entry is read once as a parent (12 B: column,
-    # M, G_a) and written once as a child (12 B); an expanded trie node reads
-    # two 32-byte occurrence blocks and its 24-byte record
+    # algorithmic bytes: a DP entry is read once as a parent (12 B: column, M,
+    # G_a) and written once as a child (12 B)
     ent_leaf = kstats["entries_leaf"]
     ent_trie = kstats["entries"] - ent_leaf
-    if dom == "k_leaf":
-        alg = 24.0 * ent_leaf
-    elif dom == "k_expand":
-        alg = 24.0 * ent_trie + 88.0 * kstats["nodes"]
-    else:
-        alg = 16.0 * kstats["raw_hits"] * 2
+    units = {"k_rows": ent_trie, "k_leaf": ent_leaf}.get(dom, kstats["raw_hits"])
+    alg = 24.0 * units
     achieved = alg / (groups[dom] / 1000.0) / 1e9 if groups[dom] > 0 else 0.0
+    traffic = measured_traffic(dom, units)
     roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": None, "peak_source": src,
+            "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": src,
+            "algorithmic_bytes_per_unit": 24, "unit_of_work": "DP entry",
             "group_ms_per_step": {k: round(v / args.steps, 3) for k, v in groups.items()}}
     cpu = None
     if not args.no_cpu:

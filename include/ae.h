@@ -90,8 +90,11 @@ typedef struct {
     int32_t seed_depth;     /* depth the trie walk started at */
     double  ms_trie, ms_leaf, ms_reduce, ms_total;   /* host wall time per phase */
     /* with ae_options.profile: device time of the kernels, by kind, from CUDA
-     * events recorded on the search's stream around each launch group */
-    double  ms_k_expand, ms_k_leaf, ms_k_sort, ms_k_other;
+     * events recorded on the search's stream around each launch group:
+     * ms_k_rows = the row kernel of the trie levels, ms_k_expand = the child
+     * ranges with their scan and compaction, ms_k_leaf = the text-position
+     * sweep, ms_k_sort = radix sorts, ms_k_other = the rest */
+    double  ms_k_expand, ms_k_leaf, ms_k_sort, ms_k_other, ms_k_rows;
     int64_t leaf_max_steps;   /* longest text walk of one sweep task (positions) */
     int64_t leaf_max_width;   /* widest row met by the sweep (entries) */
     int64_t ws_bytes;         /* device bytes held by the library's working buffers */
@@ -105,6 +108,8 @@ typedef struct {
     int64_t batch_columns;  /* query columns processed per batch */
     int32_t leaf_capacity;  /* initial per-task row capacity of the sweep, in entries */
     int32_t profile;        /* 1: time kernel groups with CUDA events (ae_stats.ms_k_*) */
+    int32_t leaf_delay;     /* levels (0-14) a single-occurrence trie node keeps expanding in the
+                               trie walk before its row moves to the text-position sweep */
 } ae_options;
 
 /* Fill *opt with the defaults. */

@@ -41,7 +41,8 @@ class ae_query(ctypes.Structure):
 class ae_options(ctypes.Structure):
     _fields_ = [("qprefix_seed", ctypes.c_int32), ("leaf_segment", ctypes.c_int32),
                 ("item_columns", ctypes.c_int64), ("batch_columns", ctypes.c_int64),
-                ("leaf_capacity", ctypes.c_int32), ("profile", ctypes.c_int32)]
+                ("leaf_capacity", ctypes.c_int32), ("profile", ctypes.c_int32),
+                ("leaf_delay", ctypes.c_int32)]
 
 
 class ae_stats(ctypes.Structure):
@@ -54,7 +55,8 @@ class ae_stats(ctypes.Structure):
                 ("ms_leaf", ctypes.c_double), ("ms_reduce", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("ms_k_expand", ctypes.c_double),
                 ("ms_k_leaf", ctypes.c_double), ("ms_k_sort", ctypes.c_double),
-                ("ms_k_other", ctypes.c_double), ("leaf_max_steps", ctypes.c_int64),
+                ("ms_k_other", ctypes.c_double), ("ms_k_rows", ctypes.c_double),
+                ("leaf_max_steps", ctypes.c_int64),
                 ("leaf_max_width", ctypes.c_int64), ("ws_bytes", ctypes.c_int64)]
 
 

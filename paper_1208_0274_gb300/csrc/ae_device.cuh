@@ -91,6 +91,24 @@ __device__ __forceinline__ uint32_t occ_of(const IndexView &ix, int c, uint32_t 
     return SIGMA == 4 ? occ_dna(ix, c, k) : occ_prot(ix, c, k);
 }
 
+// The letter stored in BWT row k (the sentinel row reads as letter 0; callers
+// check dollar_row).
+template <int SIGMA>
+__device__ __forceinline__ int bwt_letter(const IndexView &ix, uint32_t k) {
+    const int r = k & 63;
+    if (SIGMA == 4) {
+        const uint32_t *blk = ix.occ + (size_t)(k >> 6) * AE_DNA_BLOCK_WORDS;
+        return (int)((__ldg(blk + 4 + (r >> 4)) >> (2 * (r & 15))) & 3u);
+    } else {
+        const uint32_t *blk = ix.occ + (size_t)(k >> 6) * AE_PROT_BLOCK_WORDS;
+        const uint64_t *pl = reinterpret_cast<const uint64_t *>(blk + 22);
+        int code = 0;
+#pragma unroll
+        for (int t = 0; t < 5; ++t) code |= (int)((__ldg(pl + t) >> r) & 1ull) << t;
+        return code;
+    }
+}
+
 __device__ __forceinline__ void load_matrix(const ScoreView &sc, int8_t *smat) {
     for (int t = threadIdx.x; t < AE_MAX_SIGMA * AE_MAX_SIGMA; t += blockDim.x) smat[t] = sc.mat[t];
     __syncthreads();

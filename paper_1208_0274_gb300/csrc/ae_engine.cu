@@ -149,8 +149,8 @@ struct Workspace {
     DevBuf scratch, next_seg;
     // output
     DevBuf uniq, uflags, uoff, qcount;
-    DevBuf stats, segs, ctr;
-    double fr_ratio = 0.5, lf_ratio = 0.25, hit_ratio = 0.5;
+    DevBuf stats, segs, ctr, seg_cnt, seg_hit;
+    double fr_ratio = 1.2, lf_ratio = 0.6, hit_ratio = 0.5;
     // pinned host staging
     uint64_t *h_tot = nullptr;
     bool h_tot_static = false;
@@ -161,7 +161,7 @@ struct Workspace {
                          &aM[1], &aGa[0], &aGa[1], &nodes[0], &nodes[1], &cnt[0], &cnt[1], &cnt[2], &cnt[3],
                          &cnt[4], &off[0], &off[1], &off[2], &off[3], &off[4], &totals, &scan_tmp, &lj, &lM,
                          &lGa, &inj, &rhits, &sk0, &sv0, &sk1, &sv1, &sort_tmp, &hkey, &hscore, &hcount, &hk1,
-                         &hv1, &scratch, &next_seg, &uniq, &uflags, &uoff, &qcount, &stats, &segs, &ctr};
+                         &hv1, &scratch, &next_seg, &uniq, &uflags, &uoff, &qcount, &stats, &segs, &ctr, &seg_cnt, &seg_hit};
         for (DevBuf *b : all)
             if (b->p && !b->carved) {
                 cudaFree(b->p);
@@ -176,7 +176,7 @@ struct Workspace {
                          &aM[1], &aGa[0], &aGa[1], &nodes[0], &nodes[1], &cnt[0], &cnt[1], &cnt[2], &cnt[3],
                          &cnt[4], &off[0], &off[1], &off[2], &off[3], &off[4], &totals, &scan_tmp, &lj, &lM,
                          &lGa, &inj, &rhits, &sk0, &sv0, &sk1, &sv1, &sort_tmp, &hkey, &hscore, &hcount, &hk1,
-                         &hv1, &scratch, &next_seg, &uniq, &uflags, &uoff, &qcount, &stats, &segs, &ctr};
+                         &hv1, &scratch, &next_seg, &uniq, &uflags, &uoff, &qcount, &stats, &segs, &ctr, &seg_cnt, &seg_hit};
         for (DevBuf *b : all) {
             b->p = nullptr;
             b->bytes = 0;
@@ -311,7 +311,7 @@ int seed_depth(const ScoreView &sc, int32_t Hmin, bool qprefix) {
 struct Prof {
     bool on = false;
     cudaStream_t st = nullptr;
-    std::vector<cudaEvent_t> ev[4];
+    std::vector<cudaEvent_t> ev[5];
     void mark(int k) {
         if (!on) return;
         cudaEvent_t e;
@@ -333,7 +333,7 @@ struct Prof {
             for (cudaEvent_t e : v) cudaEventDestroy(e);
     }
 };
-enum { K_EXPAND = 0, K_LEAF = 1, K_SORT = 2, K_OTHER = 3 };
+enum { K_EXPAND = 0, K_LEAF = 1, K_SORT = 2, K_OTHER = 3, K_ROWS = 4 };
 
 struct Search {
     const ae_index *idx;
@@ -466,120 +466,119 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
     ensure(w->totals, 64, st);
     ensure(w->ctr, sizeof(LevelCounters), st);
     while (F > 0 && depth <= L_max_all) {
-        const int64_t S = F * sigma;
-        // children ranges (backward-search step per letter)
-        for (int k = 0; k < 4; ++k) ensure(w->cnt[k], S * 4, st);
-        for (int k = 0; k < 2; ++k) ensure(w->off[k], S * 8, st);
-        ensure(w->scan_tmp, ae_scan_tmp_words(S, 5) * 8, st);
+        // children per node (backward-search step per letter), scanned into
+        // segment and triple offsets
+        for (int k = 0; k < 2; ++k) {
+            ensure(w->cnt[k], F * 4, st);
+            ensure(w->off[k], F * 8, st);
+        }
+        ensure(w->scan_tmp, ae_scan_tmp_words(F, 5) * 8, st);
         ChildrenArgs ca;
         ca.ix = ix;
         ca.items = d_items;
         ca.nodes = ptr<Node>(w->nodes[cur]);
         ca.nnodes = F;
-        ca.clo = ptr<uint32_t>(w->cnt[0]);
-        ca.chi = ptr<uint32_t>(w->cnt[1]);
-        ca.flag = ptr<uint32_t>(w->cnt[2]);
-        ca.len = ptr<uint32_t>(w->cnt[3]);
+        ca.nseg = ptr<uint32_t>(w->cnt[0]);
+        ca.ntrip = ptr<uint32_t>(w->cnt[1]);
         ca.stats = ptr<DevStats>(w->stats);
         prof.mark(K_EXPAND);
         ae_children(ca, st);
-        const uint32_t *cin[2] = {ca.flag, ca.len};
+        const uint32_t *cin[2] = {ca.nseg, ca.ntrip};
         uint64_t *cout[2] = {ptr<uint64_t>(w->off[0]), ptr<uint64_t>(w->off[1])};
-        ae_scan_u32(cin, cout, 2, S, ptr<uint64_t>(w->totals), ptr<uint64_t>(w->scan_tmp), st);
+        ae_scan_u32(cin, cout, 2, F, ptr<uint64_t>(w->totals), ptr<uint64_t>(w->scan_tmp), st);
         prof.mark(K_EXPAND);
         CU(cudaMemcpyAsync(tot(), w->totals.p, 16, cudaMemcpyDeviceToHost, st));
         sync();
         const int64_t nseg = (int64_t)tot()[0], ntrip = (int64_t)tot()[1];
         if (nseg == 0) break;
         ensure(w->segs, nseg * sizeof(Seg), st);
+        ensure(w->seg_cnt, nseg * 4, st);
+        ensure(w->seg_hit, nseg * 4, st);
         prof.mark(K_EXPAND);
-        ae_compact_segs(ca.clo, ca.chi, ca.flag, ca.len, cout[0], cout[1], S, sigma, ca.nodes, d_items, qv,
-                        ptr<Seg>(w->segs), st);
+        ae_compact_segs(ca, cout[0], cout[1], ptr<Seg>(w->segs), st);
         prof.mark(K_EXPAND);
         const int nxt = cur ^ 1;
-        // output capacities (grown and the level rerun if a reservation overflows)
-        // outputs per triple seen so far (each parent entry is one triple per
-        // non-empty child), with headroom; a reservation past these reruns the level
-        int64_t fr_cap = (int64_t)(ntrip * w->fr_ratio) + 4096;
-        int64_t lf_cap = lf_ent_base + (int64_t)(ntrip * w->lf_ratio) + 4096;
-        int64_t hit_cap = rh_base + ntrip / 64 + 4096;
+        RowsArgs ra;
+        memset(&ra, 0, sizeof(ra));
+        ra.ix = ix;
+        ra.sc = sc;
+        ra.qv = qv;
+        ra.items = d_items;
+        ra.nodes = ptr<Node>(w->nodes[cur]);
+        ra.pj = ptr<int32_t>(w->aj[cur]);
+        ra.pM = ptr<int32_t>(w->aM[cur]);
+        ra.pGa = ptr<int32_t>(w->aGa[cur]);
+        ra.segs = ptr<Seg>(w->segs);
+        ra.nseg_dev = ptr<uint64_t>(w->totals);
+        ra.ntrip_dev = ptr<uint64_t>(w->totals) + 1;
+        ra.seg_cnt = ptr<uint32_t>(w->seg_cnt);
+        ra.seg_hit = ptr<uint32_t>(w->seg_hit);
+        ra.ctr = ptr<LevelCounters>(w->ctr);
+        ra.stats = ptr<DevStats>(w->stats);
+        ra.leaf_delay = opt.leaf_delay;
+        // count pass: exact output sizes of this level
         LevelCounters h0;
         memset(&h0, 0, sizeof(h0));
         h0.lf_ent = (unsigned long long)lf_ent_base;
         h0.lf_node = (unsigned long long)lf_node_base;
         h0.hits = (unsigned long long)rh_base;
-        for (int attempt = 0;; ++attempt) {
-            if (attempt > 8) throw ae_error{AE_ENOMEM};
-            ensure(w->aj[nxt], fr_cap * 4, st);
-            ensure(w->aM[nxt], fr_cap * 4, st);
-            ensure(w->aGa[nxt], fr_cap * 4, st);
-            ensure(w->nodes[nxt], std::max<int64_t>(nseg, 1) * sizeof(Node), st);
-            ensure_keep(w->lj, (size_t)lf_cap * 4, (size_t)lf_ent_base * 4, st);
-            ensure_keep(w->lM, (size_t)lf_cap * 4, (size_t)lf_ent_base * 4, st);
-            ensure_keep(w->lGa, (size_t)lf_cap * 4, (size_t)lf_ent_base * 4, st);
-            ensure_keep(w->inj, (size_t)(lf_node_base + nseg + 1) * sizeof(Inject),
-                        (size_t)lf_node_base * sizeof(Inject), st);
-            ensure_keep(w->rhits, (size_t)hit_cap * sizeof(RangeHit), (size_t)rh_base * sizeof(RangeHit), st);
-            CU(cudaMemcpyAsync(w->ctr.p, &h0, sizeof(h0), cudaMemcpyHostToDevice, st));
-            RowsArgs ra;
-            memset(&ra, 0, sizeof(ra));
-            ra.ix = ix;
-            ra.sc = sc;
-            ra.qv = qv;
-            ra.items = d_items;
-            ra.nodes = ptr<Node>(w->nodes[cur]);
-            ra.pj = ptr<int32_t>(w->aj[cur]);
-            ra.pM = ptr<int32_t>(w->aM[cur]);
-            ra.pGa = ptr<int32_t>(w->aGa[cur]);
-            ra.segs = ptr<Seg>(w->segs);
-            ra.nseg_dev = ptr<uint64_t>(w->totals);
-            ra.ntrip_dev = ptr<uint64_t>(w->totals) + 1;
-            ra.fj = ptr<int32_t>(w->aj[nxt]);
-            ra.fM = ptr<int32_t>(w->aM[nxt]);
-            ra.fGa = ptr<int32_t>(w->aGa[nxt]);
-            ra.fnodes = ptr<Node>(w->nodes[nxt]);
-            ra.fr_ent_cap = (uint64_t)fr_cap;
-            ra.fr_node_cap = (uint64_t)nseg;
-            ra.lj = ptr<int32_t>(w->lj);
-            ra.lM = ptr<int32_t>(w->lM);
-            ra.lGa = ptr<int32_t>(w->lGa);
-            ra.inj = ptr<Inject>(w->inj);
-            ra.lf_ent_cap = (uint64_t)lf_cap;
-            ra.lf_node_cap = (uint64_t)(lf_node_base + nseg);
-            ra.rhits = ptr<RangeHit>(w->rhits);
-            ra.hit_cap = (uint64_t)hit_cap;
-            ra.ctr = ptr<LevelCounters>(w->ctr);
-            ra.stats = attempt == 0 ? ptr<DevStats>(w->stats) : nullptr;
-            prof.mark(K_EXPAND);
-            ae_rows(ra, num_sms * 4, st);
-            prof.mark(K_EXPAND);
-            LevelCounters hc;
-            const int64_t lf_ent_prev = lf_ent_base;
-            CU(cudaMemcpyAsync(tot(), w->ctr.p, sizeof(hc), cudaMemcpyDeviceToHost, st));
-            sync();
-            memcpy(&hc, tot(), sizeof(hc));
-            if (!hc.overflow) {
-                F = (int64_t)hc.fr_node;
-                lf_ent_base = (int64_t)hc.lf_ent;
-                lf_node_base = (int64_t)hc.lf_node;
-                rh_base = (int64_t)hc.hits;
-                const double fr_r = (double)hc.fr_ent / (double)ntrip;
-                const double lf_r = (double)((int64_t)hc.lf_ent - lf_ent_prev) / (double)ntrip;
-                w->fr_ratio = std::max(w->fr_ratio * 0.9, std::min(2.0, fr_r * 1.2 + 0.02));
-                w->lf_ratio = std::max(w->lf_ratio * 0.9, std::min(2.0, lf_r * 1.2 + 0.02));
-                if (trace())
-                    fprintf(stderr, "[ae level] depth %d nodes %lld segs %lld triples %lld -> frontier %lld, leaf %lld entries, attempts %d\n",
-                            depth, (long long)F, (long long)nseg, (long long)ntrip, (long long)hc.fr_ent,
-                            (long long)((int64_t)hc.lf_ent - lf_ent_prev), attempt + 1);
-                break;
-            }
-            fr_cap = std::max<int64_t>(fr_cap, (int64_t)hc.fr_ent + 1024);
-            lf_cap = std::max<int64_t>(lf_cap, (int64_t)hc.lf_ent + 1024);
-            hit_cap = std::max<int64_t>(hit_cap, (int64_t)hc.hits + 1024);
-        }
+        CU(cudaMemcpyAsync(w->ctr.p, &h0, sizeof(h0), cudaMemcpyHostToDevice, st));
+        prof.mark(K_ROWS);
+        ae_rows(ra, false, num_sms * 4, st);
+        prof.mark(K_ROWS);
+        LevelCounters hc;
+        CU(cudaMemcpyAsync(tot(), w->ctr.p, sizeof(hc), cudaMemcpyDeviceToHost, st));
+        sync();
+        memcpy(&hc, tot(), sizeof(hc));
+        const int64_t fr_ent = (int64_t)hc.c_fr_ent, fr_node = (int64_t)hc.c_fr_node;
+        const int64_t lf_ent = (int64_t)hc.c_lf_ent, lf_node = (int64_t)hc.c_lf_node, hits = (int64_t)hc.c_hits;
+        ensure(w->aj[nxt], std::max<int64_t>(fr_ent, 1) * 4, st);
+        ensure(w->aM[nxt], std::max<int64_t>(fr_ent, 1) * 4, st);
+        ensure(w->aGa[nxt], std::max<int64_t>(fr_ent, 1) * 4, st);
+        ensure(w->nodes[nxt], std::max<int64_t>(fr_node, 1) * sizeof(Node), st);
+        ensure_keep(w->lj, (size_t)(lf_ent_base + lf_ent + 1) * 4, (size_t)lf_ent_base * 4, st);
+        ensure_keep(w->lM, (size_t)(lf_ent_base + lf_ent + 1) * 4, (size_t)lf_ent_base * 4, st);
+        ensure_keep(w->lGa, (size_t)(lf_ent_base + lf_ent + 1) * 4, (size_t)lf_ent_base * 4, st);
+        ensure_keep(w->inj, (size_t)(lf_node_base + lf_node + 1) * sizeof(Inject),
+                    (size_t)lf_node_base * sizeof(Inject), st);
+        ensure_keep(w->rhits, (size_t)(rh_base + hits + 1) * sizeof(RangeHit), (size_t)rh_base * sizeof(RangeHit),
+                    st);
+        ra.fj = ptr<int32_t>(w->aj[nxt]);
+        ra.fM = ptr<int32_t>(w->aM[nxt]);
+        ra.fGa = ptr<int32_t>(w->aGa[nxt]);
+        ra.fnodes = ptr<Node>(w->nodes[nxt]);
+        ra.fr_ent_cap = (uint64_t)fr_ent;
+        ra.fr_node_cap = (uint64_t)fr_node;
+        ra.lj = ptr<int32_t>(w->lj);
+        ra.lM = ptr<int32_t>(w->lM);
+        ra.lGa = ptr<int32_t>(w->lGa);
+        ra.inj = ptr<Inject>(w->inj);
+        ra.lf_ent_cap = (uint64_t)(lf_ent_base + lf_ent);
+        ra.lf_node_cap = (uint64_t)(lf_node_base + lf_node);
+        ra.rhits = ptr<RangeHit>(w->rhits);
+        ra.hit_cap = (uint64_t)(rh_base + hits);
+        ra.stats = ptr<DevStats>(w->stats);
+        prof.mark(K_ROWS);
+        ae_rows(ra, true, num_sms * 4, st);
+        prof.mark(K_ROWS);
+        if (trace())
+            fprintf(stderr, "[ae level] depth %d nodes %lld segs %lld triples %lld -> frontier %lld nodes %lld, leaf %lld rows %lld\n",
+                    depth, (long long)F, (long long)nseg, (long long)ntrip, (long long)fr_ent, (long long)fr_node,
+                    (long long)lf_ent, (long long)lf_node);
+        lf_ent_base += lf_ent;
+        lf_node_base += lf_node;
+        rh_base += hits;
         cur = nxt;
+        F = fr_node;
         ++depth;
         stats.levels++;
+    }
+    {
+        LevelCounters hc;
+        CU(cudaMemcpyAsync(tot(), w->ctr.p, sizeof(hc), cudaMemcpyDeviceToHost, st));
+        sync();
+        memcpy(&hc, tot(), sizeof(hc));
+        if (hc.overflow) throw ae_error{AE_ECUDA};
     }
     CU(cudaGetLastError());
     sync();
@@ -815,7 +814,8 @@ ae_status search_core(const ae_index *idx, Workspace *w, const int64_t *offsets,
     memset(&s.stats, 0, sizeof(s.stats));
     ae_options_default(&s.opt);
     if (opt) s.opt = *opt;
-    if (s.opt.item_columns < 1 || s.opt.batch_columns < 1 || s.opt.leaf_capacity < 64 || s.opt.leaf_segment < 0)
+    if (s.opt.item_columns < 1 || s.opt.batch_columns < 1 || s.opt.leaf_capacity < 64 || s.opt.leaf_segment < 0 ||
+        s.opt.leaf_delay < 0 || s.opt.leaf_delay > 14)
         return AE_EINVAL;
     ae_status e = make_score(scoring, s.ix.sigma, s.sc);
     if (e != AE_OK) return e;
@@ -833,6 +833,7 @@ ae_status search_core(const ae_index *idx, Workspace *w, const int64_t *offsets,
     }
     // keys of the max-plus scan stay within int32
     if ((int64_t)mmax * (-(int64_t)s.sc.ss + s.sc.gmax + 1) >= (1ll << 30)) return AE_EUNSUPPORTED;
+    if (nq >= (1 << 24)) return AE_EUNSUPPORTED;
     s.be = bits_for(std::max<int64_t>(s.ix.n - 1, 1));
     s.bj = bits_for(std::max(mmax - 1, 1));
     s.bq = bits_for(std::max(nq - 1, 1));
@@ -893,6 +894,7 @@ ae_status search_core(const ae_index *idx, Workspace *w, const int64_t *offsets,
         s.stats.leaf_max_width = (int64_t)ds.leaf_max_width;
         s.stats.ws_bytes = g_ws_bytes;
         s.stats.ms_k_expand = s.prof.ms(K_EXPAND);
+        s.stats.ms_k_rows = s.prof.ms(K_ROWS);
         s.stats.ms_k_leaf = s.prof.ms(K_LEAF);
         s.stats.ms_k_sort = s.prof.ms(K_SORT);
         s.stats.ms_k_other = s.prof.ms(K_OTHER);
@@ -922,6 +924,7 @@ void ae_options_default(ae_options *opt) {
     opt->batch_columns = 1 << 20;
     opt->leaf_capacity = 4096;
     opt->profile = 0;
+    opt->leaf_delay = 8;
 }
 
 const char *ae_strerror(int32_t status) {

@@ -67,7 +67,8 @@ struct WorkItem {
 
 // A frontier node: SA range [lo, hi) of the reversed prefix at this depth,
 // its row stored at [off, off + cnt) of the level arena.  cnt == ROOT_ROW
-// marks the implicit depth-0 row (M(0, j) = 0 for the item's columns).
+// marks the implicit depth-0 row (M(0, j) = 0 for the item's columns); `item`
+// is the work item of a root node and the query id of every other node.
 struct Node {
     uint32_t lo, hi;
     int32_t item;

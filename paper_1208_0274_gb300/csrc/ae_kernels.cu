@@ -292,7 +292,7 @@ __global__ void k_seed_nodes(SeedArgs a, const uint64_t *keys, const uint32_t *v
             Node nd;
             nd.lo = lo;
             nd.hi = hi;
-            nd.item = (int32_t)(key >> (bits * a.d0));
+            nd.item = a.items[(int32_t)(key >> (bits * a.d0))].qid;   // query id, 0 levels unique
             nd.cnt = 0;
             nd.off = (uint64_t)t;
             nodes[k] = nd;
@@ -346,7 +346,7 @@ __device__ __forceinline__ int64_t upper_bound_g(const int32_t *a, int64_t n, in
 // The walk jumps to the next injection when R has no live entry.  Rows live
 // in per-warp global scratch (cap entries per buffer); a row that outgrows it
 // sets leaf_overflow and the host reruns with a larger cap.
-__global__ void __launch_bounds__(128) k_leaf(LeafArgs a) {
+__global__ void __launch_bounds__(128, 6) k_leaf(LeafArgs a) {
     __shared__ int8_t smat[AE_MAX_SIGMA * AE_MAX_SIGMA];
     load_matrix(a.sc, smat);
     const int lane = threadIdx.x & 31;
@@ -361,7 +361,7 @@ __global__ void __launch_bounds__(128) k_leaf(LeafArgs a) {
     Buf Cb = {wb + 6 * cap, wb + 7 * cap, wb + 8 * cap};
     Buf C2 = {wb + 9 * cap, wb + 10 * cap, wb + 11 * cap};
     const uint64_t jmask = (1ull << a.bj) - 1ull;
-    unsigned long long st_rows = 0, st_ent = 0, st_t[3] = {0, 0, 0};
+    unsigned long long st_rows = 0, st_ent = 0, st_t0 = 0, st_t1 = 0, st_t2 = 0;
     bool overflow = false;
 
     while (!overflow) {
@@ -379,18 +379,81 @@ __global__ void __launch_bounds__(128) k_leaf(LeafArgs a) {
         // R lives in registers (lane i holds entry i) while it has <= 32 entries
         bool inreg = false;
         int32_t rj = 0, rM = AE_NEG, rGa = AE_NEG;
+        // text window: lane i holds T[tw_base + i] (one coalesced 32-byte load per
+        // 32 positions instead of a dependent random read per step)
+        int64_t tw_base = -64;
+        uint32_t tw = 0;
+        // key (query, text end) of injection k, the next one to merge
+        int32_t nk_qid = -1, nk_e = -1;
+        if (k < kend) {
+            const Inject In = a.inj[a.order[k]];
+            nk_qid = In.qid;
+            nk_e = In.e;
+        }
         while (true) {
             int64_t clen = 0;
-            if (rlen > 0 && inreg && p + 1 < a.ix.n) {
-                bool inj_next = false;
-                if (k < kend) {
-                    const Inject In = a.inj[a.order[k]];
-                    inj_next = In.qid == qid && In.e == p + 1;
+            if (rlen == 0 && k < kend) {
+                // ---- jump to a lone injected row: it is already a finished row
+                const Inject I0 = a.inj[a.order[k]];
+                int32_t q2 = -1, e2 = -1;
+                if (k + 1 < kend) {
+                    const Inject I1 = a.inj[a.order[k + 1]];
+                    q2 = I1.qid;
+                    e2 = I1.e;
                 }
+                if (I0.cnt <= 32 && !(q2 == I0.qid && e2 == I0.e)) {
+                    p = I0.e;
+                    if (I0.qid != qid) {
+                        qid = I0.qid;
+                        m = a.qv.m[qid];
+                        H = a.qv.H[qid];
+                        P = a.qv.codes + a.qv.off[qid];
+                    }
+                    rlen = I0.cnt;
+                    if (lane < rlen) {
+                        rj = a.lj[I0.off + lane];
+                        rM = a.lM[I0.off + lane];
+                        rGa = a.lGa[I0.off + lane];
+                    }
+                    inreg = true;
+                    ++k;
+                    nk_qid = q2;
+                    nk_e = e2;
+                    const uint32_t h = (lane < rlen && rM >= H) ? 1u : 0u;
+                    const uint32_t hi = warp_incl_sum(h);
+                    const uint32_t htot = __shfl_sync(FULL, hi, 31);
+                    if (htot) {
+                        unsigned long long hbase = 0;
+                        if (lane == 0) hbase = atomicAdd(a.hit_count, (unsigned long long)htot);
+                        hbase = __shfl_sync(FULL, hbase, 0);
+                        if (hbase + htot <= a.hit_cap) {
+                            if (h) {
+                                const uint64_t kq = ((uint64_t)qid << (a.be + a.bj)) |
+                                                    ((uint64_t)(uint32_t)p << a.bj);
+                                a.hit_key[hbase + hi - 1] = kq | ((uint64_t)rj & jmask);
+                                a.hit_score[hbase + hi - 1] = rM;
+                            }
+                        } else if (lane == 0) {
+                            atomicAdd(&a.stats->hit_overflow, 1ull);
+                        }
+                    }
+                    st_t0 += (unsigned long long)rlen;
+                    ++st_rows;
+                    ++seg_steps;
+                    st_ent += (unsigned long long)rlen;
+                    continue;
+                }
+            }
+            if (rlen > 0 && inreg && p + 1 < a.ix.n) {
+                const bool inj_next = nk_qid == qid && nk_e == p + 1;
                 if (!inj_next) {
                     // ---- fast step: gen + horizontal finish in registers
                     ++p;
-                    const int c = a.ix.text[p];
+                    if (p < tw_base || p >= tw_base + 32) {
+                        tw_base = p;
+                        tw = (p + lane < a.ix.n) ? a.ix.text[p + lane] : 0u;
+                    }
+                    const int c = (int)__shfl_sync(FULL, tw, (int)(p - tw_base));
                     const bool valid = lane < rlen;
                     int32_t j = valid ? rj : m, M = valid ? rM : AE_NEG, Ga = valid ? rGa : AE_NEG;
                     int32_t jn = __shfl_down_sync(FULL, j, 1);
@@ -459,10 +522,14 @@ __global__ void __launch_bounds__(128) k_leaf(LeafArgs a) {
                     }
                     if (o.aliveA) {
                         const int tier = (Dp > AE_NEG) + (GaA > AE_NEG) + (o.GbA > thr_of(colA, m, H, g));
-                        st_t[min(max(tier, 1), 3) - 1]++;
+                        st_t0 += tier <= 1;
+                        st_t1 += tier == 2;
+                        st_t2 += tier >= 3;
                     }
-                    if (o.aliveB) st_t[((Dk > AE_NEG) && (o.GbB > thr_of(colA + 1, m, H, g))) ? 1 : 0]++;
-                    st_t[0] += nR;
+                    if (o.aliveB) {
+                        if ((Dk > AE_NEG) && (o.GbB > thr_of(colA + 1, m, H, g))) ++st_t1; else ++st_t0;
+                    }
+                    st_t0 += nR;
                     const int64_t e0 = (int64_t)(ci - cn);
                     if (tot > cap) {
                         overflow = true;
@@ -566,7 +633,11 @@ __global__ void __launch_bounds__(128) k_leaf(LeafArgs a) {
             } else {
                 ++p;
                 if (p >= a.ix.n) break;
-                const int c = a.ix.text[p];
+                if (p < tw_base || p >= tw_base + 32) {
+                    tw_base = p;
+                    tw = (p + lane < a.ix.n) ? a.ix.text[p + lane] : 0u;
+                }
+                const int c = (int)__shfl_sync(FULL, tw, (int)(p - tw_base));
                 // ---- generate slots from R with letter c
                 int32_t prev_j = -2, prev_M = AE_NEG;
                 for (int64_t base = 0; base < rlen; base += 32) {
@@ -690,6 +761,13 @@ __global__ void __launch_bounds__(128) k_leaf(LeafArgs a) {
                 __syncwarp();
             }
             if (overflow) break;
+            if (k < kend) {
+                const Inject In = a.inj[a.order[k]];
+                nk_qid = In.qid;
+                nk_e = In.e;
+            } else {
+                nk_qid = nk_e = -1;
+            }
             // ---- finish: horizontal gaps, prune, hits -> Rn
             int64_t nlen = 0;
             int32_t carry = AE_KNEG;
@@ -740,13 +818,15 @@ __global__ void __launch_bounds__(128) k_leaf(LeafArgs a) {
                     Rn.M[e0] = o.MA;
                     Rn.Ga[e0] = Ga;
                     int tier = (Mp > AE_NEG) + (Ga > AE_NEG) + (o.GbA > thr_of(col, m, H, g));
-                    st_t[min(max(tier, 1), 3) - 1]++;
+                    st_t0 += tier <= 1;
+                        st_t1 += tier == 2;
+                        st_t2 += tier >= 3;
                     if (hA && hok) {
                         a.hit_key[h0] = kq | ((uint64_t)col & jmask);
                         a.hit_score[h0] = o.MA;
                     }
                 }
-                st_t[0] += nR;
+                st_t0 += nR;
                 unsigned rmask = __ballot_sync(FULL, nR > 0);
                 while (rmask) {
                     const int L = __ffs(rmask) - 1;
@@ -797,7 +877,7 @@ __global__ void __launch_bounds__(128) k_leaf(LeafArgs a) {
             atomicMax(&a.stats->leaf_max_width, seg_width);
         }
     }
-    unsigned long long t0 = st_t[0], t1 = st_t[1], t2 = st_t[2];
+    unsigned long long t0 = st_t0, t1 = st_t1, t2 = st_t2;
     for (int d = 16; d > 0; d >>= 1) {
         t0 += __shfl_down_sync(FULL, t0, d);
         t1 += __shfl_down_sync(FULL, t1, d);

@@ -51,31 +51,31 @@ struct ChildrenArgs {
     const WorkItem *items;
     const Node *nodes;
     int64_t nnodes;
-    uint32_t *clo, *chi, *flag, *len;     // nnodes * sigma each
+    uint32_t *nseg, *ntrip;               // per node: non-empty children, triples
     DevStats *stats;
 };
 void ae_children(const ChildrenArgs &a, cudaStream_t st);
 
-// A non-empty child with everything its row computation needs (so a lane
-// reads one record instead of following node -> item -> query pointers):
-// SA range, letter, row length (= parent entries), first triple, parent row
-// offset (root rows: the work item's columns), query id, length, threshold
-// and letter offset.
+// A non-empty child (32 bytes): SA range, row length (= parent entries; bits
+// 0-27 of len, bits 28-31 = levels the parent has been a single occurrence),
+// first triple, and either the parent row's offset or, for the implicit root
+// row, the work item's columns [c0, c1) packed as c0 | c1 << 32.  cq packs the
+// letter (bits 0-4), the query id (bits 5-28) and the root flag (bit 31).
 struct Seg {
     uint32_t lo, hi;
-    uint32_t len, c;
+    uint32_t len, cq;
     uint64_t toff;
     uint64_t poff;
-    int32_t qid, m, H, item;
-    int64_t qoff;
-    int32_t c0, c1;     // c0 < 0: a regular row; else the implicit root row over [c0, c1)
 };
-void ae_compact_segs(const uint32_t *clo, const uint32_t *chi, const uint32_t *flag, const uint32_t *len,
-                     const uint64_t *fpos, const uint64_t *toff, int64_t N, int sigma, const Node *nodes,
-                     const WorkItem *items, QueryView qv, Seg *segs, cudaStream_t st);
+void ae_compact_segs(const ChildrenArgs &a, const uint64_t *seg_off, const uint64_t *trip_off, Seg *segs,
+                     cudaStream_t st);
 
+// Counters of one level: totals from the count pass (c_*), reservation
+// cursors of the write pass, and the two passes' task counters.
 struct LevelCounters {
-    unsigned long long fr_ent, fr_node, lf_ent, lf_node, hits, overflow, task, pad;
+    unsigned long long c_fr_ent, c_fr_node, c_lf_ent, c_lf_node, c_hits;
+    unsigned long long fr_ent, fr_node, lf_ent, lf_node, hits;
+    unsigned long long overflow, task_c, task_w, pad;
 };
 
 struct RowsArgs {
@@ -97,9 +97,10 @@ struct RowsArgs {
     uint64_t hit_cap;
     LevelCounters *ctr;
     DevStats *stats;
+    int32_t leaf_delay;                   // levels a single-occurrence child stays in the walk
+    uint32_t *seg_cnt, *seg_hit;          // per segment: outputs and hits (count pass -> write pass)
 };
-void ae_rows(const RowsArgs &a, int blocks, cudaStream_t st);
-
+void ae_rows(const RowsArgs &a, bool write, int blocks, cudaStream_t st);
 struct LeafArgs {
     IndexView ix;
     ScoreView sc;

@@ -22,56 +22,95 @@
 namespace {
 using namespace aedev;
 
+// Child ranges of node nd (Section 5 (3)): one backward-search step per
+// letter; a single occurrence has only the child BWT[lo] (one LF step).
+// Calls f(letter, lo', hi') for every non-empty child in letter order.
+template <int SIGMA, typename F>
+__device__ __forceinline__ void for_children(const IndexView &ix, const Node &nd, F f) {
+    if (nd.hi - nd.lo == 1) {
+        if ((int64_t)nd.lo == ix.dollar_row) return;
+        const int b = bwt_letter<SIGMA>(ix, nd.lo);
+        const uint32_t lo = ix.C[b] + occ_of<SIGMA>(ix, b, nd.lo);
+        f(b, lo, lo + 1);
+        return;
+    }
+    for (int c = 0; c < SIGMA; ++c) {
+        const uint32_t lo = ix.C[c] + occ_of<SIGMA>(ix, c, nd.lo);
+        const uint32_t hi = ix.C[c] + occ_of<SIGMA>(ix, c, nd.hi);
+        if (hi > lo) f(c, lo, hi);
+    }
+}
+
+__device__ __forceinline__ uint32_t row_len(const ChildrenArgs &a, const Node &nd) {
+    if (nd.cnt == AE_ROOT_ROW) {
+        const WorkItem it = a.items[nd.item];
+        return (uint32_t)(it.c1 - it.c0);
+    }
+    return nd.cnt;
+}
+
+// Per node: how many non-empty children and how many triples (child, parent
+// entry) they carry.
 template <int SIGMA>
 __global__ void k_children(ChildrenArgs a) {
-    const int64_t N = a.nnodes * SIGMA;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t v = t / SIGMA;
-        const int c = (int)(t - v * SIGMA);
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < a.nnodes;
+         v += (int64_t)gridDim.x * blockDim.x) {
         const Node nd = a.nodes[v];
-        const uint32_t lo = a.ix.C[c] + occ_of<SIGMA>(a.ix, c, nd.lo);
-        const uint32_t hi = a.ix.C[c] + occ_of<SIGMA>(a.ix, c, nd.hi);
-        uint32_t len = 0;
-        if (hi > lo) {
-            if (nd.cnt == AE_ROOT_ROW) {
-                const WorkItem it = a.items[nd.item];
-                len = (uint32_t)(it.c1 - it.c0);
-            } else {
-                len = nd.cnt;
-            }
-        }
-        a.clo[t] = lo;
-        a.chi[t] = hi;
-        a.len[t] = len;
-        a.flag[t] = len > 0 ? 1u : 0u;
+        const uint32_t len = row_len(a, nd);
+        uint32_t nseg = 0;
+        for_children<SIGMA>(a.ix, nd, [&](int, uint32_t, uint32_t) { ++nseg; });
+        a.nseg[v] = len ? nseg : 0u;
+        a.ntrip[v] = len ? nseg * len : 0u;
     }
     if (a.stats && blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(&a.stats->nodes, (unsigned long long)a.nnodes);
 }
 
+// Per node: write its non-empty children as segments at the scanned offsets.
 template <int SIGMA>
-__global__ void k_compact(const uint32_t *clo, const uint32_t *chi, const uint32_t *flag, const uint32_t *len,
-                          const uint64_t *fpos, const uint64_t *toff, int64_t N, const Node *nodes,
-                          const WorkItem *items, QueryView qv, Seg *segs) {
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
-        if (!flag[t]) continue;
-        const Node nd = nodes[t / SIGMA];
-        const WorkItem it = items[nd.item];
-        Seg s;
-        s.lo = clo[t];
-        s.hi = chi[t];
-        s.len = len[t];
-        s.c = (uint32_t)(t % SIGMA);
-        s.toff = toff[t];
-        s.poff = nd.cnt == AE_ROOT_ROW ? 0 : nd.off;
-        s.qid = it.qid;
-        s.m = qv.m[it.qid];
-        s.H = qv.H[it.qid];
-        s.item = nd.item;
-        s.qoff = qv.off[it.qid];
-        s.c0 = nd.cnt == AE_ROOT_ROW ? it.c0 : -1;
-        s.c1 = it.c1;
-        segs[fpos[t]] = s;
+__global__ void k_compact(ChildrenArgs a, const uint64_t *seg_off, const uint64_t *trip_off, Seg *segs) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < a.nnodes;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const Node nd = a.nodes[v];
+        const uint32_t len = row_len(a, nd);
+        if (!len) continue;
+        const bool root = nd.cnt == AE_ROOT_ROW;
+        uint64_t so = seg_off[v], to = trip_off[v];
+        uint32_t cq_hi;
+        uint64_t poff;
+        uint32_t len_hi = 0;
+        if (root) {
+            const WorkItem it = a.items[nd.item];
+            cq_hi = ((uint32_t)it.qid << 5) | 0x80000000u;
+            poff = (uint64_t)(uint32_t)it.c0 | ((uint64_t)(uint32_t)it.c1 << 32);
+        } else {
+            // nd.item packs the query id (bits 0-23) and the levels the node has
+            // been a single occurrence (bits 24-31)
+            cq_hi = ((uint32_t)nd.item & 0xFFFFFFu) << 5;
+            len_hi = ((uint32_t)nd.item >> 24) << 28;
+            poff = nd.off;
+        }
+        for_children<SIGMA>(a.ix, nd, [&](int c, uint32_t lo, uint32_t hi) {
+            Seg s;
+            s.lo = lo;
+            s.hi = hi;
+            s.len = len | len_hi;
+            s.cq = (uint32_t)c | cq_hi;
+            s.toff = to;
+            s.poff = poff;
+            segs[so++] = s;
+            to += len;
+        });
     }
+}
+
+// A child stays in the trie walk (instead of going to the text-position
+// sweep) while it has several occurrences, or for the first `delay` levels
+// after it became a single occurrence: short-lived rows then die here, packed
+// many to a warp, and only the long-lived ones reach the sweep, which merges
+// rows meeting at one text position.
+__device__ __forceinline__ bool seg_stays(const Seg &sg, int delay) {
+    if (sg.hi - sg.lo >= 2) return true;
+    return (int)(sg.len >> 28) + 1 <= delay;
 }
 
 constexpr int RW_WARPS = 8;
@@ -123,19 +162,20 @@ __device__ void run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, ui
         sg.toff = 0;
         sg.poff = 0;
         sg.lo = sg.hi = 0;
-        sg.c = 0;
-        sg.qid = 0;
-        sg.m = 1;
-        sg.H = 1;
-        sg.qoff = 0;
-        sg.c0 = -1;
-        sg.c1 = 0;
+        sg.cq = 0;
         if (valid) sg = a.segs[sid];
         const int64_t k = valid ? (int64_t)(t - sg.toff) : 0;
-        const int32_t m = sg.m, H = sg.H;
-        const uint8_t *P = a.qv.codes + sg.qoff;
-        const int c = (int)sg.c;
-        const bool root = sg.c0 >= 0;
+        const uint32_t slen = sg.len & 0x0FFFFFFFu;
+        const int c = (int)(sg.cq & 31u);
+        const int32_t qid = (int32_t)((sg.cq >> 5) & 0xFFFFFFu);
+        const bool root = (sg.cq >> 31) != 0;
+        int32_t m = 1, H = 1;
+        const uint8_t *P = a.qv.codes;
+        if (valid) {
+            m = a.qv.m[qid];
+            H = a.qv.H[qid];
+            P += a.qv.off[qid];
+        }
         // ---- slots of this lane (see slot_finish)
         int32_t colA = m, MpA = AE_NEG, GaA = AE_NEG, MpB = AE_NEG, next_col = m;
         int32_t Dprev = AE_NEG, Gap = AE_NEG, Dk = AE_NEG;
@@ -153,7 +193,7 @@ __device__ void run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, ui
         int32_t pjv = __shfl_up_sync(FULL, j, 1), pMv = __shfl_up_sync(FULL, M, 1);
         if (valid && !root) {
             const bool next_in = (lane < 31) && (((heads >> (lane + 1)) & 1u) == 0);
-            if (!next_in) jn = (k + 1 < (int64_t)sg.len) ? a.pj[sg.poff + k + 1] : m;
+            if (!next_in) jn = (k + 1 < (int64_t)slen) ? a.pj[sg.poff + k + 1] : m;
             if (lane == first_lane) {   // first lane of its segment in this chunk
                 if (k > 0) {
                     pjv = a.pj[sg.poff + k - 1];
@@ -166,11 +206,12 @@ __device__ void run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, ui
         }
         if (valid) {
             if (root) {
-                colA = sg.c0 + (int32_t)k;
+                const int32_t c0 = (int32_t)(uint32_t)sg.poff, c1 = (int32_t)(uint32_t)(sg.poff >> 32);
+                colA = c0 + (int32_t)k;
                 const int32_t D = delta_of(sc, smat, c, P[colA]);
                 Dprev = D > thr_of(colA, m, H, g) ? D : AE_NEG;
                 MpA = Dprev;
-                next_col = (colA + 1 < sg.c1) ? colA + 1 : m;
+                next_col = (colA + 1 < c1) ? colA + 1 : m;
             } else {
                 colA = j;
                 const int32_t tA = thr_of(j, m, H, g);
@@ -210,7 +251,7 @@ __device__ void run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, ui
         {
             const int64_t k31 = __shfl_sync(FULL, k, 31);
             const bool v31 = __shfl_sync(FULL, valid, 31);
-            const uint32_t len31 = __shfl_sync(FULL, sg.len, 31);
+            const uint32_t len31 = __shfl_sync(FULL, slen, 31);
             const int32_t inc31 = __shfl_sync(FULL, incl, 31);
             const bool goes_on = v31 && (k31 + 1 < (int64_t)len31);
             carry = goes_on ? inc31 : AE_KNEG;
@@ -219,7 +260,7 @@ __device__ void run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, ui
         }
 
         // ---- counts, segmented sums
-        const bool kind1 = valid && (sg.hi - sg.lo >= 2);
+        const bool kind1 = valid && seg_stays(sg, a.leaf_delay);
         const uint32_t nA = o.aliveA, nB = o.aliveB, nR = (uint32_t)o.run_len;
         const uint32_t cnt = nA + nB + nR;
         const uint32_t hA = o.aliveA && o.MA >= H, hB = o.aliveB && o.MB >= H;
@@ -287,11 +328,11 @@ __device__ void run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, ui
         if (kind1) {
             uint64_t hp = h0;
             if (hA) {
-                RangeHit r = {sg.lo, sg.hi, sg.qid, colA, o.MA, 0};
+                RangeHit r = {sg.lo, sg.hi, qid, colA, o.MA, 0};
                 a.rhits[hp++] = r;
             }
             if (hB) {
-                RangeHit r = {sg.lo, sg.hi, sg.qid, colA + 1, o.MB, 0};
+                RangeHit r = {sg.lo, sg.hi, qid, colA + 1, o.MB, 0};
                 a.rhits[hp++] = r;
             }
         }
@@ -310,7 +351,7 @@ __device__ void run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, ui
             int32_t *rM = (int32_t *)__shfl_sync(FULL, (unsigned long long)oM, L);
             int32_t *rG = (int32_t *)__shfl_sync(FULL, (unsigned long long)oGa, L);
             const uint32_t rlo = __shfl_sync(FULL, sg.lo, L), rhi = __shfl_sync(FULL, sg.hi, L);
-            const int32_t rq = __shfl_sync(FULL, sg.qid, L);
+            const int32_t rq = __shfl_sync(FULL, qid, L);
             for (int32_t tt = lane; tt < rl; tt += 32) {
                 const int32_t col = s0 + tt;
                 const int32_t v = sc.sg - col * u + K;
@@ -327,7 +368,13 @@ __device__ void run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, ui
     }
 }
 
-template <int SIGMA>
+// One row pass over all triples.  WRITE = false: every task counts its
+// segments' outputs into seg_cnt/seg_hit and adds the level totals (so the
+// host can size the next arenas exactly).  WRITE = true: every task reads its
+// segments' counts, reserves its output ranges with one atomic per arena,
+// writes the child node / injection records, and recomputes and writes the
+// rows and the hits of multi-occurrence children.
+template <int SIGMA, bool WRITE>
 __global__ void __launch_bounds__(RW_WARPS * 32, 4) k_rows(RowsArgs a) {
     __shared__ int8_t smat[AE_MAX_SIGMA * AE_MAX_SIGMA];
     __shared__ TaskSmem smem[RW_WARPS];
@@ -339,9 +386,10 @@ __global__ void __launch_bounds__(RW_WARPS * 32, 4) k_rows(RowsArgs a) {
     const uint64_t ntask = (T + W - 1) / W;
     unsigned long long st0 = 0, st1 = 0, st2 = 0;
     unsigned long long st_ent = 0;
+    unsigned long long *task_ctr = WRITE ? &a.ctr->task_w : &a.ctr->task_c;
     while (true) {
         unsigned long long task = 0;
-        if (lane == 0) task = atomicAdd(&a.ctr->task, 1ull);
+        if (lane == 0) task = atomicAdd(task_ctr, 1ull);
         task = __shfl_sync(FULL, task, 0);
         if (task >= ntask) break;
         const uint64_t w_lo = task * W, w_hi = min(T, w_lo + W);
@@ -355,28 +403,41 @@ __global__ void __launch_bounds__(RW_WARPS * 32, 4) k_rows(RowsArgs a) {
         if (s_first >= s_last) continue;
         const uint64_t nsg = s_last - s_first;
         const Seg lastseg = a.segs[s_last - 1];
-        const uint64_t t_beg = a.segs[s_first].toff, t_end = lastseg.toff + lastseg.len;
-        for (uint64_t r = lane; r < nsg; r += 32) {
-            sm.cnt[r] = 0;
-            sm.hit[r] = 0;
+        const uint64_t t_beg = a.segs[s_first].toff, t_end = lastseg.toff + (lastseg.len & 0x0FFFFFFFu);
+        if (!WRITE) {
+            for (uint64_t r = lane; r < nsg; r += 32) {
+                sm.cnt[r] = 0;
+                sm.hit[r] = 0;
+            }
+            __syncwarp();
+            run_task<SIGMA, false>(a, smat, sm, s_first, s_last, t_beg, t_end, st0, st1, st2);
+            __syncwarp();
+        } else {
+            for (uint64_t r = lane; r < nsg; r += 32) {
+                sm.cnt[r] = a.seg_cnt[s_first + r];
+                sm.hit[r] = a.seg_hit[s_first + r];
+            }
+            __syncwarp();
         }
-        __syncwarp();
-        run_task<SIGMA, false>(a, smat, sm, s_first, s_last, t_beg, t_end, st0, st1, st2);
-        __syncwarp();
-        // ---- exclusive prefixes per kind, one reservation per arena
+        // ---- per-kind totals and exclusive prefixes in segment order
         uint64_t acc[5] = {0, 0, 0, 0, 0};   // fr_ent, lf_ent, fr_node, lf_node, hits
         for (uint64_t r0 = 0; r0 < nsg; r0 += 32) {
             const uint64_t r = r0 + lane;
             uint32_t v[5] = {0, 0, 0, 0, 0};
+            bool k1 = false;
             if (r < nsg) {
                 const Seg sg = a.segs[s_first + r];
-                const bool k1 = sg.hi - sg.lo >= 2;
+                k1 = seg_stays(sg, a.leaf_delay);
                 const uint32_t cn = sm.cnt[r];
                 v[0] = k1 ? cn : 0u;
                 v[1] = k1 ? 0u : cn;
                 v[2] = (k1 && cn) ? 1u : 0u;
                 v[3] = (!k1 && cn) ? 1u : 0u;
                 v[4] = sm.hit[r];
+                if (!WRITE) {
+                    a.seg_cnt[s_first + r] = cn;
+                    a.seg_hit[s_first + r] = sm.hit[r];
+                }
             }
             uint64_t ex[5];
 #pragma unroll
@@ -390,13 +451,21 @@ __global__ void __launch_bounds__(RW_WARPS * 32, 4) k_rows(RowsArgs a) {
                 ex[q] = acc[q] + x - v[q];
                 acc[q] += __shfl_sync(FULL, x, 31);
             }
-            if (r < nsg) {
-                // temporarily keep the in-task prefixes
-                const Seg sg = a.segs[s_first + r];
-                const bool k1 = sg.hi - sg.lo >= 2;
+            if (WRITE && r < nsg) {
                 sm.base[r] = k1 ? ex[0] : ex[1];
                 sm.hbase[r] = ex[4] | ((uint64_t)(k1 ? ex[2] : ex[3]) << 40);
             }
+        }
+        if (!WRITE) {
+            if (lane == 0) {
+                if (acc[0]) atomicAdd(&a.ctr->c_fr_ent, (unsigned long long)acc[0]);
+                if (acc[1]) atomicAdd(&a.ctr->c_lf_ent, (unsigned long long)acc[1]);
+                if (acc[2]) atomicAdd(&a.ctr->c_fr_node, (unsigned long long)acc[2]);
+                if (acc[3]) atomicAdd(&a.ctr->c_lf_node, (unsigned long long)acc[3]);
+                if (acc[4]) atomicAdd(&a.ctr->c_hits, (unsigned long long)acc[4]);
+            }
+            st_ent += acc[0] + acc[1];
+            continue;
         }
         unsigned long long b[5] = {0, 0, 0, 0, 0};
         if (lane == 0) {
@@ -408,7 +477,8 @@ __global__ void __launch_bounds__(RW_WARPS * 32, 4) k_rows(RowsArgs a) {
         }
 #pragma unroll
         for (int q = 0; q < 5; ++q) b[q] = __shfl_sync(FULL, b[q], 0);
-        st_ent += acc[0] + acc[1];
+        // the count pass sized every arena exactly; a reservation past the end
+        // means the two passes disagreed, which is reported, never written
         const bool ovf = b[0] + acc[0] > a.fr_ent_cap || b[1] + acc[1] > a.lf_ent_cap ||
                          b[2] + acc[2] > a.fr_node_cap || b[3] + acc[3] > a.lf_node_cap || b[4] + acc[4] > a.hit_cap;
         if (ovf) {
@@ -418,7 +488,7 @@ __global__ void __launch_bounds__(RW_WARPS * 32, 4) k_rows(RowsArgs a) {
         __syncwarp();
         for (uint64_t r = lane; r < nsg; r += 32) {
             const Seg sg = a.segs[s_first + r];
-            const bool k1 = sg.hi - sg.lo >= 2;
+            const bool k1 = seg_stays(sg, a.leaf_delay);
             const uint32_t cn = sm.cnt[r];
             const uint64_t nodeix = sm.hbase[r] >> 40;
             const uint64_t hx = sm.hbase[r] & ((1ull << 40) - 1);
@@ -430,13 +500,15 @@ __global__ void __launch_bounds__(RW_WARPS * 32, 4) k_rows(RowsArgs a) {
                     Node cn_;
                     cn_.lo = sg.lo;
                     cn_.hi = sg.hi;
-                    cn_.item = sg.item;
+                    // query id, and how many levels the child has been a single occurrence
+                    const uint32_t uq = (sg.hi - sg.lo == 1) ? (sg.len >> 28) + 1u : 0u;
+                    cn_.item = (int32_t)(((sg.cq >> 5) & 0xFFFFFFu) | (uq << 24));
                     cn_.cnt = cn;
                     cn_.off = base;
                     a.fnodes[b[2] + nodeix] = cn_;
                 } else {
                     Inject in;
-                    in.qid = sg.qid;
+                    in.qid = (int32_t)((sg.cq >> 5) & 0xFFFFFFu);
                     in.e = a.ix.tend[sg.lo];
                     in.cnt = cn;
                     in.pad = 0;
@@ -480,26 +552,28 @@ void ae_children(const ChildrenArgs &a, cudaStream_t st) {
     if (a.nnodes <= 0) return;
     ++g_launches;
     if (a.ix.sigma == 4)
-        k_children<4><<<grid_for(a.nnodes * 4, 256), 256, 0, st>>>(a);
+        k_children<4><<<grid_for(a.nnodes, 256), 256, 0, st>>>(a);
     else
-        k_children<20><<<grid_for(a.nnodes * 20, 256), 256, 0, st>>>(a);
+        k_children<20><<<grid_for(a.nnodes, 256), 256, 0, st>>>(a);
 }
 
-void ae_compact_segs(const uint32_t *clo, const uint32_t *chi, const uint32_t *flag, const uint32_t *len,
-                     const uint64_t *fpos, const uint64_t *toff, int64_t N, int sigma, const Node *nodes,
-                     const WorkItem *items, QueryView qv, Seg *segs, cudaStream_t st) {
-    if (N <= 0) return;
-    ++g_launches;
-    if (sigma == 4)
-        k_compact<4><<<grid_for(N, 256), 256, 0, st>>>(clo, chi, flag, len, fpos, toff, N, nodes, items, qv, segs);
-    else
-        k_compact<20><<<grid_for(N, 256), 256, 0, st>>>(clo, chi, flag, len, fpos, toff, N, nodes, items, qv, segs);
-}
-
-void ae_rows(const RowsArgs &a, int blocks, cudaStream_t st) {
+void ae_compact_segs(const ChildrenArgs &a, const uint64_t *seg_off, const uint64_t *trip_off, Seg *segs,
+                     cudaStream_t st) {
+    if (a.nnodes <= 0) return;
     ++g_launches;
     if (a.ix.sigma == 4)
-        k_rows<4><<<blocks, RW_WARPS * 32, 0, st>>>(a);
+        k_compact<4><<<grid_for(a.nnodes, 256), 256, 0, st>>>(a, seg_off, trip_off, segs);
     else
-        k_rows<20><<<blocks, RW_WARPS * 32, 0, st>>>(a);
+        k_compact<20><<<grid_for(a.nnodes, 256), 256, 0, st>>>(a, seg_off, trip_off, segs);
+}
+
+void ae_rows(const RowsArgs &a, bool write, int blocks, cudaStream_t st) {
+    ++g_launches;
+    if (a.ix.sigma == 4) {
+        if (write) k_rows<4, true><<<blocks, RW_WARPS * 32, 0, st>>>(a);
+        else k_rows<4, false><<<blocks, RW_WARPS * 32, 0, st>>>(a);
+    } else {
+        if (write) k_rows<20, true><<<blocks, RW_WARPS * 32, 0, st>>>(a);
+        else k_rows<20, false><<<blocks, RW_WARPS * 32, 0, st>>>(a);
+    }
 }

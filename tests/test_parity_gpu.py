@@ -75,7 +75,8 @@ def test_dna_small_workload_full_parity(small):
 
 @pytest.mark.parametrize("opts", [dict(qprefix_seed=0), dict(leaf_segment=1), dict(leaf_segment=7),
                                   dict(item_columns=97), dict(item_columns=250, batch_columns=300),
-                                  dict(leaf_capacity=64)])
+                                  dict(leaf_capacity=64), dict(leaf_delay=0), dict(leaf_delay=3),
+                                  dict(leaf_delay=14, leaf_segment=5)])
 def test_dna_small_knobs_do_not_change_hits(small, opts):
     wl, idx = small
     want = want_hits(wl.text, wl.queries[0], wl.scheme, wl.H[0])
@@ -99,7 +100,8 @@ def test_random_planted_cases(si):
         for H in (4, 9, 17):
             for seed_on in (1, 0):
                 opts = ae.make_options(qprefix_seed=seed_on, leaf_segment=int(rng.integers(1, 40)),
-                                       item_columns=int(rng.integers(3, 500)))
+                                       item_columns=int(rng.integers(3, 500)),
+                                       leaf_delay=int(rng.integers(0, 15)))
                 hits, _ = ae.ae_search(idx, [P], scheme, [H], options=opts)
                 assert_same(hits, want_hits(T, P, scheme, H), f"case {case} H {H} seed {seed_on}")
         idx.close()
