@@ -29,7 +29,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from workloads import DNA_SCALE_H, Scheme, dna_scale_query, dna_scale_text, dna_small  # noqa: E402
+from workloads import DNA_SCALE_H, Scheme, dna_scale_bench, dna_small  # noqa: E402
 
 METRIC = "effective GCUPS (m*n/time) at bit-exact hits, batched"
 
@@ -76,15 +76,7 @@ def make_workload(args):
                              "150-300 bp copies (10% subs, 2% indels), <1,-3,-5,-2>, H=30",
                  "n": int(wl.text.size), "queries": 1, "sum_m": int(wl.queries[0].size)})
     lengths = [int(x) for x in args.lengths.split(",")]
-    seed = 20120802
-    text = dna_scale_text(seed, args.n)
-    rng = np.random.default_rng(seed + 1)
-    queries, H = [], []
-    for m in lengths:
-        for _ in range(args.per_length):
-            q, _ = dna_scale_query(text, m, rng)
-            queries.append(q)
-            H.append(DNA_SCALE_H.get(m, 21))
+    text, queries, H, _ = dna_scale_bench(n=args.n, lengths=lengths, per_length=args.per_length)
     desc = {"workload": f"dna_scale: {args.n:,} bp i.i.d. text at 41% GC; {args.per_length} queries each of "
                         f"{'/'.join(str(x) for x in lengths)} bp with 1% planted from the text at 5-15% "
                         f"divergence; <1,-3,-5,-2>; H={'/'.join(str(DNA_SCALE_H.get(m, 21)) for m in lengths)} "

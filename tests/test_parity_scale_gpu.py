@@ -1,0 +1,115 @@
+"""Parity at the benchmark's full size, in the benchmark's launch configuration.
+
+The 100 Mbp DNA workload (8 queries each of 10 kbp, 100 kbp and 1 Mbp with
+planted homologs) is searched exactly as bench.py does it, through
+ae_search_device. The oracle cannot redo all 8.9e14 cells, so it checks sampled
+windows of (text ends [a, b]) x (query ends < j0) exactly.
+
+Why a window is exact: an alignment that ends at query position j < j0 uses at
+most j0 query letters. By the argument of Theorem 1 (Eq. 1 with m = j0), a
+result that reaches H then spans at most L_max(j0) text letters. So the
+full-matrix oracle run on T[a - L_max(j0) .. b] x P[0 .. j0) computes the true
+largest similarity of every cell in the window. The GPU results falling in the
+window must equal the oracle's results there, hit for hit.
+
+The windows are: every planted homolog of the 10 kbp queries with the whole
+query; two planted homologs of 100 kbp queries with the whole query; random
+text windows with query prefixes for the other queries.
+"""
+import os
+import time
+from concurrent.futures import ProcessPoolExecutor
+import multiprocessing as mp
+
+import numpy as np
+import pytest
+
+import oracle
+from workloads import Scheme, dna_scale_bench
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_1208_0274_gb300 import ae  # noqa: E402
+
+SCHEME = Scheme(1, -3, -5, -2)
+
+
+def _oracle_window(args):
+    text_slice, a0, a, q_prefix, H = args
+    oi, oj, os_ = oracle.sw_hits(text_slice, q_prefix, SCHEME, H, row_lo=a - a0)
+    return oi + a0, oj, os_
+
+
+def _windows(text, queries, H, spans, rng):
+    n = text.size
+    out = []   # (query index, a, b, j0)
+    for qi, (q, sp) in enumerate(zip(queries, spans)):
+        m = q.size
+        if m <= 10_000:
+            for (s, L, y) in sp:
+                out.append((qi, max(0, s - 300), min(n - 1, s + L + 300), m))
+            r = int(rng.integers(0, n - 30_000))
+            out.append((qi, r, r + 30_000, m))
+        elif m <= 100_000:
+            if qi % 8 < 2:
+                s, L, y = sp[0]
+                out.append((qi, max(0, s - 300), min(n - 1, s + L + 300), m))
+            else:
+                r = int(rng.integers(0, n - 200_000))
+                out.append((qi, r, r + 200_000, 20_000))
+        else:
+            r = int(rng.integers(0, n - 150_000))
+            out.append((qi, r, r + 150_000, 30_000))
+            for (s, L, y) in sp:
+                if y + L + 100 <= 30_000:
+                    out.append((qi, max(0, s - 300), min(n - 1, s + L + 300), 30_000))
+    return out
+
+
+def test_full_size_workload_windows_match_oracle():
+    oracle.build()
+    text, queries, H, spans = dna_scale_bench()
+    idx = ae.ae_index_build(text, ae.AE_DNA)
+    seq = np.concatenate(queries)
+    offsets = np.concatenate([[0], np.cumsum([q.size for q in queries])]).astype(np.int64)
+    d_seq = torch.from_numpy(seq).cuda()
+    opts = ae.make_options(profile=1)        # the benchmark's options
+    cap = 1 << 26
+    out = torch.empty(cap * 16, dtype=torch.uint8, device="cuda")
+    st, counts = ae.ae_search_device(idx, d_seq.data_ptr(), offsets, SCHEME, H, out.data_ptr(), cap, options=opts)
+    assert st == ae.AE_OK, ae.strerror(st)
+    hits = out[: int(counts.sum()) * 16].cpu().numpy().view(ae.HIT_DTYPE)
+    starts = np.concatenate([[0], np.cumsum(counts)])
+    per_query = [hits[starts[k]:starts[k + 1]] for k in range(len(queries))]
+    assert all(np.all(np.diff(p["text_end"]) >= 0) for p in per_query)
+
+    wins = _windows(text, queries, H, spans, np.random.default_rng(77))
+    jobs = []
+    for (qi, a, b, j0) in wins:
+        Lmax = oracle.length_bound(j0, H[qi], SCHEME)[1]
+        a0 = max(0, a - Lmax)
+        jobs.append((text[a0:b + 1].copy(), a0, a, queries[qi][:j0].copy(), H[qi]))
+    t0 = time.time()
+    workers = min(len(jobs), max(1, (os.cpu_count() or 2) - 1))
+    with ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        results = list(ex.map(_oracle_window, jobs))
+    checked = 0
+    for (qi, a, b, j0), (oi, oj, os_) in zip(wins, results):
+        g = per_query[qi]
+        sel = (g["text_end"] >= a) & (g["text_end"] <= b) & (g["query_end"] < j0)
+        got = g[sel]
+        want = np.zeros(oi.size, dtype=ae.HIT_DTYPE)
+        want["text_end"], want["query_end"], want["score"] = oi, oj, os_
+        if not np.array_equal(got, want):
+            gs = {(int(x), int(y)): int(z) for x, y, z in got}
+            ws = {(int(x), int(y)): int(z) for x, y, z in want}
+            bad = [(k, gs.get(k), ws.get(k)) for k in set(gs) | set(ws) if gs.get(k) != ws.get(k)][:5]
+            raise AssertionError(f"query {qi} window [{a}, {b}] x [0, {j0}): {len(got)} vs {len(want)}: {bad}")
+        checked += want.size
+    print(f"{len(wins)} windows, {checked} hits identical, oracle {time.time() - t0:.0f} s")
+    assert checked > 10_000
+    idx.close()

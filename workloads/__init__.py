@@ -251,6 +251,21 @@ def dna_scale(seed=20120802, n=100_000_000, lengths=(10_000, 100_000, 1_000_000)
                      "gc": 0.41, "planted": spans})
 
 
+def dna_scale_bench(seed=20120802, n=100_000_000, lengths=(10_000, 100_000, 1_000_000), per_length=8):
+    """The benchmark's scaled DNA workload: (text, queries, H, planted spans).
+    Spans are (text start, length, query start) of each planted segment."""
+    text = dna_scale_text(seed, n)
+    rng = np.random.default_rng(seed + 1)
+    queries, H, spans = [], [], []
+    for m in lengths:
+        for _ in range(per_length):
+            q, sp = dna_scale_query(text, m, rng)
+            queries.append(q)
+            H.append(DNA_SCALE_H.get(m, _nearest_H(m)))
+            spans.append(sp)
+    return text, queries, H, spans
+
+
 def _nearest_H(m):
     keys = sorted(DNA_SCALE_H)
     k = min(keys, key=lambda x: abs(math.log(x) - math.log(max(m, 1))))
