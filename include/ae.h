@@ -87,6 +87,7 @@ typedef struct {
     int64_t entries_leaf;   /* of `entries`, those written by the text-position sweep */
     int64_t launches;       /* kernel launches issued by the search */
     int32_t levels;         /* trie levels expanded */
+    int32_t levels_int16;   /* of them, levels whose rows were int16x2 pairs */
     int32_t seed_depth;     /* depth the trie walk started at */
     double  ms_trie, ms_leaf, ms_reduce, ms_total;   /* host wall time per phase */
     /* with ae_options.profile: device time of the kernels, by kind, from CUDA
@@ -110,6 +111,9 @@ typedef struct {
     int32_t profile;        /* 1: time kernel groups with CUDA events (ae_stats.ms_k_*) */
     int32_t leaf_delay;     /* levels (0-14) a single-occurrence trie node keeps expanding in the
                                trie walk before its row moves to the text-position sweep */
+    int32_t int16_limit;    /* trie rows are stored as int16x2 (M, G_a) pairs while depth * g_max
+                               stays <= this (<= 32000; 0 = int32 throughout); past it the
+                               frontier is unpacked to int32 and the walk continues exactly */
 } ae_options;
 
 /* Fill *opt with the defaults. */

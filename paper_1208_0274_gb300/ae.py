@@ -42,7 +42,7 @@ class ae_options(ctypes.Structure):
     _fields_ = [("qprefix_seed", ctypes.c_int32), ("leaf_segment", ctypes.c_int32),
                 ("item_columns", ctypes.c_int64), ("batch_columns", ctypes.c_int64),
                 ("leaf_capacity", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("leaf_delay", ctypes.c_int32)]
+                ("leaf_delay", ctypes.c_int32), ("int16_limit", ctypes.c_int32)]
 
 
 class ae_stats(ctypes.Structure):
@@ -51,7 +51,7 @@ class ae_stats(ctypes.Structure):
                 ("injections", ctypes.c_int64), ("raw_hits", ctypes.c_int64),
                 ("hits", ctypes.c_int64), ("entries_leaf", ctypes.c_int64),
                 ("launches", ctypes.c_int64), ("levels", ctypes.c_int32),
-                ("seed_depth", ctypes.c_int32), ("ms_trie", ctypes.c_double),
+                ("levels_int16", ctypes.c_int32), ("seed_depth", ctypes.c_int32), ("ms_trie", ctypes.c_double),
                 ("ms_leaf", ctypes.c_double), ("ms_reduce", ctypes.c_double),
                 ("ms_total", ctypes.c_double), ("ms_k_expand", ctypes.c_double),
                 ("ms_k_leaf", ctypes.c_double), ("ms_k_sort", ctypes.c_double),

@@ -109,6 +109,39 @@ __device__ __forceinline__ int bwt_letter(const IndexView &ix, uint32_t k) {
     }
 }
 
+// ---- the int16x2 route of the trie walk.  A row entry's (M, G_a) pair is
+// stored in one 32-bit word, M in the low and G_a in the high halfword.  Live
+// states are positive and at most depth * g_max, which the engine keeps below
+// 32,768 while it uses this route; a dead state is stored as AE_DEAD16, far
+// enough from -32,768 that adding a gap charge cannot wrap.
+#define AE_DEAD16 (-16000)
+
+__device__ __forceinline__ uint32_t pack_mg(int32_t M, int32_t Ga) {
+    const int32_t m = M > 0 ? M : AE_DEAD16, g = Ga > 0 ? Ga : AE_DEAD16;
+    return ((uint32_t)m & 0xFFFFu) | ((uint32_t)g << 16);
+}
+__device__ __forceinline__ int32_t mg_lo(uint32_t v) {
+    const int32_t x = (int32_t)(int16_t)(v & 0xFFFFu);
+    return x > 0 ? x : AE_NEG;
+}
+__device__ __forceinline__ int32_t mg_hi(uint32_t v) {
+    const int32_t x = (int32_t)(int16_t)(v >> 16);
+    return x > 0 ? x : AE_NEG;
+}
+// Vertical gap of Section 2.2, G_a' = max(G_a + s_s, M + s_g + s_s), on the
+// packed pair: swap the halfwords and take one DPX add-max per halfword.
+__device__ __forceinline__ int32_t gap_from_mg(uint32_t mg, int32_t ss, int32_t oe) {
+    const uint32_t sw = __byte_perm(mg, 0, 0x1032);                       // G_a | M << 16
+    const uint32_t c = __vadd2(mg, (uint32_t)oe & 0xFFFFu);                // low: M + s_g + s_s
+    const uint32_t r = __viaddmax_s16x2(sw, (uint32_t)ss & 0xFFFFu, c);   // low: max(G_a + s_s, c)
+    const int32_t x = (int32_t)(int16_t)(r & 0xFFFFu);
+    return x > AE_DEAD16 / 2 ? x : AE_NEG;
+}
+// The same update on int32 states (AE_NEG stays far below every live value).
+__device__ __forceinline__ int32_t gap_from_i32(int32_t M, int32_t Ga, int32_t ss, int32_t oe) {
+    return __viaddmax_s32(Ga, ss, M + oe);
+}
+
 __device__ __forceinline__ void load_matrix(const ScoreView &sc, int8_t *smat) {
     for (int t = threadIdx.x; t < AE_MAX_SIGMA * AE_MAX_SIGMA; t += blockDim.x) smat[t] = sc.mat[t];
     __syncthreads();

@@ -383,6 +383,10 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
     int cur = 0;
     int64_t F = 0;
     int depth = d0;
+    // int16x2 rows while every live state fits: states at depth d are at most
+    // d * g_max; past the limit the frontier is unpacked to int32 once
+    bool i16 = opt.int16_limit > 0 && (int64_t)(d0 + 1) * sc.gmax <= opt.int16_limit;
+    int64_t cur_ent = 0;
     if (d0 >= 1) {
         // ---- seed: (item, (d0)-gram) keys of every start column, sorted
         std::vector<int64_t> ipos(nitems + 1, 0);
@@ -404,6 +408,7 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
         sa.nitems = nitems;
         sa.d0 = d0;
         sa.npos = npos;
+        sa.int16 = i16 ? 1 : 0;
         ensure(w->sk0, npos * 8, st);
         ensure(w->sv0, npos * 4, st);
         ensure(w->sk1, npos * 8, st);
@@ -435,6 +440,7 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
         CU(cudaMemcpyAsync(tot(), w->totals.p, 8, cudaMemcpyDeviceToHost, st));
         sync();
         F = (int64_t)tot()[0];
+        cur_ent = npos;
     } else {
         // ---- root: one node per item with the implicit row M(0, j) = 0
         std::vector<Node> roots(nitems);
@@ -466,6 +472,13 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
     ensure(w->totals, 64, st);
     ensure(w->ctr, sizeof(LevelCounters), st);
     while (F > 0 && depth <= L_max_all) {
+        if (i16 && (int64_t)(depth + 1) * sc.gmax > opt.int16_limit) {
+            ensure(w->aGa[cur], std::max<int64_t>(cur_ent, 1) * 4, st);
+            prof.mark(K_OTHER);
+            ae_mg_to_i32(ptr<int32_t>(w->aM[cur]), ptr<int32_t>(w->aGa[cur]), cur_ent, st);
+            prof.mark(K_OTHER);
+            i16 = false;
+        }
         // children per node (backward-search step per letter), scanned into
         // segment and triple offsets
         for (int k = 0; k < 2; ++k) {
@@ -516,6 +529,7 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
         ra.ctr = ptr<LevelCounters>(w->ctr);
         ra.stats = ptr<DevStats>(w->stats);
         ra.leaf_delay = opt.leaf_delay;
+        ra.int16 = i16 ? 1 : 0;
         // count pass: exact output sizes of this level
         LevelCounters h0;
         memset(&h0, 0, sizeof(h0));
@@ -534,7 +548,7 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
         const int64_t lf_ent = (int64_t)hc.c_lf_ent, lf_node = (int64_t)hc.c_lf_node, hits = (int64_t)hc.c_hits;
         ensure(w->aj[nxt], std::max<int64_t>(fr_ent, 1) * 4, st);
         ensure(w->aM[nxt], std::max<int64_t>(fr_ent, 1) * 4, st);
-        ensure(w->aGa[nxt], std::max<int64_t>(fr_ent, 1) * 4, st);
+        if (!i16) ensure(w->aGa[nxt], std::max<int64_t>(fr_ent, 1) * 4, st);
         ensure(w->nodes[nxt], std::max<int64_t>(fr_node, 1) * sizeof(Node), st);
         ensure_keep(w->lj, (size_t)(lf_ent_base + lf_ent + 1) * 4, (size_t)lf_ent_base * 4, st);
         ensure_keep(w->lM, (size_t)(lf_ent_base + lf_ent + 1) * 4, (size_t)lf_ent_base * 4, st);
@@ -570,8 +584,10 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
         rh_base += hits;
         cur = nxt;
         F = fr_node;
+        cur_ent = fr_ent;
         ++depth;
         stats.levels++;
+        if (i16) stats.levels_int16++;
     }
     {
         LevelCounters hc;
@@ -815,7 +831,7 @@ ae_status search_core(const ae_index *idx, Workspace *w, const int64_t *offsets,
     ae_options_default(&s.opt);
     if (opt) s.opt = *opt;
     if (s.opt.item_columns < 1 || s.opt.batch_columns < 1 || s.opt.leaf_capacity < 64 || s.opt.leaf_segment < 0 ||
-        s.opt.leaf_delay < 0 || s.opt.leaf_delay > 14)
+        s.opt.leaf_delay < 0 || s.opt.leaf_delay > 14 || s.opt.int16_limit < 0 || s.opt.int16_limit > 32000)
         return AE_EINVAL;
     ae_status e = make_score(scoring, s.ix.sigma, s.sc);
     if (e != AE_OK) return e;
@@ -925,6 +941,7 @@ void ae_options_default(ae_options *opt) {
     opt->leaf_capacity = 4096;
     opt->profile = 0;
     opt->leaf_delay = 8;
+    opt->int16_limit = 32000;
 }
 
 const char *ae_strerror(int32_t status) {

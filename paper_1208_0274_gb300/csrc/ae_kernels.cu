@@ -276,8 +276,12 @@ __global__ void k_seed_nodes(SeedArgs a, const uint64_t *keys, const uint32_t *v
     const uint64_t gmask = (1ull << (bits * a.d0)) - 1ull;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
         aj[t] = (int32_t)vals[t] + a.d0 - 1;
-        aM[t] = a.d0 * a.sc.sa;
-        aGa[t] = AE_NEG;
+        if (a.int16) {
+            reinterpret_cast<uint32_t *>(aM)[t] = pack_mg(a.d0 * a.sc.sa, AE_NEG);
+        } else {
+            aM[t] = a.d0 * a.sc.sa;
+            aGa[t] = AE_NEG;
+        }
         if (flags[t]) {
             uint64_t key = keys[t];
             uint64_t gram = key & gmask;
@@ -473,7 +477,7 @@ __global__ void __launch_bounds__(128, 6) k_leaf(LeafArgs a) {
                             const int32_t D = pMv + delta_of(sc, smat, c, P[j]);
                             Dp = D > tA ? D : AE_NEG;
                         }
-                        const int32_t gap = max(Ga > AE_NEG ? Ga + sc.ss : AE_NEG, M + oe);
+                        const int32_t gap = gap_from_i32(M, Ga, sc.ss, oe);
                         GaA = gap > tA ? gap : AE_NEG;
                         MpA = max(Dp, GaA);
                         hasB = (j + 1 < m) && (j + 1 != jn);
@@ -662,7 +666,7 @@ __global__ void __launch_bounds__(128, 6) k_leaf(LeafArgs a) {
                         const int32_t tA = thr_of(j, m, H, g);
                         int32_t Dp = AE_NEG;
                         if (pjv + 1 == j && pMv > AE_NEG) Dp = pMv + delta_of(sc, smat, c, P[j]);
-                        int32_t gap = max(Ga > AE_NEG ? Ga + sc.ss : AE_NEG, M + oe);
+                        const int32_t gap = gap_from_i32(M, Ga, sc.ss, oe);
                         GaA = gap > tA ? gap : AE_NEG;
                         Dp = Dp > tA ? Dp : AE_NEG;
                         MpA = max(Dp, GaA);

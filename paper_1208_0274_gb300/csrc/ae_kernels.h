@@ -36,6 +36,7 @@ struct SeedArgs {
     int32_t nitems;
     int32_t d0;                // seed depth (>= 1)
     int64_t npos;
+    int32_t int16;             // 1: write the seed rows as packed int16x2 pairs into aM
 };
 // keys = (item << 2*d0... packed gram), vals = query start column y.
 void ae_seed_keys(const SeedArgs &a, uint64_t *keys, uint32_t *vals, cudaStream_t st);
@@ -99,8 +100,10 @@ struct RowsArgs {
     DevStats *stats;
     int32_t leaf_delay;                   // levels a single-occurrence child stays in the walk
     uint32_t *seg_cnt, *seg_hit;          // per segment: outputs and hits (count pass -> write pass)
+    int32_t int16;                        // 1: parent and frontier rows are packed int16x2 (M | G_a << 16) in pM / fM
 };
 void ae_rows(const RowsArgs &a, bool write, int blocks, cudaStream_t st);
+void ae_mg_to_i32(int32_t *M, int32_t *Ga, int64_t n, cudaStream_t st);
 struct LeafArgs {
     IndexView ix;
     ScoreView sc;

@@ -136,7 +136,7 @@ __device__ __forceinline__ uint64_t lower_bound_toff(const Seg *segs, uint64_t n
 // [s_first, s_last).  Pass 1 (WRITE = false) adds each segment's output and
 // hit counts into sm; pass 2 writes entries and hits at sm.base/hbase plus
 // the running counts.
-template <int SIGMA, bool WRITE>
+template <int SIGMA, bool WRITE, bool I16>
 __device__ void run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, uint64_t s_first, uint64_t s_last,
                          uint64_t t_beg, uint64_t t_end, unsigned long long &st0, unsigned long long &st1,
                          unsigned long long &st2) {
@@ -184,10 +184,16 @@ __device__ void run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, ui
         const int first_lane = 31 - __clz(heads & le);
         // neighbours inside the segment
         int32_t j = m, M = AE_NEG, Ga = AE_NEG;
+        uint32_t mg = 0;
         if (valid && !root) {
             j = a.pj[sg.poff + k];
-            M = a.pM[sg.poff + k];
-            Ga = a.pGa[sg.poff + k];
+            if (I16) {
+                mg = reinterpret_cast<const uint32_t *>(a.pM)[sg.poff + k];
+                M = mg_lo(mg);
+            } else {
+                M = a.pM[sg.poff + k];
+                Ga = a.pGa[sg.poff + k];
+            }
         }
         int32_t jn = __shfl_down_sync(FULL, j, 1);
         int32_t pjv = __shfl_up_sync(FULL, j, 1), pMv = __shfl_up_sync(FULL, M, 1);
@@ -197,7 +203,8 @@ __device__ void run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, ui
             if (lane == first_lane) {   // first lane of its segment in this chunk
                 if (k > 0) {
                     pjv = a.pj[sg.poff + k - 1];
-                    pMv = a.pM[sg.poff + k - 1];
+                    pMv = I16 ? mg_lo(reinterpret_cast<const uint32_t *>(a.pM)[sg.poff + k - 1])
+                              : a.pM[sg.poff + k - 1];
                 } else {
                     pjv = -2;
                     pMv = AE_NEG;
@@ -219,7 +226,7 @@ __device__ void run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, ui
                     const int32_t D = pMv + delta_of(sc, smat, c, P[j]);
                     Dprev = D > tA ? D : AE_NEG;
                 }
-                const int32_t gap = max(Ga > AE_NEG ? Ga + sc.ss : AE_NEG, M + oe);
+                const int32_t gap = I16 ? gap_from_mg(mg, sc.ss, oe) : gap_from_i32(M, Ga, sc.ss, oe);
                 Gap = gap > tA ? gap : AE_NEG;
                 MpA = max(Dprev, Gap);
                 GaA = Gap;
@@ -289,13 +296,15 @@ __device__ void run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, ui
         (void)overflow_task;
         uint64_t e0 = 0, h0 = 0;
         int32_t *oj = nullptr, *oM = nullptr, *oGa = nullptr;
+        // frontier rows of the int16 route are packed pairs (oGa = null)
+        const bool packed = I16 && kind1;
         if (valid) {
             e0 = sm.base[rel] + sm.cnt[rel] + (ci - cnt);
             h0 = sm.hbase[rel] + sm.hit[rel] + (hi - hcnt);
             if (kind1) {
                 oj = a.fj;
                 oM = a.fM;
-                oGa = a.fGa;
+                oGa = I16 ? nullptr : a.fGa;
             } else {
                 oj = a.lj;
                 oM = a.lM;
@@ -309,8 +318,12 @@ __device__ void run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, ui
         }
         if (o.aliveA) {
             oj[e0] = colA;
-            oM[e0] = o.MA;
-            oGa[e0] = GaA;
+            if (packed) {
+                reinterpret_cast<uint32_t *>(oM)[e0] = pack_mg(o.MA, GaA);
+            } else {
+                oM[e0] = o.MA;
+                oGa[e0] = GaA;
+            }
             const int tier = (Dprev > AE_NEG) + (Gap > AE_NEG) + (o.GbA > thr_of(colA, m, H, g));
             st0 += tier <= 1;
             st1 += tier == 2;
@@ -318,8 +331,12 @@ __device__ void run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, ui
         }
         if (o.aliveB) {
             oj[e0 + nA] = colA + 1;
-            oM[e0 + nA] = o.MB;
-            oGa[e0 + nA] = AE_NEG;
+            if (packed) {
+                reinterpret_cast<uint32_t *>(oM)[e0 + nA] = pack_mg(o.MB, AE_NEG);
+            } else {
+                oM[e0 + nA] = o.MB;
+                oGa[e0 + nA] = AE_NEG;
+            }
             const int tier = (Dk > AE_NEG) + (o.GbB > thr_of(colA + 1, m, H, g));
             st0 += tier <= 1;
             st1 += tier == 2;
@@ -356,8 +373,12 @@ __device__ void run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, ui
                 const int32_t col = s0 + tt;
                 const int32_t v = sc.sg - col * u + K;
                 rj[d0 + tt] = col;
-                rM[d0 + tt] = v;
-                rG[d0 + tt] = AE_NEG;
+                if (rG) {
+                    rM[d0 + tt] = v;
+                    rG[d0 + tt] = AE_NEG;
+                } else {
+                    reinterpret_cast<uint32_t *>(rM)[d0 + tt] = pack_mg(v, AE_NEG);
+                }
                 if (k1 && tt < rh) {
                     RangeHit r = {rlo, rhi, rq, col, v, 0};
                     a.rhits[hd + tt] = r;
@@ -374,7 +395,7 @@ __device__ void run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, ui
 // segments' counts, reserves its output ranges with one atomic per arena,
 // writes the child node / injection records, and recomputes and writes the
 // rows and the hits of multi-occurrence children.
-template <int SIGMA, bool WRITE>
+template <int SIGMA, bool WRITE, bool I16>
 __global__ void __launch_bounds__(RW_WARPS * 32, 4) k_rows(RowsArgs a) {
     __shared__ int8_t smat[AE_MAX_SIGMA * AE_MAX_SIGMA];
     __shared__ TaskSmem smem[RW_WARPS];
@@ -410,7 +431,7 @@ __global__ void __launch_bounds__(RW_WARPS * 32, 4) k_rows(RowsArgs a) {
                 sm.hit[r] = 0;
             }
             __syncwarp();
-            run_task<SIGMA, false>(a, smat, sm, s_first, s_last, t_beg, t_end, st0, st1, st2);
+            run_task<SIGMA, false, I16>(a, smat, sm, s_first, s_last, t_beg, t_end, st0, st1, st2);
             __syncwarp();
         } else {
             for (uint64_t r = lane; r < nsg; r += 32) {
@@ -520,7 +541,7 @@ __global__ void __launch_bounds__(RW_WARPS * 32, 4) k_rows(RowsArgs a) {
             sm.hit[r] = 0;
         }
         __syncwarp();
-        run_task<SIGMA, true>(a, smat, sm, s_first, s_last, t_beg, t_end, st0, st1, st2);
+        run_task<SIGMA, true, I16>(a, smat, sm, s_first, s_last, t_beg, t_end, st0, st1, st2);
         __syncwarp();
     }
     if (a.stats) {
@@ -567,13 +588,37 @@ void ae_compact_segs(const ChildrenArgs &a, const uint64_t *seg_off, const uint6
         k_compact<20><<<grid_for(a.nnodes, 256), 256, 0, st>>>(a, seg_off, trip_off, segs);
 }
 
+template <int SIGMA, bool I16>
+void launch_rows(const RowsArgs &a, bool write, int blocks, cudaStream_t st) {
+    if (write)
+        k_rows<SIGMA, true, I16><<<blocks, RW_WARPS * 32, 0, st>>>(a);
+    else
+        k_rows<SIGMA, false, I16><<<blocks, RW_WARPS * 32, 0, st>>>(a);
+}
+
 void ae_rows(const RowsArgs &a, bool write, int blocks, cudaStream_t st) {
     ++g_launches;
     if (a.ix.sigma == 4) {
-        if (write) k_rows<4, true><<<blocks, RW_WARPS * 32, 0, st>>>(a);
-        else k_rows<4, false><<<blocks, RW_WARPS * 32, 0, st>>>(a);
+        if (a.int16) launch_rows<4, true>(a, write, blocks, st);
+        else launch_rows<4, false>(a, write, blocks, st);
     } else {
-        if (write) k_rows<20, true><<<blocks, RW_WARPS * 32, 0, st>>>(a);
-        else k_rows<20, false><<<blocks, RW_WARPS * 32, 0, st>>>(a);
+        if (a.int16) launch_rows<20, true>(a, write, blocks, st);
+        else launch_rows<20, false>(a, write, blocks, st);
     }
+}
+
+// Leave the int16 route: unpack a level arena of (M | G_a << 16) pairs into
+// int32 M (in place) and G_a.
+__global__ void k_mg_to_i32(int32_t *M, int32_t *Ga, int64_t n) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t v = reinterpret_cast<const uint32_t *>(M)[t];
+        Ga[t] = mg_hi(v);
+        M[t] = mg_lo(v);
+    }
+}
+
+void ae_mg_to_i32(int32_t *M, int32_t *Ga, int64_t n, cudaStream_t st) {
+    if (n <= 0) return;
+    ++g_launches;
+    k_mg_to_i32<<<grid_for(n, 256), 256, 0, st>>>(M, Ga, n);
 }

@@ -71,12 +71,14 @@ def test_dna_small_workload_full_parity(small):
     assert_same(hits, want, "dna_small")
     st = ae.ae_last_stats()
     assert st["entries"] > 0 and st["hits"] == want.size and st["seed_depth"] == 3
+    assert st["levels_int16"] == st["levels"]          # DNA rows never leave the int16 route here
 
 
 @pytest.mark.parametrize("opts", [dict(qprefix_seed=0), dict(leaf_segment=1), dict(leaf_segment=7),
                                   dict(item_columns=97), dict(item_columns=250, batch_columns=300),
                                   dict(leaf_capacity=64), dict(leaf_delay=0), dict(leaf_delay=3),
-                                  dict(leaf_delay=14, leaf_segment=5)])
+                                  dict(leaf_delay=14, leaf_segment=5), dict(int16_limit=0),
+                                  dict(int16_limit=6), dict(int16_limit=13, leaf_delay=14)])
 def test_dna_small_knobs_do_not_change_hits(small, opts):
     wl, idx = small
     want = want_hits(wl.text, wl.queries[0], wl.scheme, wl.H[0])
@@ -101,7 +103,8 @@ def test_random_planted_cases(si):
             for seed_on in (1, 0):
                 opts = ae.make_options(qprefix_seed=seed_on, leaf_segment=int(rng.integers(1, 40)),
                                        item_columns=int(rng.integers(3, 500)),
-                                       leaf_delay=int(rng.integers(0, 15)))
+                                       leaf_delay=int(rng.integers(0, 15)),
+                                       int16_limit=int(rng.choice([0, 5, 9, 32000])))
                 hits, _ = ae.ae_search(idx, [P], scheme, [H], options=opts)
                 assert_same(hits, want_hits(T, P, scheme, H), f"case {case} H {H} seed {seed_on}")
         idx.close()
@@ -147,8 +150,10 @@ def test_protein_blosum62():
         flip = rng.random(L) < 0.4
         seg[flip] = np.frombuffer(PROTEIN, dtype=np.uint8)[rng.integers(0, 20, size=int(flip.sum()))]
         P[m // 4:m // 4 + L] = seg
-        hits, _ = ae.ae_search(idx, [P], scheme, [H])
-        assert_same(hits, want_hits(T, P, scheme, H, alphabet=PROTEIN), f"protein m={m}")
+        want = want_hits(T, P, scheme, H, alphabet=PROTEIN)
+        for lim in (32000, 40, 0):
+            hits, _ = ae.ae_search(idx, [P], scheme, [H], options=ae.make_options(int16_limit=lim))
+            assert_same(hits, want, f"protein m={m} int16_limit={lim}")
     idx.close()
 
 
