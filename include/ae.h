@@ -192,6 +192,18 @@ ae_status ae_search_device_static(const ae_index *idx, const uint8_t *d_seq, con
                                   const ae_options *opt, ae_hit *d_hits, int64_t capacity,
                                   int64_t *counts, void *stream);
 
+/* Working memory.  ae_search and ae_search_device keep one workspace per
+ * (index, stream): device buffers that only grow, reused by the next search on
+ * that stream.  Searches on different streams run concurrently (an index is
+ * shareable across threads); searches on one stream are serialised by the
+ * library.  ae_workspace_info reports the device bytes held by the workspace
+ * of `stream` (0 if it has none) and by all workspaces of the process;
+ * ae_workspace_release waits for that stream's running search, then frees its
+ * workspace (the next search on the stream starts a new one).
+ * Errors: AE_EINVAL (idx NULL). */
+ae_status ae_workspace_info(const ae_index *idx, void *stream, int64_t *bytes, int64_t *process_bytes);
+ae_status ae_workspace_release(ae_index *idx, void *stream);
+
 /* Counters of the calling thread's last search. */
 ae_status ae_last_stats(ae_stats *out);
 

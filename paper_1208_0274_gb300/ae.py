@@ -78,6 +78,8 @@ def _load():
         "ae_hits_free": (None, [V]),
         "ae_search_device": (I32, [V, V, V, I32, V, V, V, V, I64, V, V]),
         "ae_search_device_static": (I32, [V, V, V, I32, V, V, V, V, I64, V, V]),
+        "ae_workspace_info": (I32, [V, V, V, V]),
+        "ae_workspace_release": (I32, [V, V]),
         "ae_last_stats": (I32, [V]),
         "ae_suffix_array": (I32, [V, I64, I32, V]),
         "ae_plan": (I32, [I64, I32, V, I32, V, V, V]),
@@ -278,6 +280,18 @@ def ae_search_device_static(index, d_seq_ptr, offsets, scheme, H, d_hits_ptr, ca
     if st not in (AE_OK, AE_EOVERFLOW, AE_EUNSUPPORTED):
         _check(st, "ae_search_device_static")
     return st, counts[:nq].copy()
+
+
+def ae_workspace_info(index, stream=None):
+    """(bytes held by the workspace of `stream`, bytes held by all workspaces)."""
+    b, t = ctypes.c_int64(0), ctypes.c_int64(0)
+    _check(lib.ae_workspace_info(index.handle, _stream_handle(stream), ctypes.byref(b), ctypes.byref(t)),
+           "ae_workspace_info")
+    return b.value, t.value
+
+
+def ae_workspace_release(index, stream=None):
+    _check(lib.ae_workspace_release(index.handle, _stream_handle(stream)), "ae_workspace_release")
 
 
 def ae_last_stats():

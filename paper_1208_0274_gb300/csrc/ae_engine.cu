@@ -16,6 +16,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <atomic>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -54,7 +55,7 @@ struct ae_error {
         if (_e != cudaSuccess) throw ae_error{AE_ECUDA}; \
     } while (0)
 
-int64_t g_ws_bytes = 0;   // device bytes held by all workspaces of the process
+std::atomic<int64_t> g_ws_bytes{0};   // device bytes held by all workspaces of the process
 bool mem_trace() {
     static int on = -1;
     if (on < 0) on = getenv("AE_TRACE_MEM") != nullptr;
@@ -70,7 +71,7 @@ void trace_alloc(size_t nb, bool ok) {
     size_t fr = 0, tot = 0;
     cudaMemGetInfo(&fr, &tot);
     fprintf(stderr, "[ae mem] alloc %.3f GB %s; workspaces hold %.3f GB; device free %.3f of %.3f GB\n", nb / 1e9,
-            ok ? "ok" : "FAILED", g_ws_bytes / 1e9, fr / 1e9, tot / 1e9);
+            ok ? "ok" : "FAILED", g_ws_bytes.load() / 1e9, fr / 1e9, tot / 1e9);
 }
 
 // Grow-only device buffer; contents are not preserved.
@@ -154,30 +155,39 @@ struct Workspace {
     // pinned host staging
     uint64_t *h_tot = nullptr;
     bool h_tot_static = false;
+    uint8_t *h_stage = nullptr;   // pinned copy of the ASCII queries of ae_search (grow-only)
+    size_t h_stage_bytes = 0;
     int32_t leaf_cap = 0;
+    std::mutex busy;              // one search at a time per workspace (per stream)
+
+    int64_t device_bytes() {
+        int64_t t = 0;
+        for (DevBuf *b : bufs())
+            if (!b->carved) t += (int64_t)b->bytes;
+        return t;
+    }
+
+    std::vector<DevBuf *> bufs() {
+        return {&ascii, &codes, &qoff, &qm, &qH, &items, &item_pos, &bad, &aj[0], &aj[1], &aM[0],
+                &aM[1], &aGa[0], &aGa[1], &nodes[0], &nodes[1], &cnt[0], &cnt[1], &cnt[2], &cnt[3],
+                &cnt[4], &off[0], &off[1], &off[2], &off[3], &off[4], &totals, &scan_tmp, &lj, &lM,
+                &lGa, &inj, &rhits, &sk0, &sv0, &sk1, &sv1, &sort_tmp, &hkey, &hscore, &hcount, &hk1,
+                &hv1, &scratch, &next_seg, &uniq, &uflags, &uoff, &qcount, &stats, &segs, &ctr, &seg_cnt, &seg_hit};
+    }
 
     ~Workspace() {
-        DevBuf *all[] = {&ascii, &codes, &qoff, &qm, &qH, &items, &item_pos, &bad, &aj[0], &aj[1], &aM[0],
-                         &aM[1], &aGa[0], &aGa[1], &nodes[0], &nodes[1], &cnt[0], &cnt[1], &cnt[2], &cnt[3],
-                         &cnt[4], &off[0], &off[1], &off[2], &off[3], &off[4], &totals, &scan_tmp, &lj, &lM,
-                         &lGa, &inj, &rhits, &sk0, &sv0, &sk1, &sv1, &sort_tmp, &hkey, &hscore, &hcount, &hk1,
-                         &hv1, &scratch, &next_seg, &uniq, &uflags, &uoff, &qcount, &stats, &segs, &ctr, &seg_cnt, &seg_hit};
-        for (DevBuf *b : all)
+        for (DevBuf *b : bufs())
             if (b->p && !b->carved) {
                 cudaFree(b->p);
                 g_ws_bytes -= (int64_t)b->bytes;
             }
         if (h_tot && !h_tot_static) cudaFreeHost(h_tot);
+        if (h_stage) cudaFreeHost(h_stage);
     }
 
     // Forget every carved buffer (the next static call carves them again).
     void forget_carved() {
-        DevBuf *all[] = {&ascii, &codes, &qoff, &qm, &qH, &items, &item_pos, &bad, &aj[0], &aj[1], &aM[0],
-                         &aM[1], &aGa[0], &aGa[1], &nodes[0], &nodes[1], &cnt[0], &cnt[1], &cnt[2], &cnt[3],
-                         &cnt[4], &off[0], &off[1], &off[2], &off[3], &off[4], &totals, &scan_tmp, &lj, &lM,
-                         &lGa, &inj, &rhits, &sk0, &sv0, &sk1, &sv1, &sort_tmp, &hkey, &hscore, &hcount, &hk1,
-                         &hv1, &scratch, &next_seg, &uniq, &uflags, &uoff, &qcount, &stats, &segs, &ctr, &seg_cnt, &seg_hit};
-        for (DevBuf *b : all) {
+        for (DevBuf *b : bufs()) {
             b->p = nullptr;
             b->bytes = 0;
             b->carved = false;
@@ -1025,10 +1035,21 @@ ae_status ae_search(const ae_index *idx, const ae_query *queries, int32_t nq, co
     }
     try {
         Workspace *w = workspace_for(idx, st);
+        std::lock_guard<std::mutex> busy(w->busy);
         const int64_t total_len = off[nq];
         uint8_t *h_ascii = nullptr;
         if (total_len > 0) {
-            CU(cudaMallocHost(&h_ascii, (size_t)total_len));
+            if ((size_t)total_len > w->h_stage_bytes) {
+                CU(cudaStreamSynchronize(st));
+                if (w->h_stage) cudaFreeHost(w->h_stage);
+                w->h_stage = nullptr;
+                w->h_stage_bytes = 0;
+                size_t nb = std::max((size_t)total_len, w->h_stage_bytes + w->h_stage_bytes / 4);
+                nb = std::max<size_t>(nb, 1 << 16);
+                CU(cudaMallocHost(&w->h_stage, nb));
+                w->h_stage_bytes = nb;
+            }
+            h_ascii = w->h_stage;
             for (int q = 0; q < nq; ++q)
                 if (queries[q].len) memcpy(h_ascii + off[q], queries[q].seq, (size_t)queries[q].len);
         }
@@ -1043,7 +1064,6 @@ ae_status ae_search(const ae_index *idx, const ae_query *queries, int32_t nq, co
         int bad = 0;
         CU(cudaMemcpyAsync(&bad, w->bad.p, 4, cudaMemcpyDeviceToHost, st));
         CU(cudaStreamSynchronize(st));
-        if (h_ascii) cudaFreeHost(h_ascii);
         if (bad) return AE_EINVAL;
         ae_hit *dev = nullptr;
         std::vector<int64_t> cnt;
@@ -1083,6 +1103,7 @@ ae_status ae_search_device(const ae_index *idx, const uint8_t *d_seq, const int6
     if (offsets[0] != 0 || total_len < 0) return AE_EINVAL;
     try {
         Workspace *w = workspace_for(idx, st);
+        std::lock_guard<std::mutex> busy(w->busy);
         ensure(w->codes, std::max<int64_t>(total_len, 1), st);
         ensure(w->bad, 4, st);
         CU(cudaMemsetAsync(w->bad.p, 0, 4, st));
@@ -1109,6 +1130,47 @@ ae_status ae_search_device(const ae_index *idx, const uint8_t *d_seq, const int6
     } catch (const std::bad_alloc &) {
         return AE_ENOMEM;
     }
+    return AE_OK;
+}
+
+ae_status ae_workspace_info(const ae_index *idx, void *stream, int64_t *bytes, int64_t *process_bytes) {
+    if (!idx) return AE_EINVAL;
+    ae_index *x = const_cast<ae_index *>(idx);
+    int64_t b = 0;
+    {
+        std::lock_guard<std::mutex> g(x->mu);
+        for (auto &p : x->ws)
+            if (p.first == (cudaStream_t)stream) {
+                std::lock_guard<std::mutex> busy(p.second->busy);
+                b = p.second->device_bytes();
+            }
+    }
+    if (bytes) *bytes = b;
+    if (process_bytes) *process_bytes = g_ws_bytes.load();
+    return AE_OK;
+}
+
+ae_status ae_workspace_release(ae_index *idx, void *stream) {
+    if (!idx) return AE_EINVAL;
+    Workspace *w = nullptr;
+    {
+        std::lock_guard<std::mutex> g(idx->mu);
+        for (size_t k = 0; k < idx->ws.size(); ++k)
+            if (idx->ws[k].first == (cudaStream_t)stream) {
+                w = idx->ws[k].second;
+                idx->ws.erase(idx->ws.begin() + (long)k);
+                break;
+            }
+    }
+    if (!w) return AE_OK;
+    {
+        // wait for a search still running on this stream in another thread
+        std::lock_guard<std::mutex> busy(w->busy);
+        if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) {
+            cudaGetLastError();
+        }
+    }
+    delete w;
     return AE_OK;
 }
 
