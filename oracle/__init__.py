@@ -23,7 +23,12 @@ Contents (each follows the passage it cites):
 * ``length_bound`` (Eq. 1), ``q_prefix`` (Eq. 2), ``entry_bound`` (Lemma 4 and
   Eq. 4) — closed forms of the paper, used as pins of the analysis.
 
-Every function is parity-pinned by tests in ``tests/test_oracle_pins.py``.
+* ``mlp_oracle`` (submodule) — the work predictor's features, network,
+  gradients and Adam step in fp64, with optional bfloat16 rounding of matrix
+  operands; pinned in ``tests/test_mlp_oracle.py``.
+
+Every function of this file is parity-pinned by tests in
+``tests/test_oracle_pins.py``.
 """
 from __future__ import annotations
 
