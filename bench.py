@@ -44,6 +44,8 @@ def parse():
     p.add_argument("--requests", type=int, default=1000, help="dna_serve: number of requests")
     p.add_argument("--rate", type=float, default=200.0, help="dna_serve: Poisson arrival rate (1/s)")
     p.add_argument("--slots", type=int, default=3, help="dna_serve: concurrent search slots")
+    p.add_argument("--train-queries", type=int, default=256, help="dna_serve: searches logged to train the predictor")
+    p.add_argument("--work-budget", type=float, default=4e8, help="dna_serve: predicted DP entries per batch")
     p.add_argument("--lengths", type=str, default="10000,100000,1000000")
     p.add_argument("--per-length", type=int, default=8)
     p.add_argument("--n", type=int, default=100_000_000)
@@ -400,50 +402,81 @@ def run_ours(args):
 
 def run_serve(args):
     """Request loop: Poisson arrivals of DNA queries (70% of 200 bp-2 kbp, 30%
-    of 2-100 kbp, log-uniform) against the resident 100 Mbp index, served by
-    concurrent slots with admission by free device memory, then the same
-    arrivals served one query at a time.  Reports queries/s and p50/p99
-    latency of both; the hits of every request must be identical."""
+    of 2-100 kbp, log-uniform) against the resident 100 Mbp index.  The same
+    arrivals are served (1) by the learned policy: concurrent slots, requests
+    of least predicted work first within a work budget, predicted hit records
+    as buffer hints, admission by predicted device memory; (2) by FIFO
+    continuous batching (columns budget, admission by a per-letter memory
+    bound); (3) one query at a time.  Reports queries/s and p50/p99 latency of
+    each; the hits of every request must be identical across the three."""
     import torch
     ws, rank, local = dist_env()
     if rank != 0:
         return 0
     torch.cuda.set_device(local)
     from paper_1208_0274_gb300 import ae, serve
+    from paper_1208_0274_gb300.predictor import WorkPredictor
     text = dna_scale_text(n=args.n)
     wl = dna_serve(text, k=args.requests, rate=args.rate)
     scheme = wl.scheme
     idx = ae.ae_index_build(text, ae.AE_DNA)
-    reqs = [serve.Request(rid=k, query=q, H=int(h), arrival=float(a))
-            for k, (q, h, a) in enumerate(zip(wl.queries, wl.H, wl.arrivals))]
-    srv = serve.Server(idx, scheme, nslots=args.slots)
+
+    def fresh():
+        return [serve.Request(rid=k, query=q, H=int(h), arrival=float(a))
+                for k, (q, h, a) in enumerate(zip(wl.queries, wl.H, wl.arrivals))]
+
+    # predictor: trained on searches of other queries of the same mix, logged alone
+    t0 = time.perf_counter()
+    tw = dna_serve(text, seed=20120806, k=args.train_queries, rate=args.rate)
+    pred = WorkPredictor(idx, scheme, seed=1)
+    T = pred.log_searches(tw.queries, tw.H)
+    X = pred.features(tw.queries)
+    loss = pred.fit(X, T)
+    t_train = time.perf_counter() - t0
     warm = sorted(wl.queries, key=lambda q: -q.size)[:8]
-    srv.warmup(warm, [21] * len(warm))
-    clocks = Clocks(local)
-    clocks.start()
-    rep = srv.run(reqs)
-    clk = clocks.stop()
-    served = {r.rid: r.hits for r in rep.requests}
-    base_reqs = [serve.Request(rid=r.rid, query=r.query, H=r.H, arrival=r.arrival) for r in reqs]
-    warm_st = torch.cuda.Stream()
-    ae.ae_search(idx, warm, scheme, [21] * len(warm), stream=warm_st)
-    base = serve.one_at_a_time(idx, scheme, base_reqs, stream=warm_st)
-    same = all(np.array_equal(served[r.rid], r.hits) for r in base.requests)
+
+    def serve_once(**kw):
+        srv = serve.Server(idx, scheme, nslots=args.slots, **kw)
+        srv.warmup(warm, [21] * len(warm))
+        srv.leaf_sweeps, srv.batches_run = 0, 0
+        clocks = Clocks(local)
+        clocks.start()
+        rep = srv.run(fresh())
+        clk = clocks.stop()
+        out = {"queries_per_s": round(rep.qps, 3), "p50_ms": round(rep.p50_ms, 3), "p99_ms": round(rep.p99_ms, 3),
+               "wall_s": round(rep.wall, 3), "batches": rep.batches, "mean_batch": round(rep.mean_batch, 3),
+               "peak_concurrency": rep.peak_concurrency, "admission_waits": srv.admission_waits,
+               "leaf_sweeps": srv.leaf_sweeps}
+        for st in srv.streams:
+            ae.ae_workspace_release(idx, st)
+        return rep, out, clk
+
+    rep_l, learned, clk = serve_once(predictor=pred, work_budget=args.work_budget)
+    rep_f, fifo, _ = serve_once()
+    base_st = torch.cuda.Stream()
+    ae.ae_search(idx, warm, scheme, [21] * len(warm), stream=base_st)
+    base = serve.one_at_a_time(idx, scheme, fresh(), stream=base_st)
+    ref = {r.rid: r.hits for r in base.requests}
+    same = all(np.array_equal(ref[r.rid], r.hits) for r in rep_l.requests) and \
+        all(np.array_equal(ref[r.rid], r.hits) for r in rep_f.requests)
     sum_m = int(sum(q.size for q in wl.queries))
     line = {"metric": "queries/s and p50/p99 latency (ms) under Poisson arrivals, continuous batching",
-            "value": round(rep.qps, 3), "unit": "queries/s", "n_gpus": 1, "steps": 1, "warmup": 1,
-            "ms_per_step": round(rep.wall * 1000, 3), "higher_is_better": True, "scaling": "weak",
+            "value": learned["queries_per_s"], "unit": "queries/s", "n_gpus": 1, "steps": 1, "warmup": 1,
+            "ms_per_step": round(rep_l.wall * 1000, 3), "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int32", "data": "synthetic",
             "config": {"workload": f"dna_serve: {args.requests} requests, Poisson {args.rate:g}/s, DNA queries "
                                    f"200 bp-100 kbp (70% under 2 kbp, log-uniform) vs {args.n:,} bp index",
-                       "slots": args.slots, "sum_m": sum_m},
-            "p50_ms": round(rep.p50_ms, 3), "p99_ms": round(rep.p99_ms, 3),
-            "effective_gcups": round(sum_m * text.size / rep.wall / 1e9, 3),
-            "batches": rep.batches, "mean_batch": round(rep.mean_batch, 3),
-            "peak_concurrency": rep.peak_concurrency, "admission_waits": srv.admission_waits,
+                       "slots": args.slots, "sum_m": sum_m, "work_budget": args.work_budget},
+            "p50_ms": learned["p50_ms"], "p99_ms": learned["p99_ms"],
+            "effective_gcups": round(sum_m * text.size / rep_l.wall / 1e9, 3),
+            "learned": learned, "fifo": fifo,
             "one_at_a_time": {"queries_per_s": round(base.qps, 3), "p50_ms": round(base.p50_ms, 3),
                               "p99_ms": round(base.p99_ms, 3), "wall_s": round(base.wall, 3)},
-            "hits_identical": bool(same), "hits": int(sum(h.size for h in served.values())),
+            "predictor": {"train_queries": args.train_queries, "train_s": round(t_train, 3),
+                          "final_loss": round(float(loss), 5),
+                          "bytes_per_entry": round(pred.bytes_per_entry, 3), "fixed_bytes": int(pred.fixed_bytes),
+                          "hit_margin": round(pred.hit_margin, 3)},
+            "hits_identical": bool(same), "hits": int(sum(h.size for h in ref.values())),
             "clocks": clk}
     print(json.dumps(line), flush=True)
     idx.close()

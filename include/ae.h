@@ -99,6 +99,9 @@ typedef struct {
     int64_t leaf_max_steps;   /* longest text walk of one sweep task (positions) */
     int64_t leaf_max_width;   /* widest row met by the sweep (entries) */
     int64_t ws_bytes;         /* device bytes held by the library's working buffers */
+    int64_t leaf_sweeps;      /* launches of the text-position sweep (one per batch, plus one per
+                                 rerun after its hit buffer or a row buffer overflowed) */
+    int64_t leaf_raw_hits;    /* hit records written by the sweep (before the per-cell max) */
 } ae_stats;
 
 /* Engine knobs (NULL = defaults).  None of them changes the result set. */
@@ -114,6 +117,11 @@ typedef struct {
     int32_t int16_limit;    /* trie rows are stored as int16x2 (M, G_a) pairs while depth * g_max
                                stays <= this (<= 32000; 0 = int32 throughout); past it the
                                frontier is unpacked to int32 and the walk continues exactly */
+    const int64_t *hint_hits; /* host, one per query, or NULL: expected hit records of the query's
+                                 text-position sweep (e.g. from ae_mlp_forward); each batch's sweep
+                                 hit buffer is then sized from the hints of its queries instead of
+                                 from the previous searches on the stream.  A low hint costs one
+                                 rerun of the sweep, never a result */
 } ae_options;
 
 /* Fill *opt with the defaults. */

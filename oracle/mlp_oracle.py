@@ -11,10 +11,12 @@ written out here from the definitions:
 
 * ``features`` — 66 numbers per query: the 3-mer spectrum (64 relative
   frequencies over the m-2 windows, index 16*a + 4*b + c for letters a b c
-  in ACGT order), log1p(m), and the spectrum-weighted mean of log1p(size of
-  the suffix-array interval of each 3-mer), the interval size being the
-  number of occurrences of the 3-mer in the text (Section 2.3: the range of
-  a string in the suffix array holds one row per occurrence).
+  in ACGT order), log1p(m), and the mean over the query's windows of K
+  letters, K = ceil(log4(n+1)) + 4, of log1p(size of the suffix-array
+  interval of the window), the interval size being the number of
+  occurrences of the window in the text (Section 2.3: the range of a string
+  in the suffix array holds one row per occurrence). Counted here directly
+  on the text, without an index.
 * ``forward`` / ``loss_and_grads`` — the 66-128-128-2 perceptron
   y = W3 relu(W2 relu(W1 x + b1) + b2) + b3 with the loss
   L = sum((y - t)^2) / (2 B) over a batch of B, and its exact gradients by the
@@ -22,12 +24,14 @@ written out here from the definitions:
   (inputs, weights, activations, upstream gradients) to bfloat16 with
   round-to-nearest-even, the precision the GPU kernels multiply in; products
   are then summed in fp64.
-* ``adam`` — one Adam step (Kingma and Ba, 2015, Algorithm 1).
+* ``adam`` — one Adam step (Kingma and Ba, 2015, Algorithm 1) with decoupled
+  weight decay (Loshchilov and Hutter, 2019).
 
 Pins (tests/test_mlp_oracle.py): central finite differences of the loss
 against ``loss_and_grads``; features on hand-counted strings; the
 interval-size feature against a brute-force substring count; bf16 rounding on
-hand-picked bit patterns; Adam's first step equals lr * sign(g).
+hand-picked bit patterns; Adam's first step equals lr * sign(g), and weight
+decay alone shrinks a parameter by the factor (1 - lr * wd).
 """
 from __future__ import annotations
 
@@ -112,13 +116,14 @@ def loss_and_grads(params, X, T, bf16=False):
     return L, pack(g)
 
 
-def adam(params, grads, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
-    """One Adam step at step number t >= 1; returns new (params, m, v)."""
+def adam(params, grads, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8, wd=0.0):
+    """One Adam step at step number t >= 1 with decoupled weight decay wd;
+    returns new (params, m, v)."""
     m = beta1 * m + (1.0 - beta1) * grads
     v = beta2 * v + (1.0 - beta2) * grads * grads
     mh = m / (1.0 - beta1 ** t)
     vh = v / (1.0 - beta2 ** t)
-    return params - lr * mh / (np.sqrt(vh) + eps), m, v
+    return params - lr * (mh / (np.sqrt(vh) + eps) + wd * params), m, v
 
 
 def kmer3_counts(codes):
@@ -142,10 +147,29 @@ def encode(seq):
     return c
 
 
+def interval_window(n):
+    """Window length K = ceil(log4(n + 1)) + 4 (at most 32)."""
+    k = 0
+    while 4 ** k < n + 1:
+        k += 1
+    return min(k + 4, 32)
+
+
+def _window_codes(c, K):
+    c = np.asarray(c, dtype=np.int64)
+    if c.size < K:
+        return np.zeros(0, dtype=np.int64)
+    v = np.zeros(c.size - K + 1, dtype=np.int64)
+    for i in range(K):
+        v = v * 4 + c[i:c.size - K + 1 + i]
+    return v
+
+
 def features(text, queries):
     """66 features per query (rows), from the definitions above."""
-    occ = kmer3_counts(encode(text))
-    lw = np.log1p(occ.astype(np.float64))
+    t = encode(text)
+    K = interval_window(t.size)
+    words, occ = np.unique(_window_codes(t, K), return_counts=True)
     F = np.zeros((len(queries), 66), dtype=np.float64)
     for r, q in enumerate(queries):
         c = encode(q)
@@ -154,7 +178,12 @@ def features(text, queries):
         if w > 0:
             F[r, :64] = cnt / w
         F[r, 64] = np.log1p(c.size)
-        F[r, 65] = float((F[r, :64] * lw).sum())
+        qw = _window_codes(c, K)
+        if qw.size:
+            pos = np.searchsorted(words, qw)
+            pos = np.minimum(pos, max(words.size - 1, 0))
+            found = (words.size > 0) & (words[pos] == qw) if words.size else np.zeros(qw.size, bool)
+            F[r, 65] = float(np.log1p(np.where(found, occ[pos], 0)).mean())
     return F
 
 

@@ -42,7 +42,8 @@ class ae_options(ctypes.Structure):
     _fields_ = [("qprefix_seed", ctypes.c_int32), ("leaf_segment", ctypes.c_int32),
                 ("item_columns", ctypes.c_int64), ("batch_columns", ctypes.c_int64),
                 ("leaf_capacity", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("leaf_delay", ctypes.c_int32), ("int16_limit", ctypes.c_int32)]
+                ("leaf_delay", ctypes.c_int32), ("int16_limit", ctypes.c_int32),
+                ("hint_hits", ctypes.c_void_p)]
 
 
 class ae_stats(ctypes.Structure):
@@ -57,7 +58,8 @@ class ae_stats(ctypes.Structure):
                 ("ms_k_leaf", ctypes.c_double), ("ms_k_sort", ctypes.c_double),
                 ("ms_k_other", ctypes.c_double), ("ms_k_rows", ctypes.c_double),
                 ("leaf_max_steps", ctypes.c_int64),
-                ("leaf_max_width", ctypes.c_int64), ("ws_bytes", ctypes.c_int64)]
+                ("leaf_max_width", ctypes.c_int64), ("ws_bytes", ctypes.c_int64),
+                ("leaf_sweeps", ctypes.c_int64), ("leaf_raw_hits", ctypes.c_int64)]
 
 
 def _load():
@@ -79,6 +81,15 @@ def _load():
         "ae_search_device": (I32, [V, V, V, I32, V, V, V, V, I64, V, V]),
         "ae_search_device_static": (I32, [V, V, V, I32, V, V, V, V, I64, V, V]),
         "ae_workspace_info": (I32, [V, V, V, V]),
+        "ae_mlp_create": (I32, [ctypes.c_uint64, V]),
+        "ae_mlp_free": (None, [V]),
+        "ae_mlp_set_params": (I32, [V, V]),
+        "ae_mlp_get_params": (I32, [V, V]),
+        "ae_mlp_set_norm": (I32, [V, V, V, V, V]),
+        "ae_mlp_features": (I32, [V, V, V, I32, V, V]),
+        "ae_mlp_forward": (I32, [V, V, I32, V, V]),
+        "ae_mlp_loss_grad": (I32, [V, V, V, I32, V, V, V]),
+        "ae_mlp_train": (I32, [V, V, V, I32, I32, I32, ctypes.c_float, ctypes.c_float, ctypes.c_uint64, V, V]),
         "ae_workspace_release": (I32, [V, V]),
         "ae_last_stats": (I32, [V]),
         "ae_suffix_array": (I32, [V, I64, I32, V]),
@@ -138,11 +149,17 @@ def ae_options_default():
     return o
 
 
-def make_options(**kw):
+def make_options(hint_hits=None, **kw):
+    """ae_options with the given fields set.  hint_hits: per-query expected
+    sweep hit records (kept alive on the returned object)."""
     o = ae_options_default()
     for k, v in kw.items():
         if v is not None:
             setattr(o, k, int(v))
+    if hint_hits is not None:
+        h = np.ascontiguousarray(np.asarray(hint_hits, dtype=np.int64))
+        o._hint_ref = h
+        o.hint_hits = h.ctypes.data
     return o
 
 
@@ -329,3 +346,79 @@ def encode_codes(seq, alphabet=AE_DNA):
     if c.size and c.max() == 255:
         raise ValueError("letter outside the alphabet")
     return c
+
+
+# ------------------------------------------------------------------ work predictor (include/ae_mlp.h)
+
+MLP_IN, MLP_HIDDEN, MLP_OUT, MLP_PARAMS = 66, 128, 2, 25346
+
+
+class Mlp:
+    """Owns one ae_mlp*.  Device arrays are passed as raw addresses (e.g. a
+    torch tensor's data_ptr()); host arrays as numpy float32."""
+
+    def __init__(self, seed=0):
+        h = ctypes.c_void_p(0)
+        _check(lib.ae_mlp_create(ctypes.c_uint64(seed), ctypes.byref(h)), "ae_mlp_create")
+        self._h = h
+
+    @property
+    def handle(self):
+        if not self._h:
+            raise ValueError("model is closed")
+        return self._h
+
+    def close(self):
+        if self._h:
+            lib.ae_mlp_free(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_params(self, params):
+        p = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+        if p.size != MLP_PARAMS:
+            raise ValueError("wrong parameter count")
+        _check(lib.ae_mlp_set_params(self.handle, p.ctypes.data), "ae_mlp_set_params")
+
+    def get_params(self):
+        p = np.empty(MLP_PARAMS, dtype=np.float32)
+        _check(lib.ae_mlp_get_params(self.handle, p.ctypes.data), "ae_mlp_get_params")
+        return p
+
+    def set_norm(self, x_mu, x_sd, y_mu, y_sd):
+        arrs = [np.ascontiguousarray(np.asarray(a, dtype=np.float32)) for a in (x_mu, x_sd, y_mu, y_sd)]
+        _check(lib.ae_mlp_set_norm(self.handle, *[a.ctypes.data for a in arrs]), "ae_mlp_set_norm")
+
+    def forward(self, d_x_ptr, B, d_y_ptr, stream=None):
+        _check(lib.ae_mlp_forward(self.handle, ctypes.c_void_p(int(d_x_ptr)), int(B), ctypes.c_void_p(int(d_y_ptr)),
+                                  _stream_handle(stream)), "ae_mlp_forward")
+
+    def loss_grad(self, d_x_ptr, d_t_ptr, B, want_grads=True, stream=None):
+        loss = ctypes.c_float(0)
+        g = np.empty(MLP_PARAMS, dtype=np.float32) if want_grads else None
+        _check(lib.ae_mlp_loss_grad(self.handle, ctypes.c_void_p(int(d_x_ptr)), ctypes.c_void_p(int(d_t_ptr)), int(B),
+                                    ctypes.byref(loss), g.ctypes.data if g is not None else None,
+                                    _stream_handle(stream)), "ae_mlp_loss_grad")
+        return loss.value, g
+
+    def train(self, d_x_ptr, d_t_ptr, n, epochs, batch, lr, weight_decay=0.0, seed=0, stream=None):
+        loss = ctypes.c_float(0)
+        _check(lib.ae_mlp_train(self.handle, ctypes.c_void_p(int(d_x_ptr)), ctypes.c_void_p(int(d_t_ptr)), int(n),
+                                int(epochs), int(batch), ctypes.c_float(lr), ctypes.c_float(weight_decay),
+                                ctypes.c_uint64(seed),
+                                ctypes.byref(loss), _stream_handle(stream)), "ae_mlp_train")
+        return loss.value
+
+
+def ae_mlp_features(index, d_seq_ptr, offsets, d_feat_ptr, stream=None):
+    """Features (nq x 66, device) of the queries in d_seq (device ASCII, back to
+    back) delimited by offsets (host int64, nq+1)."""
+    off = np.ascontiguousarray(np.asarray(offsets, dtype=np.int64))
+    nq = off.size - 1
+    _check(lib.ae_mlp_features(index.handle, ctypes.c_void_p(int(d_seq_ptr)), off.ctypes.data, nq,
+                               ctypes.c_void_p(int(d_feat_ptr)), _stream_handle(stream)), "ae_mlp_features")

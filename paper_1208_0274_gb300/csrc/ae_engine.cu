@@ -215,6 +215,8 @@ struct ae_index {
     }
 };
 
+const IndexView *ae_index_view(const ae_index *idx) { return &idx->view; }
+
 namespace {
 
 Workspace *workspace_for(const ae_index *cidx, cudaStream_t st) {
@@ -359,6 +361,7 @@ struct Search {
     int be, bj, bq;
     int d0;
     int64_t nhits = 0;        // point hits accumulated in w->hkey/hscore
+    double batch_hint = -1;   // expected sweep hit records of the current batch (< 0: no hints)
     ae_stats stats;
     int num_sms = 152;
     Prof prof;
@@ -389,6 +392,14 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
     CU(cudaMemcpyAsync(w->items.p, items.data(), sizeof(WorkItem) * items.size(), cudaMemcpyHostToDevice, st));
     const WorkItem *d_items = ptr<WorkItem>(w->items);
     auto t0 = std::chrono::steady_clock::now();
+    batch_hint = -1;
+    if (opt.hint_hits) {       // each query's hint, pro rata to its columns in this batch
+        batch_hint = 0;
+        for (const WorkItem &it : items)
+            if (m[it.qid] > 0)
+                batch_hint += (double)std::max<int64_t>(opt.hint_hits[it.qid], 0) * (double)(it.c1 - it.c0) /
+                              (double)m[it.qid];
+    }
 
     int cur = 0;
     int64_t F = 0;
@@ -683,7 +694,8 @@ void Search::leaf_phase(int64_t ninj) {
     if (w->leaf_cap < opt.leaf_capacity) w->leaf_cap = opt.leaf_capacity;
     ensure(w->next_seg, 8, st);
     ensure(w->hcount, 8, st);
-    int64_t hit_cap = std::max<int64_t>(1 << 20, (int64_t)(ninj * w->hit_ratio) + 4096);
+    int64_t hit_cap = std::max<int64_t>(1 << 20, batch_hint >= 0 ? (int64_t)(1.25 * batch_hint) + 65536
+                                                                 : (int64_t)(ninj * w->hit_ratio) + 4096);
     for (int attempt = 0; attempt < 12; ++attempt) {
         ensure(w->scratch, (size_t)ae_leaf_scratch_words(w->leaf_cap, nwarps) * 4, st);
         hits_reserve(hit_cap);
@@ -721,6 +733,7 @@ void Search::leaf_phase(int64_t ninj) {
         la.bj = bj;
         la.stats = ptr<DevStats>(w->stats);
         prof.mark(K_LEAF);
+        ++stats.leaf_sweeps;
         ae_leaf_sweep(la, blocks, threads, st);
         prof.mark(K_LEAF);
         CU(cudaGetLastError());
@@ -746,6 +759,7 @@ void Search::leaf_phase(int64_t ninj) {
         }
         w->hit_ratio = std::max(w->hit_ratio * 0.9,
                                 std::min(64.0, 1.3 * (double)((int64_t)hdr[0] - nhits) / (double)ninj + 0.01));
+        stats.leaf_raw_hits += (int64_t)hdr[0] - nhits;
         nhits = (int64_t)hdr[0];
         return;
     }
@@ -952,6 +966,7 @@ void ae_options_default(ae_options *opt) {
     opt->profile = 0;
     opt->leaf_delay = 8;
     opt->int16_limit = 32000;
+    opt->hint_hits = nullptr;
 }
 
 const char *ae_strerror(int32_t status) {

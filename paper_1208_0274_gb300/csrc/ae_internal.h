@@ -126,3 +126,6 @@ ae_status ae_host_index_build(const uint8_t *codes, int64_t n, int32_t alphabet,
 void ae_host_index_free(HostIndex *h);
 ae_status ae_host_index_save(const HostIndex *h, const char *path);
 ae_status ae_host_index_load(const char *path, HostIndex *h);
+
+// Device view of a built index (pointers into the index's device memory).
+const IndexView *ae_index_view(const ae_index *idx);

@@ -5,15 +5,23 @@ device slots and memory free up; their searches overlap on the GPU.
 
 * `nslots` slots, each a CUDA stream with its own library workspace
   (ae_search keeps one workspace per stream), run searches concurrently.
-* A free slot takes every request that has arrived and is waiting, up to
-  `max_columns` query letters and within the free-device-memory budget, and
-  runs them as one ae_search batch. Requests that arrive while that batch runs
-  wait for the next free slot, so the batch composition follows the arrivals
-  (iteration-level batching); there is no fixed batch size.
-* Admission: a batch is only started if the device memory it is predicted to
-  need (`bytes_per_column` times its letters, or the learned predictor's
-  estimate) is below the free device memory minus `reserve_bytes`; otherwise
-  the slot waits for another slot to finish.
+* A free slot takes waiting requests that have arrived and runs them as one
+  ae_search batch. Requests that arrive while batches run wait for the next
+  free slot, so batch composition follows the arrivals; there is no fixed
+  batch size.
+* Policy "fifo" (no predictor): arrival order, up to `max_columns` query
+  letters per batch.
+* Policy "predicted" (with a WorkPredictor): each request's search work
+  (DP entries) and sweep hit records are predicted when it is first
+  considered; the slot takes the requests of least predicted work first
+  (requests that waited longer than `max_wait` go first, in arrival order),
+  up to `work_budget` predicted entries per batch, and passes the predicted
+  hit records to the engine as ae_options.hint_hits.
+* Admission: a batch starts only if the growth of the slot's workspace it is
+  predicted to need (`bytes_per_column` per letter, or the predictor's device
+  bytes) fits in the free device memory minus `reserve_bytes`; otherwise the
+  slot waits for another slot to finish. A slot with nothing else running is
+  always admitted.
 * The latency of a request is the time from its arrival to its results being
   in host memory.
 
@@ -42,6 +50,8 @@ class Request:
     finish: float = -1.0
     hits: np.ndarray | None = None
     batch: int = -1
+    pred_work: float = -1.0        # predicted DP entries (predicted policy)
+    pred_hits: int = -1            # predicted sweep hit records (predicted policy)
 
 
 @dataclass
@@ -64,24 +74,29 @@ def _percentile(x, q):
 class Server:
     """`nslots` concurrent search slots over one index.
 
-    predictor: callable(list of queries) -> predicted device bytes of one
-    search over them (frontier, leaf rows and hit records), or None to use
-    `bytes_per_column` per query letter.  mem_info: callable() -> (free,
-    total) device bytes (torch.cuda.mem_get_info by default).  search_fn and
-    workspace_fn replace ae_search / ae_workspace_info (for host-only tests).
+    predictor: a WorkPredictor (paper_1208_0274_gb300.predictor) or None.
+    mem_info: callable() -> (free, total) device bytes (torch.cuda.mem_get_info
+    by default).  search_fn(queries, Hs, stream, hints) and
+    workspace_fn(stream) replace ae_search / ae_workspace_info, and
+    predict_fn(queries) -> (work, hits) replaces the predictor (host-only
+    tests).
     """
 
     def __init__(self, index, scheme, nslots=3, max_columns=1 << 18, bytes_per_column=100_000,
-                 reserve_bytes=4 << 30, options=None, predictor=None, mem_info=None, streams=None,
-                 search_fn=None, workspace_fn=None):
+                 reserve_bytes=4 << 30, options=None, predictor=None, work_budget=None, max_wait=0.25,
+                 mem_info=None, streams=None, search_fn=None, workspace_fn=None, predict_fn=None):
         self.index = index
         self.scheme = scheme
         self.nslots = nslots
         self.max_columns = max_columns
         self.bytes_per_column = bytes_per_column
         self.reserve_bytes = reserve_bytes
-        self.options = options
+        self.options = dict(options or {})
         self.predictor = predictor
+        self.predict_fn = predict_fn
+        self.policy = "predicted" if (predictor is not None or predict_fn is not None) else "fifo"
+        self.work_budget = work_budget
+        self.max_wait = max_wait
         if streams is None or mem_info is None:
             import torch
             if streams is None:
@@ -90,30 +105,80 @@ class Server:
                 mem_info = torch.cuda.mem_get_info
         self.streams = list(streams)
         self.mem_info = mem_info
-        self.search_fn = search_fn or (lambda qs, Hs, stream: ae.ae_search(
-            self.index, qs, self.scheme, Hs, options=self.options, stream=stream))
+        self.search_fn = search_fn or self._search
         self.workspace_fn = workspace_fn or (lambda stream: ae.ae_workspace_info(self.index, stream)[0])
         self._lock = threading.Condition()
         self._growth_in_flight = 0
         self.admission_waits = 0
+        self.leaf_sweeps = 0
+        self.batches_run = 0
 
-    def need_bytes(self, queries):
-        if self.predictor is not None:
-            return int(self.predictor(queries))
-        return int(sum(q.size for q in queries) * self.bytes_per_column)
+    def _search(self, qs, Hs, stream, hints=None):
+        opts = ae.make_options(hint_hits=hints, **self.options)
+        out = ae.ae_search(self.index, qs, self.scheme, Hs, options=opts, stream=stream)
+        st = ae.ae_last_stats()
+        with self._lock:
+            self.leaf_sweeps += st["leaf_sweeps"]
+            self.batches_run += 1
+        return out
+
+    # -- predictions ----------------------------------------------------------------------------
+    def _predict(self, reqs):
+        new = [r for r in reqs if r.pred_work < 0]
+        if not new:
+            return
+        qs = [r.query for r in new]
+        if self.predict_fn is not None:
+            work, hits = self.predict_fn(qs)
+        else:
+            work = self.predictor.work(qs)
+            hits = self.predictor.hint_hits(qs)
+        for r, w, h in zip(new, work, hits):
+            r.pred_work = float(w)
+            r.pred_hits = int(h)
+
+    def need_bytes(self, batch):
+        if self.policy == "predicted" and self.predictor is not None:
+            p = self.predictor
+            return int(p.fixed_bytes + sum(r.pred_work for r in batch) * p.bytes_per_entry
+                       + 12.0 * sum(r.pred_hits for r in batch))
+        return int(sum(r.query.size for r in batch) * self.bytes_per_column)
+
+    def _take(self, pending, now):
+        """Remove and return the next batch from `pending` under the policy."""
+        if self.policy == "fifo":
+            batch, cols = [], 0
+            while pending and (not batch or cols + pending[0].query.size <= self.max_columns):
+                r = pending.pop(0)
+                batch.append(r)
+                cols += r.query.size
+            return batch
+        self._predict(pending)
+        old = [r for r in pending if now - r.arrival > self.max_wait]
+        order = old + sorted((r for r in pending if now - r.arrival <= self.max_wait), key=lambda r: r.pred_work)
+        budget = self.work_budget if self.work_budget is not None else float("inf")
+        batch, work, cols = [], 0.0, 0
+        for r in order:
+            if batch and (work + r.pred_work > budget or cols + r.query.size > self.max_columns):
+                break
+            batch.append(r)
+            work += r.pred_work
+            cols += r.query.size
+        taken = set(id(r) for r in batch)
+        pending[:] = [r for r in pending if id(r) not in taken]
+        return batch
 
     def warmup(self, queries, Hs):
         """Run one search per slot so every workspace has grown before requests
         are timed (growth frees and reallocates device buffers)."""
         for st in self.streams:
-            self.search_fn(queries, Hs, st)
+            self.search_fn(queries, Hs, st, None)
 
     def run(self, requests, time_limit=None):
-        """Serve `requests` (sorted by arrival) in real time; returns a ServeReport."""
+        """Serve `requests` in real time; returns a ServeReport."""
         reqs = sorted(requests, key=lambda r: r.arrival)
         pending = []
         nxt = 0
-        done = 0
         active = 0
         peak = 0
         nbatches = 0
@@ -133,7 +198,7 @@ class Server:
                 nxt += 1
 
         def slot_loop(s):
-            nonlocal done, active, peak, nbatches, stop
+            nonlocal active, peak, nbatches, stop
             stream = self.streams[s]
             while True:
                 with cond:
@@ -142,12 +207,8 @@ class Server:
                         if stop or (nxt >= len(reqs) and not pending):
                             return
                         if pending:
-                            batch, cols = [], 0
-                            while pending and (not batch or cols + pending[0].query.size <= self.max_columns):
-                                r = pending.pop(0)
-                                batch.append(r)
-                                cols += r.query.size
-                            need = self.need_bytes([r.query for r in batch])
+                            batch = self._take(pending, now())
+                            need = self.need_bytes(batch)
                             # the slot's workspace is reused: only its growth needs free memory
                             growth = max(0, need - self.workspace_fn(stream))
                             free, _ = self.mem_info()
@@ -171,7 +232,8 @@ class Server:
                 for r in batch:
                     r.start = ts
                     r.batch = bid
-                hits, counts = self.search_fn([r.query for r in batch], [r.H for r in batch], stream)
+                hints = [r.pred_hits for r in batch] if self.policy == "predicted" else None
+                hits, counts = self.search_fn([r.query for r in batch], [r.H for r in batch], stream, hints)
                 tf = now()
                 off = 0
                 for r, c in zip(batch, counts):
@@ -180,7 +242,6 @@ class Server:
                     off += int(c)
                 with cond:
                     active -= 1
-                    done += len(batch)
                     self._growth_in_flight -= growth
                     if time_limit is not None and now() > time_limit:
                         stop = True

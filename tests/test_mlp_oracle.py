@@ -62,32 +62,42 @@ def test_bf16_rounding_on_bit_patterns():
 
 
 def test_features_on_hand_counted_strings():
-    F = mo.features(b"ACGTACGT", [b"AAAA", b"ACG", b"AC", b"ACGTAC"])
+    # text of 8 letters: K = ceil(log4 9) + 4 = 6
+    text = b"ACGTACGT"
+    assert mo.interval_window(8) == 6
+    F = mo.features(text, [b"AAAA", b"ACG", b"AC", b"ACGTAC", b"CGTACGT"])
     # AAAA: windows AAA, AAA -> spectrum[0] = 1
     assert F[0, 0] == 1.0 and F[0, 1:64].sum() == 0.0
     # ACG is 3-mer index 16*0 + 4*1 + 2 = 6
     assert F[1, 6] == 1.0 and F[1, :64].sum() == 1.0
     # AC has no 3-mer
-    assert F[2, :64].sum() == 0.0 and F[2, 65] == 0.0
+    assert F[2, :64].sum() == 0.0
     # ACGTAC: ACG, CGT, GTA, TAC -> indices 6, 27, 44, 49, a quarter each
     assert set(np.nonzero(F[3, :64])[0]) == {6, 27, 44, 49} and np.allclose(F[3, [6, 27, 44, 49]], 0.25)
-    assert np.allclose(F[:, 64], np.log1p([4, 3, 2, 6]))
-    # text ACGTACGT has ACG twice, CGT twice, GTA once, TAC once
-    assert np.isclose(F[3, 65], 0.25 * (2 * np.log1p(2) + 2 * np.log1p(1)))
+    assert np.allclose(F[:, 64], np.log1p([4, 3, 2, 6, 7]))
+    # windows of 6: shorter queries have none; ACGTAC occurs once in the text;
+    # CGTACGT has windows CGTACG (once) and GTACGT (once)
+    assert list(F[:3, 65]) == [0.0, 0.0, 0.0]
+    assert np.isclose(F[3, 65], np.log1p(1)) and np.isclose(F[4, 65], np.log1p(1))
+    F2 = mo.features(b"ACGTACGTAAAAAAAAAA", [b"AAAAAAA", b"CCCCCCCC"])   # n = 18: K = 7
+    # AAAAAAA occurs at 4 positions of the run of ten A; CCCCCCC nowhere
+    assert np.isclose(F2[0, 65], np.log1p(4)) and F2[1, 65] == 0.0
 
 
 def test_interval_feature_against_brute_force_substring_count():
     rng = np.random.default_rng(5)
     letters = np.frombuffer(b"ACGT", dtype=np.uint8)
     text = rng.choice(letters, size=3000).tobytes()
-    q = rng.choice(letters, size=40).tobytes()
+    q = bytes(text[1000:1030]) + rng.choice(letters, size=20).tobytes()
+    K = mo.interval_window(len(text))
+    assert K == 10
     F = mo.features(text, [q])
     want = 0.0
-    for k in range(len(q) - 2):
-        w = q[k:k + 3]
-        occ = sum(1 for s in range(len(text) - 2) if text[s:s + 3] == w)
-        want += np.log1p(occ) / (len(q) - 2)
-    assert np.isclose(F[0, 65], want)
+    for k in range(len(q) - K + 1):
+        w = q[k:k + K]
+        occ = sum(1 for s in range(len(text) - K + 1) if text[s:s + K] == w)
+        want += np.log1p(occ) / (len(q) - K + 1)
+    assert np.isclose(F[0, 65], want) and want > 0
 
 
 def test_adam_first_step_moves_each_parameter_by_lr_times_the_gradient_sign():
@@ -97,3 +107,6 @@ def test_adam_first_step_moves_each_parameter_by_lr_times_the_gradient_sign():
     p1, m, v = mo.adam(p, g, z, z, t=1, lr=0.01, eps=0.0)
     assert np.allclose(p1, p - 0.01 * np.sign(g))
     assert np.allclose(m, 0.1 * g) and np.allclose(v, 0.001 * g * g)
+    # with a zero gradient, decoupled weight decay alone scales the parameter by (1 - lr * wd)
+    p2, _, _ = mo.adam(p, z, z, z, t=1, lr=0.01, wd=0.5)
+    assert np.allclose(p2, p * (1 - 0.005))

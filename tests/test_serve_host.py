@@ -67,7 +67,7 @@ def test_requests_are_admitted_while_others_run_and_get_their_own_results():
     reqs = _requests(120, rate=2000.0, seed=1)
     srv = serve.Server(None, None, nslots=3, bytes_per_column=1000, reserve_bytes=0, mem_info=dev.mem_info,
                        streams=["s0", "s1", "s2"], workspace_fn=dev.workspace,
-                       search_fn=lambda qs, Hs, st: dev.search(qs, Hs, st, 1000))
+                       search_fn=lambda qs, Hs, st, hints: dev.search(qs, Hs, st, 1000))
     rep = srv.run(reqs)
     assert len(rep.requests) == 120
     for r in rep.requests:
@@ -86,7 +86,7 @@ def test_admission_keeps_workspace_growth_within_free_memory():
     reqs = _requests(60, rate=5000.0, seed=2)
     srv = serve.Server(None, None, nslots=4, max_columns=5000, bytes_per_column=bpc, reserve_bytes=0,
                        mem_info=dev.mem_info, streams=[0, 1, 2, 3], workspace_fn=dev.workspace,
-                       search_fn=lambda qs, Hs, st: dev.search(qs, Hs, st, bpc))
+                       search_fn=lambda qs, Hs, st, hints: dev.search(qs, Hs, st, bpc))
     rep = srv.run(reqs)                     # FakeDevice.search asserts used <= total
     assert len(rep.requests) == 60
     assert dev.peak_used <= total
@@ -101,7 +101,7 @@ def test_a_lone_slot_is_always_admitted():
     reqs = _requests(5, rate=1000.0, seed=3)
     srv = serve.Server(None, None, nslots=2, bytes_per_column=0, reserve_bytes=100, mem_info=dev.mem_info,
                        streams=[0, 1], workspace_fn=dev.workspace,
-                       search_fn=lambda qs, Hs, st: dev.search(qs, Hs, st, 0))
+                       search_fn=lambda qs, Hs, st, hints: dev.search(qs, Hs, st, 0))
     rep = srv.run(reqs)
     assert len(rep.requests) == 5
 
@@ -113,3 +113,48 @@ def test_poisson_arrivals_have_the_requested_rate():
     gaps = np.diff(np.concatenate([[0.0], t]))
     assert abs(gaps.mean() - 1 / 200.0) < 0.05 / 200.0
     assert abs(gaps.std() - 1 / 200.0) < 0.05 / 200.0     # exponential: sd = mean
+
+
+def test_predicted_policy_takes_least_work_first_within_a_budget_and_passes_hints():
+    dev = FakeDevice(total=1 << 40)
+    seen = []
+
+    def search(qs, Hs, st, hints):
+        seen.append(([q.size for q in qs], list(hints)))
+        return dev.search(qs, Hs, st, 1)
+
+    # all requests are waiting when the single slot first looks: it must take
+    # them in order of predicted work (= length here), budget-limited
+    reqs = _requests(40, rate=1e9, seed=5)
+    srv = serve.Server(None, None, nslots=1, bytes_per_column=0, reserve_bytes=0, mem_info=dev.mem_info,
+                       streams=[0], workspace_fn=dev.workspace, search_fn=search, work_budget=6000,
+                       max_wait=1e9, predict_fn=lambda qs: ([float(q.size) for q in qs], [7 * q.size for q in qs]))
+    rep = srv.run(reqs)
+    assert len(rep.requests) == 40
+    for r in rep.requests:
+        assert np.array_equal(r.hits, _fake_hits(r.query))
+    sizes0, hints0 = seen[0]
+    assert hints0 == [7 * m for m in sizes0]
+    assert sizes0 == sorted(sizes0) and (sum(sizes0) <= 6000 or len(sizes0) == 1)
+    smallest = min(q.query.size for q in reqs)
+    assert sizes0[0] == smallest
+
+
+def test_requests_waiting_longer_than_max_wait_go_first():
+    dev = FakeDevice(total=1 << 40)
+    order = []
+
+    def search(qs, Hs, st, hints):
+        order.extend(q.size for q in qs)
+        return dev.search(qs, Hs, st, 1)
+
+    big = np.zeros(50_000, np.uint8)
+    small = [np.zeros(100 + k, np.uint8) for k in range(30)]
+    reqs = [serve.Request(rid=0, query=big, H=1, arrival=0.0)]
+    reqs += [serve.Request(rid=k + 1, query=q, H=1, arrival=0.0) for k, q in enumerate(small)]
+    srv = serve.Server(None, None, nslots=1, bytes_per_column=0, reserve_bytes=0, mem_info=dev.mem_info,
+                       streams=[0], workspace_fn=dev.workspace, search_fn=search, work_budget=500,
+                       max_wait=0.0, predict_fn=lambda qs: ([float(q.size) for q in qs], [0] * len(qs)))
+    time.sleep(0.01)
+    srv.run(reqs)
+    assert order[0] == 50_000          # waited past max_wait: goes first despite its size
