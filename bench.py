@@ -29,7 +29,8 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-from workloads import DNA_SCALE_H, Scheme, dna_scale_bench, dna_scale_text, dna_serve, dna_small  # noqa: E402
+from workloads import (DNA_SCALE_H, Scheme, dna_batch, dna_scale_bench, dna_scale_text, dna_serve,  # noqa: E402
+                       dna_small)
 
 METRIC = "effective GCUPS (m*n/time) at bit-exact hits, batched"
 
@@ -40,7 +41,9 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="dna_scale", choices=["dna_scale", "dna_small", "dna_serve"])
+    p.add_argument("--workload", default="dna_scale", choices=["dna_scale", "dna_small", "dna_serve", "dna_batch"])
+    p.add_argument("--queries", type=int, default=4096, help="dna_batch: number of queries")
+    p.add_argument("--plain-sample", type=int, default=256, help="dna_batch: queries timed one launch at a time")
     p.add_argument("--requests", type=int, default=1000, help="dna_serve: number of requests")
     p.add_argument("--rate", type=float, default=200.0, help="dna_serve: Poisson arrival rate (1/s)")
     p.add_argument("--slots", type=int, default=3, help="dna_serve: concurrent search slots")
@@ -483,10 +486,122 @@ def run_serve(args):
     return 0 if same else 1
 
 
+def run_batch(args):
+    """Many queries of uneven length (log-uniform 100-20,000 bp, 1% planted)
+    against the resident 100 Mbp index.  A step is one search of all queries:
+    the autotuned configuration (engine batch size, leaf delay, streams) with
+    the queries packed onto the streams by predicted work (LPT).  Also timed:
+    the same configuration with static round-robin packing, and single-query
+    launches on a sample (queries/s)."""
+    import torch
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return 0
+    torch.cuda.set_device(local)
+    from paper_1208_0274_gb300 import ae, autotune
+    from paper_1208_0274_gb300.batch import search_many
+    from paper_1208_0274_gb300.predictor import WorkPredictor
+    text = dna_scale_text(n=args.n)
+    wl = dna_batch(text, k=args.queries)
+    qs, Hs, scheme = wl.queries, wl.H, wl.scheme
+    idx = ae.ae_index_build(text, ae.AE_DNA)
+    sum_m = int(sum(q.size for q in qs))
+    cells = sum_m * text.size
+
+    t0 = time.perf_counter()
+    tw = dna_batch(text, seed=20120807, k=args.train_queries)
+    pred = WorkPredictor(idx, scheme, seed=1)
+    T = pred.log_searches(tw.queries, tw.H)
+    pred.fit(pred.features(tw.queries), T)
+    t_train = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    cfg, cached = autotune.tune(idx, qs, Hs, scheme, sample=512)
+    t_tune = time.perf_counter() - t0
+    log(f"tuned {cfg} (cached {cached}) in {t_tune:.1f} s; predictor trained in {t_train:.1f} s")
+    opts = {"batch_columns": cfg["batch_columns"], "leaf_delay": cfg["leaf_delay"]}
+    streams = [torch.cuda.Stream() for _ in range(cfg["nstreams"])]
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device="cuda")
+
+    def step(policy):
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        out, info = search_many(idx, qs, Hs, scheme, nstreams=cfg["nstreams"], policy=policy, predictor=pred,
+                                options=opts, streams=streams)
+        torch.cuda.synchronize()
+        return time.perf_counter() - t1, out, info
+
+    for _ in range(args.warmup):
+        step("lpt")
+    clocks = Clocks(local)
+    clocks.start()
+    times, info = [], None
+    for _ in range(args.steps):
+        dt, out_l, info = step("lpt")
+        times.append(dt)
+    clk = clocks.stop()
+    rr_times = []
+    for _ in range(max(1, args.steps)):
+        dt, out_r, info_r = step("round_robin")
+        rr_times.append(dt)
+    same = all(np.array_equal(a, b) for a, b in zip(out_l, out_r))
+    # the two packings at three streams (the autotuner's choice may be fewer)
+    multi = {}
+    streams3 = [torch.cuda.Stream() for _ in range(3)]
+    for policy in ("lpt", "round_robin"):
+        flush.fill_(2)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        out_m, info_m = search_many(idx, qs, Hs, scheme, nstreams=3, policy=policy, predictor=pred,
+                                    options=opts, streams=streams3)
+        torch.cuda.synchronize()
+        multi[policy] = {"ms_per_step": round(1000 * (time.perf_counter() - t1), 3), "groups": info_m["groups"]}
+        same &= all(np.array_equal(a, b) for a, b in zip(out_l, out_m))
+    for st_ in streams3:
+        ae.ae_workspace_release(idx, st_)
+    # single-query launches on a sample (the static plain form)
+    rng = np.random.default_rng(3)
+    pick = rng.choice(len(qs), size=min(args.plain_sample, len(qs)), replace=False)
+    st = torch.cuda.Stream()
+    ae.ae_search(idx, [qs[pick[0]]], scheme, [Hs[pick[0]]], stream=st)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    plain_same = True
+    for k in pick:
+        h, _ = ae.ae_search(idx, [qs[k]], scheme, [Hs[k]], stream=st)
+        plain_same &= bool(np.array_equal(h, out_l[k]))
+    t_plain = time.perf_counter() - t1
+    m_plain = int(sum(qs[k].size for k in pick))
+    ms = 1000 * sum(times) / len(times)
+    line = {"metric": "effective GCUPS (m*n/time) and queries/s, batched + learned packing vs static",
+            "value": round(cells / (ms / 1000) / 1e9, 3), "unit": "GCUPS", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(ms, 3), "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+            "config": {"workload": f"dna_batch: {len(qs)} DNA queries, lengths log-uniform 100-20,000 bp (1% planted), "
+                                   f"vs {args.n:,} bp index; H by length (E=10)",
+                       "sum_m": sum_m, "tuned": cfg, "tune_cached": cached,
+                       "l2": "flushed between timed steps (512 MiB write)"},
+            "queries_per_s": round(len(qs) / (ms / 1000), 3),
+            "round_robin": {"ms_per_step": round(1000 * sum(rr_times) / len(rr_times), 3),
+                            "value": round(cells / (sum(rr_times) / len(rr_times)) / 1e9, 3),
+                            "groups": info_r["groups"]},
+            "lpt_groups": info["groups"], "leaf_sweeps": info["leaf_sweeps"], "gpu_launches": info["launches"],
+            "three_streams": multi,
+            "single_query": {"queries": len(pick), "queries_per_s": round(len(pick) / t_plain, 3),
+                             "value": round(m_plain * text.size / t_plain / 1e9, 3), "unit": "GCUPS"},
+            "predictor_train_s": round(t_train, 3), "tune_s": round(t_tune, 3),
+            "hits_identical": bool(same and plain_same), "hits": int(sum(h.size for h in out_l)), "clocks": clk}
+    print(json.dumps(line), flush=True)
+    idx.close()
+    return 0 if (same and plain_same) else 1
+
+
 def main():
     args = parse()
     if args.workload == "dna_serve":
         return run_serve(args)
+    if args.workload == "dna_batch":
+        return run_batch(args)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)
