@@ -157,11 +157,12 @@ def peaks():
 
 
 def measured_traffic(kernel, units):
-    """DRAM bytes (read + write) of `kernel` for `units` DP entries, from the
-    per-entry figure of its last ncu capture (profiles/dram_per_entry.txt).
+    """DRAM bytes (read + write) of `kernel` for `units` work units (triples
+    for k_rows, sweep entries for k_leaf), from the per-unit figure of its last
+    ncu capture (profiles/dram_per_unit.txt: `kernel bytes_per_unit sha1`).
     None if there is no capture or the kernel's source changed since."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "dram_per_entry.txt")
+    path = os.path.join(ROOT, "profiles", "dram_per_unit.txt")
     src_of = {"k_rows": "ae_trie.cu", "k_leaf": "ae_kernels.cu"}
     if kernel not in src_of or not os.path.exists(path):
         return None
@@ -174,6 +175,16 @@ def measured_traffic(kernel, units):
                 return None
             return int(float(parts[1]) * units)
     return None
+
+
+# Integer peak of the GB300: 152 SMs x 64 INT32 lanes per clock (16 per SM
+# sub-partition) x 2,070 MHz.
+INT_PEAK_GOPS = 152 * 64 * 2.070
+# Algorithmic integer operations of one (child, parent entry) triple of the
+# row update, and of one sweep entry: slot A (add, select, two adds and a max
+# for G_a, a max, a threshold compare), slot B (add, select, compare), one
+# add-max for G_b.
+OPS_PER_TRIPLE = 12
 
 
 def cpu_baseline(text, queries, scheme, H, seconds):
@@ -278,7 +289,8 @@ def run_ours(args):
             f"k_rows {st['ms_k_rows']:.1f} ms, k_children {st['ms_k_expand']:.1f} ms, k_leaf {st['ms_k_leaf']:.1f} ms, "
             f"k_sort {st['ms_k_sort']:.1f} ms, k_other {st['ms_k_other']:.1f} ms, launches {st['launches']}, "
             f"leaf rows {st['leaf_rows']:,} max steps {st['leaf_max_steps']:,} max width {st['leaf_max_width']:,}, "
-            f"injections {st['injections']:,}, levels {st['levels']}, ws {st['ws_bytes'] / 1e9:.1f} GB")
+            f"injections {st['injections']:,}, levels {st['levels']}, triples {st['triples']:,}, "
+            f"ws {st['ws_bytes'] / 1e9:.1f} GB")
 
     clocks = Clocks(local)
     if dist:
@@ -287,7 +299,7 @@ def run_ours(args):
     clocks.start()
     ev = []
     kstats = {"ms_k_expand": 0.0, "ms_k_rows": 0.0, "ms_k_leaf": 0.0, "ms_k_sort": 0.0, "ms_k_other": 0.0,
-              "launches": 0, "levels": 0,
+              "launches": 0, "levels": 0, "triples": 0, "leaf_sweeps": 0,
               "entries": 0, "entries_leaf": 0, "nodes": 0, "hits": 0, "raw_hits": 0}
     for s in range(args.steps):
         with torch.cuda.stream(stream):
@@ -372,18 +384,28 @@ def run_ours(args):
               "k_children": kstats["ms_k_expand"], "k_sort": kstats["ms_k_sort"], "k_other": kstats["ms_k_other"]}
     dom = max(groups, key=groups.get)
     peak, src = peaks()
-    # algorithmic bytes: a DP entry is read once as a parent (12 B: column, M,
-    # G_a) and written once as a child (12 B)
     ent_leaf = kstats["entries_leaf"]
     ent_trie = kstats["entries"] - ent_leaf
-    units = {"k_rows": ent_trie, "k_leaf": ent_leaf}.get(dom, kstats["raw_hits"])
-    alg = 24.0 * units
-    achieved = alg / (groups[dom] / 1000.0) / 1e9 if groups[dom] > 0 else 0.0
+    # integer-ALU view (the bound ncu measures for k_rows and k_leaf): algorithmic ops per second
+    units = {"k_rows": kstats["triples"], "k_leaf": ent_leaf}.get(dom, kstats["raw_hits"])
+    launches_dom = {"k_rows": 2 * kstats["levels"], "k_leaf": max(1, kstats["leaf_sweeps"])}.get(dom, 1)
+    sec = groups[dom] / 1000.0
+    ops = OPS_PER_TRIPLE * units
+    achieved = ops / sec / 1e9 if sec > 0 else 0.0
     traffic = measured_traffic(dom, units)
-    roof = {"kernel": dom, "bound": "hbm", "achieved": round(achieved, 2), "peak": peak, "unit": "GB/s",
-            "frac": round(achieved / peak, 4), "traffic": traffic, "peak_source": src,
-            "algorithmic_bytes_per_unit": 24, "unit_of_work": "DP entry",
+    roof = {"kernel": dom, "bound": "alu", "achieved": round(achieved, 2), "peak": round(INT_PEAK_GOPS, 1),
+            "unit": "Gop/s", "frac": round(achieved / INT_PEAK_GOPS, 5),
+            "traffic": None if traffic is None else int(traffic / launches_dom),
+            "peak_source": "derived: 152 SMs x 64 INT32 lanes x 2070 MHz",
+            "ops_per_unit": OPS_PER_TRIPLE, "unit_of_work": "triple (child, parent entry)" if dom == "k_rows"
+            else "sweep entry", "units_per_launch": int(units / launches_dom),
             "group_ms_per_step": {k: round(v / args.steps, 3) for k, v in groups.items()}}
+    # bytes view: 24 B per DP entry (read as parent, written as child) against the measured HBM copy bandwidth
+    ent = {"k_rows": ent_trie, "k_leaf": ent_leaf}.get(dom, 0)
+    gbs = 24.0 * ent / sec / 1e9 if sec > 0 else 0.0
+    roof_hbm = {"kernel": dom, "bound": "hbm", "achieved": round(gbs, 2), "peak": peak, "unit": "GB/s",
+                "frac": round(gbs / peak, 4), "peak_source": src, "algorithmic_bytes_per_unit": 24,
+                "unit_of_work": "DP entry"}
     cpu = None
     if not args.no_cpu:
         import oracle
@@ -395,6 +417,7 @@ def run_ours(args):
             "queries_per_s": round(qps, 3), "hits_per_step": int(kstats["hits"] / max(args.steps, 1)),
             "entries_per_step": int(kstats["entries"] / max(args.steps, 1)),
             "gpu_launches": int(kstats["launches"]), "plain": plain, "e2e": e2e, "roofline": roof,
+            "roofline_hbm": roof_hbm,
             "cpu_baseline": cpu, "clocks": clk}
     print(json.dumps(line), flush=True)
     idx.close()

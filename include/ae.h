@@ -102,6 +102,8 @@ typedef struct {
     int64_t leaf_sweeps;      /* launches of the text-position sweep (one per batch, plus one per
                                  rerun after its hit buffer or a row buffer overflowed) */
     int64_t leaf_raw_hits;    /* hit records written by the sweep (before the per-cell max) */
+    int64_t triples;          /* (child, parent entry) pairs the trie levels evaluated: every
+                                 non-empty child of a node with every entry of the node's row */
 } ae_stats;
 
 /* Engine knobs (NULL = defaults).  None of them changes the result set. */

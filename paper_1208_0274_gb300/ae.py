@@ -59,7 +59,8 @@ class ae_stats(ctypes.Structure):
                 ("ms_k_other", ctypes.c_double), ("ms_k_rows", ctypes.c_double),
                 ("leaf_max_steps", ctypes.c_int64),
                 ("leaf_max_width", ctypes.c_int64), ("ws_bytes", ctypes.c_int64),
-                ("leaf_sweeps", ctypes.c_int64), ("leaf_raw_hits", ctypes.c_int64)]
+                ("leaf_sweeps", ctypes.c_int64), ("leaf_raw_hits", ctypes.c_int64),
+                ("triples", ctypes.c_int64)]
 
 
 def _load():

@@ -524,6 +524,7 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
         CU(cudaMemcpyAsync(tot(), w->totals.p, 16, cudaMemcpyDeviceToHost, st));
         sync();
         const int64_t nseg = (int64_t)tot()[0], ntrip = (int64_t)tot()[1];
+        stats.triples += ntrip;
         if (nseg == 0) break;
         ensure(w->segs, nseg * sizeof(Seg), st);
         ensure(w->seg_cnt, nseg * 4, st);
