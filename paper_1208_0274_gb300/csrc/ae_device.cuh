@@ -40,9 +40,9 @@ __device__ __forceinline__ int32_t floordiv32(int32_t a, int32_t b) {  // b > 0
 }
 
 // Theorem 2 threshold of query column j (0-based): an entry lives iff > thr.
+// int32 is exact: the engine admits only m * (g + 1) < 2^30, and j <= m.
 __device__ __forceinline__ int32_t thr_of(int32_t j, int32_t m, int32_t H, int32_t g) {
-    int64_t t = (int64_t)H - 1 - (int64_t)(m - 1 - j) * g;
-    return t > 0 ? (int32_t)t : 0;
+    return max(H - 1 - (m - 1 - j) * g, 0);
 }
 
 __device__ __forceinline__ int32_t delta_of(const ScoreView &sc, const int8_t *smat, int c, int q) {

@@ -868,9 +868,11 @@ ae_status search_core(const ae_index *idx, Workspace *w, const int64_t *offsets,
         int64_t len = offsets[q + 1] - offsets[q];
         if (len < 0 || len >= (1 << 28) || H[q] < 1) return AE_EINVAL;
         s.m[q] = (int32_t)len;
-        s.H[q] = H[q];
+        // no score reaches 2^30 (m * g_max < 2^30 is checked below), so a larger
+        // threshold selects the same (empty) set and keeps device arithmetic in int32
+        s.H[q] = std::min<int32_t>(H[q], 1 << 30);
         mmax = std::max(mmax, (int32_t)len);
-        Hmin = std::min(Hmin, H[q]);
+        Hmin = std::min(Hmin, s.H[q]);
     }
     // keys of the max-plus scan stay within int32
     if ((int64_t)mmax * (-(int64_t)s.sc.ss + s.sc.gmax + 1) >= (1ll << 30)) return AE_EUNSUPPORTED;

@@ -144,16 +144,22 @@ __device__ void run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, ui
     const unsigned le = (lane == 31) ? 0xffffffffu : ((1u << (lane + 1)) - 1u);
     const ScoreView &sc = a.sc;
     const int32_t u = -sc.ss, oe = sc.sg + sc.ss, g = sc.gmax;
+    // a gap state reached from slot value M' can be live only if M' > |s_g + s_s|
+    // (Eq. 3): weaker slots give the G_b scan no key, and a chunk without a key
+    // or an incoming carry skips the scan
+    const int32_t strong = -oe;
     uint64_t sbase = s_first;
     int32_t carry = AE_KNEG;
-    for (uint64_t t0 = t_beg; t0 < t_end; t0 += 32) {
-        const uint64_t t = t0 + lane;
-        const bool valid = t < t_end;
-        const uint64_t woff = (sbase + lane < s_last) ? a.segs[sbase + lane].toff : ~0ull;
+    // triple offsets relative to the task (a task spans < 2^32 triples)
+    const uint32_t t_len = (uint32_t)(t_end - t_beg);
+    for (uint32_t t0 = 0; t0 < t_len; t0 += 32) {
+        const uint32_t t = t0 + lane;
+        const bool valid = t < t_len;
+        const uint32_t woff = (sbase + lane < s_last) ? (uint32_t)(a.segs[sbase + lane].toff - t_beg) : 0xFFFFFFFFu;
         int i = 0;
 #pragma unroll
         for (int step = 16; step > 0; step >>= 1) {
-            const uint64_t o = __shfl_sync(FULL, woff, i + step);
+            const uint32_t o = __shfl_sync(FULL, woff, i + step);
             if (o <= t) i += step;
         }
         const uint64_t sid = sbase + i;
@@ -164,7 +170,7 @@ __device__ void run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, ui
         sg.lo = sg.hi = 0;
         sg.cq = 0;
         if (valid) sg = a.segs[sid];
-        const int64_t k = valid ? (int64_t)(t - sg.toff) : 0;
+        const int32_t k = valid ? (int32_t)(t - (uint32_t)(sg.toff - t_beg)) : 0;
         const uint32_t slen = sg.len & 0x0FFFFFFFu;
         const int c = (int)(sg.cq & 31u);
         const int32_t qid = (int32_t)((sg.cq >> 5) & 0xFFFFFFu);
@@ -199,7 +205,7 @@ __device__ void run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, ui
         int32_t pjv = __shfl_up_sync(FULL, j, 1), pMv = __shfl_up_sync(FULL, M, 1);
         if (valid && !root) {
             const bool next_in = (lane < 31) && (((heads >> (lane + 1)) & 1u) == 0);
-            if (!next_in) jn = (k + 1 < (int64_t)slen) ? a.pj[sg.poff + k + 1] : m;
+            if (!next_in) jn = ((uint32_t)k + 1 < slen) ? a.pj[sg.poff + k + 1] : m;
             if (lane == first_lane) {   // first lane of its segment in this chunk
                 if (k > 0) {
                     pjv = a.pj[sg.poff + k - 1];
@@ -239,28 +245,31 @@ __device__ void run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, ui
                 next_col = jn;
             }
         }
-        // ---- segmented max-plus scan of the keys M'(k) + k*u
-        const int32_t keyA = MpA > AE_NEG ? MpA + colA * u : AE_KNEG;
-        const int32_t keyB = MpB > AE_NEG ? MpB + (colA + 1) * u : AE_KNEG;
+        // ---- segmented max-plus scan of the keys M'(k) + k*u of strong slots
+        const int32_t keyA = MpA > strong ? MpA + colA * u : AE_KNEG;
+        const int32_t keyB = MpB > strong ? MpB + (colA + 1) * u : AE_KNEG;
         int32_t incl = max(keyA, keyB);
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int32_t o = __shfl_up_sync(FULL, incl, d);
-            if (lane - d >= first_lane) incl = max(incl, o);
-        }
-        const int64_t k0 = __shfl_sync(FULL, k, 0);
+        const int32_t k0 = __shfl_sync(FULL, k, 0);
         const bool cont = (first_lane == 0) && valid && k0 > 0;   // segment continues from the last chunk
-        if (cont) incl = max(incl, carry);
-        int32_t excl = __shfl_up_sync(FULL, incl, 1);
-        if (lane - 1 < first_lane) excl = cont ? carry : AE_KNEG;
+        int32_t excl = AE_KNEG;
+        if (__any_sync(FULL, incl > AE_KNEG || (cont && carry > AE_KNEG))) {
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int32_t o = __shfl_up_sync(FULL, incl, d);
+                if (lane - d >= first_lane) incl = max(incl, o);
+            }
+            if (cont) incl = max(incl, carry);
+            excl = __shfl_up_sync(FULL, incl, 1);
+            if (lane - 1 < first_lane) excl = cont ? carry : AE_KNEG;
+        }
         SlotOut o;
         slot_finish(colA, MpA, hasB, MpB, next_col, excl, incl, sc, m, H, u, valid, o);
         {
-            const int64_t k31 = __shfl_sync(FULL, k, 31);
+            const uint32_t k31 = (uint32_t)__shfl_sync(FULL, k, 31);
             const bool v31 = __shfl_sync(FULL, valid, 31);
             const uint32_t len31 = __shfl_sync(FULL, slen, 31);
             const int32_t inc31 = __shfl_sync(FULL, incl, 31);
-            const bool goes_on = v31 && (k31 + 1 < (int64_t)len31);
+            const bool goes_on = v31 && (k31 + 1 < len31);
             carry = goes_on ? inc31 : AE_KNEG;
             const uint64_t sid31 = __shfl_sync(FULL, sid, 31);
             sbase = goes_on ? sid31 : sid31 + 1;
@@ -272,14 +281,24 @@ __device__ void run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, ui
         const uint32_t cnt = nA + nB + nR;
         const uint32_t hA = o.aliveA && o.MA >= H, hB = o.aliveB && o.MB >= H;
         const uint32_t hcnt = kind1 ? (hA + hB + (uint32_t)o.run_hits) : 0u;
+        // segmented inclusive sums of cnt and hcnt: without a run in the chunk every
+        // term is a 0/1 flag and the sums are population counts of ballots
         uint32_t ci = cnt, hi = hcnt;
+        if (__any_sync(FULL, nR > 0)) {
 #pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const uint32_t oc = __shfl_up_sync(FULL, ci, d), oh = __shfl_up_sync(FULL, hi, d);
-            if (lane - d >= first_lane) {
-                ci += oc;
-                hi += oh;
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t oc = __shfl_up_sync(FULL, ci, d), oh = __shfl_up_sync(FULL, hi, d);
+                if (lane - d >= first_lane) {
+                    ci += oc;
+                    hi += oh;
+                }
             }
+        } else {
+            const unsigned in_seg = le & ~((1u << first_lane) - 1u);     // lanes first_lane..lane
+            const unsigned bA = __ballot_sync(FULL, o.aliveA), bB = __ballot_sync(FULL, o.aliveB);
+            const unsigned bhA = __ballot_sync(FULL, kind1 && hA), bhB = __ballot_sync(FULL, kind1 && hB);
+            ci = __popc(bA & in_seg) + __popc(bB & in_seg);
+            hi = __popc(bhA & in_seg) + __popc(bhB & in_seg);
         }
         const bool is_last = valid && (lane == 31 || ((heads >> (lane + 1)) & 1u));
         const uint64_t rel = sid - s_first;
