@@ -150,7 +150,7 @@ struct Workspace {
     DevBuf scratch, next_seg;
     // output
     DevBuf uniq, uflags, uoff, qcount;
-    DevBuf stats, segs, ctr, seg_cnt, seg_hit;
+    DevBuf stats, segs, ctr, seg_cnt, seg_hit, task_first;
     double fr_ratio = 1.2, lf_ratio = 0.6, hit_ratio = 0.5;
     // pinned host staging
     uint64_t *h_tot = nullptr;
@@ -172,7 +172,8 @@ struct Workspace {
                 &aM[1], &aGa[0], &aGa[1], &nodes[0], &nodes[1], &cnt[0], &cnt[1], &cnt[2], &cnt[3],
                 &cnt[4], &off[0], &off[1], &off[2], &off[3], &off[4], &totals, &scan_tmp, &lj, &lM,
                 &lGa, &inj, &rhits, &sk0, &sv0, &sk1, &sv1, &sort_tmp, &hkey, &hscore, &hcount, &hk1,
-                &hv1, &scratch, &next_seg, &uniq, &uflags, &uoff, &qcount, &stats, &segs, &ctr, &seg_cnt, &seg_hit};
+                &hv1, &scratch, &next_seg, &uniq, &uflags, &uoff, &qcount, &stats, &segs, &ctr, &seg_cnt, &seg_hit,
+                &task_first};
     }
 
     ~Workspace() {
@@ -529,8 +530,9 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
         ensure(w->segs, nseg * sizeof(Seg), st);
         ensure(w->seg_cnt, nseg * 4, st);
         ensure(w->seg_hit, nseg * 4, st);
+        ensure(w->task_first, (ntrip / AE_ROW_TASK + 2) * 8, st);
         prof.mark(K_EXPAND);
-        ae_compact_segs(ca, cout[0], cout[1], ptr<Seg>(w->segs), st);
+        ae_compact_segs(ca, cout[0], cout[1], ptr<Seg>(w->segs), ptr<uint64_t>(w->task_first), st);
         prof.mark(K_EXPAND);
         const int nxt = cur ^ 1;
         RowsArgs ra;
@@ -548,6 +550,7 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
         ra.ntrip_dev = ptr<uint64_t>(w->totals) + 1;
         ra.seg_cnt = ptr<uint32_t>(w->seg_cnt);
         ra.seg_hit = ptr<uint32_t>(w->seg_hit);
+        ra.task_first = ptr<uint64_t>(w->task_first);
         ra.ctr = ptr<LevelCounters>(w->ctr);
         ra.stats = ptr<DevStats>(w->stats);
         ra.leaf_delay = opt.leaf_delay;

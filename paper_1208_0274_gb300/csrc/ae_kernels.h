@@ -68,7 +68,13 @@ struct Seg {
     uint64_t toff;
     uint64_t poff;
 };
+// Triples per k_rows task window.  A task takes the segments that start in
+// its window (the last one may run past it).
+constexpr int AE_ROW_TASK = 128;
+// k_compact also writes task_first[w] = the first segment starting at or
+// after triple w * AE_ROW_TASK, for every window w < ceil(triples / AE_ROW_TASK).
 void ae_compact_segs(const ChildrenArgs &a, const uint64_t *seg_off, const uint64_t *trip_off, Seg *segs,
+                     uint64_t *task_first,
                      cudaStream_t st);
 
 // Counters of one level: totals from the count pass (c_*), reservation
@@ -100,6 +106,7 @@ struct RowsArgs {
     DevStats *stats;
     int32_t leaf_delay;                   // levels a single-occurrence child stays in the walk
     uint32_t *seg_cnt, *seg_hit;          // per segment: outputs and hits (count pass -> write pass)
+    const uint64_t *task_first;           // per task window: its first segment (from k_compact)
     int32_t int16;                        // 1: parent and frontier rows are packed int16x2 (M | G_a << 16) in pM / fM
 };
 void ae_rows(const RowsArgs &a, bool write, int blocks, cudaStream_t st);

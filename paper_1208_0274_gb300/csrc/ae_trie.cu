@@ -67,7 +67,8 @@ __global__ void k_children(ChildrenArgs a) {
 
 // Per node: write its non-empty children as segments at the scanned offsets.
 template <int SIGMA>
-__global__ void k_compact(ChildrenArgs a, const uint64_t *seg_off, const uint64_t *trip_off, Seg *segs) {
+__global__ void k_compact(ChildrenArgs a, const uint64_t *seg_off, const uint64_t *trip_off, Seg *segs,
+                          uint64_t *task_first) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < a.nnodes;
          v += (int64_t)gridDim.x * blockDim.x) {
         const Node nd = a.nodes[v];
@@ -97,7 +98,12 @@ __global__ void k_compact(ChildrenArgs a, const uint64_t *seg_off, const uint64_
             s.cq = (uint32_t)c | cq_hi;
             s.toff = to;
             s.poff = poff;
-            segs[so++] = s;
+            segs[so] = s;
+            // task windows that begin inside this segment: the first segment at or
+            // after the window start is this one (start on its first triple) or the next
+            for (uint64_t b = (to + AE_ROW_TASK - 1) / AE_ROW_TASK * AE_ROW_TASK; b < to + len; b += AE_ROW_TASK)
+                task_first[b / AE_ROW_TASK] = b == to ? so : so + 1;
+            ++so;
             to += len;
         });
     }
@@ -114,7 +120,8 @@ __device__ __forceinline__ bool seg_stays(const Seg &sg, int delay) {
 }
 
 constexpr int RW_WARPS = 8;
-constexpr int RW_TASK = 128;   // triples per task window = max segments per task
+constexpr int RW_TASK = AE_ROW_TASK;   // triples per task window = max segments per task
+constexpr int RW_GRAB = 4;             // tasks per take from the task counter
 
 struct TaskSmem {
     uint32_t cnt[RW_TASK];
@@ -122,15 +129,6 @@ struct TaskSmem {
     uint64_t base[RW_TASK];
     uint64_t hbase[RW_TASK];
 };
-
-__device__ __forceinline__ uint64_t lower_bound_toff(const Seg *segs, uint64_t n, uint64_t t) {
-    uint64_t lo = 0, hi = n;
-    while (lo < hi) {
-        uint64_t mid = (lo + hi) >> 1;
-        if (segs[mid].toff < t) lo = mid + 1; else hi = mid;
-    }
-    return lo;
-}
 
 // Process the triples [t_beg, t_end) of one task, whose segments are
 // [s_first, s_last).  Pass 1 (WRITE = false) adds each segment's output and
@@ -427,19 +425,15 @@ __global__ void __launch_bounds__(RW_WARPS * 32, 4) k_rows(RowsArgs a) {
     unsigned long long st0 = 0, st1 = 0, st2 = 0;
     unsigned long long st_ent = 0;
     unsigned long long *task_ctr = WRITE ? &a.ctr->task_w : &a.ctr->task_c;
-    while (true) {
-        unsigned long long task = 0;
-        if (lane == 0) task = atomicAdd(task_ctr, 1ull);
-        task = __shfl_sync(FULL, task, 0);
-        if (task >= ntask) break;
-        const uint64_t w_lo = task * W, w_hi = min(T, w_lo + W);
-        uint64_t s_first = 0, s_last = 0;
-        if (lane == 0) {
-            s_first = lower_bound_toff(a.segs, S, w_lo);
-            s_last = lower_bound_toff(a.segs, S, w_hi);
-        }
-        s_first = __shfl_sync(FULL, s_first, 0);
-        s_last = __shfl_sync(FULL, s_last, 0);
+    uint64_t tot_c[5] = {0, 0, 0, 0, 0};    // count pass: this warp's level totals
+    // tasks are taken RW_GRAB at a time: one atomic on the shared counter per grab
+    for (uint64_t tb = 0;;) {
+        if (lane == 0) tb = atomicAdd(task_ctr, (unsigned long long)RW_GRAB);
+        tb = __shfl_sync(FULL, tb, 0);
+        if (tb >= ntask) break;
+    for (uint64_t task = tb; task < tb + RW_GRAB && task < ntask; ++task) {
+        const uint64_t s_first = a.task_first[task];
+        const uint64_t s_last = task + 1 < ntask ? a.task_first[task + 1] : S;
         if (s_first >= s_last) continue;
         const uint64_t nsg = s_last - s_first;
         const Seg lastseg = a.segs[s_last - 1];
@@ -459,7 +453,9 @@ __global__ void __launch_bounds__(RW_WARPS * 32, 4) k_rows(RowsArgs a) {
             }
             __syncwarp();
         }
-        // ---- per-kind totals and exclusive prefixes in segment order
+        // ---- per-kind totals and exclusive prefixes in segment order.  Per-segment
+        // counts of one group of 32 fit 32-bit sums unless a segment holds more than
+        // 2^24 outputs (a long gap run); such groups take 64-bit shuffles.
         uint64_t acc[5] = {0, 0, 0, 0, 0};   // fr_ent, lf_ent, fr_node, lf_node, hits
         for (uint64_t r0 = 0; r0 < nsg; r0 += 32) {
             const uint64_t r = r0 + lane;
@@ -479,17 +475,43 @@ __global__ void __launch_bounds__(RW_WARPS * 32, 4) k_rows(RowsArgs a) {
                     a.seg_hit[s_first + r] = sm.hit[r];
                 }
             }
+            const bool big = __any_sync(FULL, v[0] > (1u << 24) || v[1] > (1u << 24) || v[4] > (1u << 24));
+            if (!WRITE && !big) {
+#pragma unroll
+                for (int q = 0; q < 5; ++q) acc[q] += __reduce_add_sync(FULL, v[q]);
+                continue;
+            }
             uint64_t ex[5];
+            if (!big) {
+                const unsigned before = (1u << lane) - 1u;
+                const unsigned b2 = __ballot_sync(FULL, v[2]), b3 = __ballot_sync(FULL, v[3]);
+                ex[2] = acc[2] + __popc(b2 & before);
+                ex[3] = acc[3] + __popc(b3 & before);
+                acc[2] += __popc(b2);
+                acc[3] += __popc(b3);
 #pragma unroll
-            for (int q = 0; q < 5; ++q) {
-                uint64_t x = v[q];
+                for (int q = 0; q < 5; q += (q == 1 ? 3 : 1)) {   // q = 0, 1, 4
+                    uint32_t x = v[q];
 #pragma unroll
-                for (int d = 1; d < 32; d <<= 1) {
-                    const uint64_t y = __shfl_up_sync(FULL, x, d);
-                    if (lane >= d) x += y;
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const uint32_t y = __shfl_up_sync(FULL, x, d);
+                        if (lane >= d) x += y;
+                    }
+                    ex[q] = acc[q] + (x - v[q]);
+                    acc[q] += __shfl_sync(FULL, x, 31);
                 }
-                ex[q] = acc[q] + x - v[q];
-                acc[q] += __shfl_sync(FULL, x, 31);
+            } else {
+#pragma unroll
+                for (int q = 0; q < 5; ++q) {
+                    uint64_t x = v[q];
+#pragma unroll
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const uint64_t y = __shfl_up_sync(FULL, x, d);
+                        if (lane >= d) x += y;
+                    }
+                    ex[q] = acc[q] + x - v[q];
+                    acc[q] += __shfl_sync(FULL, x, 31);
+                }
             }
             if (WRITE && r < nsg) {
                 sm.base[r] = k1 ? ex[0] : ex[1];
@@ -497,13 +519,8 @@ __global__ void __launch_bounds__(RW_WARPS * 32, 4) k_rows(RowsArgs a) {
             }
         }
         if (!WRITE) {
-            if (lane == 0) {
-                if (acc[0]) atomicAdd(&a.ctr->c_fr_ent, (unsigned long long)acc[0]);
-                if (acc[1]) atomicAdd(&a.ctr->c_lf_ent, (unsigned long long)acc[1]);
-                if (acc[2]) atomicAdd(&a.ctr->c_fr_node, (unsigned long long)acc[2]);
-                if (acc[3]) atomicAdd(&a.ctr->c_lf_node, (unsigned long long)acc[3]);
-                if (acc[4]) atomicAdd(&a.ctr->c_hits, (unsigned long long)acc[4]);
-            }
+#pragma unroll
+            for (int q = 0; q < 5; ++q) tot_c[q] += acc[q];
             st_ent += acc[0] + acc[1];
             continue;
         }
@@ -563,6 +580,14 @@ __global__ void __launch_bounds__(RW_WARPS * 32, 4) k_rows(RowsArgs a) {
         run_task<SIGMA, true, I16>(a, smat, sm, s_first, s_last, t_beg, t_end, st0, st1, st2);
         __syncwarp();
     }
+    }
+    if (!WRITE && lane == 0) {
+        if (tot_c[0]) atomicAdd(&a.ctr->c_fr_ent, (unsigned long long)tot_c[0]);
+        if (tot_c[1]) atomicAdd(&a.ctr->c_lf_ent, (unsigned long long)tot_c[1]);
+        if (tot_c[2]) atomicAdd(&a.ctr->c_fr_node, (unsigned long long)tot_c[2]);
+        if (tot_c[3]) atomicAdd(&a.ctr->c_lf_node, (unsigned long long)tot_c[3]);
+        if (tot_c[4]) atomicAdd(&a.ctr->c_hits, (unsigned long long)tot_c[4]);
+    }
     if (a.stats) {
         unsigned long long t0 = st0, t1 = st1, t2 = st2;
         for (int d = 16; d > 0; d >>= 1) {
@@ -598,13 +623,13 @@ void ae_children(const ChildrenArgs &a, cudaStream_t st) {
 }
 
 void ae_compact_segs(const ChildrenArgs &a, const uint64_t *seg_off, const uint64_t *trip_off, Seg *segs,
-                     cudaStream_t st) {
+                     uint64_t *task_first, cudaStream_t st) {
     if (a.nnodes <= 0) return;
     ++g_launches;
     if (a.ix.sigma == 4)
-        k_compact<4><<<grid_for(a.nnodes, 256), 256, 0, st>>>(a, seg_off, trip_off, segs);
+        k_compact<4><<<grid_for(a.nnodes, 256), 256, 0, st>>>(a, seg_off, trip_off, segs, task_first);
     else
-        k_compact<20><<<grid_for(a.nnodes, 256), 256, 0, st>>>(a, seg_off, trip_off, segs);
+        k_compact<20><<<grid_for(a.nnodes, 256), 256, 0, st>>>(a, seg_off, trip_off, segs, task_first);
 }
 
 template <int SIGMA, bool I16>
