@@ -150,7 +150,7 @@ struct Workspace {
     DevBuf scratch, next_seg;
     // output
     DevBuf uniq, uflags, uoff, qcount;
-    DevBuf stats, segs, ctr, seg_cnt, seg_hit, task_first;
+    DevBuf stats, segs, ctr, seg_cnt, seg_hit, task_first, task_tot, task_off, task_tmp, task_sum;
     double fr_ratio = 1.2, lf_ratio = 0.6, hit_ratio = 0.5;
     // pinned host staging
     uint64_t *h_tot = nullptr;
@@ -173,7 +173,7 @@ struct Workspace {
                 &cnt[4], &off[0], &off[1], &off[2], &off[3], &off[4], &totals, &scan_tmp, &lj, &lM,
                 &lGa, &inj, &rhits, &sk0, &sv0, &sk1, &sv1, &sort_tmp, &hkey, &hscore, &hcount, &hk1,
                 &hv1, &scratch, &next_seg, &uniq, &uflags, &uoff, &qcount, &stats, &segs, &ctr, &seg_cnt, &seg_hit,
-                &task_first};
+                &task_first, &task_tot, &task_off, &task_tmp, &task_sum};
     }
 
     ~Workspace() {
@@ -562,8 +562,23 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
         h0.lf_node = (unsigned long long)lf_node_base;
         h0.hits = (unsigned long long)rh_base;
         CU(cudaMemcpyAsync(w->ctr.p, &h0, sizeof(h0), cudaMemcpyHostToDevice, st));
+        const int64_t ntask = (ntrip + AE_ROW_TASK - 1) / AE_ROW_TASK;
+        ensure(w->task_tot, (size_t)std::max<int64_t>(ntask, 1) * 5 * 4, st);
+        ensure(w->task_off, (size_t)std::max<int64_t>(ntask, 1) * 5 * 8, st);
+        ensure(w->task_tmp, (size_t)ae_scan_tmp_words(std::max<int64_t>(ntask, 1), 5) * 8, st);
+        ensure(w->task_sum, 5 * 8, st);
+        ra.task_tot = ptr<uint32_t>(w->task_tot);
+        ra.task_stride = (uint64_t)ntask;
         prof.mark(K_ROWS);
         ae_rows(ra, false, num_sms * 4, st);
+        // write-pass bases: exclusive scan of the per-task output counts
+        const uint32_t *tin[5];
+        uint64_t *tout[5];
+        for (int q = 0; q < 5; ++q) {
+            tin[q] = ptr<uint32_t>(w->task_tot) + q * ntask;
+            tout[q] = ptr<uint64_t>(w->task_off) + q * ntask;
+        }
+        ae_scan_u32(tin, tout, 5, ntask, ptr<uint64_t>(w->task_sum), ptr<uint64_t>(w->task_tmp), st);
         prof.mark(K_ROWS);
         LevelCounters hc;
         CU(cudaMemcpyAsync(tot(), w->ctr.p, sizeof(hc), cudaMemcpyDeviceToHost, st));
@@ -597,6 +612,12 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
         ra.rhits = ptr<RangeHit>(w->rhits);
         ra.hit_cap = (uint64_t)(rh_base + hits);
         ra.stats = ptr<DevStats>(w->stats);
+        ra.task_off = hc.wide ? nullptr : ptr<uint64_t>(w->task_off);
+        ra.base_off[0] = 0;
+        ra.base_off[1] = (uint64_t)lf_ent_base;
+        ra.base_off[2] = 0;
+        ra.base_off[3] = (uint64_t)lf_node_base;
+        ra.base_off[4] = (uint64_t)rh_base;
         prof.mark(K_ROWS);
         ae_rows(ra, true, num_sms * 4, st);
         prof.mark(K_ROWS);

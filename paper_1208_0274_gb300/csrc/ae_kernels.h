@@ -82,7 +82,7 @@ void ae_compact_segs(const ChildrenArgs &a, const uint64_t *seg_off, const uint6
 struct LevelCounters {
     unsigned long long c_fr_ent, c_fr_node, c_lf_ent, c_lf_node, c_hits;
     unsigned long long fr_ent, fr_node, lf_ent, lf_node, hits;
-    unsigned long long overflow, task_c, task_w, pad;
+    unsigned long long overflow, task_c, task_w, wide;   // wide: a task total passed 2^32 - 1
 };
 
 struct RowsArgs {
@@ -107,6 +107,13 @@ struct RowsArgs {
     int32_t leaf_delay;                   // levels a single-occurrence child stays in the walk
     uint32_t *seg_cnt, *seg_hit;          // per segment: outputs and hits (count pass -> write pass)
     const uint64_t *task_first;           // per task window: its first segment (from k_compact)
+    // count pass: per task and arena kind (fr_ent, lf_ent, fr_node, lf_node, hits) its output
+    // count, at task_tot[kind * task_stride + task]; write pass: their exclusive scan task_off
+    // (or NULL: reserve with atomics on ctr) plus the level bases base_off[kind]
+    uint32_t *task_tot;
+    const uint64_t *task_off;
+    uint64_t task_stride;
+    uint64_t base_off[5];
     int32_t int16;                        // 1: parent and frontier rows are packed int16x2 (M | G_a << 16) in pM / fM
 };
 void ae_rows(const RowsArgs &a, bool write, int blocks, cudaStream_t st);

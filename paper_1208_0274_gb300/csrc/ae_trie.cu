@@ -434,7 +434,10 @@ __global__ void __launch_bounds__(RW_WARPS * 32, 4) k_rows(RowsArgs a) {
     for (uint64_t task = tb; task < tb + RW_GRAB && task < ntask; ++task) {
         const uint64_t s_first = a.task_first[task];
         const uint64_t s_last = task + 1 < ntask ? a.task_first[task + 1] : S;
-        if (s_first >= s_last) continue;
+        if (s_first >= s_last) {
+            if (!WRITE && lane < 5) a.task_tot[lane * a.task_stride + task] = 0u;
+            continue;
+        }
         const uint64_t nsg = s_last - s_first;
         const Seg lastseg = a.segs[s_last - 1];
         const uint64_t t_beg = a.segs[s_first].toff, t_end = lastseg.toff + (lastseg.len & 0x0FFFFFFFu);
@@ -520,20 +523,33 @@ __global__ void __launch_bounds__(RW_WARPS * 32, 4) k_rows(RowsArgs a) {
         }
         if (!WRITE) {
 #pragma unroll
-            for (int q = 0; q < 5; ++q) tot_c[q] += acc[q];
+            for (int q = 0; q < 5; ++q) {
+                tot_c[q] += acc[q];
+                if (lane == q) {
+                    a.task_tot[q * a.task_stride + task] = (uint32_t)acc[q];
+                    if (acc[q] > 0xFFFFFFFFull) atomicExch(&a.ctr->wide, 1ull);
+                }
+            }
             st_ent += acc[0] + acc[1];
             continue;
         }
+        // output ranges of this task: the scanned count-pass totals, or (after a
+        // task total too wide for the scan) one atomic reservation per arena
         unsigned long long b[5] = {0, 0, 0, 0, 0};
-        if (lane == 0) {
-            b[0] = atomicAdd(&a.ctr->fr_ent, (unsigned long long)acc[0]);
-            b[1] = atomicAdd(&a.ctr->lf_ent, (unsigned long long)acc[1]);
-            b[2] = atomicAdd(&a.ctr->fr_node, (unsigned long long)acc[2]);
-            b[3] = atomicAdd(&a.ctr->lf_node, (unsigned long long)acc[3]);
-            b[4] = atomicAdd(&a.ctr->hits, (unsigned long long)acc[4]);
-        }
+        if (a.task_off) {
 #pragma unroll
-        for (int q = 0; q < 5; ++q) b[q] = __shfl_sync(FULL, b[q], 0);
+            for (int q = 0; q < 5; ++q) b[q] = a.base_off[q] + a.task_off[q * a.task_stride + task];
+        } else {
+            if (lane == 0) {
+                b[0] = atomicAdd(&a.ctr->fr_ent, (unsigned long long)acc[0]);
+                b[1] = atomicAdd(&a.ctr->lf_ent, (unsigned long long)acc[1]);
+                b[2] = atomicAdd(&a.ctr->fr_node, (unsigned long long)acc[2]);
+                b[3] = atomicAdd(&a.ctr->lf_node, (unsigned long long)acc[3]);
+                b[4] = atomicAdd(&a.ctr->hits, (unsigned long long)acc[4]);
+            }
+#pragma unroll
+            for (int q = 0; q < 5; ++q) b[q] = __shfl_sync(FULL, b[q], 0);
+        }
         // the count pass sized every arena exactly; a reservation past the end
         // means the two passes disagreed, which is reported, never written
         const bool ovf = b[0] + acc[0] > a.fr_ent_cap || b[1] + acc[1] > a.lf_ent_cap ||
