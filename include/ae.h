@@ -80,7 +80,7 @@ typedef struct {
     int64_t nodes;          /* trie nodes whose rows were computed (range size >= 2) */
     int64_t leaf_rows;      /* rows computed along unique text positions */
     int64_t entries;        /* live DP entries written */
-    int64_t entries_tier[3];
+    int64_t entries_tier[3];   /* with ae_options.tier_stats: trie entries by cost tier */
     int64_t injections;     /* trie rows handed to the text-position sweep */
     int64_t raw_hits;       /* hit records before the per-cell max */
     int64_t hits;           /* distinct (query, text end, query end) results */
@@ -124,6 +124,8 @@ typedef struct {
                                  hit buffer is then sized from the hints of its queries instead of
                                  from the previous searches on the stream.  A low hint costs one
                                  rerun of the sweep, never a result */
+    int32_t tier_stats;       /* 1: count trie entries by cost tier into ae_stats.entries_tier
+                                 (a few instructions per entry); 0: leave them 0 */
 } ae_options;
 
 /* Fill *opt with the defaults. */

@@ -43,7 +43,7 @@ class ae_options(ctypes.Structure):
                 ("item_columns", ctypes.c_int64), ("batch_columns", ctypes.c_int64),
                 ("leaf_capacity", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("leaf_delay", ctypes.c_int32), ("int16_limit", ctypes.c_int32),
-                ("hint_hits", ctypes.c_void_p)]
+                ("hint_hits", ctypes.c_void_p), ("tier_stats", ctypes.c_int32)]
 
 
 class ae_stats(ctypes.Structure):

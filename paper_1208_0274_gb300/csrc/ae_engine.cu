@@ -150,7 +150,7 @@ struct Workspace {
     DevBuf scratch, next_seg;
     // output
     DevBuf uniq, uflags, uoff, qcount;
-    DevBuf stats, segs, ctr, seg_cnt, seg_hit, task_first, task_tot, task_off, task_tmp, task_sum;
+    DevBuf stats, segs, ctr, seg_cnt, seg_hit, task_first, task_tot, task_off, task_tmp, task_sum, res, task_flag;
     double fr_ratio = 1.2, lf_ratio = 0.6, hit_ratio = 0.5;
     // pinned host staging
     uint64_t *h_tot = nullptr;
@@ -173,7 +173,7 @@ struct Workspace {
                 &cnt[4], &off[0], &off[1], &off[2], &off[3], &off[4], &totals, &scan_tmp, &lj, &lM,
                 &lGa, &inj, &rhits, &sk0, &sv0, &sk1, &sv1, &sort_tmp, &hkey, &hscore, &hcount, &hk1,
                 &hv1, &scratch, &next_seg, &uniq, &uflags, &uoff, &qcount, &stats, &segs, &ctr, &seg_cnt, &seg_hit,
-                &task_first, &task_tot, &task_off, &task_tmp, &task_sum};
+                &task_first, &task_tot, &task_off, &task_tmp, &task_sum, &res, &task_flag};
     }
 
     ~Workspace() {
@@ -555,6 +555,7 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
         ra.stats = ptr<DevStats>(w->stats);
         ra.leaf_delay = opt.leaf_delay;
         ra.int16 = i16 ? 1 : 0;
+        ra.tiers = opt.tier_stats ? 1 : 0;
         // count pass: exact output sizes of this level
         LevelCounters h0;
         memset(&h0, 0, sizeof(h0));
@@ -569,6 +570,14 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
         ensure(w->task_sum, 5 * 8, st);
         ra.task_tot = ptr<uint32_t>(w->task_tot);
         ra.task_stride = (uint64_t)ntask;
+        ra.res = nullptr;
+        ra.task_flag = nullptr;
+        if (i16 && !opt.tier_stats) {
+            ensure(w->res, (size_t)std::max<int64_t>(ntrip, 1) * 4, st);
+            ensure(w->task_flag, (size_t)std::max<int64_t>(ntask, 1), st);
+            ra.res = ptr<uint32_t>(w->res);
+            ra.task_flag = ptr<uint8_t>(w->task_flag);
+        }
         prof.mark(K_ROWS);
         ae_rows(ra, false, num_sms * 4, st);
         // write-pass bases: exclusive scan of the per-task output counts
@@ -756,6 +765,7 @@ void Search::leaf_phase(int64_t ninj) {
         la.hit_cap = (uint64_t)(nhits + hit_cap);
         la.be = be;
         la.bj = bj;
+        la.tiers = opt.tier_stats ? 1 : 0;
         la.stats = ptr<DevStats>(w->stats);
         prof.mark(K_LEAF);
         ++stats.leaf_sweeps;
@@ -994,6 +1004,7 @@ void ae_options_default(ae_options *opt) {
     opt->leaf_delay = 8;
     opt->int16_limit = 32000;
     opt->hint_hits = nullptr;
+    opt->tier_stats = 0;
 }
 
 const char *ae_strerror(int32_t status) {

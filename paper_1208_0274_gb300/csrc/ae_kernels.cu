@@ -441,7 +441,7 @@ __global__ void __launch_bounds__(128, 6) k_leaf(LeafArgs a) {
                             atomicAdd(&a.stats->hit_overflow, 1ull);
                         }
                     }
-                    st_t0 += (unsigned long long)rlen;
+                    if (a.tiers && lane == 0) st_t0 += (unsigned long long)rlen;   // warp-uniform count
                     ++st_rows;
                     ++seg_steps;
                     st_ent += (unsigned long long)rlen;
@@ -524,16 +524,18 @@ __global__ void __launch_bounds__(128, 6) k_leaf(LeafArgs a) {
                     } else if (htot && lane == 0) {
                         atomicAdd(&a.stats->hit_overflow, 1ull);
                     }
-                    if (o.aliveA) {
-                        const int tier = (Dp > AE_NEG) + (GaA > AE_NEG) + (o.GbA > thr_of(colA, m, H, g));
-                        st_t0 += tier <= 1;
-                        st_t1 += tier == 2;
-                        st_t2 += tier >= 3;
+                    if (a.tiers) {
+                        if (o.aliveA) {
+                            const int tier = (Dp > AE_NEG) + (GaA > AE_NEG) + (o.GbA > thr_of(colA, m, H, g));
+                            st_t0 += tier <= 1;
+                            st_t1 += tier == 2;
+                            st_t2 += tier >= 3;
+                        }
+                        if (o.aliveB) {
+                            if ((Dk > AE_NEG) && (o.GbB > thr_of(colA + 1, m, H, g))) ++st_t1; else ++st_t0;
+                        }
+                        st_t0 += nR;
                     }
-                    if (o.aliveB) {
-                        if ((Dk > AE_NEG) && (o.GbB > thr_of(colA + 1, m, H, g))) ++st_t1; else ++st_t0;
-                    }
-                    st_t0 += nR;
                     const int64_t e0 = (int64_t)(ci - cn);
                     if (tot > cap) {
                         overflow = true;
@@ -642,6 +644,156 @@ __global__ void __launch_bounds__(128, 6) k_leaf(LeafArgs a) {
                     tw = (p + lane < a.ix.n) ? a.ix.text[p + lane] : 0u;
                 }
                 const int c = (int)__shfl_sync(FULL, tw, (int)(p - tw_base));
+                if (!(nk_qid == qid && nk_e == p)) {
+                    // ---- wide step with nothing to merge: slots and the horizontal
+                    // finish chunk by chunk, straight from R into Rn (same result
+                    // as generate + finish below, one pass over the row)
+                    int64_t nlen = 0;
+                    int32_t carry = AE_KNEG, prev_j = -2, prev_M = AE_NEG;
+                    for (int64_t base = 0; base < rlen; base += 32) {
+                        const int64_t idx = base + lane;
+                        const bool valid = idx < rlen;
+                        int32_t j = m, M = AE_NEG, Ga = AE_NEG;
+                        if (valid) {
+                            j = R.j[idx];
+                            M = R.M[idx];
+                            Ga = R.Ga[idx];
+                        }
+                        int32_t jn = __shfl_down_sync(FULL, j, 1);
+                        if (lane == 31 && idx + 1 < rlen) jn = R.j[idx + 1];
+                        if (idx + 1 >= rlen) jn = m;
+                        int32_t pjv = __shfl_up_sync(FULL, j, 1), pMv = __shfl_up_sync(FULL, M, 1);
+                        if (lane == 0) {
+                            pjv = prev_j;
+                            pMv = prev_M;
+                        }
+                        int32_t colA = m, MpA = AE_NEG, GaA = AE_NEG, MpB = AE_NEG, next_col = m;
+                        int32_t Dp = AE_NEG, Dk = AE_NEG;
+                        bool hasB = false;
+                        if (valid) {
+                            colA = j;
+                            const int32_t tA = thr_of(j, m, H, g);
+                            if (pjv + 1 == j && pMv > AE_NEG) {
+                                const int32_t D = pMv + delta_of(sc, smat, c, P[j]);
+                                Dp = D > tA ? D : AE_NEG;
+                            }
+                            const int32_t gap = gap_from_i32(M, Ga, sc.ss, oe);
+                            GaA = gap > tA ? gap : AE_NEG;
+                            MpA = max(Dp, GaA);
+                            hasB = (j + 1 < m) && (j + 1 != jn);
+                            if (hasB) {
+                                const int32_t D = M + delta_of(sc, smat, c, P[j + 1]);
+                                Dk = D > thr_of(j + 1, m, H, g) ? D : AE_NEG;
+                                MpB = Dk;
+                            }
+                            next_col = jn;
+                        }
+                        const int32_t keyA = MpA > AE_NEG ? MpA + colA * u : AE_KNEG;
+                        const int32_t keyB = MpB > AE_NEG ? MpB + (colA + 1) * u : AE_KNEG;
+                        int32_t incl = warp_incl_max(max(keyA, keyB));
+                        int32_t excl = __shfl_up_sync(FULL, incl, 1);
+                        if (lane == 0) excl = AE_KNEG;
+                        incl = max(incl, carry);
+                        excl = max(excl, carry);
+                        SlotOut o;
+                        slot_finish(colA, MpA, hasB, MpB, next_col, excl, incl, sc, m, H, u, valid, o);
+                        carry = __shfl_sync(FULL, incl, 31);
+                        prev_j = __shfl_sync(FULL, j, 31);
+                        prev_M = __shfl_sync(FULL, M, 31);
+                        const uint32_t nA = o.aliveA, nB = o.aliveB, nR = (uint32_t)o.run_len;
+                        const uint32_t cn = nA + nB + nR;
+                        const uint32_t ci = warp_incl_sum(cn);
+                        const uint32_t tot = __shfl_sync(FULL, ci, 31);
+                        if (nlen + tot > cap) {
+                            overflow = true;
+                            break;
+                        }
+                        const uint32_t hA = o.aliveA && o.MA >= H, hB = o.aliveB && o.MB >= H;
+                        const uint32_t hc = hA + hB + (uint32_t)o.run_hits;
+                        const uint32_t hi = warp_incl_sum(hc);
+                        const uint32_t htot = __shfl_sync(FULL, hi, 31);
+                        unsigned long long hbase = 0;
+                        if (htot) {
+                            if (lane == 0) hbase = atomicAdd(a.hit_count, (unsigned long long)htot);
+                            hbase = __shfl_sync(FULL, hbase, 0);
+                        }
+                        const bool hok = hbase + htot <= a.hit_cap;
+                        const uint64_t kq = ((uint64_t)qid << (a.be + a.bj)) | ((uint64_t)(uint32_t)p << a.bj);
+                        const int64_t e0 = nlen + (int64_t)(ci - cn);
+                        const uint64_t h0 = hbase + hi - hc;
+                        if (o.aliveA) {
+                            Rn.j[e0] = colA;
+                            Rn.M[e0] = o.MA;
+                            Rn.Ga[e0] = GaA;
+                            if (hA && hok) {
+                                a.hit_key[h0] = kq | ((uint64_t)colA & jmask);
+                                a.hit_score[h0] = o.MA;
+                            }
+                            if (a.tiers) {
+                                const int tier = (Dp > AE_NEG) + (GaA > AE_NEG) + (o.GbA > thr_of(colA, m, H, g));
+                                st_t0 += tier <= 1;
+                                st_t1 += tier == 2;
+                                st_t2 += tier >= 3;
+                            }
+                        }
+                        if (o.aliveB) {
+                            Rn.j[e0 + nA] = colA + 1;
+                            Rn.M[e0 + nA] = o.MB;
+                            Rn.Ga[e0 + nA] = AE_NEG;
+                            if (hB && hok) {
+                                a.hit_key[h0 + hA] = kq | ((uint64_t)(colA + 1) & jmask);
+                                a.hit_score[h0 + hA] = o.MB;
+                            }
+                            if (a.tiers) {
+                                if ((Dk > AE_NEG) && (o.GbB > thr_of(colA + 1, m, H, g))) ++st_t1; else ++st_t0;
+                            }
+                        }
+                        if (a.tiers) st_t0 += nR;
+                        unsigned rmask = __ballot_sync(FULL, nR > 0);
+                        while (rmask) {
+                            const int L = __ffs(rmask) - 1;
+                            rmask &= rmask - 1;
+                            const int32_t s0 = __shfl_sync(FULL, o.run_start, L);
+                            const int32_t rl = __shfl_sync(FULL, o.run_len, L);
+                            const int32_t rh = __shfl_sync(FULL, o.run_hits, L);
+                            const int32_t K = __shfl_sync(FULL, incl, L);
+                            const int64_t d0 = __shfl_sync(FULL, e0 + nA + nB, L);
+                            const uint64_t hd = __shfl_sync(FULL, h0 + hA + hB, L);
+                            for (int32_t t = lane; t < rl; t += 32) {
+                                const int32_t cc = s0 + t;
+                                const int32_t v = sc.sg - cc * u + K;
+                                Rn.j[d0 + t] = cc;
+                                Rn.M[d0 + t] = v;
+                                Rn.Ga[d0 + t] = AE_NEG;
+                                if (t < rh && hok) {
+                                    a.hit_key[hd + t] = kq | ((uint64_t)cc & jmask);
+                                    a.hit_score[hd + t] = v;
+                                }
+                            }
+                        }
+                        if (htot && !hok && lane == 0) atomicAdd(&a.stats->hit_overflow, 1ull);
+                        nlen += tot;
+                    }
+                    __syncwarp();
+                    if (overflow) break;
+                    Buf t = R;
+                    R = Rn;
+                    Rn = t;
+                    rlen = nlen;
+                    ++st_rows;
+                    ++seg_steps;
+                    seg_width = max(seg_width, (unsigned long long)nlen);
+                    st_ent += (unsigned long long)nlen;
+                    if (rlen <= 32) {
+                        if (lane < rlen) {
+                            rj = R.j[lane];
+                            rM = R.M[lane];
+                            rGa = R.Ga[lane];
+                        }
+                        inreg = true;
+                    }
+                    continue;
+                }
                 // ---- generate slots from R with letter c
                 int32_t prev_j = -2, prev_M = AE_NEG;
                 for (int64_t base = 0; base < rlen; base += 32) {
@@ -821,16 +973,18 @@ __global__ void __launch_bounds__(128, 6) k_leaf(LeafArgs a) {
                     Rn.j[e0] = col;
                     Rn.M[e0] = o.MA;
                     Rn.Ga[e0] = Ga;
-                    int tier = (Mp > AE_NEG) + (Ga > AE_NEG) + (o.GbA > thr_of(col, m, H, g));
-                    st_t0 += tier <= 1;
+                    if (a.tiers) {
+                        const int tier = (Mp > AE_NEG) + (Ga > AE_NEG) + (o.GbA > thr_of(col, m, H, g));
+                        st_t0 += tier <= 1;
                         st_t1 += tier == 2;
                         st_t2 += tier >= 3;
+                    }
                     if (hA && hok) {
                         a.hit_key[h0] = kq | ((uint64_t)col & jmask);
                         a.hit_score[h0] = o.MA;
                     }
                 }
-                st_t0 += nR;
+                if (a.tiers) st_t0 += nR;
                 unsigned rmask = __ballot_sync(FULL, nR > 0);
                 while (rmask) {
                     const int L = __ffs(rmask) - 1;

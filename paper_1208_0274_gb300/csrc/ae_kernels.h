@@ -115,6 +115,11 @@ struct RowsArgs {
     uint64_t task_stride;
     uint64_t base_off[5];
     int32_t int16;                        // 1: parent and frontier rows are packed int16x2 (M | G_a << 16) in pM / fM
+    int32_t tiers;                        // 1: count entries by cost tier (ae_stats.entries_tier)
+    // int16x2 route without tier counting: per triple the final slot values of the count
+    // pass (M_A | M_B << 16, 0 = dead) and per task whether it produced a gap run
+    uint32_t *res;
+    uint8_t *task_flag;
 };
 void ae_rows(const RowsArgs &a, bool write, int blocks, cudaStream_t st);
 void ae_mg_to_i32(int32_t *M, int32_t *Ga, int64_t n, cudaStream_t st);
@@ -137,6 +142,7 @@ struct LeafArgs {
     unsigned long long *hit_count;
     uint64_t hit_cap;
     int32_t be, bj;               // key packing widths
+    int32_t tiers;                // 1: count entries by cost tier
     DevStats *stats;
 };
 void ae_inject_keys(const Inject *inj, int64_t ninj, uint64_t *keys, uint32_t *vals, cudaStream_t st);

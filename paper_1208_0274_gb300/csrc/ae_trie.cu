@@ -134,10 +134,16 @@ struct TaskSmem {
 // [s_first, s_last).  Pass 1 (WRITE = false) adds each segment's output and
 // hit counts into sm; pass 2 writes entries and hits at sm.base/hbase plus
 // the running counts.
+//
+// With a.res (int16x2 route), the count pass also stores each triple's final
+// slot values (M of slot A in the low, of slot B in the high halfword; 0 =
+// dead), and the return value tells whether any triple of the task produced
+// a gap run; tasks without runs are then written by run_task_stored.
 template <int SIGMA, bool WRITE, bool I16>
-__device__ void run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, uint64_t s_first, uint64_t s_last,
+__device__ bool run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, uint64_t s_first, uint64_t s_last,
                          uint64_t t_beg, uint64_t t_end, unsigned long long &st0, unsigned long long &st1,
                          unsigned long long &st2) {
+    bool any_run = false;
     const int lane = threadIdx.x & 31;
     const unsigned le = (lane == 31) ? 0xffffffffu : ((1u << (lane + 1)) - 1u);
     const ScoreView &sc = a.sc;
@@ -305,6 +311,9 @@ __device__ void run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, ui
                 sm.cnt[rel] += ci;
                 sm.hit[rel] += hi;
             }
+            if (I16 && a.res && valid)
+                a.res[t_beg + t] = (o.aliveA ? (uint32_t)o.MA : 0u) | ((o.aliveB ? (uint32_t)o.MB : 0u) << 16);
+            any_run |= __any_sync(FULL, nR > 0);
             __syncwarp();
             continue;
         }
@@ -341,10 +350,12 @@ __device__ void run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, ui
                 oM[e0] = o.MA;
                 oGa[e0] = GaA;
             }
-            const int tier = (Dprev > AE_NEG) + (Gap > AE_NEG) + (o.GbA > thr_of(colA, m, H, g));
-            st0 += tier <= 1;
-            st1 += tier == 2;
-            st2 += tier == 3;
+            if (a.tiers) {
+                const int tier = (Dprev > AE_NEG) + (Gap > AE_NEG) + (o.GbA > thr_of(colA, m, H, g));
+                st0 += tier <= 1;
+                st1 += tier == 2;
+                st2 += tier == 3;
+            }
         }
         if (o.aliveB) {
             oj[e0 + nA] = colA + 1;
@@ -354,11 +365,13 @@ __device__ void run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, ui
                 oM[e0 + nA] = o.MB;
                 oGa[e0 + nA] = AE_NEG;
             }
-            const int tier = (Dk > AE_NEG) + (o.GbB > thr_of(colA + 1, m, H, g));
-            st0 += tier <= 1;
-            st1 += tier == 2;
+            if (a.tiers) {
+                const int tier = (Dk > AE_NEG) + (o.GbB > thr_of(colA + 1, m, H, g));
+                st0 += tier <= 1;
+                st1 += tier == 2;
+            }
         }
-        st0 += nR;
+        if (a.tiers) st0 += nR;
         if (kind1) {
             uint64_t hp = h0;
             if (hA) {
@@ -400,6 +413,133 @@ __device__ void run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, ui
                     RangeHit r = {rlo, rhi, rq, col, v, 0};
                     a.rhits[hd + tt] = r;
                 }
+            }
+        }
+        __syncwarp();
+    }
+    return any_run;
+}
+
+// Write pass of a task without gap runs, from the slot values the count pass
+// stored (int16x2 route): the same outputs at the same places as run_task
+// with WRITE, without recomputing the recurrence.  G_a of slot A is the
+// vertical gap of the parent entry (Section 2.2), recomputed from the parent.
+template <int SIGMA>
+__device__ void run_task_stored(const RowsArgs &a, TaskSmem &sm, uint64_t s_first, uint64_t s_last,
+                                uint64_t t_beg, uint64_t t_end) {
+    const int lane = threadIdx.x & 31;
+    const unsigned le = (lane == 31) ? 0xffffffffu : ((1u << (lane + 1)) - 1u);
+    const ScoreView &sc = a.sc;
+    const int32_t oe = sc.sg + sc.ss, g = sc.gmax;
+    uint64_t sbase = s_first;
+    const uint32_t t_len = (uint32_t)(t_end - t_beg);
+    for (uint32_t t0 = 0; t0 < t_len; t0 += 32) {
+        const uint32_t t = t0 + lane;
+        const bool valid = t < t_len;
+        const uint32_t woff = (sbase + lane < s_last) ? (uint32_t)(a.segs[sbase + lane].toff - t_beg) : 0xFFFFFFFFu;
+        int i = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const uint32_t o = __shfl_sync(FULL, woff, i + step);
+            if (o <= t) i += step;
+        }
+        const uint64_t sid = sbase + i;
+        Seg sg;
+        sg.len = 0;
+        sg.toff = 0;
+        sg.poff = 0;
+        sg.lo = sg.hi = 0;
+        sg.cq = 0;
+        if (valid) sg = a.segs[sid];
+        const int32_t k = valid ? (int32_t)(t - (uint32_t)(sg.toff - t_beg)) : 0;
+        const uint32_t slen = sg.len & 0x0FFFFFFFu;
+        const int32_t qid = (int32_t)((sg.cq >> 5) & 0xFFFFFFu);
+        const bool root = (sg.cq >> 31) != 0;
+        const unsigned heads = __ballot_sync(FULL, !valid || k == 0 || lane == 0);
+        const int first_lane = 31 - __clz(heads & le);
+        const uint32_t w = valid ? a.res[t_beg + t] : 0u;
+        const int32_t MA = (int32_t)(w & 0xFFFFu), MB = (int32_t)(w >> 16);
+        const bool aliveA = MA > 0, aliveB = MB > 0;
+        int32_t colA = 0, GaA = AE_NEG, H = 1, m = 1;
+        if (valid) {
+            H = a.qv.H[qid];
+            if (root) {
+                colA = (int32_t)(uint32_t)sg.poff + k;
+            } else {
+                colA = a.pj[sg.poff + k];
+                if (aliveA) {
+                    m = a.qv.m[qid];
+                    const uint32_t mg = reinterpret_cast<const uint32_t *>(a.pM)[sg.poff + k];
+                    const int32_t gap = gap_from_mg(mg, sc.ss, oe);
+                    GaA = gap > thr_of(colA, m, H, g) ? gap : AE_NEG;
+                }
+            }
+        }
+        {
+            const uint32_t k31 = (uint32_t)__shfl_sync(FULL, k, 31);
+            const bool v31 = __shfl_sync(FULL, valid, 31);
+            const uint32_t len31 = __shfl_sync(FULL, slen, 31);
+            const uint64_t sid31 = __shfl_sync(FULL, sid, 31);
+            sbase = (v31 && k31 + 1 < len31) ? sid31 : sid31 + 1;
+        }
+        const bool kind1 = valid && seg_stays(sg, a.leaf_delay);
+        const uint32_t nA = aliveA, nB = aliveB;
+        const uint32_t cnt = nA + nB;
+        const uint32_t hA = aliveA && MA >= H, hB = aliveB && MB >= H;
+        const uint32_t hcnt = kind1 ? (hA + hB) : 0u;
+        const unsigned in_seg = le & ~((1u << first_lane) - 1u);
+        const unsigned bA = __ballot_sync(FULL, aliveA), bB = __ballot_sync(FULL, aliveB);
+        const unsigned bhA = __ballot_sync(FULL, kind1 && hA), bhB = __ballot_sync(FULL, kind1 && hB);
+        const uint32_t ci = __popc(bA & in_seg) + __popc(bB & in_seg);
+        const uint32_t hi = __popc(bhA & in_seg) + __popc(bhB & in_seg);
+        const bool is_last = valid && (lane == 31 || ((heads >> (lane + 1)) & 1u));
+        const uint64_t rel = sid - s_first;
+        uint64_t e0 = 0, h0 = 0;
+        int32_t *oj = nullptr, *oM = nullptr, *oGa = nullptr;
+        if (valid) {
+            e0 = sm.base[rel] + sm.cnt[rel] + (ci - cnt);
+            h0 = sm.hbase[rel] + sm.hit[rel] + (hi - hcnt);
+            if (kind1) {
+                oj = a.fj;
+                oM = a.fM;
+            } else {
+                oj = a.lj;
+                oM = a.lM;
+                oGa = a.lGa;
+            }
+        }
+        __syncwarp();
+        if (is_last) {
+            sm.cnt[rel] += ci;
+            sm.hit[rel] += hi;
+        }
+        if (aliveA) {
+            oj[e0] = colA;
+            if (kind1) {
+                reinterpret_cast<uint32_t *>(oM)[e0] = pack_mg(MA, GaA);
+            } else {
+                oM[e0] = MA;
+                oGa[e0] = GaA;
+            }
+        }
+        if (aliveB) {
+            oj[e0 + nA] = colA + 1;
+            if (kind1) {
+                reinterpret_cast<uint32_t *>(oM)[e0 + nA] = pack_mg(MB, AE_NEG);
+            } else {
+                oM[e0 + nA] = MB;
+                oGa[e0 + nA] = AE_NEG;
+            }
+        }
+        if (kind1) {
+            uint64_t hp = h0;
+            if (hA) {
+                RangeHit r = {sg.lo, sg.hi, qid, colA, MA, 0};
+                a.rhits[hp++] = r;
+            }
+            if (hB) {
+                RangeHit r = {sg.lo, sg.hi, qid, colA + 1, MB, 0};
+                a.rhits[hp++] = r;
             }
         }
         __syncwarp();
@@ -447,7 +587,8 @@ __global__ void __launch_bounds__(RW_WARPS * 32, 4) k_rows(RowsArgs a) {
                 sm.hit[r] = 0;
             }
             __syncwarp();
-            run_task<SIGMA, false, I16>(a, smat, sm, s_first, s_last, t_beg, t_end, st0, st1, st2);
+            const bool any_run = run_task<SIGMA, false, I16>(a, smat, sm, s_first, s_last, t_beg, t_end, st0, st1, st2);
+            if (I16 && a.res && lane == 0) a.task_flag[task] = any_run ? 1 : 0;
             __syncwarp();
         } else {
             for (uint64_t r = lane; r < nsg; r += 32) {
@@ -593,7 +734,10 @@ __global__ void __launch_bounds__(RW_WARPS * 32, 4) k_rows(RowsArgs a) {
             sm.hit[r] = 0;
         }
         __syncwarp();
-        run_task<SIGMA, true, I16>(a, smat, sm, s_first, s_last, t_beg, t_end, st0, st1, st2);
+        if (I16 && a.res && !a.task_flag[task])
+            run_task_stored<SIGMA>(a, sm, s_first, s_last, t_beg, t_end);
+        else
+            run_task<SIGMA, true, I16>(a, smat, sm, s_first, s_last, t_beg, t_end, st0, st1, st2);
         __syncwarp();
     }
     }

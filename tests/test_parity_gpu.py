@@ -72,6 +72,12 @@ def test_dna_small_workload_full_parity(small):
     st = ae.ae_last_stats()
     assert st["entries"] > 0 and st["hits"] == want.size and st["seed_depth"] == 3
     assert st["levels_int16"] == st["levels"]          # DNA rows never leave the int16 route here
+    assert st["entries_tier"] == [0, 0, 0]             # tier counting is off by default
+    # with tier_stats every entry (of the trie levels and of the sweep) falls in one tier
+    hits2, _ = ae.ae_search(idx, wl.queries, wl.scheme, wl.H, options=ae.make_options(tier_stats=1))
+    assert np.array_equal(hits2, hits)
+    st2 = ae.ae_last_stats()
+    assert sum(st2["entries_tier"]) == st2["entries"] and st2["entries_tier"][0] > 0
 
 
 @pytest.mark.parametrize("opts", [dict(qprefix_seed=0), dict(leaf_segment=1), dict(leaf_segment=7),
