@@ -769,6 +769,7 @@ void Search::leaf_phase(int64_t ninj) {
         la.stats = ptr<DevStats>(w->stats);
         prof.mark(K_LEAF);
         ++stats.leaf_sweeps;
+        const auto t_sweep = std::chrono::steady_clock::now();
         ae_leaf_sweep(la, blocks, threads, st);
         prof.mark(K_LEAF);
         CU(cudaGetLastError());
@@ -781,9 +782,9 @@ void Search::leaf_phase(int64_t ninj) {
         hdr[1] = tot()[1];
         hdr[2] = tot()[2];
         if (trace())
-            fprintf(stderr, "[ae leaf] injections %lld attempt %d: hits %llu (cap %lld), row overflow %llu, hit overflow %llu, cap %d\n",
-                    (long long)ninj, attempt, hdr[0] - (unsigned long long)nhits, (long long)hit_cap, hdr[1], hdr[2],
-                    w->leaf_cap);
+            fprintf(stderr, "[ae leaf] injections %lld (tasks %lld of %d) attempt %d: %.2f ms, hits %llu (cap %lld), row overflow %llu, hit overflow %llu, cap %d\n",
+                    (long long)ninj, (long long)la.nseg, la.seg, attempt, ms_since(t_sweep),
+                    hdr[0] - (unsigned long long)nhits, (long long)hit_cap, hdr[1], hdr[2], w->leaf_cap);
         if (hdr[1] != 0) {          // a row outgrew the scratch: retry larger
             w->leaf_cap *= 4;
             continue;
@@ -792,7 +793,10 @@ void Search::leaf_phase(int64_t ninj) {
             hit_cap = (int64_t)hdr[0] - nhits + 1024;
             continue;
         }
-        w->hit_ratio = std::max(w->hit_ratio * 0.9,
+        // hit records per injection vary by batch (homologous queries write many
+        // more): keep the largest ratio seen, so a workspace sizes for its worst
+        // batch instead of rerunning the sweep
+        w->hit_ratio = std::max(w->hit_ratio,
                                 std::min(64.0, 1.3 * (double)((int64_t)hdr[0] - nhits) / (double)ninj + 0.01));
         stats.leaf_raw_hits += (int64_t)hdr[0] - nhits;
         nhits = (int64_t)hdr[0];

@@ -342,6 +342,69 @@ __device__ __forceinline__ int64_t upper_bound_g(const int32_t *a, int64_t n, in
     return lo;
 }
 
+// Hit records of the sweep are staged per warp in shared memory and appended
+// to the global buffer LEAF_HS at a time, so that the walk along a homologous
+// region (hits in most chunks) does not take an atomic on the shared counter
+// per chunk.  A chunk with more than LEAF_HS hits reserves global space itself.
+constexpr int LEAF_HS = 256;
+constexpr int LEAF_WARPS = 4;   // k_leaf runs 128-thread blocks
+
+struct HitStage {
+    uint64_t *key;
+    int32_t *score;
+    uint32_t n;   // staged records (warp-uniform)
+};
+
+__device__ __forceinline__ void stage_flush(HitStage &hs, const LeafArgs &a, int lane) {
+    __syncwarp();
+    if (hs.n == 0) return;
+    unsigned long long g = 0;
+    if (lane == 0) g = atomicAdd(a.hit_count, (unsigned long long)hs.n);
+    g = __shfl_sync(FULL, g, 0);
+    if (g + hs.n <= a.hit_cap) {
+        for (uint32_t i = lane; i < hs.n; i += 32) {
+            a.hit_key[g + i] = hs.key[i];
+            a.hit_score[g + i] = hs.score[i];
+        }
+    } else if (lane == 0) {
+        atomicAdd(&a.stats->hit_overflow, 1ull);
+    }
+    __syncwarp();
+    hs.n = 0;
+}
+
+// Slots for htot records of this chunk (warp-uniform call): in the stage
+// (staged) or in the global buffer (ok = within its capacity).
+__device__ __forceinline__ uint64_t stage_reserve(HitStage &hs, const LeafArgs &a, int lane, uint32_t htot,
+                                                  bool &staged, bool &ok) {
+    if (htot > (uint32_t)LEAF_HS) {
+        unsigned long long g = 0;
+        if (lane == 0) g = atomicAdd(a.hit_count, (unsigned long long)htot);
+        g = __shfl_sync(FULL, g, 0);
+        staged = false;
+        ok = g + htot <= a.hit_cap;
+        if (!ok && lane == 0) atomicAdd(&a.stats->hit_overflow, 1ull);
+        return g;
+    }
+    if (hs.n + htot > (uint32_t)LEAF_HS) stage_flush(hs, a, lane);
+    staged = true;
+    ok = true;
+    const uint64_t b = hs.n;
+    hs.n += htot;
+    return b;
+}
+
+__device__ __forceinline__ void hit_put(HitStage &hs, const LeafArgs &a, bool staged, uint64_t slot, uint64_t key,
+                                        int32_t score) {
+    if (staged) {
+        hs.key[slot] = key;
+        hs.score[slot] = score;
+    } else {
+        a.hit_key[slot] = key;
+        a.hit_score[slot] = score;
+    }
+}
+
 // One warp per segment of `seg` consecutive injections (sorted by query and
 // text end).  The warp carries a row R along text positions p, p+1, ...:
 //   candidates of row p+1 = the vertical and diagonal slots generated from R
@@ -352,10 +415,13 @@ __device__ __forceinline__ int64_t upper_bound_g(const int32_t *a, int64_t n, in
 // sets leaf_overflow and the host reruns with a larger cap.
 __global__ void __launch_bounds__(128, 6) k_leaf(LeafArgs a) {
     __shared__ int8_t smat[AE_MAX_SIGMA * AE_MAX_SIGMA];
+    __shared__ uint64_t s_hkey[LEAF_WARPS][LEAF_HS];
+    __shared__ int32_t s_hscore[LEAF_WARPS][LEAF_HS];
     load_matrix(a.sc, smat);
     const int lane = threadIdx.x & 31;
     const int gw = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     if (gw >= a.nwarps) return;
+    HitStage hstage = {s_hkey[(threadIdx.x >> 5) & (LEAF_WARPS - 1)], s_hscore[(threadIdx.x >> 5) & (LEAF_WARPS - 1)], 0u};
     const ScoreView &sc = a.sc;
     const int32_t u = -sc.ss, oe = sc.sg + sc.ss, g = sc.gmax;
     const int64_t cap = a.cap;
@@ -427,18 +493,11 @@ __global__ void __launch_bounds__(128, 6) k_leaf(LeafArgs a) {
                     const uint32_t hi = warp_incl_sum(h);
                     const uint32_t htot = __shfl_sync(FULL, hi, 31);
                     if (htot) {
-                        unsigned long long hbase = 0;
-                        if (lane == 0) hbase = atomicAdd(a.hit_count, (unsigned long long)htot);
-                        hbase = __shfl_sync(FULL, hbase, 0);
-                        if (hbase + htot <= a.hit_cap) {
-                            if (h) {
-                                const uint64_t kq = ((uint64_t)qid << (a.be + a.bj)) |
-                                                    ((uint64_t)(uint32_t)p << a.bj);
-                                a.hit_key[hbase + hi - 1] = kq | ((uint64_t)rj & jmask);
-                                a.hit_score[hbase + hi - 1] = rM;
-                            }
-                        } else if (lane == 0) {
-                            atomicAdd(&a.stats->hit_overflow, 1ull);
+                        bool staged, hok;
+                        const uint64_t hbase = stage_reserve(hstage, a, lane, htot, staged, hok);
+                        if (hok && h) {
+                            const uint64_t kq = ((uint64_t)qid << (a.be + a.bj)) | ((uint64_t)(uint32_t)p << a.bj);
+                            hit_put(hstage, a, staged, hbase + hi - 1, kq | ((uint64_t)rj & jmask), rM);
                         }
                     }
                     if (a.tiers && lane == 0) st_t0 += (unsigned long long)rlen;   // warp-uniform count
@@ -504,25 +563,14 @@ __global__ void __launch_bounds__(128, 6) k_leaf(LeafArgs a) {
                     const uint32_t hc = hA + hB + (uint32_t)o.run_hits;
                     const uint32_t hi = warp_incl_sum(hc);
                     const uint32_t htot = __shfl_sync(FULL, hi, 31);
-                    unsigned long long hbase = 0;
-                    if (htot) {
-                        if (lane == 0) hbase = atomicAdd(a.hit_count, (unsigned long long)htot);
-                        hbase = __shfl_sync(FULL, hbase, 0);
-                    }
-                    const bool hok = hbase + htot <= a.hit_cap;
+                    bool staged = true, hok = true;
+                    uint64_t hbase = 0;
+                    if (htot) hbase = stage_reserve(hstage, a, lane, htot, staged, hok);
                     const uint64_t kq = ((uint64_t)qid << (a.be + a.bj)) | ((uint64_t)(uint32_t)p << a.bj);
                     const uint64_t h0 = hbase + hi - hc;
                     if (hok) {
-                        if (hA) {
-                            a.hit_key[h0] = kq | ((uint64_t)colA & jmask);
-                            a.hit_score[h0] = o.MA;
-                        }
-                        if (hB) {
-                            a.hit_key[h0 + hA] = kq | ((uint64_t)(colA + 1) & jmask);
-                            a.hit_score[h0 + hA] = o.MB;
-                        }
-                    } else if (htot && lane == 0) {
-                        atomicAdd(&a.stats->hit_overflow, 1ull);
+                        if (hA) hit_put(hstage, a, staged, h0, kq | ((uint64_t)colA & jmask), o.MA);
+                        if (hB) hit_put(hstage, a, staged, h0 + hA, kq | ((uint64_t)(colA + 1) & jmask), o.MB);
                     }
                     if (a.tiers) {
                         if (o.aliveA) {
@@ -561,10 +609,7 @@ __global__ void __launch_bounds__(128, 6) k_leaf(LeafArgs a) {
                                 R.M[d0 + t] = v;
                                 R.Ga[d0 + t] = AE_NEG;
                             }
-                            if (t < rh && hok) {
-                                a.hit_key[hd + t] = kq | ((uint64_t)cc & jmask);
-                                a.hit_score[hd + t] = v;
-                            }
+                            if (t < rh && hok) hit_put(hstage, a, staged, hd + t, kq | ((uint64_t)cc & jmask), v);
                         }
                     }
                     if (spill) {
@@ -626,7 +671,9 @@ __global__ void __launch_bounds__(128, 6) k_leaf(LeafArgs a) {
                 __syncwarp();
             }
             inreg = false;
+            int64_t nlen = 0;   // length of the finished row at p, kept in Rn
             if (rlen == 0) {
+                // a new walk: the row at p is the union of the rows injected there
                 if (k >= kend) break;
                 const Inject I0 = a.inj[a.order[k]];
                 p = I0.e;
@@ -644,158 +691,9 @@ __global__ void __launch_bounds__(128, 6) k_leaf(LeafArgs a) {
                     tw = (p + lane < a.ix.n) ? a.ix.text[p + lane] : 0u;
                 }
                 const int c = (int)__shfl_sync(FULL, tw, (int)(p - tw_base));
-                if (!(nk_qid == qid && nk_e == p)) {
-                    // ---- wide step with nothing to merge: slots and the horizontal
-                    // finish chunk by chunk, straight from R into Rn (same result
-                    // as generate + finish below, one pass over the row)
-                    int64_t nlen = 0;
-                    int32_t carry = AE_KNEG, prev_j = -2, prev_M = AE_NEG;
-                    for (int64_t base = 0; base < rlen; base += 32) {
-                        const int64_t idx = base + lane;
-                        const bool valid = idx < rlen;
-                        int32_t j = m, M = AE_NEG, Ga = AE_NEG;
-                        if (valid) {
-                            j = R.j[idx];
-                            M = R.M[idx];
-                            Ga = R.Ga[idx];
-                        }
-                        int32_t jn = __shfl_down_sync(FULL, j, 1);
-                        if (lane == 31 && idx + 1 < rlen) jn = R.j[idx + 1];
-                        if (idx + 1 >= rlen) jn = m;
-                        int32_t pjv = __shfl_up_sync(FULL, j, 1), pMv = __shfl_up_sync(FULL, M, 1);
-                        if (lane == 0) {
-                            pjv = prev_j;
-                            pMv = prev_M;
-                        }
-                        int32_t colA = m, MpA = AE_NEG, GaA = AE_NEG, MpB = AE_NEG, next_col = m;
-                        int32_t Dp = AE_NEG, Dk = AE_NEG;
-                        bool hasB = false;
-                        if (valid) {
-                            colA = j;
-                            const int32_t tA = thr_of(j, m, H, g);
-                            if (pjv + 1 == j && pMv > AE_NEG) {
-                                const int32_t D = pMv + delta_of(sc, smat, c, P[j]);
-                                Dp = D > tA ? D : AE_NEG;
-                            }
-                            const int32_t gap = gap_from_i32(M, Ga, sc.ss, oe);
-                            GaA = gap > tA ? gap : AE_NEG;
-                            MpA = max(Dp, GaA);
-                            hasB = (j + 1 < m) && (j + 1 != jn);
-                            if (hasB) {
-                                const int32_t D = M + delta_of(sc, smat, c, P[j + 1]);
-                                Dk = D > thr_of(j + 1, m, H, g) ? D : AE_NEG;
-                                MpB = Dk;
-                            }
-                            next_col = jn;
-                        }
-                        const int32_t keyA = MpA > AE_NEG ? MpA + colA * u : AE_KNEG;
-                        const int32_t keyB = MpB > AE_NEG ? MpB + (colA + 1) * u : AE_KNEG;
-                        int32_t incl = warp_incl_max(max(keyA, keyB));
-                        int32_t excl = __shfl_up_sync(FULL, incl, 1);
-                        if (lane == 0) excl = AE_KNEG;
-                        incl = max(incl, carry);
-                        excl = max(excl, carry);
-                        SlotOut o;
-                        slot_finish(colA, MpA, hasB, MpB, next_col, excl, incl, sc, m, H, u, valid, o);
-                        carry = __shfl_sync(FULL, incl, 31);
-                        prev_j = __shfl_sync(FULL, j, 31);
-                        prev_M = __shfl_sync(FULL, M, 31);
-                        const uint32_t nA = o.aliveA, nB = o.aliveB, nR = (uint32_t)o.run_len;
-                        const uint32_t cn = nA + nB + nR;
-                        const uint32_t ci = warp_incl_sum(cn);
-                        const uint32_t tot = __shfl_sync(FULL, ci, 31);
-                        if (nlen + tot > cap) {
-                            overflow = true;
-                            break;
-                        }
-                        const uint32_t hA = o.aliveA && o.MA >= H, hB = o.aliveB && o.MB >= H;
-                        const uint32_t hc = hA + hB + (uint32_t)o.run_hits;
-                        const uint32_t hi = warp_incl_sum(hc);
-                        const uint32_t htot = __shfl_sync(FULL, hi, 31);
-                        unsigned long long hbase = 0;
-                        if (htot) {
-                            if (lane == 0) hbase = atomicAdd(a.hit_count, (unsigned long long)htot);
-                            hbase = __shfl_sync(FULL, hbase, 0);
-                        }
-                        const bool hok = hbase + htot <= a.hit_cap;
-                        const uint64_t kq = ((uint64_t)qid << (a.be + a.bj)) | ((uint64_t)(uint32_t)p << a.bj);
-                        const int64_t e0 = nlen + (int64_t)(ci - cn);
-                        const uint64_t h0 = hbase + hi - hc;
-                        if (o.aliveA) {
-                            Rn.j[e0] = colA;
-                            Rn.M[e0] = o.MA;
-                            Rn.Ga[e0] = GaA;
-                            if (hA && hok) {
-                                a.hit_key[h0] = kq | ((uint64_t)colA & jmask);
-                                a.hit_score[h0] = o.MA;
-                            }
-                            if (a.tiers) {
-                                const int tier = (Dp > AE_NEG) + (GaA > AE_NEG) + (o.GbA > thr_of(colA, m, H, g));
-                                st_t0 += tier <= 1;
-                                st_t1 += tier == 2;
-                                st_t2 += tier >= 3;
-                            }
-                        }
-                        if (o.aliveB) {
-                            Rn.j[e0 + nA] = colA + 1;
-                            Rn.M[e0 + nA] = o.MB;
-                            Rn.Ga[e0 + nA] = AE_NEG;
-                            if (hB && hok) {
-                                a.hit_key[h0 + hA] = kq | ((uint64_t)(colA + 1) & jmask);
-                                a.hit_score[h0 + hA] = o.MB;
-                            }
-                            if (a.tiers) {
-                                if ((Dk > AE_NEG) && (o.GbB > thr_of(colA + 1, m, H, g))) ++st_t1; else ++st_t0;
-                            }
-                        }
-                        if (a.tiers) st_t0 += nR;
-                        unsigned rmask = __ballot_sync(FULL, nR > 0);
-                        while (rmask) {
-                            const int L = __ffs(rmask) - 1;
-                            rmask &= rmask - 1;
-                            const int32_t s0 = __shfl_sync(FULL, o.run_start, L);
-                            const int32_t rl = __shfl_sync(FULL, o.run_len, L);
-                            const int32_t rh = __shfl_sync(FULL, o.run_hits, L);
-                            const int32_t K = __shfl_sync(FULL, incl, L);
-                            const int64_t d0 = __shfl_sync(FULL, e0 + nA + nB, L);
-                            const uint64_t hd = __shfl_sync(FULL, h0 + hA + hB, L);
-                            for (int32_t t = lane; t < rl; t += 32) {
-                                const int32_t cc = s0 + t;
-                                const int32_t v = sc.sg - cc * u + K;
-                                Rn.j[d0 + t] = cc;
-                                Rn.M[d0 + t] = v;
-                                Rn.Ga[d0 + t] = AE_NEG;
-                                if (t < rh && hok) {
-                                    a.hit_key[hd + t] = kq | ((uint64_t)cc & jmask);
-                                    a.hit_score[hd + t] = v;
-                                }
-                            }
-                        }
-                        if (htot && !hok && lane == 0) atomicAdd(&a.stats->hit_overflow, 1ull);
-                        nlen += tot;
-                    }
-                    __syncwarp();
-                    if (overflow) break;
-                    Buf t = R;
-                    R = Rn;
-                    Rn = t;
-                    rlen = nlen;
-                    ++st_rows;
-                    ++seg_steps;
-                    seg_width = max(seg_width, (unsigned long long)nlen);
-                    st_ent += (unsigned long long)nlen;
-                    if (rlen <= 32) {
-                        if (lane < rlen) {
-                            rj = R.j[lane];
-                            rM = R.M[lane];
-                            rGa = R.Ga[lane];
-                        }
-                        inreg = true;
-                    }
-                    continue;
-                }
-                // ---- generate slots from R with letter c
-                int32_t prev_j = -2, prev_M = AE_NEG;
+                // ---- slots from R with letter c and the horizontal finish, chunk by
+                // chunk, straight into Rn (the finished row at p) with its hits
+                int32_t carry = AE_KNEG, prev_j = -2, prev_M = AE_NEG;
                 for (int64_t base = 0; base < rlen; base += 32) {
                     const int64_t idx = base + lane;
                     const bool valid = idx < rlen;
@@ -813,97 +711,172 @@ __global__ void __launch_bounds__(128, 6) k_leaf(LeafArgs a) {
                         pjv = prev_j;
                         pMv = prev_M;
                     }
-                    int32_t MpA = AE_NEG, GaA = AE_NEG, MpB = AE_NEG;
+                    int32_t colA = m, MpA = AE_NEG, GaA = AE_NEG, MpB = AE_NEG, next_col = m;
+                    int32_t Dp = AE_NEG, Dk = AE_NEG;
+                    bool hasB = false;
                     if (valid) {
+                        colA = j;
                         const int32_t tA = thr_of(j, m, H, g);
-                        int32_t Dp = AE_NEG;
-                        if (pjv + 1 == j && pMv > AE_NEG) Dp = pMv + delta_of(sc, smat, c, P[j]);
+                        if (pjv + 1 == j && pMv > AE_NEG) {
+                            const int32_t D = pMv + delta_of(sc, smat, c, P[j]);
+                            Dp = D > tA ? D : AE_NEG;
+                        }
                         const int32_t gap = gap_from_i32(M, Ga, sc.ss, oe);
                         GaA = gap > tA ? gap : AE_NEG;
-                        Dp = Dp > tA ? Dp : AE_NEG;
                         MpA = max(Dp, GaA);
-                        if (j + 1 < m && j + 1 != jn) {
-                            int32_t D = M + delta_of(sc, smat, c, P[j + 1]);
-                            MpB = D > thr_of(j + 1, m, H, g) ? D : AE_NEG;
+                        hasB = (j + 1 < m) && (j + 1 != jn);
+                        if (hasB) {
+                            const int32_t D = M + delta_of(sc, smat, c, P[j + 1]);
+                            Dk = D > thr_of(j + 1, m, H, g) ? D : AE_NEG;
+                            MpB = Dk;
                         }
+                        next_col = jn;
                     }
-                    const uint32_t oA = MpA > AE_NEG, oB = MpB > AE_NEG;
-                    const uint32_t cn = oA + oB;
+                    const int32_t keyA = MpA > AE_NEG ? MpA + colA * u : AE_KNEG;
+                    const int32_t keyB = MpB > AE_NEG ? MpB + (colA + 1) * u : AE_KNEG;
+                    int32_t incl = warp_incl_max(max(keyA, keyB));
+                    int32_t excl = __shfl_up_sync(FULL, incl, 1);
+                    if (lane == 0) excl = AE_KNEG;
+                    incl = max(incl, carry);
+                    excl = max(excl, carry);
+                    SlotOut o;
+                    slot_finish(colA, MpA, hasB, MpB, next_col, excl, incl, sc, m, H, u, valid, o);
+                    carry = __shfl_sync(FULL, incl, 31);
+                    prev_j = __shfl_sync(FULL, j, 31);
+                    prev_M = __shfl_sync(FULL, M, 31);
+                    const uint32_t nA = o.aliveA, nB = o.aliveB, nR = (uint32_t)o.run_len;
+                    const uint32_t cn = nA + nB + nR;
                     const uint32_t ci = warp_incl_sum(cn);
                     const uint32_t tot = __shfl_sync(FULL, ci, 31);
-                    if (clen + tot > cap) {
+                    if (nlen + tot > cap) {
                         overflow = true;
                         break;
                     }
-                    const int64_t d = clen + ci - cn;
-                    if (oA) {
-                        Cb.j[d] = j;
-                        Cb.M[d] = MpA;
-                        Cb.Ga[d] = GaA;
+                    const uint32_t hA = o.aliveA && o.MA >= H, hB = o.aliveB && o.MB >= H;
+                    const uint32_t hc = hA + hB + (uint32_t)o.run_hits;
+                    const uint32_t hi = warp_incl_sum(hc);
+                    const uint32_t htot = __shfl_sync(FULL, hi, 31);
+                    bool staged = true, hok = true;
+                    uint64_t hbase = 0;
+                    if (htot) hbase = stage_reserve(hstage, a, lane, htot, staged, hok);
+                    const uint64_t kq = ((uint64_t)qid << (a.be + a.bj)) | ((uint64_t)(uint32_t)p << a.bj);
+                    const int64_t e0 = nlen + (int64_t)(ci - cn);
+                    const uint64_t h0 = hbase + hi - hc;
+                    if (o.aliveA) {
+                        Rn.j[e0] = colA;
+                        Rn.M[e0] = o.MA;
+                        Rn.Ga[e0] = GaA;
+                        if (hA && hok) hit_put(hstage, a, staged, h0, kq | ((uint64_t)colA & jmask), o.MA);
+                        if (a.tiers) {
+                            const int tier = (Dp > AE_NEG) + (GaA > AE_NEG) + (o.GbA > thr_of(colA, m, H, g));
+                            st_t0 += tier <= 1;
+                            st_t1 += tier == 2;
+                            st_t2 += tier >= 3;
+                        }
                     }
-                    if (oB) {
-                        Cb.j[d + oA] = j + 1;
-                        Cb.M[d + oA] = MpB;
-                        Cb.Ga[d + oA] = AE_NEG;
+                    if (o.aliveB) {
+                        Rn.j[e0 + nA] = colA + 1;
+                        Rn.M[e0 + nA] = o.MB;
+                        Rn.Ga[e0 + nA] = AE_NEG;
+                        if (hB && hok) hit_put(hstage, a, staged, h0 + hA, kq | ((uint64_t)(colA + 1) & jmask), o.MB);
+                        if (a.tiers) {
+                            if ((Dk > AE_NEG) && (o.GbB > thr_of(colA + 1, m, H, g))) ++st_t1; else ++st_t0;
+                        }
                     }
-                    clen += tot;
-                    prev_j = __shfl_sync(FULL, j, 31);
-                    prev_M = __shfl_sync(FULL, M, 31);
+                    if (a.tiers) st_t0 += nR;
+                    unsigned rmask = __ballot_sync(FULL, nR > 0);
+                    while (rmask) {
+                        const int L = __ffs(rmask) - 1;
+                        rmask &= rmask - 1;
+                        const int32_t s0 = __shfl_sync(FULL, o.run_start, L);
+                        const int32_t rl = __shfl_sync(FULL, o.run_len, L);
+                        const int32_t rh = __shfl_sync(FULL, o.run_hits, L);
+                        const int32_t K = __shfl_sync(FULL, incl, L);
+                        const int64_t d0 = __shfl_sync(FULL, e0 + nA + nB, L);
+                        const uint64_t hd = __shfl_sync(FULL, h0 + hA + hB, L);
+                        for (int32_t t = lane; t < rl; t += 32) {
+                            const int32_t cc = s0 + t;
+                            const int32_t v = sc.sg - cc * u + K;
+                            Rn.j[d0 + t] = cc;
+                            Rn.M[d0 + t] = v;
+                            Rn.Ga[d0 + t] = AE_NEG;
+                            if (t < rh && hok) hit_put(hstage, a, staged, hd + t, kq | ((uint64_t)cc & jmask), v);
+                        }
+                    }
+                    nlen += tot;
                 }
                 __syncwarp();
                 if (overflow) break;
+                st_ent += (unsigned long long)nlen;
             }
-            // ---- merge the rows injected at (qid, p)
+            // ---- merge the rows injected at (qid, p).  They are finished rows, and
+            // the union of two finished rows taken by maximum per column is again
+            // finished (each is closed under the horizontal-gap recurrence), so the
+            // merge needs no second finish.  Cells where an injected row brings a
+            // new or larger value report their hits here.
             while (k < kend) {
                 const Inject I = a.inj[a.order[k]];
                 if (I.qid != qid || I.e != p) break;
                 ++k;
                 const int32_t *ij = a.lj + I.off, *iM = a.lM + I.off, *iGa = a.lGa + I.off;
                 const int64_t icnt = I.cnt;
-                if (clen + icnt > cap) {
+                if (nlen + icnt > cap) {
                     overflow = true;
                     break;
                 }
-                for (int64_t base = 0; base < clen; base += 32) {
+                for (int64_t base = 0; base < nlen; base += 32) {
                     const int64_t idx = base + lane;
-                    if (idx < clen) {
-                        const int32_t x = Cb.j[idx];
+                    if (idx < nlen) {
+                        const int32_t x = Rn.j[idx];
                         const int64_t d = idx + lower_bound_g(ij, icnt, x);
                         C2.j[d] = x;
-                        C2.M[d] = Cb.M[idx];
-                        C2.Ga[d] = Cb.Ga[idx];
+                        C2.M[d] = Rn.M[idx];
+                        C2.Ga[d] = Rn.Ga[idx];
                     }
                 }
                 for (int64_t base = 0; base < icnt; base += 32) {
                     const int64_t idx = base + lane;
                     if (idx < icnt) {
                         const int32_t y = ij[idx];
-                        const int64_t d = idx + upper_bound_g(Cb.j, clen, y);
-                        C2.j[d] = y;
+                        const int64_t d = idx + upper_bound_g(Rn.j, nlen, y);
+                        C2.j[d] = (int32_t)((uint32_t)y | 0x80000000u);   // tag: from the injected row
                         C2.M[d] = iM[idx];
                         C2.Ga[d] = iGa[idx];
                     }
                 }
                 __syncwarp();
-                const int64_t len2 = clen + icnt;
+                // an equal column appears twice: the walked entry first, then the injected one
+                const int64_t len2 = nlen + icnt;
                 int64_t out = 0;
+                const uint64_t kq = ((uint64_t)qid << (a.be + a.bj)) | ((uint64_t)(uint32_t)p << a.bj);
                 for (int64_t base = 0; base < len2; base += 32) {
                     const int64_t idx = base + lane;
                     const bool valid = idx < len2;
                     int32_t j = 0, Mv = AE_NEG, Gv = AE_NEG;
-                    bool keep = false;
+                    bool keep = false, hit = false, fresh = false;
                     if (valid) {
-                        j = C2.j[idx];
+                        const uint32_t raw = (uint32_t)C2.j[idx];
+                        j = (int32_t)(raw & 0x7FFFFFFFu);
+                        const bool from_inj = raw >> 31;
                         Mv = C2.M[idx];
                         Gv = C2.Ga[idx];
-                        keep = !(idx > 0 && C2.j[idx - 1] == j);
-                        if (idx + 1 < len2 && C2.j[idx + 1] == j) {
-                            Mv = max(Mv, C2.M[idx + 1]);
-                            Gv = max(Gv, C2.Ga[idx + 1]);
+                        keep = !(idx > 0 && (int32_t)((uint32_t)C2.j[idx - 1] & 0x7FFFFFFFu) == j);
+                        if (keep) {
+                            if (idx + 1 < len2 && (int32_t)((uint32_t)C2.j[idx + 1] & 0x7FFFFFFFu) == j) {
+                                const int32_t Mi = C2.M[idx + 1];
+                                hit = Mi > Mv && Mi >= H;
+                                Mv = max(Mv, Mi);
+                                Gv = max(Gv, C2.Ga[idx + 1]);
+                            } else {
+                                fresh = from_inj;
+                                hit = from_inj && Mv >= H;
+                            }
                         }
                     }
                     const uint32_t ci = warp_incl_sum(keep ? 1u : 0u);
                     const uint32_t tot = __shfl_sync(FULL, ci, 31);
+                    const uint32_t hi = warp_incl_sum(hit ? 1u : 0u);
+                    const uint32_t htot = __shfl_sync(FULL, hi, 31);
                     __syncwarp();
                     if (keep) {
                         const int64_t d = out + ci - 1;
@@ -911,10 +884,20 @@ __global__ void __launch_bounds__(128, 6) k_leaf(LeafArgs a) {
                         Cb.M[d] = Mv;
                         Cb.Ga[d] = Gv;
                     }
+                    if (htot) {
+                        bool staged, hok;
+                        const uint64_t hbase = stage_reserve(hstage, a, lane, htot, staged, hok);
+                        if (hok && hit) hit_put(hstage, a, staged, hbase + hi - 1, kq | ((uint64_t)j & jmask), Mv);
+                    }
+                    if (a.tiers && fresh) ++st_t0;
                     out += tot;
                 }
-                clen = out;
                 __syncwarp();
+                st_ent += (unsigned long long)(out - nlen);
+                Buf t = Rn;
+                Rn = Cb;
+                Cb = t;
+                nlen = out;
             }
             if (overflow) break;
             if (k < kend) {
@@ -924,94 +907,6 @@ __global__ void __launch_bounds__(128, 6) k_leaf(LeafArgs a) {
             } else {
                 nk_qid = nk_e = -1;
             }
-            // ---- finish: horizontal gaps, prune, hits -> Rn
-            int64_t nlen = 0;
-            int32_t carry = AE_KNEG;
-            for (int64_t base = 0; base < clen; base += 32) {
-                const int64_t idx = base + lane;
-                const bool valid = idx < clen;
-                int32_t col = m, Mp = AE_NEG, Ga = AE_NEG;
-                if (valid) {
-                    col = Cb.j[idx];
-                    Mp = Cb.M[idx];
-                    Ga = Cb.Ga[idx];
-                }
-                int32_t nc = __shfl_down_sync(FULL, col, 1);
-                if (lane == 31 && idx + 1 < clen) nc = Cb.j[idx + 1];
-                if (idx + 1 >= clen) nc = m;
-                const int32_t key = Mp > AE_NEG ? Mp + col * u : AE_KNEG;
-                int32_t incl = warp_incl_max(key);
-                int32_t excl = __shfl_up_sync(FULL, incl, 1);
-                if (lane == 0) excl = AE_KNEG;
-                incl = max(incl, carry);
-                excl = max(excl, carry);
-                SlotOut o;
-                slot_finish(col, Mp, false, AE_NEG, nc, excl, incl, sc, m, H, u, valid, o);
-                carry = __shfl_sync(FULL, incl, 31);
-                const uint32_t nA = o.aliveA, nR = (uint32_t)o.run_len;
-                const uint32_t cn = nA + nR;
-                const uint32_t ci = warp_incl_sum(cn);
-                const uint32_t tot = __shfl_sync(FULL, ci, 31);
-                if (nlen + tot > cap) {
-                    overflow = true;
-                    break;
-                }
-                const uint32_t hA = o.aliveA && o.MA >= H;
-                const uint32_t hc = hA + (uint32_t)o.run_hits;
-                const uint32_t hi = warp_incl_sum(hc);
-                const uint32_t htot = __shfl_sync(FULL, hi, 31);
-                unsigned long long hbase = 0;
-                if (htot) {
-                    if (lane == 0) hbase = atomicAdd(a.hit_count, (unsigned long long)htot);
-                    hbase = __shfl_sync(FULL, hbase, 0);
-                }
-                const bool hok = hbase + htot <= a.hit_cap;
-                const uint64_t kq = ((uint64_t)qid << (a.be + a.bj)) | ((uint64_t)(uint32_t)p << a.bj);
-                const int64_t e0 = nlen + ci - cn;
-                const uint64_t h0 = hbase + hi - hc;
-                if (o.aliveA) {
-                    Rn.j[e0] = col;
-                    Rn.M[e0] = o.MA;
-                    Rn.Ga[e0] = Ga;
-                    if (a.tiers) {
-                        const int tier = (Mp > AE_NEG) + (Ga > AE_NEG) + (o.GbA > thr_of(col, m, H, g));
-                        st_t0 += tier <= 1;
-                        st_t1 += tier == 2;
-                        st_t2 += tier >= 3;
-                    }
-                    if (hA && hok) {
-                        a.hit_key[h0] = kq | ((uint64_t)col & jmask);
-                        a.hit_score[h0] = o.MA;
-                    }
-                }
-                if (a.tiers) st_t0 += nR;
-                unsigned rmask = __ballot_sync(FULL, nR > 0);
-                while (rmask) {
-                    const int L = __ffs(rmask) - 1;
-                    rmask &= rmask - 1;
-                    const int32_t s0 = __shfl_sync(FULL, o.run_start, L);
-                    const int32_t rl = __shfl_sync(FULL, o.run_len, L);
-                    const int32_t rh = __shfl_sync(FULL, o.run_hits, L);
-                    const int32_t K = __shfl_sync(FULL, incl, L);
-                    const int64_t d0 = __shfl_sync(FULL, e0 + nA, L);
-                    const uint64_t hd = __shfl_sync(FULL, h0 + hA, L);
-                    for (int32_t t = lane; t < rl; t += 32) {
-                        const int32_t cc = s0 + t;
-                        const int32_t v = sc.sg - cc * u + K;
-                        Rn.j[d0 + t] = cc;
-                        Rn.M[d0 + t] = v;
-                        Rn.Ga[d0 + t] = AE_NEG;
-                        if (t < rh && hok) {
-                            a.hit_key[hd + t] = kq | ((uint64_t)cc & jmask);
-                            a.hit_score[hd + t] = v;
-                        }
-                    }
-                }
-                if (!hok && lane == 0) atomicAdd(&a.stats->hit_overflow, 1ull);
-                nlen += tot;
-            }
-            __syncwarp();
-            if (overflow) break;
             Buf t = R;
             R = Rn;
             Rn = t;
@@ -1019,7 +914,6 @@ __global__ void __launch_bounds__(128, 6) k_leaf(LeafArgs a) {
             ++st_rows;
             ++seg_steps;
             seg_width = max(seg_width, (unsigned long long)nlen);
-            st_ent += (unsigned long long)nlen;
             if (rlen <= 32) {
                 if (lane < rlen) {
                     rj = R.j[lane];
@@ -1035,6 +929,7 @@ __global__ void __launch_bounds__(128, 6) k_leaf(LeafArgs a) {
             atomicMax(&a.stats->leaf_max_width, seg_width);
         }
     }
+    stage_flush(hstage, a, lane);
     unsigned long long t0 = st_t0, t1 = st_t1, t2 = st_t2;
     for (int d = 16; d > 0; d >>= 1) {
         t0 += __shfl_down_sync(FULL, t0, d);
