@@ -973,6 +973,9 @@ ae_status search_core(const ae_index *idx, Workspace *w, const int64_t *offsets,
         s.stats.entries_leaf = (int64_t)ds.entries_leaf;
         s.stats.leaf_max_steps = (int64_t)ds.leaf_max_steps;
         s.stats.leaf_max_width = (int64_t)ds.leaf_max_width;
+        if (trace())
+            fprintf(stderr, "[ae leaf] longest sweep task %.2f Mcycles (%.2f ms at 2.07 GHz)\n",
+                    ds.leaf_max_cycles / 1e6, ds.leaf_max_cycles / 2.07e6);
         s.stats.ws_bytes = g_ws_bytes;
         s.stats.ms_k_expand = s.prof.ms(K_EXPAND);
         s.stats.ms_k_rows = s.prof.ms(K_ROWS);

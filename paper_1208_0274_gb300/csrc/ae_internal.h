@@ -103,7 +103,8 @@ struct DevStats {
     unsigned long long leaf_overflow, hit_overflow;
     unsigned long long entries_leaf;
     unsigned long long leaf_max_steps, leaf_max_width;
-    unsigned long long pad[3];
+    unsigned long long leaf_max_cycles;   // longest sweep task (SM clock cycles)
+    unsigned long long pad[2];
 };
 
 // ---------------------------------------------------------------- host index

@@ -446,6 +446,7 @@ __global__ void __launch_bounds__(128, 6) k_leaf(LeafArgs a) {
         int32_t p = -1, qid = -1, m = 0, H = 0;
         const uint8_t *P = nullptr;
         unsigned long long seg_steps = 0, seg_width = 0;
+        const long long task_t0 = clock64();
         // R lives in registers (lane i holds entry i) while it has <= 32 entries
         bool inreg = false;
         int32_t rj = 0, rM = AE_NEG, rGa = AE_NEG;
@@ -820,6 +821,22 @@ __global__ void __launch_bounds__(128, 6) k_leaf(LeafArgs a) {
                 ++k;
                 const int32_t *ij = a.lj + I.off, *iM = a.lM + I.off, *iGa = a.lGa + I.off;
                 const int64_t icnt = I.cnt;
+                // an injected row whose every entry the walked row already has with
+                // M and G_a at least as large changes nothing (its hits were reported
+                // with the walked values): skip it.  Along a homologous region the row
+                // walked from earlier starts usually dominates the later forks.
+                bool dominated = nlen > 0;
+                for (int64_t base = 0; dominated && base < icnt; base += 32) {
+                    const int64_t idx = base + lane;
+                    bool ok = true;
+                    if (idx < icnt) {
+                        const int32_t y = ij[idx];
+                        const int64_t q = lower_bound_g(Rn.j, nlen, y);
+                        ok = q < nlen && Rn.j[q] == y && Rn.M[q] >= iM[idx] && Rn.Ga[q] >= iGa[idx];
+                    }
+                    dominated = __all_sync(FULL, ok);
+                }
+                if (dominated) continue;
                 if (nlen + icnt > cap) {
                     overflow = true;
                     break;
@@ -927,6 +944,7 @@ __global__ void __launch_bounds__(128, 6) k_leaf(LeafArgs a) {
         if (lane == 0) {
             atomicMax(&a.stats->leaf_max_steps, seg_steps);
             atomicMax(&a.stats->leaf_max_width, seg_width);
+            atomicMax(&a.stats->leaf_max_cycles, (unsigned long long)(clock64() - task_t0));
         }
     }
     stage_flush(hstage, a, lane);
