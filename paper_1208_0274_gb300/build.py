@@ -39,6 +39,7 @@ def build(force=False, verbose=False):
     os.makedirs(BUILD, exist_ok=True)
     nvcc = _nvcc()
     common = ["-O3", "-std=c++17", "-Xcompiler", "-fPIC", "-I", os.path.join(ROOT, "include"), "-I", CSRC]
+    common += os.environ.get("AE_NVCC_EXTRA", "").split()   # extra defines for tuning builds
 
     def compile_one(src):
         obj = os.path.join(BUILD, src + ".o")

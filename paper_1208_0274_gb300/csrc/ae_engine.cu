@@ -579,7 +579,7 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
             ra.task_flag = ptr<uint8_t>(w->task_flag);
         }
         prof.mark(K_ROWS);
-        ae_rows(ra, false, num_sms * 4, st);
+        ae_rows(ra, false, num_sms * ae_rows_blocks_per_sm(false), st);
         // write-pass bases: exclusive scan of the per-task output counts
         const uint32_t *tin[5];
         uint64_t *tout[5];
@@ -628,7 +628,7 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
         ra.base_off[3] = (uint64_t)lf_node_base;
         ra.base_off[4] = (uint64_t)rh_base;
         prof.mark(K_ROWS);
-        ae_rows(ra, true, num_sms * 4, st);
+        ae_rows(ra, true, num_sms * ae_rows_blocks_per_sm(true), st);
         prof.mark(K_ROWS);
         if (trace())
             fprintf(stderr, "[ae level] depth %d nodes %lld segs %lld triples %lld -> frontier %lld nodes %lld, leaf %lld rows %lld\n",

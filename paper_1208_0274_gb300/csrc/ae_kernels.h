@@ -122,6 +122,7 @@ struct RowsArgs {
     uint8_t *task_flag;
 };
 void ae_rows(const RowsArgs &a, bool write, int blocks, cudaStream_t st);
+int ae_rows_blocks_per_sm(bool write);   // blocks per SM to launch a k_rows pass with (one full wave)
 void ae_mg_to_i32(int32_t *M, int32_t *Ga, int64_t n, cudaStream_t st);
 struct LeafArgs {
     IndexView ix;

@@ -122,6 +122,16 @@ __device__ __forceinline__ bool seg_stays(const Seg &sg, int delay) {
 constexpr int RW_WARPS = 8;
 constexpr int RW_TASK = AE_ROW_TASK;   // triples per task window = max segments per task
 constexpr int RW_GRAB = 4;             // tasks per take from the task counter
+// Resident blocks per SM the two passes are compiled for (and launched with):
+// the kernel is bound by memory latency per triple, so more resident warps
+// beat more registers (measured on the 100 Mbp workload: 6 blocks of 8 warps)
+#ifndef AE_RW_MINB_COUNT
+#define AE_RW_MINB_COUNT 6
+#endif
+#ifndef AE_RW_MINB_WRITE
+#define AE_RW_MINB_WRITE 6
+#endif
+constexpr int RW_MINB_COUNT = AE_RW_MINB_COUNT, RW_MINB_WRITE = AE_RW_MINB_WRITE;
 
 struct TaskSmem {
     uint32_t cnt[RW_TASK];
@@ -553,7 +563,7 @@ __device__ void run_task_stored(const RowsArgs &a, TaskSmem &sm, uint64_t s_firs
 // writes the child node / injection records, and recomputes and writes the
 // rows and the hits of multi-occurrence children.
 template <int SIGMA, bool WRITE, bool I16>
-__global__ void __launch_bounds__(RW_WARPS * 32, 4) k_rows(RowsArgs a) {
+__global__ void __launch_bounds__(RW_WARPS * 32, WRITE ? RW_MINB_WRITE : RW_MINB_COUNT) k_rows(RowsArgs a) {
     __shared__ int8_t smat[AE_MAX_SIGMA * AE_MAX_SIGMA];
     __shared__ TaskSmem smem[RW_WARPS];
     load_matrix(a.sc, smat);
@@ -799,6 +809,8 @@ void launch_rows(const RowsArgs &a, bool write, int blocks, cudaStream_t st) {
     else
         k_rows<SIGMA, false, I16><<<blocks, RW_WARPS * 32, 0, st>>>(a);
 }
+
+int ae_rows_blocks_per_sm(bool write) { return write ? RW_MINB_WRITE : RW_MINB_COUNT; }
 
 void ae_rows(const RowsArgs &a, bool write, int blocks, cudaStream_t st) {
     ++g_launches;
