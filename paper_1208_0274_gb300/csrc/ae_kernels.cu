@@ -413,7 +413,12 @@ __device__ __forceinline__ void hit_put(HitStage &hs, const LeafArgs &a, bool st
 // The walk jumps to the next injection when R has no live entry.  Rows live
 // in per-warp global scratch (cap entries per buffer); a row that outgrows it
 // sets leaf_overflow and the host reruns with a larger cap.
-__global__ void __launch_bounds__(128, 6) k_leaf(LeafArgs a) {
+// The sweep's time is set by its longest walks (one warp each), which run
+// fastest with registers to spare: 3 resident blocks per SM (measured).
+#ifndef AE_LEAF_MINB
+#define AE_LEAF_MINB 3
+#endif
+__global__ void __launch_bounds__(128, AE_LEAF_MINB) k_leaf(LeafArgs a) {
     __shared__ int8_t smat[AE_MAX_SIGMA * AE_MAX_SIGMA];
     __shared__ uint64_t s_hkey[LEAF_WARPS][LEAF_HS];
     __shared__ int32_t s_hscore[LEAF_WARPS][LEAF_HS];
