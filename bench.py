@@ -59,6 +59,7 @@ def parse():
     p.add_argument("--leaf-segment", type=int, default=None)
     p.add_argument("--item-columns", type=int, default=None)
     p.add_argument("--batch-columns", type=int, default=None)
+    p.add_argument("--leaf-delay", type=int, default=None)
     p.add_argument("--verbose", action="store_true")
     return p.parse_args()
 
@@ -261,7 +262,7 @@ def run_ours(args):
     n = text.size
     stream = torch.cuda.Stream()
     opts = ae.make_options(leaf_segment=args.leaf_segment, item_columns=args.item_columns,
-                           batch_columns=args.batch_columns, profile=1)
+                           batch_columns=args.batch_columns, leaf_delay=args.leaf_delay, profile=1)
     seq = np.concatenate(qs) if qs else np.zeros(0, np.uint8)
     offsets = np.concatenate([[0], np.cumsum([q.size for q in qs])]).astype(np.int64)
     d_seq = torch.from_numpy(seq).to(f"cuda:{local}")

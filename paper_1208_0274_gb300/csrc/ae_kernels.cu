@@ -405,6 +405,44 @@ __device__ __forceinline__ void hit_put(HitStage &hs, const LeafArgs &a, bool st
     }
 }
 
+// Slots of one sweep entry (see slot_finish): slot A at the entry's column,
+// slot B at the next column unless the next entry is there.
+struct Slots {
+    int32_t colA, MpA, GaA, MpB, Dp, Dk, next_col;
+    bool hasB;
+};
+
+__device__ __forceinline__ void make_slots(const ScoreView &sc, const int8_t *smat, int c, const uint8_t *P, int32_t m,
+                                           int32_t H, int32_t g, int32_t oe, bool valid, int32_t j, int32_t M,
+                                           int32_t Ga, int32_t pj, int32_t pM, int32_t jn, Slots &s) {
+    s.colA = m;
+    s.MpA = s.GaA = s.MpB = s.Dp = s.Dk = AE_NEG;
+    s.next_col = m;
+    s.hasB = false;
+    if (!valid) return;
+    s.colA = j;
+    const int32_t tA = thr_of(j, m, H, g);
+    if (pj + 1 == j && pM > AE_NEG) {
+        const int32_t D = pM + delta_of(sc, smat, c, P[j]);
+        s.Dp = D > tA ? D : AE_NEG;
+    }
+    const int32_t gap = gap_from_i32(M, Ga, sc.ss, oe);
+    s.GaA = gap > tA ? gap : AE_NEG;
+    s.MpA = max(s.Dp, s.GaA);
+    s.hasB = (j + 1 < m) && (j + 1 != jn);
+    if (s.hasB) {
+        const int32_t D = M + delta_of(sc, smat, c, P[j + 1]);
+        s.Dk = D > thr_of(j + 1, m, H, g) ? D : AE_NEG;
+        s.MpB = s.Dk;
+    }
+    s.next_col = jn;
+}
+
+#ifndef AE_LEAF_E
+#define AE_LEAF_E 2
+#endif
+constexpr int LEAF_E = AE_LEAF_E;   // row entries per lane in the wide sweep step
+
 // One warp per segment of `seg` consecutive injections (sorted by query and
 // text end).  The warp carries a row R along text positions p, p+1, ...:
 //   candidates of row p+1 = the vertical and diagonal slots generated from R
@@ -697,116 +735,132 @@ __global__ void __launch_bounds__(128, AE_LEAF_MINB) k_leaf(LeafArgs a) {
                     tw = (p + lane < a.ix.n) ? a.ix.text[p + lane] : 0u;
                 }
                 const int c = (int)__shfl_sync(FULL, tw, (int)(p - tw_base));
-                // ---- slots from R with letter c and the horizontal finish, chunk by
-                // chunk, straight into Rn (the finished row at p) with its hits
+                // ---- slots from R with letter c and the horizontal finish, straight
+                // into Rn (the finished row at p) with its hits.  Each lane takes
+                // LEAF_E consecutive entries (a lane-local prefix, then one warp scan
+                // per quantity), so a wide row needs LEAF_E times fewer warp steps.
                 int32_t carry = AE_KNEG, prev_j = -2, prev_M = AE_NEG;
-                for (int64_t base = 0; base < rlen; base += 32) {
-                    const int64_t idx = base + lane;
-                    const bool valid = idx < rlen;
-                    int32_t j = m, M = AE_NEG, Ga = AE_NEG;
-                    if (valid) {
-                        j = R.j[idx];
-                        M = R.M[idx];
-                        Ga = R.Ga[idx];
+                for (int64_t base = 0; base < rlen; base += 32 * LEAF_E) {
+                    const int64_t i0 = base + (int64_t)lane * LEAF_E;
+                    int32_t jj[LEAF_E], MM[LEAF_E], GG[LEAF_E];
+#pragma unroll
+                    for (int e = 0; e < LEAF_E; ++e) {
+                        const bool v = i0 + e < rlen;
+                        jj[e] = v ? R.j[i0 + e] : m;
+                        MM[e] = v ? R.M[i0 + e] : AE_NEG;
+                        GG[e] = v ? R.Ga[i0 + e] : AE_NEG;
                     }
-                    int32_t jn = __shfl_down_sync(FULL, j, 1);
-                    if (lane == 31 && idx + 1 < rlen) jn = R.j[idx + 1];
-                    if (idx + 1 >= rlen) jn = m;
-                    int32_t pjv = __shfl_up_sync(FULL, j, 1), pMv = __shfl_up_sync(FULL, M, 1);
+                    int32_t jnext = __shfl_down_sync(FULL, jj[0], 1);
+                    if (lane == 31) jnext = (base + 32 * LEAF_E < rlen) ? R.j[base + 32 * LEAF_E] : m;
+                    int32_t pj0 = __shfl_up_sync(FULL, jj[LEAF_E - 1], 1), pM0 = __shfl_up_sync(FULL, MM[LEAF_E - 1], 1);
                     if (lane == 0) {
-                        pjv = prev_j;
-                        pMv = prev_M;
+                        pj0 = prev_j;
+                        pM0 = prev_M;
                     }
-                    int32_t colA = m, MpA = AE_NEG, GaA = AE_NEG, MpB = AE_NEG, next_col = m;
-                    int32_t Dp = AE_NEG, Dk = AE_NEG;
-                    bool hasB = false;
-                    if (valid) {
-                        colA = j;
-                        const int32_t tA = thr_of(j, m, H, g);
-                        if (pjv + 1 == j && pMv > AE_NEG) {
-                            const int32_t D = pMv + delta_of(sc, smat, c, P[j]);
-                            Dp = D > tA ? D : AE_NEG;
-                        }
-                        const int32_t gap = gap_from_i32(M, Ga, sc.ss, oe);
-                        GaA = gap > tA ? gap : AE_NEG;
-                        MpA = max(Dp, GaA);
-                        hasB = (j + 1 < m) && (j + 1 != jn);
-                        if (hasB) {
-                            const int32_t D = M + delta_of(sc, smat, c, P[j + 1]);
-                            Dk = D > thr_of(j + 1, m, H, g) ? D : AE_NEG;
-                            MpB = Dk;
-                        }
-                        next_col = jn;
+                    Slots sl[LEAF_E];
+                    int32_t lk[LEAF_E];
+#pragma unroll
+                    for (int e = 0; e < LEAF_E; ++e) {
+                        const bool v = i0 + e < rlen;
+                        int32_t jn = (e + 1 < LEAF_E) ? jj[e + 1] : jnext;
+                        if (i0 + e + 1 >= rlen) jn = m;
+                        const int32_t pj = e ? jj[e - 1] : pj0, pM = e ? MM[e - 1] : pM0;
+                        make_slots(sc, smat, c, P, m, H, g, oe, v, jj[e], MM[e], GG[e], pj, pM, jn, sl[e]);
+                        const int32_t keyA = sl[e].MpA > AE_NEG ? sl[e].MpA + sl[e].colA * u : AE_KNEG;
+                        const int32_t keyB = sl[e].MpB > AE_NEG ? sl[e].MpB + (sl[e].colA + 1) * u : AE_KNEG;
+                        lk[e] = max(e ? lk[e - 1] : AE_KNEG, max(keyA, keyB));
                     }
-                    const int32_t keyA = MpA > AE_NEG ? MpA + colA * u : AE_KNEG;
-                    const int32_t keyB = MpB > AE_NEG ? MpB + (colA + 1) * u : AE_KNEG;
-                    int32_t incl = warp_incl_max(max(keyA, keyB));
-                    int32_t excl = __shfl_up_sync(FULL, incl, 1);
-                    if (lane == 0) excl = AE_KNEG;
-                    incl = max(incl, carry);
-                    excl = max(excl, carry);
-                    SlotOut o;
-                    slot_finish(colA, MpA, hasB, MpB, next_col, excl, incl, sc, m, H, u, valid, o);
-                    carry = __shfl_sync(FULL, incl, 31);
-                    prev_j = __shfl_sync(FULL, j, 31);
-                    prev_M = __shfl_sync(FULL, M, 31);
-                    const uint32_t nA = o.aliveA, nB = o.aliveB, nR = (uint32_t)o.run_len;
-                    const uint32_t cn = nA + nB + nR;
-                    const uint32_t ci = warp_incl_sum(cn);
+                    int32_t lincl = warp_incl_max(lk[LEAF_E - 1]);
+                    int32_t lexcl = __shfl_up_sync(FULL, lincl, 1);
+                    if (lane == 0) lexcl = AE_KNEG;
+                    lincl = max(lincl, carry);
+                    lexcl = max(lexcl, carry);
+                    SlotOut o[LEAF_E];
+                    int32_t ik[LEAF_E];
+                    uint32_t cl = 0, hl = 0;
+#pragma unroll
+                    for (int e = 0; e < LEAF_E; ++e) {
+                        const int32_t ex = e ? max(lexcl, lk[e - 1]) : lexcl;
+                        ik[e] = max(lexcl, lk[e]);
+                        slot_finish(sl[e].colA, sl[e].MpA, sl[e].hasB, sl[e].MpB, sl[e].next_col, ex, ik[e], sc, m, H,
+                                    u, i0 + e < rlen, o[e]);
+                        cl += (uint32_t)o[e].aliveA + (uint32_t)o[e].aliveB + (uint32_t)o[e].run_len;
+                        hl += (uint32_t)(o[e].aliveA && o[e].MA >= H) + (uint32_t)(o[e].aliveB && o[e].MB >= H) +
+                              (uint32_t)o[e].run_hits;
+                    }
+                    carry = __shfl_sync(FULL, lincl, 31);
+                    prev_j = __shfl_sync(FULL, jj[LEAF_E - 1], 31);
+                    prev_M = __shfl_sync(FULL, MM[LEAF_E - 1], 31);
+                    const uint32_t ci = warp_incl_sum(cl);
                     const uint32_t tot = __shfl_sync(FULL, ci, 31);
                     if (nlen + tot > cap) {
                         overflow = true;
                         break;
                     }
-                    const uint32_t hA = o.aliveA && o.MA >= H, hB = o.aliveB && o.MB >= H;
-                    const uint32_t hc = hA + hB + (uint32_t)o.run_hits;
-                    const uint32_t hi = warp_incl_sum(hc);
+                    const uint32_t hi = warp_incl_sum(hl);
                     const uint32_t htot = __shfl_sync(FULL, hi, 31);
                     bool staged = true, hok = true;
                     uint64_t hbase = 0;
                     if (htot) hbase = stage_reserve(hstage, a, lane, htot, staged, hok);
                     const uint64_t kq = ((uint64_t)qid << (a.be + a.bj)) | ((uint64_t)(uint32_t)p << a.bj);
-                    const int64_t e0 = nlen + (int64_t)(ci - cn);
-                    const uint64_t h0 = hbase + hi - hc;
-                    if (o.aliveA) {
-                        Rn.j[e0] = colA;
-                        Rn.M[e0] = o.MA;
-                        Rn.Ga[e0] = GaA;
-                        if (hA && hok) hit_put(hstage, a, staged, h0, kq | ((uint64_t)colA & jmask), o.MA);
-                        if (a.tiers) {
-                            const int tier = (Dp > AE_NEG) + (GaA > AE_NEG) + (o.GbA > thr_of(colA, m, H, g));
-                            st_t0 += tier <= 1;
-                            st_t1 += tier == 2;
-                            st_t2 += tier >= 3;
+                    int64_t eo = nlen + (int64_t)(ci - cl);
+                    uint64_t ho = hbase + hi - hl;
+                    int64_t run_d[LEAF_E];
+                    uint64_t run_h[LEAF_E];
+#pragma unroll
+                    for (int e = 0; e < LEAF_E; ++e) {
+                        const uint32_t nA = o[e].aliveA, nB = o[e].aliveB;
+                        const uint32_t hA = o[e].aliveA && o[e].MA >= H, hB = o[e].aliveB && o[e].MB >= H;
+                        const int32_t colA = sl[e].colA;
+                        if (o[e].aliveA) {
+                            Rn.j[eo] = colA;
+                            Rn.M[eo] = o[e].MA;
+                            Rn.Ga[eo] = sl[e].GaA;
+                            if (hA && hok) hit_put(hstage, a, staged, ho, kq | ((uint64_t)colA & jmask), o[e].MA);
+                            if (a.tiers) {
+                                const int tier = (sl[e].Dp > AE_NEG) + (sl[e].GaA > AE_NEG) +
+                                                 (o[e].GbA > thr_of(colA, m, H, g));
+                                st_t0 += tier <= 1;
+                                st_t1 += tier == 2;
+                                st_t2 += tier >= 3;
+                            }
                         }
-                    }
-                    if (o.aliveB) {
-                        Rn.j[e0 + nA] = colA + 1;
-                        Rn.M[e0 + nA] = o.MB;
-                        Rn.Ga[e0 + nA] = AE_NEG;
-                        if (hB && hok) hit_put(hstage, a, staged, h0 + hA, kq | ((uint64_t)(colA + 1) & jmask), o.MB);
-                        if (a.tiers) {
-                            if ((Dk > AE_NEG) && (o.GbB > thr_of(colA + 1, m, H, g))) ++st_t1; else ++st_t0;
+                        if (o[e].aliveB) {
+                            Rn.j[eo + nA] = colA + 1;
+                            Rn.M[eo + nA] = o[e].MB;
+                            Rn.Ga[eo + nA] = AE_NEG;
+                            if (hB && hok)
+                                hit_put(hstage, a, staged, ho + hA, kq | ((uint64_t)(colA + 1) & jmask), o[e].MB);
+                            if (a.tiers) {
+                                if ((sl[e].Dk > AE_NEG) && (o[e].GbB > thr_of(colA + 1, m, H, g))) ++st_t1; else ++st_t0;
+                            }
                         }
+                        if (a.tiers) st_t0 += (uint32_t)o[e].run_len;
+                        run_d[e] = eo + nA + nB;
+                        run_h[e] = ho + hA + hB;
+                        eo += nA + nB + (uint32_t)o[e].run_len;
+                        ho += hA + hB + (uint32_t)o[e].run_hits;
                     }
-                    if (a.tiers) st_t0 += nR;
-                    unsigned rmask = __ballot_sync(FULL, nR > 0);
-                    while (rmask) {
-                        const int L = __ffs(rmask) - 1;
-                        rmask &= rmask - 1;
-                        const int32_t s0 = __shfl_sync(FULL, o.run_start, L);
-                        const int32_t rl = __shfl_sync(FULL, o.run_len, L);
-                        const int32_t rh = __shfl_sync(FULL, o.run_hits, L);
-                        const int32_t K = __shfl_sync(FULL, incl, L);
-                        const int64_t d0 = __shfl_sync(FULL, e0 + nA + nB, L);
-                        const uint64_t hd = __shfl_sync(FULL, h0 + hA + hB, L);
-                        for (int32_t t = lane; t < rl; t += 32) {
-                            const int32_t cc = s0 + t;
-                            const int32_t v = sc.sg - cc * u + K;
-                            Rn.j[d0 + t] = cc;
-                            Rn.M[d0 + t] = v;
-                            Rn.Ga[d0 + t] = AE_NEG;
-                            if (t < rh && hok) hit_put(hstage, a, staged, hd + t, kq | ((uint64_t)cc & jmask), v);
+#pragma unroll
+                    for (int e = 0; e < LEAF_E; ++e) {
+                        unsigned rmask = __ballot_sync(FULL, o[e].run_len > 0);
+                        while (rmask) {
+                            const int L = __ffs(rmask) - 1;
+                            rmask &= rmask - 1;
+                            const int32_t s0 = __shfl_sync(FULL, o[e].run_start, L);
+                            const int32_t rl = __shfl_sync(FULL, o[e].run_len, L);
+                            const int32_t rh = __shfl_sync(FULL, o[e].run_hits, L);
+                            const int32_t K = __shfl_sync(FULL, ik[e], L);
+                            const int64_t d0 = __shfl_sync(FULL, run_d[e], L);
+                            const uint64_t hd = __shfl_sync(FULL, run_h[e], L);
+                            for (int32_t t = lane; t < rl; t += 32) {
+                                const int32_t cc = s0 + t;
+                                const int32_t v = sc.sg - cc * u + K;
+                                Rn.j[d0 + t] = cc;
+                                Rn.M[d0 + t] = v;
+                                Rn.Ga[d0 + t] = AE_NEG;
+                                if (t < rh && hok) hit_put(hstage, a, staged, hd + t, kq | ((uint64_t)cc & jmask), v);
+                            }
                         }
                     }
                     nlen += tot;
