@@ -159,6 +159,35 @@ struct SlotOut {
     int32_t run_start, run_len, run_hits;
 };
 
+// The run of columns [run_start, next_col) after a lane's slots, where only
+// G_b (key K, the inclusive prefix maximum) can be live: its live cells and
+// how many of them reach H.  G_b along the run is v(x) = s_g - x*u + K,
+// decreasing; thr(x) is non-decreasing, so the live cells form a prefix.  Most
+// runs are empty: the first cell is tested before dividing.  All terms fit
+// int32 (the engine checks m * (u + g + 1) < 2^30).
+__device__ __forceinline__ void run_of(int32_t run_start, int32_t next_col, int32_t K, const ScoreView &sc,
+                                       int32_t m, int32_t H, int32_t u, int32_t &run_len, int32_t &run_hits) {
+    run_len = 0;
+    run_hits = 0;
+    if (K <= AE_KNEG / 2 || run_start >= next_col) return;
+    const int32_t g = sc.gmax;
+    const int32_t v0 = sc.sg - run_start * u + K;
+    if (v0 > thr_of(run_start, m, H, g)) {
+        const int32_t x1 = floordiv32(sc.sg + K - 1, u);
+        const int32_t x2 = floordiv32(sc.sg + K - H + (m - 1) * g, u + g);
+        const int32_t xm = min(min(x1, x2), next_col - 1);
+        const int32_t r = xm - run_start + 1;
+        if (r > 0) {
+            run_len = r;
+            if (v0 >= H) {
+                const int32_t xh = floordiv32(sc.sg + K - H, u);
+                const int32_t rh = min(xh, run_start + r - 1) - run_start + 1;
+                run_hits = rh > 0 ? rh : 0;
+            }
+        }
+    }
+}
+
 __device__ __forceinline__ void slot_finish(int32_t colA, int32_t MpA, bool hasB, int32_t MpB,
                                             int32_t next_col, int32_t excl, int32_t incl,
                                             const ScoreView &sc, int32_t m, int32_t H, int32_t u,
@@ -178,30 +207,7 @@ __device__ __forceinline__ void slot_finish(int32_t colA, int32_t MpA, bool hasB
         o.aliveB = o.MB > thr_of(colA + 1, m, H, g);
     }
     o.run_start = hasB ? colA + 2 : colA + 1;
-    o.run_len = 0;
-    o.run_hits = 0;
-    if (valid && incl > AE_KNEG / 2 && o.run_start < next_col) {
-        // G_b along the run: v(x) = s_g - x*u + K, decreasing; thr(x) is
-        // non-decreasing, so the live cells form a prefix of the run.  Most
-        // runs are empty: test the first cell before dividing.  All terms fit
-        // int32 (the engine checks m * (u + g + 1) < 2^30).
-        const int32_t K = incl;
-        const int32_t v0 = sc.sg - o.run_start * u + K;
-        if (v0 > thr_of(o.run_start, m, H, g)) {
-            const int32_t x1 = floordiv32(sc.sg + K - 1, u);
-            const int32_t x2 = floordiv32(sc.sg + K - H + (m - 1) * g, u + g);
-            const int32_t xm = min(min(x1, x2), next_col - 1);
-            const int32_t r = xm - o.run_start + 1;
-            if (r > 0) {
-                o.run_len = r;
-                if (v0 >= H) {
-                    const int32_t xh = floordiv32(sc.sg + K - H, u);
-                    const int32_t rh = min(xh, o.run_start + r - 1) - o.run_start + 1;
-                    o.run_hits = rh > 0 ? rh : 0;
-                }
-            }
-        }
-    }
+    run_of(o.run_start, next_col, valid ? incl : AE_KNEG, sc, m, H, u, o.run_len, o.run_hits);
 }
 
 }  // namespace aedev

@@ -150,7 +150,7 @@ struct Workspace {
     DevBuf scratch, next_seg;
     // output
     DevBuf uniq, uflags, uoff, qcount;
-    DevBuf stats, segs, ctr, seg_cnt, seg_hit, task_first, task_tot, task_off, task_tmp, task_sum, res, task_flag;
+    DevBuf stats, segs, ctr, seg_cnt, seg_hit, task_first, task_tot, task_off, task_tmp, task_sum, res, res_key;
     double fr_ratio = 1.2, lf_ratio = 0.6, hit_ratio = 0.5;
     // pinned host staging
     uint64_t *h_tot = nullptr;
@@ -173,7 +173,7 @@ struct Workspace {
                 &cnt[4], &off[0], &off[1], &off[2], &off[3], &off[4], &totals, &scan_tmp, &lj, &lM,
                 &lGa, &inj, &rhits, &sk0, &sv0, &sk1, &sv1, &sort_tmp, &hkey, &hscore, &hcount, &hk1,
                 &hv1, &scratch, &next_seg, &uniq, &uflags, &uoff, &qcount, &stats, &segs, &ctr, &seg_cnt, &seg_hit,
-                &task_first, &task_tot, &task_off, &task_tmp, &task_sum, &res, &task_flag};
+                &task_first, &task_tot, &task_off, &task_tmp, &task_sum, &res, &res_key};
     }
 
     ~Workspace() {
@@ -571,12 +571,12 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
         ra.task_tot = ptr<uint32_t>(w->task_tot);
         ra.task_stride = (uint64_t)ntask;
         ra.res = nullptr;
-        ra.task_flag = nullptr;
+        ra.res_key = nullptr;
         if (i16 && !opt.tier_stats) {
             ensure(w->res, (size_t)std::max<int64_t>(ntrip, 1) * 4, st);
-            ensure(w->task_flag, (size_t)std::max<int64_t>(ntask, 1), st);
+            ensure(w->res_key, (size_t)std::max<int64_t>(ntrip, 1) * 4, st);
             ra.res = ptr<uint32_t>(w->res);
-            ra.task_flag = ptr<uint8_t>(w->task_flag);
+            ra.res_key = ptr<int32_t>(w->res_key);
         }
         prof.mark(K_ROWS);
         ae_rows(ra, false, num_sms * ae_rows_blocks_per_sm(false), st);

@@ -117,9 +117,9 @@ struct RowsArgs {
     int32_t int16;                        // 1: parent and frontier rows are packed int16x2 (M | G_a << 16) in pM / fM
     int32_t tiers;                        // 1: count entries by cost tier (ae_stats.entries_tier)
     // int16x2 route without tier counting: per triple the final slot values of the count
-    // pass (M_A | M_B << 16, 0 = dead) and per task whether it produced a gap run
+    // pass (M_A | M_B << 16, 0 = dead) and the key K of its gap run (AE_KNEG: none)
     uint32_t *res;
-    uint8_t *task_flag;
+    int32_t *res_key;
 };
 void ae_rows(const RowsArgs &a, bool write, int blocks, cudaStream_t st);
 int ae_rows_blocks_per_sm(bool write);   // blocks per SM to launch a k_rows pass with (one full wave)

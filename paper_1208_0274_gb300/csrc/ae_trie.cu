@@ -147,13 +147,11 @@ struct TaskSmem {
 //
 // With a.res (int16x2 route), the count pass also stores each triple's final
 // slot values (M of slot A in the low, of slot B in the high halfword; 0 =
-// dead), and the return value tells whether any triple of the task produced
-// a gap run; tasks without runs are then written by run_task_stored.
+// dead) and its gap-run key, and the write pass is run_task_stored.
 template <int SIGMA, bool WRITE, bool I16>
-__device__ bool run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, uint64_t s_first, uint64_t s_last,
+__device__ void run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, uint64_t s_first, uint64_t s_last,
                          uint64_t t_beg, uint64_t t_end, unsigned long long &st0, unsigned long long &st1,
                          unsigned long long &st2) {
-    bool any_run = false;
     const int lane = threadIdx.x & 31;
     const unsigned le = (lane == 31) ? 0xffffffffu : ((1u << (lane + 1)) - 1u);
     const ScoreView &sc = a.sc;
@@ -321,9 +319,10 @@ __device__ bool run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, ui
                 sm.cnt[rel] += ci;
                 sm.hit[rel] += hi;
             }
-            if (I16 && a.res && valid)
+            if (I16 && a.res && valid) {
                 a.res[t_beg + t] = (o.aliveA ? (uint32_t)o.MA : 0u) | ((o.aliveB ? (uint32_t)o.MB : 0u) << 16);
-            any_run |= __any_sync(FULL, nR > 0);
+                a.res_key[t_beg + t] = o.run_len > 0 ? incl : AE_KNEG;
+            }
             __syncwarp();
             continue;
         }
@@ -427,13 +426,13 @@ __device__ bool run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, ui
         }
         __syncwarp();
     }
-    return any_run;
 }
 
-// Write pass of a task without gap runs, from the slot values the count pass
-// stored (int16x2 route): the same outputs at the same places as run_task
-// with WRITE, without recomputing the recurrence.  G_a of slot A is the
-// vertical gap of the parent entry (Section 2.2), recomputed from the parent.
+// Write pass from the slot values the count pass stored (int16x2 route): the
+// same outputs at the same places as run_task with WRITE, without recomputing
+// the recurrence.  G_a of slot A is the vertical gap of the parent entry
+// (Section 2.2), recomputed from the parent; a gap run is rebuilt in closed
+// form from its stored key K (run_of).
 template <int SIGMA>
 __device__ void run_task_stored(const RowsArgs &a, TaskSmem &sm, uint64_t s_first, uint64_t s_last,
                                 uint64_t t_beg, uint64_t t_end) {
@@ -468,22 +467,48 @@ __device__ void run_task_stored(const RowsArgs &a, TaskSmem &sm, uint64_t s_firs
         const unsigned heads = __ballot_sync(FULL, !valid || k == 0 || lane == 0);
         const int first_lane = 31 - __clz(heads & le);
         const uint32_t w = valid ? a.res[t_beg + t] : 0u;
+        const int32_t K = valid ? a.res_key[t_beg + t] : AE_KNEG;
         const int32_t MA = (int32_t)(w & 0xFFFFu), MB = (int32_t)(w >> 16);
         const bool aliveA = MA > 0, aliveB = MB > 0;
         int32_t colA = 0, GaA = AE_NEG, H = 1, m = 1;
         if (valid) {
             H = a.qv.H[qid];
+            m = a.qv.m[qid];
             if (root) {
                 colA = (int32_t)(uint32_t)sg.poff + k;
             } else {
                 colA = a.pj[sg.poff + k];
                 if (aliveA) {
-                    m = a.qv.m[qid];
                     const uint32_t mg = reinterpret_cast<const uint32_t *>(a.pM)[sg.poff + k];
                     const int32_t gap = gap_from_mg(mg, sc.ss, oe);
                     GaA = gap > thr_of(colA, m, H, g) ? gap : AE_NEG;
                 }
             }
+        }
+        // gap run after the lane's slots (rare): rebuild its extent from K
+        int32_t run_start = 0, run_len = 0, run_hits = 0;
+        const bool chunk_runs = __any_sync(FULL, K > AE_KNEG / 2);
+        if (chunk_runs) {
+            // next parent column, as run_task derives it
+            int32_t jn = __shfl_down_sync(FULL, colA, 1);
+            const bool next_in = (lane < 31) && (((heads >> (lane + 1)) & 1u) == 0);
+            if (valid && !next_in) {
+                if (root) jn = m;
+                else jn = ((uint32_t)k + 1 < slen) ? a.pj[sg.poff + k + 1] : m;
+            }
+            int32_t next_col = m;
+            bool hasB = false;
+            if (valid) {
+                if (root) {
+                    const int32_t c1 = (int32_t)(uint32_t)(sg.poff >> 32);
+                    next_col = (colA + 1 < c1) ? colA + 1 : m;
+                } else {
+                    hasB = (colA + 1 < m) && (colA + 1 != jn);
+                    next_col = jn;
+                }
+            }
+            run_start = hasB ? colA + 2 : colA + 1;
+            run_of(run_start, next_col, K, sc, m, H, -sc.ss, run_len, run_hits);
         }
         {
             const uint32_t k31 = (uint32_t)__shfl_sync(FULL, k, 31);
@@ -493,15 +518,27 @@ __device__ void run_task_stored(const RowsArgs &a, TaskSmem &sm, uint64_t s_firs
             sbase = (v31 && k31 + 1 < len31) ? sid31 : sid31 + 1;
         }
         const bool kind1 = valid && seg_stays(sg, a.leaf_delay);
-        const uint32_t nA = aliveA, nB = aliveB;
-        const uint32_t cnt = nA + nB;
+        const uint32_t nA = aliveA, nB = aliveB, nR = (uint32_t)run_len;
+        const uint32_t cnt = nA + nB + nR;
         const uint32_t hA = aliveA && MA >= H, hB = aliveB && MB >= H;
-        const uint32_t hcnt = kind1 ? (hA + hB) : 0u;
-        const unsigned in_seg = le & ~((1u << first_lane) - 1u);
-        const unsigned bA = __ballot_sync(FULL, aliveA), bB = __ballot_sync(FULL, aliveB);
-        const unsigned bhA = __ballot_sync(FULL, kind1 && hA), bhB = __ballot_sync(FULL, kind1 && hB);
-        const uint32_t ci = __popc(bA & in_seg) + __popc(bB & in_seg);
-        const uint32_t hi = __popc(bhA & in_seg) + __popc(bhB & in_seg);
+        const uint32_t hcnt = kind1 ? (hA + hB + (uint32_t)run_hits) : 0u;
+        uint32_t ci = cnt, hi = hcnt;
+        if (chunk_runs) {
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t oc = __shfl_up_sync(FULL, ci, d), oh = __shfl_up_sync(FULL, hi, d);
+                if (lane - d >= first_lane) {
+                    ci += oc;
+                    hi += oh;
+                }
+            }
+        } else {
+            const unsigned in_seg = le & ~((1u << first_lane) - 1u);
+            const unsigned bA = __ballot_sync(FULL, aliveA), bB = __ballot_sync(FULL, aliveB);
+            const unsigned bhA = __ballot_sync(FULL, kind1 && hA), bhB = __ballot_sync(FULL, kind1 && hB);
+            ci = __popc(bA & in_seg) + __popc(bB & in_seg);
+            hi = __popc(bhA & in_seg) + __popc(bhB & in_seg);
+        }
         const bool is_last = valid && (lane == 31 || ((heads >> (lane + 1)) & 1u));
         const uint64_t rel = sid - s_first;
         uint64_t e0 = 0, h0 = 0;
@@ -552,6 +589,40 @@ __device__ void run_task_stored(const RowsArgs &a, TaskSmem &sm, uint64_t s_firs
                 a.rhits[hp++] = r;
             }
         }
+        if (chunk_runs) {
+            unsigned rmask = __ballot_sync(FULL, nR > 0);
+            while (rmask) {
+                const int L = __ffs(rmask) - 1;
+                rmask &= rmask - 1;
+                const int32_t s0 = __shfl_sync(FULL, run_start, L);
+                const int32_t rl = __shfl_sync(FULL, run_len, L);
+                const int32_t rh = __shfl_sync(FULL, run_hits, L);
+                const int32_t KL = __shfl_sync(FULL, K, L);
+                const uint64_t d0 = __shfl_sync(FULL, e0 + nA + nB, L);
+                const uint64_t hd = __shfl_sync(FULL, h0 + hA + hB, L);
+                const bool k1 = __shfl_sync(FULL, kind1, L);
+                int32_t *rj = (int32_t *)__shfl_sync(FULL, (unsigned long long)oj, L);
+                int32_t *rM = (int32_t *)__shfl_sync(FULL, (unsigned long long)oM, L);
+                int32_t *rG = (int32_t *)__shfl_sync(FULL, (unsigned long long)oGa, L);
+                const uint32_t rlo = __shfl_sync(FULL, sg.lo, L), rhi = __shfl_sync(FULL, sg.hi, L);
+                const int32_t rq = __shfl_sync(FULL, qid, L);
+                for (int32_t tt = lane; tt < rl; tt += 32) {
+                    const int32_t col = s0 + tt;
+                    const int32_t v = sc.sg + sc.ss * col + KL;   // s_g - col*u + K
+                    rj[d0 + tt] = col;
+                    if (k1) {
+                        reinterpret_cast<uint32_t *>(rM)[d0 + tt] = pack_mg(v, AE_NEG);
+                    } else {
+                        rM[d0 + tt] = v;
+                        rG[d0 + tt] = AE_NEG;
+                    }
+                    if (k1 && tt < rh) {
+                        RangeHit r = {rlo, rhi, rq, col, v, 0};
+                        a.rhits[hd + tt] = r;
+                    }
+                }
+            }
+        }
         __syncwarp();
     }
 }
@@ -597,8 +668,7 @@ __global__ void __launch_bounds__(RW_WARPS * 32, WRITE ? RW_MINB_WRITE : RW_MINB
                 sm.hit[r] = 0;
             }
             __syncwarp();
-            const bool any_run = run_task<SIGMA, false, I16>(a, smat, sm, s_first, s_last, t_beg, t_end, st0, st1, st2);
-            if (I16 && a.res && lane == 0) a.task_flag[task] = any_run ? 1 : 0;
+            run_task<SIGMA, false, I16>(a, smat, sm, s_first, s_last, t_beg, t_end, st0, st1, st2);
             __syncwarp();
         } else {
             for (uint64_t r = lane; r < nsg; r += 32) {
@@ -744,7 +814,7 @@ __global__ void __launch_bounds__(RW_WARPS * 32, WRITE ? RW_MINB_WRITE : RW_MINB
             sm.hit[r] = 0;
         }
         __syncwarp();
-        if (I16 && a.res && !a.task_flag[task])
+        if (I16 && a.res)
             run_task_stored<SIGMA>(a, sm, s_first, s_last, t_beg, t_end);
         else
             run_task<SIGMA, true, I16>(a, smat, sm, s_first, s_last, t_beg, t_end, st0, st1, st2);
