@@ -70,7 +70,12 @@ struct Seg {
 };
 // Triples per k_rows task window.  A task takes the segments that start in
 // its window (the last one may run past it).
-constexpr int AE_ROW_TASK = 128;
+// (192: the largest window whose per-warp tables leave room for 6 resident
+// blocks of 8 warps; measured best on the 100 Mbp workload)
+#ifndef AE_ROW_TASK_TRIPLES
+#define AE_ROW_TASK_TRIPLES 192
+#endif
+constexpr int AE_ROW_TASK = AE_ROW_TASK_TRIPLES;
 // k_compact also writes task_first[w] = the first segment starting at or
 // after triple w * AE_ROW_TASK, for every window w < ceil(triples / AE_ROW_TASK).
 void ae_compact_segs(const ChildrenArgs &a, const uint64_t *seg_off, const uint64_t *trip_off, Seg *segs,

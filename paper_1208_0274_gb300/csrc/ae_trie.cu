@@ -119,9 +119,15 @@ __device__ __forceinline__ bool seg_stays(const Seg &sg, int delay) {
     return (int)(sg.len >> 28) + 1 <= delay;
 }
 
-constexpr int RW_WARPS = 8;
+#ifndef AE_RW_WARPS
+#define AE_RW_WARPS 8
+#endif
+constexpr int RW_WARPS = AE_RW_WARPS;
 constexpr int RW_TASK = AE_ROW_TASK;   // triples per task window = max segments per task
-constexpr int RW_GRAB = 4;             // tasks per take from the task counter
+#ifndef AE_RW_GRAB
+#define AE_RW_GRAB 4
+#endif
+constexpr int RW_GRAB = AE_RW_GRAB;    // tasks per take from the task counter
 // Resident blocks per SM the two passes are compiled for (and launched with):
 // the kernel is bound by memory latency per triple, so more resident warps
 // beat more registers (measured on the 100 Mbp workload: 6 blocks of 8 warps)
