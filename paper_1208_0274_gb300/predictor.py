@@ -168,6 +168,13 @@ class WorkPredictor:
         P = self.predict(queries, stream)
         return np.expm1(np.maximum(P[:, 0], 0.0))
 
+    def work_and_hints(self, queries, stream=None):
+        """(expected DP entries, hit hints) per query from one forward pass."""
+        P = self.predict(queries, stream)
+        work = np.expm1(np.maximum(P[:, 0], 0.0))
+        hints = np.ceil(np.expm1(np.maximum(P[:, 1], 0.0)) * self.hit_margin).astype(np.int64)
+        return work, hints
+
     def device_bytes(self, queries, stream=None):
         """Expected device bytes of one search over `queries` together."""
         P = self.predict(queries, stream)

@@ -105,6 +105,12 @@ class Server:
                 mem_info = torch.cuda.mem_get_info
         self.streams = list(streams)
         self.mem_info = mem_info
+        # predictions run on a stream of their own: the legacy default stream would
+        # wait for (and hold up) every search in flight
+        self.pred_stream = None
+        if predictor is not None:
+            import torch
+            self.pred_stream = torch.cuda.Stream()
         self.search_fn = search_fn or self._search
         self.workspace_fn = workspace_fn or (lambda stream: ae.ae_workspace_info(self.index, stream)[0])
         self._lock = threading.Condition()
@@ -131,8 +137,7 @@ class Server:
         if self.predict_fn is not None:
             work, hits = self.predict_fn(qs)
         else:
-            work = self.predictor.work(qs)
-            hits = self.predictor.hint_hits(qs)
+            work, hits = self.predictor.work_and_hints(qs, stream=self.pred_stream)
         for r, w, h in zip(new, work, hits):
             r.pred_work = float(w)
             r.pred_hits = int(h)
