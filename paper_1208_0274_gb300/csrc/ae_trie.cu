@@ -76,6 +76,9 @@ __global__ void k_compact(ChildrenArgs a, const uint64_t *seg_off, const uint64_
         if (!len) continue;
         const bool root = nd.cnt == AE_ROOT_ROW;
         uint64_t so = seg_off[v], to = trip_off[v];
+        // next task window start at or after `to` (one division per node; the
+        // segments of a node are consecutive, so later windows follow by adding)
+        uint64_t wq = (to + AE_ROW_TASK - 1) / AE_ROW_TASK;
         uint32_t cq_hi;
         uint64_t poff;
         uint32_t len_hi = 0;
@@ -101,8 +104,7 @@ __global__ void k_compact(ChildrenArgs a, const uint64_t *seg_off, const uint64_
             segs[so] = s;
             // task windows that begin inside this segment: the first segment at or
             // after the window start is this one (start on its first triple) or the next
-            for (uint64_t b = (to + AE_ROW_TASK - 1) / AE_ROW_TASK * AE_ROW_TASK; b < to + len; b += AE_ROW_TASK)
-                task_first[b / AE_ROW_TASK] = b == to ? so : so + 1;
+            for (; wq * AE_ROW_TASK < to + len; ++wq) task_first[wq] = wq * AE_ROW_TASK == to ? so : so + 1;
             ++so;
             to += len;
         });

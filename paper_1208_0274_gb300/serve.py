@@ -158,9 +158,9 @@ class Server:
                 batch.append(r)
                 cols += r.query.size
             return batch
-        self._predict(pending)
-        old = [r for r in pending if now - r.arrival > self.max_wait]
-        order = old + sorted((r for r in pending if now - r.arrival <= self.max_wait), key=lambda r: r.pred_work)
+        ready = [r for r in pending if r.pred_work >= 0]          # predicted (others are in progress)
+        old = [r for r in ready if now - r.arrival > self.max_wait]
+        order = old + sorted((r for r in ready if now - r.arrival <= self.max_wait), key=lambda r: r.pred_work)
         budget = self.work_budget if self.work_budget is not None else float("inf")
         batch, work, cols = [], 0.0, 0
         for r in order:
@@ -211,7 +211,24 @@ class Server:
                         admit_arrivals()
                         if stop or (nxt >= len(reqs) and not pending):
                             return
-                        if pending:
+                        if pending and self.policy == "predicted":
+                            # predict new arrivals outside the lock (other slots keep
+                            # scheduling meanwhile); -2 marks a prediction in progress
+                            todo = [r for r in pending if r.pred_work == -1.0]
+                            if todo:
+                                for r in todo:
+                                    r.pred_work = -2.0
+                                cond.release()
+                                try:
+                                    self._predict(todo)
+                                except BaseException:
+                                    for r in todo:
+                                        r.pred_work = -1.0
+                                    raise
+                                finally:
+                                    cond.acquire()
+                                continue
+                        if pending and any(r.pred_work >= 0 for r in pending) or (pending and self.policy == "fifo"):
                             batch = self._take(pending, now())
                             need = self.need_bytes(batch)
                             # the slot's workspace is reused: only its growth needs free memory
