@@ -75,6 +75,24 @@ def log(*a):
     print(*a, file=sys.stderr, flush=True)
 
 
+def shard(n_items, rank, world):
+    """Items of rank `rank` of `world`: every world-th item from rank.  Queries
+    are independent problems, so the shards need no exchange."""
+    return list(range(rank, n_items, world))
+
+
+def job_totals(ms, units, dist=None, device="cpu"):
+    """Whole-job time (max over ranks) and work (sum over ranks)."""
+    if dist is None:
+        return float(ms), float(units)
+    import torch
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    c = torch.tensor([float(units)], device=device, dtype=torch.float64)
+    dist.all_reduce(c, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(c.item())
+
+
 def make_workload(args):
     """(name, text, queries, H list, scheme, description) identical on every rank."""
     scheme = Scheme(1, -3, -5, -2)
@@ -253,7 +271,7 @@ def run_ours(args):
     from paper_1208_0274_gb300 import ae
 
     name, text, queries, H, scheme, desc = make_workload(args)
-    mine = list(range(rank, len(queries), ws))
+    mine = shard(len(queries), rank, ws)
     qs = [queries[k] for k in mine]
     hs = [H[k] for k in mine]
     t0 = time.perf_counter()
@@ -320,16 +338,7 @@ def run_ours(args):
         dist.barrier()
     clk = clocks.stop()
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    tot_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([tot_ms], device=f"cuda:{local}", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        tot_ms = float(t.item())
-        c = torch.tensor([cells], device=f"cuda:{local}", dtype=torch.float64)
-        dist.all_reduce(c, op=dist.ReduceOp.SUM)
-        cells_all = float(c.item())
-    else:
-        cells_all = float(cells)
+    tot_ms, cells_all = job_totals(sum(step_ms), cells, dist, device=f"cuda:{local}")
     value = args.steps * cells_all / (tot_ms / 1000.0) / 1e9
     qps = args.steps * (len(queries) if ws > 1 else len(qs)) / (tot_ms / 1000.0)
 
@@ -365,11 +374,7 @@ def run_ours(args):
             hits, counts = ae.ae_search(idx, qs, scheme, hs, stream=stream)
             t_e.append(time.perf_counter() - t1)
             hbytes = hits.nbytes + counts.nbytes
-        et = sum(t_e) / len(t_e)
-        if dist:
-            t = torch.tensor([et], device=f"cuda:{local}", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            et = float(t.item())
+        et, _ = job_totals(sum(t_e) / len(t_e), 0, dist, device=f"cuda:{local}")
         e2e = {"value": round(cells_all / et / 1e9, 3), "unit": "GCUPS",
                "h2d_bytes_per_step": int(seq.nbytes), "d2h_bytes_per_step": int(hbytes),
                "ms_per_step": round(et * 1000, 3)}
