@@ -30,7 +30,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 from workloads import (DNA_SCALE_H, Scheme, dna_batch, dna_scale_bench, dna_scale_text, dna_serve,  # noqa: E402
-                       dna_small)
+                       dna_small, protein, PROTEIN)
 
 METRIC = "effective GCUPS (m*n/time) at bit-exact hits, batched"
 
@@ -41,7 +41,8 @@ def parse():
     p.add_argument("--steps", type=int, default=5)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    p.add_argument("--workload", default="dna_scale", choices=["dna_scale", "dna_small", "dna_serve", "dna_batch"])
+    p.add_argument("--workload", default="dna_scale",
+                   choices=["dna_scale", "dna_small", "dna_serve", "dna_batch", "protein"])
     p.add_argument("--queries", type=int, default=4096, help="dna_batch: number of queries")
     p.add_argument("--plain-sample", type=int, default=256, help="dna_batch: queries timed one launch at a time")
     p.add_argument("--requests", type=int, default=1000, help="dna_serve: number of requests")
@@ -102,6 +103,17 @@ def make_workload(args):
                 {"workload": "dna_small: 100 kbp uniform ACGT text, one 1 kbp query with 5 planted "
                              "150-300 bp copies (10% subs, 2% indels), <1,-3,-5,-2>, H=30",
                  "n": int(wl.text.size), "queries": 1, "sum_m": int(wl.queries[0].size)})
+    if args.workload == "protein":
+        n = args.n if args.n != 100_000_000 else 50_000_000
+        lengths = [100, 1000, 5000] if args.lengths == "10000,100000,1000000" else \
+            [int(x) for x in args.lengths.split(",")]
+        wl = protein(n=n, lengths=lengths, per_length=args.per_length)
+        return ("protein", wl.text, wl.queries, wl.H, wl.scheme,
+                {"workload": f"protein: {n:,} residues at background frequencies; {args.per_length} queries each of "
+                             f"{'/'.join(str(x) for x in lengths)} residues with planted homologs at 30-60% identity; "
+                             "BLOSUM62, gap -11/-1, H=50",
+                 "n": int(n), "queries": len(wl.queries), "sum_m": int(sum(q.size for q in wl.queries)),
+                 "l2": "flushed between timed steps (512 MiB write)"})
     lengths = [int(x) for x in args.lengths.split(",")]
     text, queries, H, _ = dna_scale_bench(n=args.n, lengths=lengths, per_length=args.per_length)
     desc = {"workload": f"dna_scale: {args.n:,} bp i.i.d. text at 41% GC; {args.per_length} queries each of "
@@ -206,7 +218,7 @@ INT_PEAK_GOPS = 152 * 64 * 2.070
 OPS_PER_TRIPLE = 12
 
 
-def cpu_baseline(text, queries, scheme, H, seconds):
+def cpu_baseline(text, queries, scheme, H, seconds, alphabet=b"ACGT"):
     """The oracle (plain full-matrix Smith-Waterman, one thread) on a bounded
     sample: the shortest query against a text slice sized for ~`seconds`."""
     import oracle
@@ -214,11 +226,11 @@ def cpu_baseline(text, queries, scheme, H, seconds):
     h = H[int(np.argmin([x.size for x in queries]))]
     probe = text[: max(1, 20_000_000 // max(q.size, 1))]
     t0 = time.perf_counter()
-    oracle.sw_hits(probe, q, scheme, h)
+    oracle.sw_hits(probe, q, scheme, h, alphabet=alphabet)
     rate = probe.size * q.size / max(time.perf_counter() - t0, 1e-6)
     L = int(min(text.size, max(1000, rate * seconds / q.size)))
     t0 = time.perf_counter()
-    oracle.sw_hits(text[:L], q, scheme, h)
+    oracle.sw_hits(text[:L], q, scheme, h, alphabet=alphabet)
     dt = time.perf_counter() - t0
     return {"value": round(L * q.size / dt / 1e9, 4), "unit": "GCUPS", "cores": 1, "kind": "oracle",
             "sample": f"one {q.size} bp query against the first {L:,} bp of the text "
@@ -237,15 +249,16 @@ def run_reference(args):
     # size one step at ~10 s of oracle work
     probe = text[: max(1, 20_000_000 // max(q.size, 1))]
     t0 = time.perf_counter()
-    oracle.sw_hits(probe, q, scheme, h)
+    alphabet = PROTEIN if name == "protein" else b"ACGT"
+    oracle.sw_hits(probe, q, scheme, h, alphabet=alphabet)
     rate = probe.size * q.size / max(time.perf_counter() - t0, 1e-6)
     L = int(min(text.size, max(1000, rate * 10.0 / q.size)))
     for _ in range(max(args.warmup, 0) if L * q.size < 2e9 else 0):
-        oracle.sw_hits(text[: L // 10], q, scheme, h)
+        oracle.sw_hits(text[: L // 10], q, scheme, h, alphabet=alphabet)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.sw_hits(text[:L], q, scheme, h)
+        oracle.sw_hits(text[:L], q, scheme, h, alphabet=alphabet)
         times.append(time.perf_counter() - t0)
     tot = sum(times)
     v = args.steps * L * q.size / tot / 1e9
@@ -275,8 +288,8 @@ def run_ours(args):
     qs = [queries[k] for k in mine]
     hs = [H[k] for k in mine]
     t0 = time.perf_counter()
-    idx = ae.ae_index_build(text, ae.AE_DNA)
-    log(f"[rank {rank}] index of {text.size:,} bp built in {time.perf_counter() - t0:.1f} s")
+    idx = ae.ae_index_build(text, ae.AE_PROTEIN if name == "protein" else ae.AE_DNA)
+    log(f"[rank {rank}] index of {text.size:,} letters built in {time.perf_counter() - t0:.1f} s")
     n = text.size
     stream = torch.cuda.Stream()
     opts = ae.make_options(leaf_segment=args.leaf_segment, item_columns=args.item_columns,
@@ -416,7 +429,8 @@ def run_ours(args):
     if not args.no_cpu:
         import oracle
         oracle.build()
-        cpu = cpu_baseline(text, queries, scheme, H, args.cpu_seconds)
+        cpu = cpu_baseline(text, queries, scheme, H, args.cpu_seconds,
+                           alphabet=PROTEIN if name == "protein" else b"ACGT")
     line = {"metric": METRIC, "value": round(value, 3), "unit": "GCUPS", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(tot_ms / args.steps, 3), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic", "config": desc,

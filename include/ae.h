@@ -104,6 +104,8 @@ typedef struct {
     int64_t leaf_raw_hits;    /* hit records written by the sweep (before the per-cell max) */
     int64_t triples;          /* (child, parent entry) pairs the trie levels evaluated: every
                                  non-empty child of a node with every entry of the node's row */
+    int64_t batch_splits;     /* batches that ran out of device memory and were searched again
+                                 as two halves (the result is the same) */
 } ae_stats;
 
 /* Engine knobs (NULL = defaults).  None of them changes the result set. */
@@ -126,6 +128,10 @@ typedef struct {
                                  rerun of the sweep, never a result */
     int32_t tier_stats;       /* 1: count trie entries by cost tier into ae_stats.entries_tier
                                  (a few instructions per entry); 0: leave them 0 */
+    int64_t workspace_limit;  /* > 0: cap on the device bytes of the stream's workspace; a batch
+                                 that would grow it further is searched as two halves (as after
+                                 a failed device allocation; ae_stats.batch_splits); a single
+                                 query column that does not fit gives AE_ENOMEM.  0: no cap */
 } ae_options;
 
 /* Fill *opt with the defaults. */

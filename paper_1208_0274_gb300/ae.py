@@ -43,7 +43,8 @@ class ae_options(ctypes.Structure):
                 ("item_columns", ctypes.c_int64), ("batch_columns", ctypes.c_int64),
                 ("leaf_capacity", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("leaf_delay", ctypes.c_int32), ("int16_limit", ctypes.c_int32),
-                ("hint_hits", ctypes.c_void_p), ("tier_stats", ctypes.c_int32)]
+                ("hint_hits", ctypes.c_void_p), ("tier_stats", ctypes.c_int32),
+                ("workspace_limit", ctypes.c_int64)]
 
 
 class ae_stats(ctypes.Structure):
@@ -60,7 +61,7 @@ class ae_stats(ctypes.Structure):
                 ("leaf_max_steps", ctypes.c_int64),
                 ("leaf_max_width", ctypes.c_int64), ("ws_bytes", ctypes.c_int64),
                 ("leaf_sweeps", ctypes.c_int64), ("leaf_raw_hits", ctypes.c_int64),
-                ("triples", ctypes.c_int64)]
+                ("triples", ctypes.c_int64), ("batch_splits", ctypes.c_int64)]
 
 
 def _load():

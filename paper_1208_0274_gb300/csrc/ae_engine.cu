@@ -74,6 +74,15 @@ void trace_alloc(size_t nb, bool ok) {
             ok ? "ok" : "FAILED", g_ws_bytes.load() / 1e9, fr / 1e9, tot / 1e9);
 }
 
+// Optional cap on the device bytes of the running search's workspace
+// (ae_options.workspace_limit): growth past it fails as AE_ENOMEM.
+thread_local int64_t g_ws_limit = 0;
+int64_t cur_ws_bytes();
+
+void check_limit(const DevBuf &b, size_t nb) {
+    if (g_ws_limit > 0 && cur_ws_bytes() - (int64_t)b.bytes + (int64_t)nb > g_ws_limit) throw ae_error{AE_ENOMEM};
+}
+
 // Grow-only device buffer; contents are not preserved.
 void ensure(DevBuf &b, size_t bytes, cudaStream_t st) {
     if (bytes <= b.bytes) return;
@@ -83,6 +92,7 @@ void ensure(DevBuf &b, size_t bytes, cudaStream_t st) {
     }
     size_t nb = std::max(bytes, b.bytes + b.bytes / 4);
     nb = (nb + 255) & ~size_t(255);
+    check_limit(b, nb);
     if (b.p) {
         CU(cudaStreamSynchronize(st));
         CU(cudaFree(b.p));
@@ -109,6 +119,7 @@ void ensure_keep(DevBuf &b, size_t bytes, size_t keep, cudaStream_t st) {
     }
     size_t nb = std::max(bytes, b.bytes + b.bytes / 4);
     nb = (nb + 255) & ~size_t(255);
+    check_limit(b, nb);
     void *p = nullptr;
     if (cudaMalloc(&p, nb) != cudaSuccess) {
         cudaGetLastError();
@@ -186,6 +197,24 @@ struct Workspace {
         if (h_stage) cudaFreeHost(h_stage);
     }
 
+    // Free the buffers of one batch's walk (kept: queries, counters and the point
+    // hits collected so far), before a batch is retried in smaller parts.
+    void trim_batch() {
+        DevBuf *drop[] = {&aj[0], &aj[1], &aM[0], &aM[1], &aGa[0], &aGa[1], &nodes[0], &nodes[1], &cnt[0], &cnt[1],
+                          &cnt[2], &cnt[3], &cnt[4], &off[0], &off[1], &off[2], &off[3], &off[4], &scan_tmp, &lj,
+                          &lM, &lGa, &inj, &rhits, &sk0, &sv0, &sk1, &sv1, &sort_tmp, &hk1, &hv1, &scratch, &uniq,
+                          &uflags, &uoff, &segs, &seg_cnt, &seg_hit, &task_first, &task_tot, &task_off, &task_tmp,
+                          &res, &res_key};
+        for (DevBuf *b : drop)
+            if (b->p && !b->carved) {
+                cudaFree(b->p);
+                g_ws_bytes -= (int64_t)b->bytes;
+                b->p = nullptr;
+                b->bytes = 0;
+            }
+        leaf_cap = 0;
+    }
+
     // Forget every carved buffer (the next static call carves them again).
     void forget_carved() {
         for (DevBuf *b : bufs()) {
@@ -195,6 +224,9 @@ struct Workspace {
         }
     }
 };
+
+thread_local Workspace *g_cur_ws = nullptr;   // workspace of the running search (limit accounting)
+int64_t cur_ws_bytes() { return g_cur_ws ? g_cur_ws->device_bytes() : 0; }
 
 }  // namespace
 
@@ -379,6 +411,7 @@ struct Search {
     }
 
     void run_batch(const std::vector<WorkItem> &items);
+    void run_batch_split(const std::vector<WorkItem> &items);
     void compact_hits(int64_t from);
     void leaf_phase(int64_t ninj);
     void locate_phase(int64_t nrh);
@@ -669,6 +702,41 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
 // (query, text end, query end) with the maximum score, in place.  Queries are
 // whole inside a batch by default, so the final pass then sorts far fewer
 // records; it stays exact either way.
+// A batch whose working set does not fit the device is split in two and each
+// half searched alone (batches are independent: a work item's forks start in
+// its own columns, and hits meet only at the final per-cell maximum).  The
+// failed attempt's hits are dropped; its counters stay in the statistics.
+void Search::run_batch_split(const std::vector<WorkItem> &items) {
+    const int64_t h0 = nhits;
+    try {
+        run_batch(items);
+        return;
+    } catch (const ae_error &e) {
+        if (e.st != AE_ENOMEM) throw;
+    }
+    cudaGetLastError();
+    CU(cudaStreamSynchronize(st));
+    nhits = h0;
+    ++stats.batch_splits;
+    if (!g_arena) w->trim_batch();
+    std::vector<WorkItem> a, b;
+    if (items.size() >= 2) {
+        a.assign(items.begin(), items.begin() + (long)(items.size() / 2));
+        b.assign(items.begin() + (long)(items.size() / 2), items.end());
+    } else {
+        const WorkItem it = items[0];
+        if (it.c1 - it.c0 < 2) throw ae_error{AE_ENOMEM};
+        const int32_t mid = it.c0 + (it.c1 - it.c0) / 2;
+        WorkItem x = it, y = it;
+        x.c1 = mid;
+        y.c0 = mid;
+        a.push_back(x);
+        b.push_back(y);
+    }
+    run_batch_split(a);
+    run_batch_split(b);
+}
+
 void Search::compact_hits(int64_t from) {
     const int64_t N = nhits - from;
     if (N <= 1) return;
@@ -922,6 +990,15 @@ ae_status search_core(const ae_index *idx, Workspace *w, const int64_t *offsets,
     s.d0 = seed_depth(s.sc, Hmin, s.opt.qprefix_seed != 0);
     s.stats.seed_depth = s.d0;
     s.prof.on = s.opt.profile != 0;
+    if (s.opt.workspace_limit < 0) return AE_EINVAL;
+    g_cur_ws = w;
+    g_ws_limit = g_arena ? 0 : s.opt.workspace_limit;
+    struct LimitReset {
+        ~LimitReset() {
+            g_cur_ws = nullptr;
+            g_ws_limit = 0;
+        }
+    } limit_reset;
     s.prof.st = st;
     const int64_t launches0 = ae_launches_read();
     int dev = 0;
@@ -955,13 +1032,13 @@ ae_status search_core(const ae_index *idx, Workspace *w, const int64_t *offsets,
                 batch.push_back(it);
                 cols += it.c1 - it.c0;
                 if (cols >= s.opt.batch_columns) {
-                    s.run_batch(batch);
+                    s.run_batch_split(batch);
                     batch.clear();
                     cols = 0;
                 }
             }
         }
-        if (!batch.empty()) s.run_batch(batch);
+        if (!batch.empty()) s.run_batch_split(batch);
         *total = s.finish(out_dev, counts);
         DevStats ds;
         CU(cudaMemcpyAsync(&ds, w->stats.p, sizeof(ds), cudaMemcpyDeviceToHost, st));
@@ -1012,6 +1089,7 @@ void ae_options_default(ae_options *opt) {
     opt->int16_limit = 32000;
     opt->hint_hits = nullptr;
     opt->tier_stats = 0;
+    opt->workspace_limit = 0;
 }
 
 const char *ae_strerror(int32_t status) {

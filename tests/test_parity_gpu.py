@@ -236,3 +236,25 @@ def test_index_save_load_roundtrip(small, tmp_path):
     with pytest.raises(ae.AEError) as e:
         ae.ae_index_load(p)
     assert e.value.status == ae.AE_EIO
+
+
+def test_workspace_limit_splits_batches_without_changing_hits():
+    from workloads import dna_scale_text, dna_scale_query
+    text = dna_scale_text(seed=61, n=2_000_000)
+    q, _ = dna_scale_query(text, 30_000, np.random.default_rng(62), frac=0.05)
+    idx = ae.ae_index_build(text, ae.AE_DNA)
+    st = torch.cuda.Stream()
+    base = dict(leaf_capacity=64)
+    ae.ae_workspace_release(idx, st)
+    want, wc = ae.ae_search(idx, [q], Scheme(), [22], options=ae.make_options(**base), stream=st)
+    full, _ = ae.ae_workspace_info(idx, st)
+    assert ae.ae_last_stats()["batch_splits"] == 0 and want.size > 0
+    ae.ae_workspace_release(idx, st)
+    got, gc = ae.ae_search(idx, [q], Scheme(), [22], stream=st,
+                           options=ae.make_options(workspace_limit=int(full * 0.6), **base))
+    used, _ = ae.ae_workspace_info(idx, st)
+    assert ae.ae_last_stats()["batch_splits"] >= 1
+    assert used <= int(full * 0.6)
+    assert np.array_equal(wc, gc) and np.array_equal(want, got)
+    ae.ae_workspace_release(idx, st)
+    idx.close()
