@@ -36,7 +36,7 @@ typedef enum {
     AE_EOVERFLOW = 3,     /* caller buffer too small; required sizes are returned */
     AE_ETIMEOUT = 4,      /* a bounded device wait gave up */
     AE_ECUDA = 5,         /* a CUDA runtime call failed */
-    AE_EUNSUPPORTED = 6,  /* sizes beyond what this build handles (e.g. n >= 2^31) */
+    AE_EUNSUPPORTED = 6,  /* sizes beyond the library's limits (e.g. n >= 2^31) */
     AE_EIO = 7            /* file read/write or format error */
 } ae_status;
 
