@@ -293,8 +293,14 @@ def run_ours(args):
     log(f"[rank {rank}] index of {text.size:,} letters built in {time.perf_counter() - t0:.1f} s")
     n = text.size
     stream = torch.cuda.Stream()
+    # one search over all queries: 2 M query letters per engine batch (fewer batches, fewer
+    # sweep tails; ~172 GB of workspace on the 100 Mbp workload, within the device's memory)
+    batch_columns = args.batch_columns if args.batch_columns is not None else (1 << 21)
     opts = ae.make_options(leaf_segment=args.leaf_segment, item_columns=args.item_columns,
-                           batch_columns=args.batch_columns, leaf_delay=args.leaf_delay, profile=1)
+                           batch_columns=batch_columns, leaf_delay=args.leaf_delay, profile=1)
+    opts_e2e = ae.make_options(leaf_segment=args.leaf_segment, item_columns=args.item_columns,
+                               batch_columns=batch_columns, leaf_delay=args.leaf_delay)
+    desc["batch_columns"] = batch_columns
     seq = np.concatenate(qs) if qs else np.zeros(0, np.uint8)
     offsets = np.concatenate([[0], np.cumsum([q.size for q in qs])]).astype(np.int64)
     d_seq = torch.from_numpy(seq).to(f"cuda:{local}")
@@ -385,7 +391,7 @@ def run_ours(args):
         for s in range(max(1, min(args.steps, 3))):
             torch.cuda.synchronize()
             t1 = time.perf_counter()
-            hits, counts = ae.ae_search(idx, qs, scheme, hs, stream=stream)
+            hits, counts = ae.ae_search(idx, qs, scheme, hs, options=opts_e2e, stream=stream)
             t_e.append(time.perf_counter() - t1)
             hbytes = hits.nbytes + counts.nbytes
         et, _ = job_totals(sum(t_e) / len(t_e), 0, dist, device=f"cuda:{local}")
