@@ -5,11 +5,14 @@
 //                backward-search step, lo' = C[c] + Occ(c, lo), hi' = C[c] +
 //                Occ(c, hi); a non-empty child inherits its parent's row length
 //                as the number of "triples" (child, parent entry) to compute.
-//   scan+compact the non-empty children become segments laid end to end.
+//   scan+compact the non-empty children become segments laid end to end, with
+//                a table of the first segment of every task window.
 //   k_rows       the triples are packed densely into warp lanes (many small
 //                rows share one warp); horizontal gaps use segmented max-plus
-//                scans.  Each warp task counts its outputs, reserves space with
-//                one atomic per arena, then recomputes and writes them.
+//                scans.  A count pass counts every task's outputs (and keeps
+//                each triple's final slot values); after an exclusive scan of
+//                the task totals, a write pass writes the outputs at their
+//                offsets.
 //
 // Children with one occurrence leave the trie: their rows go to the leaf
 // arena as injections for the text-position sweep.
@@ -636,11 +639,14 @@ __device__ void run_task_stored(const RowsArgs &a, TaskSmem &sm, uint64_t s_firs
 }
 
 // One row pass over all triples.  WRITE = false: every task counts its
-// segments' outputs into seg_cnt/seg_hit and adds the level totals (so the
-// host can size the next arenas exactly).  WRITE = true: every task reads its
-// segments' counts, reserves its output ranges with one atomic per arena,
-// writes the child node / injection records, and recomputes and writes the
-// rows and the hits of multi-occurrence children.
+// segments' outputs into seg_cnt/seg_hit, its totals per arena into task_tot,
+// and the level totals (so the host can size the next arenas exactly); on the
+// int16x2 route it also stores each triple's slot values and run key.
+// WRITE = true: every task takes its output ranges from the scanned task
+// totals (or, after a task total too wide for the scan, from one atomic per
+// arena), writes the child node / injection records, and writes the rows and
+// the hits of multi-occurrence children, from the stored values or by
+// recomputing them.
 template <int SIGMA, bool WRITE, bool I16>
 __global__ void __launch_bounds__(RW_WARPS * 32, WRITE ? RW_MINB_WRITE : RW_MINB_COUNT) k_rows(RowsArgs a) {
     __shared__ int8_t smat[AE_MAX_SIGMA * AE_MAX_SIGMA];
