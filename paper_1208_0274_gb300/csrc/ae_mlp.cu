@@ -36,6 +36,13 @@ constexpr int NORM_XMU = 0, NORM_XISD = NIN, NORM_YMU = 2 * NIN, NORM_YSD = 2 * 
 // product, fp32 accumulate).  Epilogue per element: + bias[n]; Z = that value
 // (pre-activation); zeroed where mask <= 0; relu; stored to C (ld ldc).  One
 // warp owns a 16 x 32 tile (four m16n8k16 products per k step of 16).
+//
+// Split K: the weight gradients are products with a small output (at most
+// 128 x 128) and K = the batch rows, which a few warps would walk alone.  With
+// `part` set, gemm() splits K into up to GEMM_KSPLIT_MAX chunks (blockIdx.y),
+// each block stores its raw partial tile to part[s][M][N], and k_gemm_reduce
+// sums the chunks in chunk order and applies the epilogue, so the result does
+// not depend on scheduling.
 
 struct GemmArgs {
     const float *A;
@@ -48,10 +55,14 @@ struct GemmArgs {
     const float *mask;
     float *Z;
     int M, N, K, relu;
+    float *part;        // split-K partials (GEMM_KSPLIT_MAX * M * N floats), or null
+    int kchunk;         // K per chunk (a multiple of 16); set by gemm()
 };
 
 constexpr int GEMM_NT = 4;      // n8 sub-tiles per warp
 constexpr int GEMM_WARPS = 4;
+constexpr int GEMM_KSPLIT_MAX = 64;
+constexpr int GEMM_TARGET_BLOCKS = 2 * 152;
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
     __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);   // .x (low half) = lo
@@ -74,16 +85,17 @@ __global__ void __launch_bounds__(GEMM_WARPS * 32) k_gemm(GemmArgs a) {
     const int64_t tile = (int64_t)blockIdx.x * GEMM_WARPS + warp;
     if (tile >= tiles_m * tiles_n) return;
     const int m0 = (int)(tile / tiles_n) * 16, n0 = (int)(tile % tiles_n) * 8 * GEMM_NT;
+    const int kbeg = (int)blockIdx.y * a.kchunk, kend = min(a.K, kbeg + a.kchunk);
     auto ldA = [&](int m, int k) -> float {
-        return (m < a.M && k < a.K) ? a.A[(int64_t)m * a.sam + (int64_t)k * a.sak] : 0.f;
+        return (m < a.M && k < kend) ? a.A[(int64_t)m * a.sam + (int64_t)k * a.sak] : 0.f;
     };
     auto ldB = [&](int k, int n) -> float {
-        return (k < a.K && n < a.N) ? a.B[(int64_t)k * a.sbk + (int64_t)n * a.sbn] : 0.f;
+        return (k < kend && n < a.N) ? a.B[(int64_t)k * a.sbk + (int64_t)n * a.sbn] : 0.f;
     };
     float acc[GEMM_NT][4];
 #pragma unroll
     for (int j = 0; j < GEMM_NT; ++j) acc[j][0] = acc[j][1] = acc[j][2] = acc[j][3] = 0.f;
-    for (int k0 = 0; k0 < a.K; k0 += 16) {
+    for (int k0 = kbeg; k0 < kend; k0 += 16) {
         // A fragment (16 x 16, row major): rows g and g+8, columns 2t, 2t+1 and 2t+8, 2t+9
         uint32_t ra[4];
         ra[0] = pack_bf16x2(ldA(m0 + g, k0 + 2 * t), ldA(m0 + g, k0 + 2 * t + 1));
@@ -107,6 +119,10 @@ __global__ void __launch_bounds__(GEMM_WARPS * 32) k_gemm(GemmArgs a) {
             const int row = m0 + g + (i >= 2 ? 8 : 0);
             const int col = n0 + 8 * j + 2 * t + (i & 1);
             if (row >= a.M || col >= a.N) continue;
+            if (gridDim.y > 1) {
+                a.part[((int64_t)blockIdx.y * a.M + row) * a.N + col] = acc[j][i];
+                continue;
+            }
             float v = acc[j][i] + (a.bias ? a.bias[col] : 0.f);
             const int64_t idx = (int64_t)row * a.ldc + col;
             if (a.Z) a.Z[idx] = v;
@@ -117,11 +133,45 @@ __global__ void __launch_bounds__(GEMM_WARPS * 32) k_gemm(GemmArgs a) {
     }
 }
 
-void gemm(const GemmArgs &a, cudaStream_t st) {
+int grid1(int64_t n, int threads) {
+    return (int)std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, 4096));
+}
+
+// sum of the split-K partials in chunk order, then the epilogue of k_gemm
+__global__ void k_gemm_reduce(GemmArgs a, int nsplit) {
+    const int64_t total = (int64_t)a.M * a.N;
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int row = (int)(e / a.N), col = (int)(e % a.N);
+        float v = 0.f;
+        for (int s = 0; s < nsplit; ++s) v += a.part[(int64_t)s * total + e];
+        v += a.bias ? a.bias[col] : 0.f;
+        const int64_t idx = (int64_t)row * a.ldc + col;
+        if (a.Z) a.Z[idx] = v;
+        if (a.mask && !(a.mask[idx] > 0.f)) v = 0.f;
+        if (a.relu) v = fmaxf(v, 0.f);
+        a.C[idx] = v;
+    }
+}
+
+void gemm(GemmArgs a, cudaStream_t st) {
     if (a.M <= 0 || a.N <= 0) return;
     const int64_t tiles = ((a.M + 15) / 16) * ((a.N + 8 * GEMM_NT - 1) / (8 * GEMM_NT));
+    const int64_t blocks = (tiles + GEMM_WARPS - 1) / GEMM_WARPS;
+    const int ksteps = (a.K + 15) / 16;
+    // chunks of at least 4 k steps, enough of them to fill the GPU
+    int nsplit = 1;
+    if (a.part && blocks < GEMM_TARGET_BLOCKS && ksteps >= 8)
+        nsplit = (int)std::min<int64_t>({GEMM_KSPLIT_MAX, (GEMM_TARGET_BLOCKS + blocks - 1) / blocks, ksteps / 4});
+    const int steps_per = (ksteps + nsplit - 1) / nsplit;
+    a.kchunk = 16 * std::max(steps_per, 1);
+    nsplit = std::max(1, (a.K + a.kchunk - 1) / a.kchunk);
     ++g_launches;
-    k_gemm<<<(unsigned)((tiles + GEMM_WARPS - 1) / GEMM_WARPS), GEMM_WARPS * 32, 0, st>>>(a);
+    k_gemm<<<dim3((unsigned)blocks, (unsigned)nsplit), GEMM_WARPS * 32, 0, st>>>(a);
+    if (nsplit > 1) {
+        ++g_launches;
+        k_gemm_reduce<<<grid1((int64_t)a.M * a.N, 256), 256, 0, st>>>(a, nsplit);
+    }
 }
 
 // ------------------------------------------------------------------ elementwise kernels
@@ -266,10 +316,6 @@ __global__ void __launch_bounds__(FEAT_THREADS) k_features(IndexView ix, const u
     }
 }
 
-int grid1(int64_t n, int threads) {
-    return (int)std::max<int64_t>(1, std::min<int64_t>((n + threads - 1) / threads, 4096));
-}
-
 uint64_t splitmix64(uint64_t &s) {
     uint64_t z = (s += 0x9E3779B97F4A7C15ull);
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
@@ -312,6 +358,7 @@ struct ae_mlp {
     int32_t cap = 0;
     float *x = nullptr, *z1 = nullptr, *a1 = nullptr, *z2 = nullptr, *a2 = nullptr, *y = nullptr, *dy = nullptr,
           *d1 = nullptr, *d2 = nullptr, *xb = nullptr, *tb = nullptr, *loss = nullptr;
+    float *part = nullptr;          // split-K partials of the weight gradients
     int32_t *perm = nullptr;
     int32_t perm_cap = 0, loss_cap = 0;
     float h_norm[NORM_SIZE];
@@ -326,7 +373,7 @@ struct ae_mlp {
     }
     ~ae_mlp() {
         free_acts();
-        for (float *b : {p, g, m, v, norm, loss})
+        for (float *b : {p, g, m, v, norm, loss, part})
             if (b) cudaFree(b);
         if (perm) cudaFree(perm);
     }
@@ -375,6 +422,7 @@ struct ae_mlp {
         // dW3 = dy^T a2
         a.A = dy, a.sam = 1, a.sak = NOUT, a.B = a2, a.sbk = NH, a.sbn = 1, a.C = g + OFF_W3, a.ldc = NH;
         a.M = NOUT, a.N = NH, a.K = rows;
+        a.part = part;
         gemm(a, st);
         colsum(dy, rows, NOUT, g + OFF_B3, st);
         // d2 = (dy W3) * [z2 > 0]
@@ -386,6 +434,7 @@ struct ae_mlp {
         a = GemmArgs{};
         a.A = d2, a.sam = 1, a.sak = NH, a.B = a1, a.sbk = NH, a.sbn = 1, a.C = g + OFF_W2, a.ldc = NH;
         a.M = NH, a.N = NH, a.K = rows;
+        a.part = part;
         gemm(a, st);
         colsum(d2, rows, NH, g + OFF_B2, st);
         // d1 = (d2 W2) * [z1 > 0]
@@ -397,6 +446,7 @@ struct ae_mlp {
         a = GemmArgs{};
         a.A = d1, a.sam = 1, a.sak = NH, a.B = x, a.sbk = NIN, a.sbn = 1, a.C = g + OFF_W1, a.ldc = NIN;
         a.M = NH, a.N = NIN, a.K = rows;
+        a.part = part;
         gemm(a, st);
         colsum(d1, rows, NH, g + OFF_B1, st);
     }
@@ -430,6 +480,8 @@ ae_status ae_mlp_create(uint64_t seed, ae_mlp **out) {
         for (float **b : {&mlp->p, &mlp->g, &mlp->m, &mlp->v})
             if (cudaMalloc(b, sizeof(float) * NPARAM) != cudaSuccess) throw mlp_error{AE_ENOMEM};
         if (cudaMalloc(&mlp->norm, sizeof(float) * NORM_SIZE) != cudaSuccess) throw mlp_error{AE_ENOMEM};
+        if (cudaMalloc(&mlp->part, sizeof(float) * GEMM_KSPLIT_MAX * NH * NH) != cudaSuccess)
+            throw mlp_error{AE_ENOMEM};
         std::vector<float> h(NPARAM, 0.f);
         uint64_t s = seed;
         auto fill = [&](int off, int rows, int cols) {

@@ -62,7 +62,7 @@ def _identity_norm(m):
     m.set_norm(np.zeros(66), np.ones(66), np.zeros(2), np.ones(2))
 
 
-@pytest.mark.parametrize("B", [1, 37, 300])
+@pytest.mark.parametrize("B", [1, 37, 300, 2053])
 def test_forward_and_gradients_match_oracle(B):
     p, X, T = _random_problem(B, seed=B)
     m = ae.Mlp(0)
