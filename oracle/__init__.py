@@ -22,6 +22,10 @@ Contents (each follows the passage it cites):
   to the same result set.
 * ``length_bound`` (Eq. 1), ``q_prefix`` (Eq. 2), ``entry_bound`` (Lemma 4 and
   Eq. 4) — closed forms of the paper, used as pins of the analysis.
+* ``suffix_array`` — the suffix array of Section 2.3 (suffixes of the codes
+  plus a smallest sentinel, in lexicographic order) as its definition: a
+  library sort of the start positions with a letter-by-letter comparator
+  (``sw_oracle.c``). This is what the index's device suffix array must match.
 
 * ``mlp_oracle`` (submodule) — the work predictor's features, network,
   gradients and Adam step in fp64, with optional bfloat16 rounding of matrix
@@ -71,6 +75,8 @@ def _load():
         lib.ae_oracle_sw_matrix.restype = ctypes.c_int
         lib.ae_oracle_sw_matrix.argtypes = [P, ctypes.c_int64, P, ctypes.c_int64, P, ctypes.c_int32,
                                             ctypes.c_int32, ctypes.c_int32, P]
+        lib.ae_oracle_suffix_array.restype = ctypes.c_int
+        lib.ae_oracle_suffix_array.argtypes = [P, ctypes.c_int64, P]
         _lib = lib
     return _lib
 
@@ -294,3 +300,18 @@ def entry_bound(sa, sb, sigma, q):
 def threshold_from_evalue(K, lam, m, n, E):
     """Section 7: H = ceil((ln(K m n) - ln E) / lambda)."""
     return int(math.ceil((math.log(K * m * n) - math.log(E)) / lam))
+
+
+# --------------------------------------------------------------------------- suffix array
+
+def suffix_array(codes):
+    """Start positions of the suffixes of ``codes`` (uint8 letter codes < 255)
+    followed by a sentinel smaller than every letter, in lexicographic order
+    of the suffixes (Section 2.3); n + 1 entries, the first is n."""
+    c = np.ascontiguousarray(np.asarray(codes, dtype=np.uint8))
+    if c.size and int(c.max()) >= 255:
+        raise ValueError("letter codes must be below 255")
+    sa = np.empty(c.size + 1, dtype=np.int32)
+    if _load().ae_oracle_suffix_array(c.ctypes.data, c.size, sa.ctypes.data) != 0:
+        raise MemoryError("oracle suffix array")
+    return sa

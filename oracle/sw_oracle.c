@@ -112,3 +112,36 @@ int ae_oracle_sw_matrix(const uint8_t *T, int64_t n, const uint8_t *P, int64_t m
     free(Vp); free(Vc); free(E);
     return 0;
 }
+
+/* Suffix array (Section 2.3): the start positions of the suffixes of
+ * codes[0..n) followed by a sentinel smaller than every letter, listed in
+ * lexicographic order of the suffixes.  Written as that definition: qsort of
+ * the n + 1 start positions with a comparator that compares two suffixes
+ * letter by letter (memcmp over the letters shifted up by one, the sentinel
+ * stored as 0).  The sentinel occurs once, so two different suffixes never
+ * compare equal.  codes are < 255.  Returns 0, or -1 when out of memory.
+ * Not reentrant (the comparator reads the text through file-level state). */
+static const uint8_t *sa_text;
+static int64_t sa_len;
+
+static int sa_compare(const void *x, const void *y) {
+    int64_t a = *(const int32_t *)x, b = *(const int32_t *)y;
+    /* the shorter suffix has sa_len - max(a, b) letters, its sentinel last */
+    int64_t len = sa_len - (a > b ? a : b);
+    int c = memcmp(sa_text + a, sa_text + b, (size_t)len);
+    if (c) return c;
+    return (a > b) - (a < b);   /* not reached: the sentinel differs */
+}
+
+int ae_oracle_suffix_array(const uint8_t *codes, int64_t n, int32_t *sa) {
+    uint8_t *s = (uint8_t *)malloc((size_t)n + 1);
+    if (!s) return -1;
+    for (int64_t i = 0; i < n; ++i) s[i] = (uint8_t)(codes[i] + 1);
+    s[n] = 0;
+    for (int64_t i = 0; i <= n; ++i) sa[i] = (int32_t)i;
+    sa_text = s;
+    sa_len = n + 1;
+    qsort(sa, (size_t)n + 1, sizeof(int32_t), sa_compare);
+    free(s);
+    return 0;
+}

@@ -235,3 +235,68 @@ def test_dna_scale_thresholds_reproduce():
     from workloads import DNA_SCALE_H
     lam, K, _ = evalue_fit.fit(300, 1000)
     assert evalue_fit.thresholds(lam, K) == DNA_SCALE_H
+
+
+# --------------------------------------------------------------------------- suffix array (Section 2.3)
+
+def test_oracle_suffix_array_paper_examples():
+    # Section 2.3: SA of GCTAGC$ is {7, 4, 6, 2, 5, 1, 3} (1-based starts)
+    t = oracle.encode(b"GCTAGC", DNA)
+    assert list(oracle.suffix_array(t) + 1) == [7, 4, 6, 2, 5, 1, 3]
+    # Section 5 (2): over T^-1 with positions kept the array reads {0, 4, 2, 6, 1, 5, 3}
+    sa = oracle.suffix_array(t[::-1].copy())
+    assert [t.size - k for k in sa] == [0, 4, 2, 6, 1, 5, 3]
+
+
+def _sa_by_list_sort(codes):
+    s = [int(c) for c in codes] + [-1]          # the sentinel below every letter
+    return sorted(range(len(s)), key=lambda k: s[k:])
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_oracle_suffix_array_bruteforce(seed):
+    rng = np.random.default_rng(100 + seed)
+    for sigma, n in [(4, 0), (4, 1), (4, 2), (2, 40), (4, 300), (20, 200)]:
+        codes = rng.integers(0, sigma, size=n).astype(np.uint8)
+        if seed % 2 and n > 7:
+            codes = np.tile(codes[: max(1, n // 9)], 10)[:n]
+        assert list(oracle.suffix_array(codes)) == _sa_by_list_sort(codes)
+
+
+def _bwt_inverse(codes, sa):
+    """Text read back from the BWT of `sa` by LF steps (the Burrows-Wheeler
+    inversion): right only if `sa` lists the suffixes in order."""
+    n = codes.size
+    bwt = np.where(sa > 0, codes[np.maximum(sa - 1, 0)].astype(np.int64), -1)
+    lf = np.empty(n + 1, dtype=np.int64)
+    lf[np.argsort(bwt, kind="stable")] = np.arange(n + 1)
+    out = np.empty(n, dtype=np.int64)
+    h = 0                                        # the row of the sentinel suffix
+    for k in range(n - 1, -1, -1):
+        out[k] = bwt[h]
+        h = lf[h]
+    return out
+
+
+@pytest.mark.parametrize("kind", ["iid", "period7", "one_letter", "protein"])
+def test_oracle_suffix_array_inverts_through_bwt(kind):
+    rng = np.random.default_rng(7)
+    n = 6000
+    if kind == "protein":
+        codes = rng.integers(0, 20, size=n).astype(np.uint8)
+    elif kind == "one_letter":
+        codes = np.zeros(n, dtype=np.uint8)
+    elif kind == "period7":
+        codes = np.tile(rng.integers(0, 4, size=7), n // 7 + 1)[:n].astype(np.uint8)
+    else:
+        codes = rng.integers(0, 4, size=n).astype(np.uint8)
+    sa = oracle.suffix_array(codes)
+    assert sa[0] == n and np.array_equal(np.sort(sa), np.arange(n + 1))
+    assert np.array_equal(_bwt_inverse(codes, sa), codes)
+    # and a misordered array fails the same check: swap two adjacent rows whose
+    # BWT letters differ (equal letters would leave the BWT string unchanged)
+    bwt = np.where(sa > 0, codes[np.maximum(sa - 1, 0)].astype(np.int64), -1)
+    p = int(np.flatnonzero(bwt[:-1] != bwt[1:])[-1])
+    bad = sa.copy()
+    bad[[p, p + 1]] = bad[[p + 1, p]]
+    assert not np.array_equal(_bwt_inverse(codes, bad), codes)
