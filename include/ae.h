@@ -143,7 +143,9 @@ void ae_options_default(ae_options *opt);
  * for protein) with sampled ranks, the text-end array (entry h = end position
  * in T of the substrings whose reverse prefixes suffix h), and the forward
  * text (Section 2.3 and Section 5 (1)-(3)).  The suffix array is built on the
- * host; the index is then copied once to the current CUDA device.
+ * current CUDA device (ae_suffix_array_device, about 33 bytes of device memory
+ * per letter while it runs).  The occurrence blocks are filled from it on the
+ * host, and the index is then copied once to the device.
  * Errors: AE_EINVAL (n < 1, unknown letter, bad alphabet), AE_EUNSUPPORTED
  * (n >= 2^31 - 1), AE_ENOMEM, AE_ECUDA. */
 ae_status ae_index_build(const uint8_t *text, int64_t n, int32_t alphabet, ae_index **out);
@@ -225,12 +227,33 @@ ae_status ae_workspace_release(ae_index *idx, void *stream);
 /* Counters of the calling thread's last search. */
 ae_status ae_last_stats(ae_stats *out);
 
-/* Host helpers used by the index build and the engine, exposed for tests. */
+/* Suffix arrays, exposed for tests and for callers that build their own
+ * indexes. */
 
 /* Suffix array of codes[0..n) followed by a sentinel smaller than every code
- * (so sa has n+1 entries and sa[0] = n).  codes are in [0, sigma).  Built with
- * induced sorting (SA-IS, Nong, Zhang & Chan 2009).  Host memory. */
+ * (so sa has n+1 entries and sa[0] = n).  codes are in [0, sigma).  Built on
+ * the host with induced sorting (SA-IS, Nong, Zhang & Chan 2009).  Host
+ * memory.  The index build uses the device version below. */
 ae_status ae_suffix_array(const uint8_t *codes, int64_t n, int32_t sigma, int32_t *sa);
+
+/* The same suffix array computed on the device, as ae_index_build does for
+ * the reversed text (Section 2.3; Section 5 (1)).  s = d_codes[0..n), or with
+ * reversed != 0 the codes read backwards (s[k] = d_codes[n-1-k]); d_sa[0..n]
+ * receives the start positions of the suffixes of s followed by a sentinel
+ * smaller than every code, in lexicographic order (d_sa[0] = n).
+ * Method: prefix doubling (Manber & Myers 1993).  Each suffix's first key
+ * packs its first 64/b letters (b bits per letter value and the sentinel),
+ * and a stable LSD radix sort groups equal keys.  The group index becomes the
+ * rank, and the next key (rank of i, rank of i + h) orders by twice as many
+ * letters.  Rounds stop when every rank is distinct.
+ * d_codes and d_sa are device memory: codes in [0, sigma), 1 <= sigma <= 255,
+ * 0 <= n < 2^31 - 2.  The call allocates and frees about 33 bytes of device
+ * memory per letter, and returns once `stream` (NULL = the legacy default
+ * stream) has finished its work.
+ * Errors: AE_EINVAL (NULL pointer, sigma out of range, a code >= sigma),
+ * AE_EUNSUPPORTED (n too large), AE_ENOMEM, AE_ECUDA. */
+ae_status ae_suffix_array_device(const uint8_t *d_codes, int64_t n, int32_t sigma, int32_t reversed, int32_t *d_sa,
+                                 void *stream);
 
 /* For a query of length m over `alphabet`: q of Eq. 2 (0 with a matrix), the
  * depth the trie walk starts at, and L_max of Eq. 1 (with the largest matrix

@@ -95,6 +95,7 @@ def _load():
         "ae_workspace_release": (I32, [V, V]),
         "ae_last_stats": (I32, [V]),
         "ae_suffix_array": (I32, [V, I64, I32, V]),
+        "ae_suffix_array_device": (I32, [V, I64, I32, I32, V, V]),
         "ae_plan": (I32, [I64, I32, V, I32, V, V, V]),
     }
     for name, (res, args) in sig.items():
@@ -327,6 +328,13 @@ def ae_suffix_array(codes, sigma):
     _check(lib.ae_suffix_array(c.ctypes.data if c.size else None, c.size, int(sigma), sa.ctypes.data),
            "ae_suffix_array")
     return sa
+
+
+def ae_suffix_array_device(d_codes_ptr, n, sigma, d_sa_ptr, reversed=False, stream=None):
+    """Device suffix array: d_sa (n + 1 int32) of the n codes at d_codes
+    (read backwards with `reversed`) plus the sentinel."""
+    _check(lib.ae_suffix_array_device(d_codes_ptr or None, int(n), int(sigma), int(bool(reversed)), d_sa_ptr,
+                                      _stream_handle(stream)), "ae_suffix_array_device")
 
 
 def ae_plan(m, scheme, H, alphabet=AE_DNA):

@@ -1075,6 +1075,49 @@ ae_status search_core(const ae_index *idx, Workspace *w, const int64_t *offsets,
 
 // ------------------------------------------------------------------ C ABI
 
+namespace {
+
+// Section 5 (1)-(2): the suffix array of the reversed text on the device
+// (prefix doubling), the occurrence blocks and text-end array filled from it
+// on the host, then the upload.
+ae_status build_index(ae_index *idx, const uint8_t *codes, int64_t n, int32_t alphabet) {
+    const int64_t N = n + 1;
+    std::vector<int32_t> sa;
+    try {
+        sa.resize((size_t)N);
+    } catch (...) {
+        return AE_ENOMEM;
+    }
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        return AE_ECUDA;
+    }
+    uint8_t *d_codes = nullptr;
+    int32_t *d_sa = nullptr;
+    ae_status res = AE_OK;
+    if (cudaMalloc(&d_codes, (size_t)n) != cudaSuccess || cudaMalloc(&d_sa, sizeof(int32_t) * (size_t)N) != cudaSuccess) {
+        cudaGetLastError();
+        res = AE_ENOMEM;
+    }
+    if (res == AE_OK && cudaMemcpyAsync(d_codes, codes, (size_t)n, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        res = AE_ECUDA;
+    if (res == AE_OK) res = ae_sa_doubling(d_codes, n, ae_alphabet_sigma(alphabet), 1, d_sa, nullptr, st);
+    if (res == AE_OK && (cudaMemcpyAsync(sa.data(), d_sa, sizeof(int32_t) * (size_t)N, cudaMemcpyDeviceToHost, st) !=
+                             cudaSuccess ||
+                         cudaStreamSynchronize(st) != cudaSuccess))
+        res = AE_ECUDA;
+    cudaStreamSynchronize(st);
+    if (d_codes) cudaFree(d_codes);
+    if (d_sa) cudaFree(d_sa);
+    cudaStreamDestroy(st);
+    if (res == AE_OK) res = ae_host_index_fill(codes, n, alphabet, sa.data(), &idx->host);
+    if (res == AE_OK) res = upload_index(idx);
+    return res;
+}
+
+}  // namespace
+
 extern "C" {
 
 void ae_options_default(ae_options *opt) {
@@ -1106,6 +1149,13 @@ const char *ae_strerror(int32_t status) {
     }
 }
 
+ae_status ae_suffix_array_device(const uint8_t *d_codes, int64_t n, int32_t sigma, int32_t reversed, int32_t *d_sa,
+                                 void *stream) {
+    if (n < 0 || sigma < 1 || sigma > 255 || (n > 0 && !d_codes) || !d_sa) return AE_EINVAL;
+    if (n + 1 >= INT32_MAX) return AE_EUNSUPPORTED;
+    return ae_sa_doubling(d_codes, n, sigma, reversed != 0, d_sa, nullptr, (cudaStream_t)stream);
+}
+
 ae_status ae_index_build(const uint8_t *text, int64_t n, int32_t alphabet, ae_index **out) {
     if (!out) return AE_EINVAL;
     *out = nullptr;
@@ -1120,8 +1170,7 @@ ae_status ae_index_build(const uint8_t *text, int64_t n, int32_t alphabet, ae_in
     if (ae_encode_letters(text, n, alphabet, codes.data()) != 0) return AE_EINVAL;
     ae_index *idx = new (std::nothrow) ae_index();
     if (!idx) return AE_ENOMEM;
-    ae_status st = ae_host_index_build(codes.data(), n, alphabet, &idx->host);
-    if (st == AE_OK) st = upload_index(idx);
+    ae_status st = build_index(idx, codes.data(), n, alphabet);
     if (st != AE_OK) {
         delete idx;
         return st;

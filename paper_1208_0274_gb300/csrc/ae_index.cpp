@@ -1,6 +1,7 @@
-// Host side of the FM index (Section 2.3 and Section 5): letter coding, the
-// suffix array of the reversed text by induced sorting, the BWT packed into
-// occurrence blocks, and the index file format.
+// Host side of the FM index (Section 2.3 and Section 5): letter coding, a host
+// suffix array by induced sorting (exported; the index build takes its suffix
+// array from the device), the BWT packed into occurrence blocks from a suffix
+// array of the reversed text, and the index file format.
 #include <stdint.h>
 #include <stdio.h>
 #include <stdlib.h>
@@ -164,19 +165,17 @@ extern "C" ae_status ae_suffix_array(const uint8_t *codes, int64_t n, int32_t si
 
 // ------------------------------------------------------------------ index build
 
-ae_status ae_host_index_build(const uint8_t *codes, int64_t n, int32_t alphabet, HostIndex *out) {
+// The index of the text codes[0..n) from the suffix array `sa` (n + 1
+// entries) of the reversed text followed by the sentinel (Section 5 (1)):
+// position k < n of the reversed text holds T[n-1-k], so its suffix starting
+// at k is the reverse of T[0..n-1-k], and the BWT letter of row h is the
+// reversed text's letter before sa[h], T[n - sa[h]].
+ae_status ae_host_index_fill(const uint8_t *codes, int64_t n, int32_t alphabet, const int32_t *sa, HostIndex *out) {
     memset(out, 0, sizeof(*out));
     int sigma = ae_alphabet_sigma(alphabet);
-    if (!sigma || n < 1) return AE_EINVAL;
+    if (!sigma || n < 1 || !sa) return AE_EINVAL;
     if (n + 1 >= INT32_MAX) return AE_EUNSUPPORTED;
     const int64_t N = n + 1;
-    // reversed text followed by the sentinel (Section 5 (1)): row k < n holds
-    // T[n-1-k], so a suffix of it starting at k is the reverse of T[0..n-1-k].
-    std::vector<uint8_t> rev(n);
-    for (int64_t k = 0; k < n; ++k) rev[k] = codes[n - 1 - k];
-    std::vector<int32_t> sa(N);
-    ae_status st = ae_suffix_array(rev.data(), n, sigma, sa.data());
-    if (st != AE_OK) return st;
 
     out->alphabet = alphabet;
     out->sigma = sigma;
@@ -202,13 +201,17 @@ ae_status ae_host_index_build(const uint8_t *codes, int64_t n, int32_t alphabet,
     out->dollar_row = -1;
     for (int64_t h = 0; h < N; ++h) {
         int64_t k = sa[h];
+        if (k < 0 || k > n) {
+            ae_host_index_free(out);
+            return AE_EINVAL;
+        }
         out->tend[h] = k < n ? (int32_t)(n - 1 - k) : -1;
         int code;
         if (k == 0) {
             out->dollar_row = h;
             code = 0;
         } else {
-            code = rev[k - 1];
+            code = codes[n - k];
         }
         int64_t b = h / AE_ROWS_PER_BLOCK, r = h % AE_ROWS_PER_BLOCK;
         uint32_t *blk = out->occ + b * out->block_words;

@@ -123,7 +123,7 @@ struct HostIndex {
 int ae_alphabet_sigma(int32_t alphabet);
 int ae_encode_letters(const uint8_t *ascii, int64_t n, int32_t alphabet, uint8_t *codes);
 void ae_letter_lut(int32_t alphabet, uint8_t lut[256]);
-ae_status ae_host_index_build(const uint8_t *codes, int64_t n, int32_t alphabet, HostIndex *out);
+ae_status ae_host_index_fill(const uint8_t *codes, int64_t n, int32_t alphabet, const int32_t *sa, HostIndex *out);
 void ae_host_index_free(HostIndex *h);
 ae_status ae_host_index_save(const HostIndex *h, const char *path);
 ae_status ae_host_index_load(const char *path, HostIndex *h);

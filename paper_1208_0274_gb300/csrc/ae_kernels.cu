@@ -25,6 +25,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <utility>
+
 #include "ae_device.cuh"
 #include "ae_kernels.h"
 
@@ -1228,4 +1231,168 @@ void ae_unique_write(const uint64_t *key, const int32_t *score, int64_t N, const
     if (N <= 0) return;
     ++g_launches;
     k_unique_write<<<grid_for(N, 256), 256, 0, st>>>(key, score, N, flag_off, be, bj, out, qcount);
+}
+
+// ------------------------------------------------------------------ suffix array by prefix doubling
+//
+// The suffix array of Section 2.3 (Section 5 (1) builds it over the reversed
+// text), computed on the device by prefix doubling (Manber & Myers, 1993):
+// every suffix gets a key that orders it by its first h letters, a stable
+// radix sort groups equal keys, the group index becomes the suffix's rank,
+// and the next key is the pair (rank of the suffix, rank of the suffix h
+// letters on), which orders by the first 2h letters.  Rounds stop when every
+// rank is distinct.  The first key packs the first 64 / b letters directly
+// (b bits per letter value, the sentinel 0 included), so an i.i.d. text of
+// 10^8 letters needs one pair round.
+
+namespace {
+
+// s[k] = letter + 1 of the text (read backwards with `reversed`), s[n] = 0
+__global__ void k_sa_letters(const uint8_t *codes, int64_t n, int reversed, int sigma, uint8_t *s, int *bad) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k <= n; k += (int64_t)gridDim.x * blockDim.x) {
+        uint8_t v = 0;
+        if (k < n) {
+            const uint8_t c = codes[reversed ? n - 1 - k : k];
+            if (c >= sigma) *bad = 1;
+            v = (uint8_t)(c + 1);
+        }
+        s[k] = v;
+    }
+}
+
+// key of suffix i: its first L letter values, b bits each, first letter highest;
+// positions past the sentinel read 0 (the sentinel is unique, so this never ties
+// two different suffixes)
+__global__ void k_sa_first_keys(const uint8_t *s, int64_t N, int b, int L, uint64_t *keys, uint32_t *vals) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t key = 0;
+        for (int t = 0; t < L; ++t) {
+            const int64_t x = i + t;
+            key = (key << b) | (uint64_t)(x < N ? s[x] : 0);
+        }
+        keys[i] = key;
+        vals[i] = (uint32_t)i;
+    }
+}
+
+// 1 where a sorted key starts a new group
+__global__ void k_sa_heads(const uint64_t *keys, int64_t N, uint32_t *head) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x)
+        head[p] = (p == 0 || keys[p] != keys[p - 1]) ? 1u : 0u;
+}
+
+// rank of suffix vals[p] = index of its group (inclusive count of heads - 1)
+__global__ void k_sa_rank(const uint32_t *vals, const uint32_t *head, const uint64_t *excl, int64_t N,
+                          uint32_t *rank, int *bad) {
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < N; p += (int64_t)gridDim.x * blockDim.x) {
+        const uint32_t i = vals[p];
+        if ((int64_t)i >= N) {
+            *bad = 2;
+            continue;
+        }
+        rank[i] = (uint32_t)(excl[p] + head[p] - 1);
+    }
+}
+
+// key of suffix i for the 2h-letter order: (rank of i, rank of i + h plus one);
+// a suffix shorter than h + 1 letters holds the sentinel in its first h letters,
+// so its rank is already unique and its second component is 0
+__global__ void k_sa_pair_keys(const uint32_t *rank, int64_t N, int64_t h, int rb, uint64_t *keys, uint32_t *vals) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < N; i += (int64_t)gridDim.x * blockDim.x) {
+        const uint64_t second = (i + h < N) ? (uint64_t)rank[i + h] + 1u : 0u;
+        keys[i] = ((uint64_t)rank[i] << rb) | second;
+        vals[i] = (uint32_t)i;
+    }
+}
+
+int sa_bits_for(uint64_t maxval) {  // bits to hold values in [0, maxval]
+    int b = 1;
+    while (b < 64 && (maxval >> b) != 0) ++b;
+    return b;
+}
+
+}  // namespace
+
+ae_status ae_sa_doubling(const uint8_t *d_codes, int64_t n, int sigma, int reversed, int32_t *d_sa, int *rounds,
+                         cudaStream_t st) {
+    const int64_t N = n + 1;
+    if (rounds) *rounds = 0;
+    const int b = sa_bits_for((uint64_t)sigma), L = 64 / b;
+    uint8_t *s = nullptr;
+    uint64_t *k0 = nullptr, *k1 = nullptr, *tmp = nullptr, *total = nullptr;
+    uint32_t *v0 = nullptr, *v1 = nullptr, *rank = nullptr;
+    int *bad = nullptr;
+    const int64_t tmp_words = std::max(ae_sort_tmp_words(N), ae_scan_tmp_words(N, 1));
+    ae_status res = AE_OK;
+    if (cudaMalloc(&s, (size_t)N) != cudaSuccess || cudaMalloc(&k0, sizeof(uint64_t) * N) != cudaSuccess ||
+        cudaMalloc(&k1, sizeof(uint64_t) * N) != cudaSuccess || cudaMalloc(&v0, sizeof(uint32_t) * N) != cudaSuccess ||
+        cudaMalloc(&v1, sizeof(uint32_t) * N) != cudaSuccess ||
+        cudaMalloc(&rank, sizeof(uint32_t) * N) != cudaSuccess ||
+        cudaMalloc(&tmp, sizeof(uint64_t) * tmp_words) != cudaSuccess ||
+        cudaMalloc(&total, sizeof(uint64_t)) != cudaSuccess || cudaMalloc(&bad, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        res = AE_ENOMEM;
+    }
+    int h_bad = 0;
+    uint64_t G = 0;
+    if (res == AE_OK && cudaMemsetAsync(bad, 0, sizeof(int), st) != cudaSuccess) res = AE_ECUDA;
+    if (res == AE_OK) {
+        g_launches += 2;
+        k_sa_letters<<<grid_for(N, 256), 256, 0, st>>>(d_codes, n, reversed, sigma, s, bad);
+        k_sa_first_keys<<<grid_for(N, 256), 256, 0, st>>>(s, N, b, L, k0, v0);
+        if (cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            res = AE_ECUDA;
+        else if (h_bad)
+            res = AE_EINVAL;
+    }
+    // (kr, vr): the sorted pairs; (kf, vf): the free pair
+    uint64_t *kr = k0, *kf = k1;
+    uint32_t *vr = v0, *vf = v1;
+    int bits = b * L;
+    int64_t h = L;
+    while (res == AE_OK) {
+        if (ae_radix_sort(kr, vr, kf, vf, N, bits, tmp, st)) {
+            std::swap(kr, kf);
+            std::swap(vr, vf);
+        }
+        if (rounds) ++*rounds;
+        g_launches += 2;
+        k_sa_heads<<<grid_for(N, 256), 256, 0, st>>>(kr, N, vf);
+        const uint32_t *in[1] = {vf};
+        uint64_t *out[1] = {kf};
+        ae_scan_u32(in, out, 1, N, total, tmp, st);
+        k_sa_rank<<<grid_for(N, 256), 256, 0, st>>>(vr, vf, kf, N, rank, bad);
+        if (cudaMemcpyAsync(&G, total, sizeof(uint64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess) {
+            res = AE_ECUDA;
+            break;
+        }
+        if (h_bad || G < 1 || (int64_t)G > N) {
+            res = AE_ECUDA;   // not a permutation: an internal error
+            break;
+        }
+        if ((int64_t)G == N) break;
+        if (h >= N) {         // every rank is distinct once h reaches N
+            res = AE_ECUDA;
+            break;
+        }
+        const int rb = sa_bits_for(G);
+        bits = rb + sa_bits_for(G - 1);
+        ++g_launches;
+        k_sa_pair_keys<<<grid_for(N, 256), 256, 0, st>>>(rank, N, h, rb, kf, vf);
+        std::swap(kr, kf);
+        std::swap(vr, vf);
+        h *= 2;
+    }
+    if (res == AE_OK &&
+        (cudaMemcpyAsync(d_sa, vr, sizeof(int32_t) * N, cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+         cudaStreamSynchronize(st) != cudaSuccess))
+        res = AE_ECUDA;
+    if (res != AE_OK) cudaStreamSynchronize(st);
+    for (void *p : {(void *)s, (void *)k0, (void *)k1, (void *)v0, (void *)v1, (void *)rank, (void *)tmp,
+                    (void *)total, (void *)bad})
+        if (p) cudaFree(p);
+    return res;
 }

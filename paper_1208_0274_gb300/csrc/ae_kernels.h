@@ -23,6 +23,14 @@ int64_t ae_sort_tmp_words(int64_t N);
 int ae_radix_sort(uint64_t *k0, uint32_t *v0, uint64_t *k1, uint32_t *v1, int64_t N, int bits,
                   uint64_t *tmp, cudaStream_t st);
 
+// Suffix array of the n codes at d_codes (read backwards with `reversed`)
+// followed by a unique smallest sentinel, into d_sa[0..n] (device), by prefix
+// doubling; *rounds receives the number of radix sorts.  Allocates and frees
+// its work buffers; returns after `st` has finished.  AE_EINVAL on a code >=
+// sigma, AE_ENOMEM, AE_ECUDA.
+ae_status ae_sa_doubling(const uint8_t *d_codes, int64_t n, int sigma, int reversed, int32_t *d_sa, int *rounds,
+                         cudaStream_t st);
+
 // Query letters -> codes; sets *bad (device int) on an unknown letter.
 void ae_encode_queries(const uint8_t *ascii, uint8_t *codes, int64_t total, int alphabet, int *bad,
                        cudaStream_t st);
