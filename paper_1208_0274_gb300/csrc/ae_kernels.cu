@@ -1340,7 +1340,8 @@ ae_status ae_sa_doubling(const uint8_t *d_codes, int64_t n, int sigma, int rever
         g_launches += 2;
         k_sa_letters<<<grid_for(N, 256), 256, 0, st>>>(d_codes, n, reversed, sigma, s, bad);
         k_sa_first_keys<<<grid_for(N, 256), 256, 0, st>>>(s, N, b, L, k0, v0);
-        if (cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess)
             res = AE_ECUDA;
         else if (h_bad)
@@ -1363,7 +1364,8 @@ ae_status ae_sa_doubling(const uint8_t *d_codes, int64_t n, int sigma, int rever
         uint64_t *out[1] = {kf};
         ae_scan_u32(in, out, 1, N, total, tmp, st);
         k_sa_rank<<<grid_for(N, 256), 256, 0, st>>>(vr, vf, kf, N, rank, bad);
-        if (cudaMemcpyAsync(&G, total, sizeof(uint64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(&G, total, sizeof(uint64_t), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaMemcpyAsync(&h_bad, bad, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
             cudaStreamSynchronize(st) != cudaSuccess) {
             res = AE_ECUDA;
