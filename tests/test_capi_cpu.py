@@ -93,3 +93,17 @@ def test_argument_errors_without_device():
 def test_options_default():
     o = ae.ae_options_default()
     assert o.qprefix_seed == 1 and o.leaf_segment >= 0 and o.item_columns > 0
+
+
+@pytest.mark.parametrize("kind", ["iid", "period5", "blocks", "protein"])
+def test_host_suffix_array_matches_oracle_at_size(kind):
+    import oracle
+    rng = np.random.default_rng(31)
+    sigma = 20 if kind == "protein" else 4
+    if kind == "period5":
+        codes = np.tile(rng.integers(0, 4, 5), 20_000).astype(np.uint8)
+    elif kind == "blocks":
+        codes = np.tile(rng.integers(0, 4, 3_001), 30).astype(np.uint8)
+    else:
+        codes = rng.integers(0, sigma, 200_003).astype(np.uint8)
+    assert np.array_equal(ae.ae_suffix_array(codes, sigma), oracle.suffix_array(codes))
