@@ -107,3 +107,12 @@ def test_host_suffix_array_matches_oracle_at_size(kind):
     else:
         codes = rng.integers(0, sigma, 200_003).astype(np.uint8)
     assert np.array_equal(ae.ae_suffix_array(codes, sigma), oracle.suffix_array(codes))
+
+
+def test_device_suffix_array_argument_errors_without_device():
+    # rejected before any device work: bad sigma, missing pointers, too long
+    for args, want in [((1, 10, 0, 0, 1), ae.AE_EINVAL), ((1, 10, 4, 0, 0), ae.AE_EINVAL),
+                       ((0, 10, 4, 0, 1), ae.AE_EINVAL), ((1, -1, 4, 0, 1), ae.AE_EINVAL),
+                       ((1, 10, 256, 0, 1), ae.AE_EINVAL), ((1, 1 << 31, 4, 0, 1), ae.AE_EUNSUPPORTED)]:
+        d_codes, n, sigma, rev, d_sa = args
+        assert ae.lib.ae_suffix_array_device(d_codes or None, n, sigma, rev, d_sa or None, None) == want
