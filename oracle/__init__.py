@@ -10,6 +10,11 @@ Contents (each follows the passage it cites):
   Smith-Waterman of ``sw_oracle.c``: the local-alignment problem of Section
   2.1 (largest similarity of T[x..i] and P[y..j] for every end pair, results
   >= H as in Algorithm 1 line 11). This is the oracle the GPU hits must match.
+* ``sw_hits_mt`` — the same recurrence on every host core: query column
+  stripes computed as a wavefront over blocks of text rows, only the edge
+  column's V and F crossing between stripes. Pinned bit for bit against
+  ``sw_hits`` (``tests/test_oracle_mt.py``); it times the CPU baseline and
+  speeds up the large parity windows.
 * ``sim_bruteforce`` / ``local_bruteforce`` — the similarity of Section 2.1
   taken literally: every global alignment of two strings is enumerated and
   scored (no dynamic programming), then maximised over all start pairs. Used
@@ -32,7 +37,7 @@ Contents (each follows the passage it cites):
   operands; pinned in ``tests/test_mlp_oracle.py``.
 
 Every function of this file is parity-pinned by tests in
-``tests/test_oracle_pins.py``.
+``tests/test_oracle_pins.py`` (``sw_hits_mt`` in ``tests/test_oracle_mt.py``).
 """
 from __future__ import annotations
 
@@ -57,7 +62,7 @@ def build(force=False):
             and os.path.getmtime(_LIBPATH) >= os.path.getmtime(src)):
         return _LIBPATH
     tmp = _LIBPATH + f".{os.getpid()}.tmp"
-    subprocess.check_call(["gcc", "-O2", "-std=c99", "-shared", "-fPIC", src, "-o", tmp])
+    subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread", src, "-o", tmp])
     os.replace(tmp, _LIBPATH)
     return _LIBPATH
 
@@ -72,6 +77,10 @@ def _load():
         lib.ae_oracle_sw_hits.argtypes = [P, ctypes.c_int64, P, ctypes.c_int64, P, ctypes.c_int32,
                                           ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                           ctypes.c_int64, P, P, P, ctypes.c_int64]
+        lib.ae_oracle_sw_hits_mt.restype = ctypes.c_int64
+        lib.ae_oracle_sw_hits_mt.argtypes = [P, ctypes.c_int64, P, ctypes.c_int64, P, ctypes.c_int32,
+                                             ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                             ctypes.c_int64, ctypes.c_int32, P, P, P, ctypes.c_int64]
         lib.ae_oracle_sw_matrix.restype = ctypes.c_int
         lib.ae_oracle_sw_matrix.argtypes = [P, ctypes.c_int64, P, ctypes.c_int64, P, ctypes.c_int32,
                                             ctypes.c_int32, ctypes.c_int32, P]
@@ -129,6 +138,40 @@ def sw_hits(text, query, scheme, H, alphabet=b"ACGT", row_lo=0):
                                     int(scheme.gap_open), int(scheme.gap_extend), int(H),
                                     int(row_lo), oi.ctypes.data, oj.ctypes.data,
                                     os_.ctypes.data, cap)
+        if cnt < 0:
+            raise RuntimeError("oracle failed")
+        if cnt <= cap:
+            return oi[:cnt], oj[:cnt], os_[:cnt]
+        cap = int(cnt)
+
+
+def host_threads():
+    """Host cores this process may run on."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except (AttributeError, OSError):
+        return os.cpu_count() or 1
+
+
+def sw_hits_mt(text, query, scheme, H, alphabet=b"ACGT", row_lo=0, threads=None):
+    """sw_hits on `threads` host threads (default: every core this process
+    may use): the same recurrence over column stripes in a wavefront, with the
+    same results in the same order."""
+    lib = _load()
+    T = np.ascontiguousarray(encode(text, alphabet))
+    P = np.ascontiguousarray(encode(query, alphabet))
+    sub = subst_table(scheme, len(alphabet))
+    nt = int(threads or host_threads())
+    cap = max(1024, 4 * (T.size + P.size))
+    while True:
+        oi = np.empty(cap, dtype=np.int64)
+        oj = np.empty(cap, dtype=np.int32)
+        os_ = np.empty(cap, dtype=np.int32)
+        cnt = lib.ae_oracle_sw_hits_mt(T.ctypes.data, T.size, P.ctypes.data, P.size,
+                                       sub.ctypes.data, len(alphabet),
+                                       int(scheme.gap_open), int(scheme.gap_extend), int(H),
+                                       int(row_lo), nt, oi.ctypes.data, oj.ctypes.data,
+                                       os_.ctypes.data, cap)
         if cnt < 0:
             raise RuntimeError("oracle failed")
         if cnt <= cap:

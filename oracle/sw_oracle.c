@@ -24,7 +24,8 @@
  * never meets H >= 1).  delta(a,b) is looked up in a sigma x sigma table
  * (s_a on the diagonal and s_b elsewhere for the paper's schemes).
  *
- * Arithmetic is int64, rows are kept two at a time, one thread.
+ * Arithmetic is int64, rows are kept two at a time; ae_oracle_sw_hits runs
+ * on one thread, ae_oracle_sw_hits_mt (end of file) on several.
  */
 #include <stdint.h>
 #include <stdlib.h>
@@ -144,4 +145,210 @@ int ae_oracle_suffix_array(const uint8_t *codes, int64_t n, int32_t *sa) {
     qsort(sa, (size_t)n + 1, sizeof(int32_t), sa_compare);
     free(s);
     return 0;
+}
+
+/* ---------------------------------------------------------------- all cores
+ *
+ * ae_oracle_sw_hits_mt: exactly the values of ae_oracle_sw_hits (the same
+ * recurrence, int64), spread over `threads` host threads.  The query columns
+ * are cut into one stripe per thread; thread t computes its stripe a block of
+ * OR_ROWS text rows at a time, after thread t-1 has finished the same rows of
+ * the stripe to its left (a wavefront over (row block, stripe) tiles).  The
+ * only values that cross a stripe edge are V and F of the edge column for
+ * each row, handed over through a small ring of row blocks.  Hits are kept
+ * per thread and merged into the row-major order of ae_oracle_sw_hits.
+ */
+#include <pthread.h>
+#include <sched.h>
+#include <stdatomic.h>
+
+#define OR_ROWS 256
+#define OR_RING 8
+
+typedef struct {
+    /* shared problem */
+    const uint8_t *T, *P;
+    int64_t n, m;
+    const int32_t *subst;
+    int32_t sigma, gap_extend, H;
+    int64_t open_ext, row_lo;
+    int nthreads;
+    /* per thread */
+    int64_t *c0;                  /* stripe t = columns [c0[t], c0[t+1]) (1-based j in (c0, c1]) */
+    atomic_llong *done;           /* rows finished by thread t */
+    int64_t *edgeV, *edgeF;       /* ring: thread t's right-edge V and F, [t][slot][row in block] */
+    int64_t **hi; int32_t **hj, **hs;
+    int64_t *hcount, *hcap;
+    int *fail;
+    atomic_int abort_all;         /* set when not every thread could be started */
+} or_job;
+
+typedef struct { or_job *job; int t; } or_arg;
+
+static void or_wait(or_job *J, atomic_llong *x, int64_t want) {
+    while (atomic_load_explicit(x, memory_order_acquire) < want) {
+        if (atomic_load_explicit(&J->abort_all, memory_order_relaxed)) return;
+        sched_yield();
+    }
+}
+
+static int or_push(or_job *J, int t, int64_t i, int32_t j, int32_t s) {
+    if (J->hcount[t] == J->hcap[t]) {
+        int64_t nc = J->hcap[t] ? 2 * J->hcap[t] : 4096;
+        int64_t *a = (int64_t *)realloc(J->hi[t], sizeof(int64_t) * (size_t)nc);
+        if (!a) return -1;
+        J->hi[t] = a;
+        int32_t *b = (int32_t *)realloc(J->hj[t], sizeof(int32_t) * (size_t)nc);
+        if (!b) return -1;
+        J->hj[t] = b;
+        int32_t *c = (int32_t *)realloc(J->hs[t], sizeof(int32_t) * (size_t)nc);
+        if (!c) return -1;
+        J->hs[t] = c;
+        J->hcap[t] = nc;
+    }
+    J->hi[t][J->hcount[t]] = i;
+    J->hj[t][J->hcount[t]] = j;
+    J->hs[t][J->hcount[t]] = s;
+    J->hcount[t]++;
+    return 0;
+}
+
+static void *or_worker(void *p) {
+    or_arg *A = (or_arg *)p;
+    or_job *J = A->job;
+    const int t = A->t;
+    const int64_t a = J->c0[t], b = J->c0[t + 1], w = b - a;   /* columns a+1 .. b */
+    int64_t *Vp = (int64_t *)malloc(sizeof(int64_t) * (size_t)(w + 1));
+    int64_t *Vc = (int64_t *)malloc(sizeof(int64_t) * (size_t)(w + 1));
+    int64_t *E = (int64_t *)malloc(sizeof(int64_t) * (size_t)(w + 1));
+    int bad = !Vp || !Vc || !E;
+    if (!bad) for (int64_t k = 0; k <= w; ++k) { Vp[k] = 0; E[k] = ORACLE_NEG; }
+    int64_t left_prev = 0;   /* V(i-1, a): the left neighbour's edge value of the previous row */
+    for (int64_t r0 = 0; r0 < J->n; r0 += OR_ROWS) {
+        const int64_t r1 = r0 + OR_ROWS < J->n ? r0 + OR_ROWS : J->n;
+        const int64_t blk = r0 / OR_ROWS, slot = blk % OR_RING;
+        if (t > 0) or_wait(J, &J->done[t - 1], r1);                 /* left stripe has these rows */
+        if (t + 1 < J->nthreads && blk >= OR_RING)                  /* right stripe consumed the slot */
+            or_wait(J, &J->done[t + 1], (blk - OR_RING + 1) * OR_ROWS);
+        if (atomic_load_explicit(&J->abort_all, memory_order_relaxed)) break;
+        const int64_t *lV = t > 0 ? J->edgeV + ((int64_t)(t - 1) * OR_RING + slot) * OR_ROWS : NULL;
+        const int64_t *lF = t > 0 ? J->edgeF + ((int64_t)(t - 1) * OR_RING + slot) * OR_ROWS : NULL;
+        int64_t *oV = J->edgeV + ((int64_t)t * OR_RING + slot) * OR_ROWS;
+        int64_t *oF = J->edgeF + ((int64_t)t * OR_RING + slot) * OR_ROWS;
+        const int64_t ge = J->gap_extend, oe = J->open_ext, H = J->H, row_lo = J->row_lo;
+        const uint8_t *Pa = J->P + a;
+        for (int64_t i = r0 + 1; i <= r1 && !bad; ++i) {
+            const int32_t *row = J->subst + (int64_t)J->T[i - 1] * J->sigma;
+            /* column a of row i (0 at the matrix edge) and its F */
+            int64_t F = t > 0 ? lF[i - 1 - r0] : ORACLE_NEG;
+            Vc[0] = t > 0 ? lV[i - 1 - r0] : 0;
+            Vp[0] = left_prev;
+            for (int64_t k = 1; k <= w; ++k) {
+                E[k] = max2(E[k] + ge, Vp[k] + oe);
+                F = max2(F + ge, Vc[k - 1] + oe);
+                int64_t v = Vp[k - 1] + row[Pa[k - 1]];
+                v = max2(v, E[k]);
+                v = max2(v, F);
+                v = max2(v, 0);
+                Vc[k] = v;
+                if (v >= H && i - 1 >= row_lo && or_push(J, t, i - 1, (int32_t)(a + k - 1), (int32_t)v)) {
+                    bad = 1;
+                    break;
+                }
+            }
+            oV[i - 1 - r0] = Vc[w];
+            oF[i - 1 - r0] = F;
+            left_prev = Vc[0];
+            int64_t *tmp = Vp; Vp = Vc; Vc = tmp;
+        }
+        if (bad) { *J->fail = 1; }
+        atomic_store_explicit(&J->done[t], r1, memory_order_release);
+    }
+    free(Vp); free(Vc); free(E);
+    return NULL;
+}
+
+/* As ae_oracle_sw_hits, on `threads` host threads (threads <= 0: 1).  Same
+ * arguments, same results in the same order, same return convention. */
+int64_t ae_oracle_sw_hits_mt(const uint8_t *T, int64_t n, const uint8_t *P, int64_t m,
+                             const int32_t *subst, int32_t sigma,
+                             int32_t gap_open, int32_t gap_extend, int32_t H,
+                             int64_t row_lo, int32_t threads,
+                             int64_t *out_i, int32_t *out_j, int32_t *out_s, int64_t cap)
+{
+    if (n < 0 || m < 0 || sigma <= 0 || !subst) return -1;
+    if (n == 0 || m == 0) return 0;
+    int nt = threads < 1 ? 1 : threads;
+    if (nt > 256) nt = 256;
+    if ((int64_t)nt > m) nt = (int)m;
+    or_job J;
+    memset(&J, 0, sizeof(J));
+    J.T = T; J.P = P; J.n = n; J.m = m; J.subst = subst; J.sigma = sigma;
+    J.gap_extend = gap_extend; J.H = H; J.open_ext = (int64_t)gap_open + gap_extend; J.row_lo = row_lo;
+    J.nthreads = nt;
+    int fail = 0;
+    J.fail = &fail;
+    J.c0 = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nt + 1));
+    J.done = (atomic_llong *)malloc(sizeof(atomic_llong) * (size_t)nt);
+    J.edgeV = (int64_t *)malloc(sizeof(int64_t) * (size_t)nt * OR_RING * OR_ROWS);
+    J.edgeF = (int64_t *)malloc(sizeof(int64_t) * (size_t)nt * OR_RING * OR_ROWS);
+    J.hi = (int64_t **)calloc((size_t)nt, sizeof(int64_t *));
+    J.hj = (int32_t **)calloc((size_t)nt, sizeof(int32_t *));
+    J.hs = (int32_t **)calloc((size_t)nt, sizeof(int32_t *));
+    J.hcount = (int64_t *)calloc((size_t)nt, sizeof(int64_t));
+    J.hcap = (int64_t *)calloc((size_t)nt, sizeof(int64_t));
+    pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * (size_t)nt);
+    or_arg *args = (or_arg *)malloc(sizeof(or_arg) * (size_t)nt);
+    int64_t result = -1;
+    if (J.c0 && J.done && J.edgeV && J.edgeF && J.hi && J.hj && J.hs && J.hcount && J.hcap && th && args) {
+        for (int t = 0; t <= nt; ++t) J.c0[t] = m * t / nt;
+        for (int t = 0; t < nt; ++t) atomic_init(&J.done[t], 0);
+        atomic_init(&J.abort_all, 0);
+        int started = 0;
+        for (int t = 0; t < nt; ++t) {
+            args[t].job = &J;
+            args[t].t = t;
+            if (pthread_create(&th[t], NULL, or_worker, &args[t]) != 0) break;
+            ++started;
+        }
+        /* the stripes wait on their neighbours: without every thread the
+         * wavefront cannot finish, so stop the others and report a failure */
+        if (started < nt) {
+            atomic_store(&J.abort_all, 1);
+            fail = 1;
+        }
+        for (int t = 0; t < started; ++t) pthread_join(th[t], NULL);
+        if (!fail) {
+            /* row-major merge: rows ascending; inside a row, stripes left to right */
+            int64_t total = 0;
+            for (int t = 0; t < nt; ++t) total += J.hcount[t];
+            int64_t *pos = (int64_t *)calloc((size_t)nt, sizeof(int64_t));
+            if (pos) {
+                int64_t k = 0;
+                while (k < total) {
+                    int64_t best = INT64_MAX;
+                    for (int t = 0; t < nt; ++t)
+                        if (pos[t] < J.hcount[t] && J.hi[t][pos[t]] < best) best = J.hi[t][pos[t]];
+                    for (int t = 0; t < nt; ++t)
+                        while (pos[t] < J.hcount[t] && J.hi[t][pos[t]] == best) {
+                            if (k < cap) {
+                                out_i[k] = best;
+                                out_j[k] = J.hj[t][pos[t]];
+                                out_s[k] = J.hs[t][pos[t]];
+                            }
+                            ++k;
+                            ++pos[t];
+                        }
+                }
+                free(pos);
+                result = total;
+            }
+        }
+    }
+    if (J.hi) for (int t = 0; t < nt; ++t) free(J.hi[t]);
+    if (J.hj) for (int t = 0; t < nt; ++t) free(J.hj[t]);
+    if (J.hs) for (int t = 0; t < nt; ++t) free(J.hs[t]);
+    free(J.hi); free(J.hj); free(J.hs); free(J.hcount); free(J.hcap);
+    free(J.c0); free((void *)J.done); free(J.edgeV); free(J.edgeF); free(th); free(args);
+    return result;
 }
