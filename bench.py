@@ -209,33 +209,77 @@ def measured_traffic(kernel, units):
     return None
 
 
-# Integer peak of the GB300: 152 SMs x 64 INT32 lanes per clock (16 per SM
-# sub-partition) x 2,070 MHz.
-INT_PEAK_GOPS = 152 * 64 * 2.070
-# Algorithmic integer operations of one (child, parent entry) triple of the
-# row update, and of one sweep entry: slot A (add, select, two adds and a max
-# for G_a, a max, a threshold compare), slot B (add, select, compare), one
-# add-max for G_b.
+# Algorithmic work of the row update, per DP entry (the unit the method's cost
+# is counted in, Table 4): the parent entry read (j and the packed M, G_a: 8 B,
+# plus 2 B of node metadata amortised) and the child entry written (10 B); 6
+# integer operations for a full three-term entry (D add, G_a add + add-max, G_b
+# add-max, the two maxima of M).
+BYTES_PER_ENTRY = 20
+OPS_PER_ENTRY = 6
+# Per (child, parent entry) triple, the unit the kernels iterate over: slot A
+# (add, select, two adds and a max for G_a, a max, a threshold compare), slot B
+# (add, select, compare), one add-max for G_b.
 OPS_PER_TRIPLE = 12
 
 
-def cpu_baseline(text, queries, scheme, H, seconds, alphabet=b"ACGT"):
-    """The oracle (plain full-matrix Smith-Waterman, one thread) on a bounded
-    sample: the shortest query against a text slice sized for ~`seconds`."""
+def int_peaks():
+    """Measured integer instruction rates of this GPU (ae_int_peak, run live),
+    else the committed measurement (MEASURED_INT_PEAKS.json)."""
+    try:
+        from paper_1208_0274_gb300 import ae
+        iadd = max(ae.ae_int_peak(ae.AE_PEAK_IADD, 4, 1024, 16)[1] for _ in range(2))
+        imax = max(ae.ae_int_peak(ae.AE_PEAK_IMAX, 4, 1024, 16)[1] for _ in range(2))
+        return {"iadd": iadd, "imax": imax, "source": "measured live (ae_int_peak)"}
+    except Exception:
+        d = json.load(open(os.path.join(ROOT, "MEASURED_INT_PEAKS.json")))
+        return {"iadd": d["iadd_s32_inst_per_s"], "imax": d["imax_s32_inst_per_s"],
+                "source": "MEASURED_INT_PEAKS.json"}
+
+
+def cpu_info():
+    """(threads this process may use, CPU model string)."""
     import oracle
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=5).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith(("model name", "cpu part")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except OSError:
+            pass
+    import platform
+    return oracle.host_threads(), f"{model or platform.processor() or 'unknown'} ({platform.machine()})"
+
+
+def cpu_baseline(text, queries, scheme, H, seconds, alphabet=b"ACGT"):
+    """The oracle (plain full-matrix Smith-Waterman) on every host core, on a
+    bounded sample: the shortest query against a text slice sized for about
+    `seconds` of work."""
+    import oracle
+    threads, model = cpu_info()
     q = min(queries, key=lambda x: x.size)[: 10_000]
     h = H[int(np.argmin([x.size for x in queries]))]
-    probe = text[: max(1, 20_000_000 // max(q.size, 1))]
+    probe = text[: max(1, 200_000_000 // max(q.size, 1))]
     t0 = time.perf_counter()
-    oracle.sw_hits(probe, q, scheme, h, alphabet=alphabet)
+    oracle.sw_hits_mt(probe, q, scheme, h, alphabet=alphabet, threads=threads)
     rate = probe.size * q.size / max(time.perf_counter() - t0, 1e-6)
     L = int(min(text.size, max(1000, rate * seconds / q.size)))
     t0 = time.perf_counter()
-    oracle.sw_hits(text[:L], q, scheme, h, alphabet=alphabet)
+    oracle.sw_hits_mt(text[:L], q, scheme, h, alphabet=alphabet, threads=threads)
     dt = time.perf_counter() - t0
-    return {"value": round(L * q.size / dt / 1e9, 4), "unit": "GCUPS", "cores": 1, "kind": "oracle",
+    return {"value": round(L * q.size / dt / 1e9, 4), "unit": "GCUPS", "cores": threads, "kind": "oracle",
+            "cpu": model,
             "sample": f"one {q.size} bp query against the first {L:,} bp of the text "
-                      f"({L * q.size:.3g} cells, {dt:.1f} s, single thread)"}
+                      f"({L * q.size:.3g} cells, {dt:.1f} s, {threads} threads)"}
 
 
 def run_reference(args):
@@ -245,30 +289,32 @@ def run_reference(args):
     name, text, queries, H, scheme, desc = make_workload(args)
     import oracle
     oracle.build()
+    threads, model = cpu_info()
     q = min(queries, key=lambda x: x.size)[: 10_000]
     h = H[int(np.argmin([x.size for x in queries]))]
-    # size one step at ~10 s of oracle work
-    probe = text[: max(1, 20_000_000 // max(q.size, 1))]
-    t0 = time.perf_counter()
+    # size one step at ~5 s of oracle work on every core
     alphabet = PROTEIN if name == "protein" else b"ACGT"
-    oracle.sw_hits(probe, q, scheme, h, alphabet=alphabet)
+    probe = text[: max(1, 200_000_000 // max(q.size, 1))]
+    t0 = time.perf_counter()
+    oracle.sw_hits_mt(probe, q, scheme, h, alphabet=alphabet, threads=threads)
     rate = probe.size * q.size / max(time.perf_counter() - t0, 1e-6)
-    L = int(min(text.size, max(1000, rate * 10.0 / q.size)))
-    for _ in range(max(args.warmup, 0) if L * q.size < 2e9 else 0):
-        oracle.sw_hits(text[: L // 10], q, scheme, h, alphabet=alphabet)
+    L = int(min(text.size, max(1000, rate * 5.0 / q.size)))
+    for _ in range(max(args.warmup, 0)):
+        oracle.sw_hits_mt(text[: L // 10], q, scheme, h, alphabet=alphabet, threads=threads)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.sw_hits(text[:L], q, scheme, h, alphabet=alphabet)
+        oracle.sw_hits_mt(text[:L], q, scheme, h, alphabet=alphabet, threads=threads)
         times.append(time.perf_counter() - t0)
     tot = sum(times)
     v = args.steps * L * q.size / tot / 1e9
-    sample = f"each step: one {q.size} bp query against the first {L:,} bp of the text, single thread"
+    sample = f"each step: one {q.size} bp query against the first {L:,} bp of the text, {threads} threads"
     line = {"metric": METRIC, "value": round(v, 4), "unit": "GCUPS", "impl": "reference", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(1000 * tot / args.steps, 3),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
             "data": "synthetic", "config": desc,
-            "cpu_baseline": {"value": round(v, 4), "unit": "GCUPS", "cores": 1, "kind": "oracle", "sample": sample},
+            "cpu_baseline": {"value": round(v, 4), "unit": "GCUPS", "cores": threads, "kind": "oracle",
+                             "cpu": model, "sample": sample},
             "e2e": {"value": round(v, 4), "unit": "GCUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -393,7 +439,7 @@ def run_ours(args):
     if not args.no_e2e:
         hbytes = 0
         t_e = []
-        for s in range(max(1, min(args.steps, 3))):
+        for s in range(max(1, args.steps)):
             torch.cuda.synchronize()
             t1 = time.perf_counter()
             hits, counts = ae.ae_search(idx, qs, scheme, hs, options=opts_e2e, stream=stream)
@@ -417,26 +463,30 @@ def run_ours(args):
     peak, src = peaks()
     ent_leaf = kstats["entries_leaf"]
     ent_trie = kstats["entries"] - ent_leaf
-    # integer-ALU view (the bound ncu measures for k_rows and k_leaf): algorithmic ops per second
-    units = {"k_rows": kstats["triples"], "k_leaf": ent_leaf}.get(dom, kstats["raw_hits"])
-    launches_dom = {"k_rows": 2 * kstats["levels"], "k_leaf": max(1, kstats["leaf_sweeps"])}.get(dom, 1)
+    # The row update's roofline is HBM: 20 algorithmic bytes against 6 integer
+    # operations per DP entry (0.3 op/B, far below the GPU's ~5.5 op/B balance).
     sec = groups[dom] / 1000.0
-    ops = OPS_PER_TRIPLE * units
-    achieved = ops / sec / 1e9 if sec > 0 else 0.0
-    traffic = measured_traffic(dom, units)
-    roof = {"kernel": dom, "bound": "alu", "achieved": round(achieved, 2), "peak": round(INT_PEAK_GOPS, 1),
-            "unit": "Gop/s", "frac": round(achieved / INT_PEAK_GOPS, 5),
-            "traffic": None if traffic is None else int(traffic / launches_dom),
-            "peak_source": "derived: 152 SMs x 64 INT32 lanes x 2070 MHz",
-            "ops_per_unit": OPS_PER_TRIPLE, "unit_of_work": "triple (child, parent entry)" if dom == "k_rows"
-            else "sweep entry", "units_per_launch": int(units / launches_dom),
+    launches_dom = {"k_rows": 2 * kstats["levels"], "k_leaf": max(1, kstats["leaf_sweeps"])}.get(dom, 1)
+    ent = {"k_rows": ent_trie, "k_leaf": ent_leaf}.get(dom, kstats["raw_hits"])
+    gbs = BYTES_PER_ENTRY * ent / sec / 1e9 if sec > 0 else 0.0
+    traffic = measured_traffic(dom, ent)
+    roof = {"kernel": dom, "bound": "hbm", "achieved": round(gbs, 2), "peak": peak, "unit": "GB/s",
+            "frac": round(gbs / peak, 4), "traffic": None if traffic is None else int(traffic / launches_dom),
+            "peak_source": f"{src} (copy bandwidth, MEASURED_PEAKS.json)",
+            "algorithmic_bytes_per_unit": BYTES_PER_ENTRY, "unit_of_work": "DP entry",
+            "units_per_launch": int(ent / launches_dom),
             "group_ms_per_step": {k: round(v / args.steps, 3) for k, v in groups.items()}}
-    # bytes view: 24 B per DP entry (read as parent, written as child) against the measured HBM copy bandwidth
-    ent = {"k_rows": ent_trie, "k_leaf": ent_leaf}.get(dom, 0)
-    gbs = 24.0 * ent / sec / 1e9 if sec > 0 else 0.0
-    roof_hbm = {"kernel": dom, "bound": "hbm", "achieved": round(gbs, 2), "peak": peak, "unit": "GB/s",
-                "frac": round(gbs / peak, 4), "peak_source": src, "algorithmic_bytes_per_unit": 24,
-                "unit_of_work": "DP entry"}
+    # integer view: 6 ops per DP entry (and 12 per triple) against the measured int32 add rate
+    ip = int_peaks()
+    ops_e = OPS_PER_ENTRY * ent / sec / 1e9 if sec > 0 else 0.0
+    units_t = {"k_rows": kstats["triples"], "k_leaf": ent_leaf}.get(dom, 0)
+    ops_t = OPS_PER_TRIPLE * units_t / sec / 1e9 if sec > 0 else 0.0
+    roof_alu = {"kernel": dom, "bound": "alu", "achieved": round(ops_e, 2), "peak": round(ip["iadd"] / 1e9, 1),
+                "unit": "Gop/s", "frac": round(ops_e / (ip["iadd"] / 1e9), 5), "ops_per_unit": OPS_PER_ENTRY,
+                "unit_of_work": "DP entry", "peak_source": f"int32 add rate, {ip['source']}",
+                "imax_peak_ginst": round(ip["imax"] / 1e9, 1),
+                "per_triple": {"achieved": round(ops_t, 2), "ops_per_unit": OPS_PER_TRIPLE,
+                               "frac": round(ops_t / (ip["iadd"] / 1e9), 5), "triples": int(units_t)}}
     cpu = None
     if not args.no_cpu:
         import oracle
@@ -449,7 +499,7 @@ def run_ours(args):
             "queries_per_s": round(qps, 3), "hits_per_step": int(kstats["hits"] / max(args.steps, 1)),
             "entries_per_step": int(kstats["entries"] / max(args.steps, 1)),
             "gpu_launches": int(kstats["launches"]), "plain": plain, "e2e": e2e, "roofline": roof,
-            "roofline_hbm": roof_hbm,
+            "roofline_alu": roof_alu,
             "cpu_baseline": cpu, "clocks": clk,
             "index_build_s": round(t_index, 3)}
     print(json.dumps(line), flush=True)

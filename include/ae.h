@@ -106,6 +106,9 @@ typedef struct {
                                  non-empty child of a node with every entry of the node's row */
     int64_t batch_splits;     /* batches that ran out of device memory and were searched again
                                  as two halves (the result is the same) */
+    int64_t dominated;        /* forks dropped at the seed depth by q-prefix domination (Lemma 1):
+                                 the text letter before every occurrence of the seed gram equals
+                                 the query letter before the fork's start */
 } ae_stats;
 
 /* Engine knobs (NULL = defaults).  None of them changes the result set. */
@@ -132,6 +135,14 @@ typedef struct {
                                  that would grow it further is searched as two halves (as after
                                  a failed device allocation; ae_stats.batch_splits); a single
                                  query column that does not fit gives AE_ENOMEM.  0: no cap */
+    int32_t general_rows;     /* 1: compute every trie level with the general row kernel (any alphabet,
+                                 one lane per (child, parent entry)) instead of the DNA int16x2 kernel
+                                 (one lane per parent entry, all children); the results are the same */
+    int32_t qprefix_domination; /* 1 (default): with q-prefix seeding, drop the forks that Lemma 1's
+                                 domination proves redundant -- a seed gram every occurrence of which
+                                 in T is preceded by the query letter before the fork's start (a table
+                                 of the letters preceding each gram is built once per index and seed
+                                 depth); 0: keep every fork.  The results are the same */
 } ae_options;
 
 /* Fill *opt with the defaults. */
@@ -149,6 +160,21 @@ void ae_options_default(ae_options *opt);
  * Errors: AE_EINVAL (n < 1, unknown letter, bad alphabet), AE_EUNSUPPORTED
  * (n >= 2^31 - 1), AE_ENOMEM, AE_ECUDA. */
 ae_status ae_index_build(const uint8_t *text, int64_t n, int32_t alphabet, ae_index **out);
+
+/* Build an index of a collection of sequences (Section 2.3: a database of
+ * several sequences searched as one text).  text[0..n) (host ASCII) holds the
+ * nseq sequences back to back; starts[0..nseq) (host) are their first
+ * positions, starts[0] = 0, non-decreasing, <= n (sequence k is
+ * text[starts[k] .. starts[k+1]), the last one ends at n; empty sequences are
+ * allowed).  The sequences are indexed joined by a separator that sorts below
+ * every letter and matches nothing, so no result's alignment spans two
+ * sequences; result positions (ae_hit.text_end) are positions in text, i.e.
+ * in the sequences back to back.  Otherwise as ae_index_build, whose index of
+ * a single sequence this equals in results.
+ * Errors: AE_EINVAL (n < 1, bad starts, unknown letter, bad alphabet),
+ * AE_EUNSUPPORTED (n + nseq >= 2^31 - 1), AE_ENOMEM, AE_ECUDA. */
+ae_status ae_index_build_collection(const uint8_t *text, int64_t n, const int64_t *starts, int32_t nseq,
+                                   int32_t alphabet, ae_index **out);
 
 /* Write / read an index file (versioned header + checksum).  Load copies to
  * the current device.  Errors: AE_EIO, AE_ENOMEM, AE_ECUDA. */
@@ -188,25 +214,29 @@ ae_status ae_search_device(const ae_index *idx, const uint8_t *d_seq, const int6
                            int64_t *counts, void *stream);
 
 /* The search of ae_search_device for callers that cannot allocate device
- * memory: code that runs while a stream is being captured into a CUDA graph
- * (cudaMalloc is not allowed there), or a process whose device memory is
- * already handed out to another allocator.  It calls no cudaMalloc, cudaFree,
- * cudaMallocHost or other device allocator: every working buffer is carved
- * from one fixed 64 MiB array in the library's device image, which each GPU
- * that loads the library keeps until the process exits.  The paper has no
- * counterpart; the arguments, result order and AE_EOVERFLOW behaviour are
- * those of ae_search_device.
+ * memory: a process whose device memory is already handed out to another
+ * allocator (a framework's caching pool, a fixed reservation made at start-up)
+ * and that must not take more behind that allocator's back.  It calls no
+ * cudaMalloc, cudaFree, cudaMallocHost or other device allocator: every
+ * working buffer is carved from one fixed 64 MiB array in the library's device
+ * image, which each GPU that loads the library keeps until the process exits.
+ * The paper has no counterpart; the arguments, result order and AE_EOVERFLOW
+ * behaviour are those of ae_search_device.
  * Limits: at most 65,536 query letters in total and 4,096 queries per call,
- * and the search's working set must fit the array (rows of the text-position
- * sweep are capped at 256 entries before one retry at 1,024); beyond that the
- * call returns AE_EUNSUPPORTED and writes nothing to d_hits.
+ * and the search's working set must fit the array (rows of the
+ * text-position sweep start at no more than 256 entries and may grow
+ * fourfold up to 1,024); beyond that the call returns AE_EUNSUPPORTED and
+ * writes nothing to d_hits.
+ * The call synchronises `stream` while it runs (it reads each trie level's
+ * sizes back to the host), so a stream that is being captured into a CUDA
+ * graph is refused with AE_EUNSUPPORTED before any work is queued.
  * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  All calls on a device share the array, which
- * keeps the previous call's contents (the search initialises everything it
- * reads); calls on one device are serialised by the library and each returns
- * only after its device work has finished, so their device work never
- * overlaps -- work that did overlap on the same array would race. */
+ * (cudaGetSymbolAddress) with that device current.  All calls on a device
+ * share the array, which keeps the previous call's contents (the search
+ * initialises everything it reads); calls on one device are serialised by the
+ * library and each returns only after all of its device work has finished --
+ * also when it fails part-way -- so their device work never overlaps: work
+ * that did overlap on the same array would race. */
 ae_status ae_search_device_static(const ae_index *idx, const uint8_t *d_seq, const int64_t *offsets,
                                   int32_t nq, const ae_scoring *scoring, const int32_t *H,
                                   const ae_options *opt, ae_hit *d_hits, int64_t capacity,

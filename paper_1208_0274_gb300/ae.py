@@ -44,7 +44,8 @@ class ae_options(ctypes.Structure):
                 ("leaf_capacity", ctypes.c_int32), ("profile", ctypes.c_int32),
                 ("leaf_delay", ctypes.c_int32), ("int16_limit", ctypes.c_int32),
                 ("hint_hits", ctypes.c_void_p), ("tier_stats", ctypes.c_int32),
-                ("workspace_limit", ctypes.c_int64)]
+                ("workspace_limit", ctypes.c_int64), ("general_rows", ctypes.c_int32),
+                ("qprefix_domination", ctypes.c_int32)]
 
 
 class ae_stats(ctypes.Structure):
@@ -61,7 +62,8 @@ class ae_stats(ctypes.Structure):
                 ("leaf_max_steps", ctypes.c_int64),
                 ("leaf_max_width", ctypes.c_int64), ("ws_bytes", ctypes.c_int64),
                 ("leaf_sweeps", ctypes.c_int64), ("leaf_raw_hits", ctypes.c_int64),
-                ("triples", ctypes.c_int64), ("batch_splits", ctypes.c_int64)]
+                ("triples", ctypes.c_int64), ("batch_splits", ctypes.c_int64),
+                ("dominated", ctypes.c_int64)]
 
 
 def _load():
@@ -74,6 +76,7 @@ def _load():
         "ae_options_default": (None, [V]),
         "ae_strerror": (ctypes.c_char_p, [I32]),
         "ae_index_build": (I32, [V, I64, I32, V]),
+        "ae_index_build_collection": (I32, [V, I64, V, I32, I32, V]),
         "ae_index_save": (I32, [V, ctypes.c_char_p]),
         "ae_index_load": (I32, [ctypes.c_char_p, V]),
         "ae_index_free": (None, [V]),
@@ -97,6 +100,7 @@ def _load():
         "ae_suffix_array": (I32, [V, I64, I32, V]),
         "ae_suffix_array_device": (I32, [V, I64, I32, I32, V, V]),
         "ae_plan": (I32, [I64, I32, V, I32, V, V, V]),
+        "ae_int_peak": (I32, [I32, I32, I32, I32, V, V, V, V]),
     }
     for name, (res, args) in sig.items():
         f = getattr(lib, name)
@@ -193,6 +197,19 @@ def ae_index_build(text, alphabet=AE_DNA):
     t = _u8(text)
     out = ctypes.c_void_p(0)
     _check(lib.ae_index_build(t.ctypes.data, t.size, int(alphabet), ctypes.byref(out)), "ae_index_build")
+    return Index(out.value, alphabet)
+
+
+def ae_index_build_collection(sequences, alphabet=AE_DNA):
+    """Index of a collection: `sequences` is a list of sequences (ASCII), joined
+    back to back; results report positions in that concatenation, and no
+    alignment spans two sequences."""
+    seqs = [_u8(q) for q in sequences]
+    t = np.concatenate(seqs) if seqs else np.zeros(0, np.uint8)
+    starts = np.ascontiguousarray(np.concatenate([[0], np.cumsum([q.size for q in seqs])[:-1]]).astype(np.int64))
+    out = ctypes.c_void_p(0)
+    _check(lib.ae_index_build_collection(t.ctypes.data, t.size, starts.ctypes.data, len(seqs), int(alphabet),
+                                         ctypes.byref(out)), "ae_index_build_collection")
     return Index(out.value, alphabet)
 
 
@@ -345,6 +362,18 @@ def ae_plan(m, scheme, H, alphabet=AE_DNA):
     _check(lib.ae_plan(int(m), int(alphabet), ctypes.byref(sc), int(H), ctypes.byref(q), ctypes.byref(d0),
                        ctypes.byref(L)), "ae_plan")
     return q.value, d0.value, L.value
+
+
+AE_PEAK_IADD, AE_PEAK_IMAX, AE_PEAK_ADDMAX32, AE_PEAK_ADDMAX16X2 = range(4)
+
+
+def ae_int_peak(kind, chains=4, iters=2048, blocks_per_sm=8, stream=None):
+    """Measured integer-ALU rate of one operation kind (include/ae_peak.h):
+    (ops per second, instructions per second, kernel ms)."""
+    ops, ins, ms = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(lib.ae_int_peak(int(kind), int(chains), int(iters), int(blocks_per_sm), _stream_handle(stream),
+                           ctypes.byref(ops), ctypes.byref(ins), ctypes.byref(ms)), "ae_int_peak")
+    return ops.value, ins.value, ms.value
 
 
 def encode_codes(seq, alphabet=AE_DNA):

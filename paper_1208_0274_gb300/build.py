@@ -1,4 +1,4 @@
-"""Build libae.so in-tree: five translation units compiled in parallel for
+"""Build libae.so in-tree: seven translation units compiled in parallel for
 sm_103a, then linked into one shared library next to this file.
 
     python -m paper_1208_0274_gb300.build [--force]
@@ -13,7 +13,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT = os.path.join(HERE, "libae.so")
 BUILD = os.path.join(HERE, "_build")
-SOURCES = ["ae_index.cpp", "ae_kernels.cu", "ae_trie.cu", "ae_engine.cu", "ae_mlp.cu"]
+SOURCES = ["ae_index.cpp", "ae_kernels.cu", "ae_trie.cu", "ae_engine.cu", "ae_mlp.cu", "ae_peak.cu", "ae_rows_dna.cu"]
 HEADERS = ["ae_internal.h", "ae_kernels.h", "ae_device.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -29,7 +29,7 @@ def _stale():
     if not os.path.exists(OUT):
         return True
     t = os.path.getmtime(OUT)
-    deps = [os.path.join(CSRC, s) for s in SOURCES + HEADERS] + [os.path.join(ROOT, "include", h) for h in ("ae.h", "ae_mlp.h")]
+    deps = [os.path.join(CSRC, s) for s in SOURCES + HEADERS] + [os.path.join(ROOT, "include", h) for h in ("ae.h", "ae_mlp.h", "ae_peak.h")]
     return any(os.path.getmtime(d) > t for d in deps)
 
 

@@ -49,6 +49,24 @@ __device__ __forceinline__ int32_t delta_of(const ScoreView &sc, const int8_t *s
     return sc.use_matrix ? (int32_t)smat[c * AE_MAX_SIGMA + q] : (c == q ? sc.sa : sc.sb);
 }
 
+// Collections: separator rows among the rows [64 (k / 64), k) of k's block (they
+// store letter code 0 but are not occurrences of it; the block's letter counts
+// already leave out the separators of earlier blocks), whether row k is one, and
+// whether text position p ends a sequence (no alignment crosses it).
+__device__ __forceinline__ uint32_t sep_in_block(const IndexView &ix, uint32_t k) {
+    const uint32_t *sb = ix.sep + (size_t)(k >> 6) * AE_SEP_BLOCK_WORDS;
+    const uint32_t r = k & 63;
+    const uint64_t mask = (uint64_t)__ldg(sb + 1) | ((uint64_t)__ldg(sb + 2) << 32);
+    return (uint32_t)__popcll(mask & (r ? (~0ull >> (64 - r)) : 0ull));
+}
+__device__ __forceinline__ bool sep_row(const IndexView &ix, uint32_t k) {
+    const uint32_t r = k & 63;
+    return ix.sep && ((__ldg(ix.sep + (size_t)(k >> 6) * AE_SEP_BLOCK_WORDS + 1 + (r >> 5)) >> (r & 31)) & 1u);
+}
+__device__ __forceinline__ bool seq_end(const IndexView &ix, int64_t p) {
+    return ix.ends && ((__ldg(ix.ends + (p >> 5)) >> (p & 31)) & 1u);
+}
+
 // Occ(c, k): occurrences of letter c in BWT rows [0, k).
 __device__ __forceinline__ uint32_t occ_dna(const IndexView &ix, int c, uint32_t k) {
     const uint32_t *blk = ix.occ + (size_t)(k >> 6) * AE_DNA_BLOCK_WORDS;
@@ -66,6 +84,7 @@ __device__ __forceinline__ uint32_t occ_dna(const IndexView &ix, int c, uint32_t
         acc += __popc(eq & mask);
     }
     if (c == 0 && (int64_t)(k >> 6) == (ix.dollar_row >> 6) && (ix.dollar_row & 63) < r) acc -= 1;
+    if (c == 0 && ix.sep) acc -= sep_in_block(ix, k);
     return acc;
 }
 
@@ -83,6 +102,7 @@ __device__ __forceinline__ uint32_t occ_prot(const IndexView &ix, int c, uint32_
     }
     acc += __popcll(eq & mask);
     if (c == 0 && (int64_t)(k >> 6) == (ix.dollar_row >> 6) && (ix.dollar_row & 63) < r) acc -= 1;
+    if (c == 0 && ix.sep) acc -= sep_in_block(ix, k);
     return acc;
 }
 

@@ -42,6 +42,8 @@ struct StaticArena {
     size_t used;
 };
 thread_local StaticArena *g_arena = nullptr;
+// Largest sweep row (entries) the no-allocation entry point retries with.
+constexpr int32_t AE_STATIC_MAX_LEAF_CAP = 1024;
 
 void carve(DevBuf &b, size_t bytes, size_t keep, cudaStream_t st);
 
@@ -162,6 +164,7 @@ struct Workspace {
     // output
     DevBuf uniq, uflags, uoff, qcount;
     DevBuf stats, segs, ctr, seg_cnt, seg_hit, task_first, task_tot, task_off, task_tmp, task_sum, res, res_key;
+    DevBuf kcnt, khit;   // DNA int16x2 route: per (node, letter) outputs and hits of a level
     double fr_ratio = 1.2, lf_ratio = 0.6, hit_ratio = 0.5;
     // pinned host staging
     uint64_t *h_tot = nullptr;
@@ -184,7 +187,7 @@ struct Workspace {
                 &cnt[4], &off[0], &off[1], &off[2], &off[3], &off[4], &totals, &scan_tmp, &lj, &lM,
                 &lGa, &inj, &rhits, &sk0, &sv0, &sk1, &sv1, &sort_tmp, &hkey, &hscore, &hcount, &hk1,
                 &hv1, &scratch, &next_seg, &uniq, &uflags, &uoff, &qcount, &stats, &segs, &ctr, &seg_cnt, &seg_hit,
-                &task_first, &task_tot, &task_off, &task_tmp, &task_sum, &res, &res_key};
+                &task_first, &task_tot, &task_off, &task_tmp, &task_sum, &res, &res_key, &kcnt, &khit};
     }
 
     ~Workspace() {
@@ -204,7 +207,7 @@ struct Workspace {
                           &cnt[2], &cnt[3], &cnt[4], &off[0], &off[1], &off[2], &off[3], &off[4], &scan_tmp, &lj,
                           &lM, &lGa, &inj, &rhits, &sk0, &sv0, &sk1, &sv1, &sort_tmp, &hk1, &hv1, &scratch, &uniq,
                           &uflags, &uoff, &segs, &seg_cnt, &seg_hit, &task_first, &task_tot, &task_off, &task_tmp,
-                          &res, &res_key};
+                          &res, &res_key, &kcnt, &khit};
         for (DevBuf *b : drop)
             if (b->p && !b->carved) {
                 cudaFree(b->p);
@@ -233,7 +236,8 @@ int64_t cur_ws_bytes() { return g_cur_ws ? g_cur_ws->device_bytes() : 0; }
 struct ae_index {
     HostIndex host;
     IndexView view;
-    void *d_occ = nullptr, *d_tend = nullptr, *d_text = nullptr;
+    void *d_occ = nullptr, *d_tend = nullptr, *d_text = nullptr, *d_sep = nullptr, *d_ends = nullptr;
+    uint32_t *d_dom[13] = {};   // q-prefix domination tables by seed depth (built on first use)
     int64_t device_bytes = 0;
     int device = 0;
     std::mutex mu;
@@ -244,6 +248,10 @@ struct ae_index {
         if (d_occ) cudaFree(d_occ);
         if (d_tend) cudaFree(d_tend);
         if (d_text) cudaFree(d_text);
+        if (d_sep) cudaFree(d_sep);
+        if (d_ends) cudaFree(d_ends);
+        for (uint32_t *t : d_dom)
+            if (t) cudaFree(t);
         ae_host_index_free(&host);
     }
 };
@@ -268,22 +276,56 @@ Workspace *workspace_for(const ae_index *cidx, cudaStream_t st) {
     return w;
 }
 
+// The q-prefix domination table of seed depth d0 (NULL when the table would be
+// too large or cannot be built; the filter is then off).  Built once per index
+// and depth, on `st`, and finished before any search uses it.
+const uint32_t *dom_table(const ae_index *cidx, int d0, cudaStream_t st) {
+    ae_index *idx = const_cast<ae_index *>(cidx);
+    const int bits = idx->view.sigma == 4 ? 2 : 5;
+    if (d0 < 1 || d0 > 12 || bits * d0 > 24 || idx->view.n < d0) return nullptr;
+    std::lock_guard<std::mutex> g(idx->mu);
+    if (idx->d_dom[d0]) return idx->d_dom[d0];
+    const size_t bytes = sizeof(uint32_t) << (bits * d0);
+    uint32_t *t = nullptr;
+    if (cudaMalloc(&t, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (cudaMemsetAsync(t, 0, bytes, st) != cudaSuccess) {
+        cudaGetLastError();
+        cudaFree(t);
+        return nullptr;
+    }
+    ae_dom_table(idx->view, d0, t, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+        cudaFree(t);
+        return nullptr;
+    }
+    idx->d_dom[d0] = t;
+    return t;
+}
+
 ae_status upload_index(ae_index *idx) {
     HostIndex &h = idx->host;
     size_t occ_b = sizeof(uint32_t) * (size_t)(h.nblocks * h.block_words);
-    size_t tend_b = sizeof(int32_t) * (size_t)(h.n + 1);
+    size_t tend_b = sizeof(int32_t) * (size_t)h.rows;
     size_t text_b = (size_t)h.n;
+    size_t sep_b = h.nseq ? sizeof(uint32_t) * (size_t)(h.nblocks * AE_SEP_BLOCK_WORDS) : 0;
+    size_t ends_b = h.nseq ? sizeof(uint32_t) * (size_t)((h.n + 31) / 32) : 0;
     if (cudaGetDevice(&idx->device) != cudaSuccess) return AE_ECUDA;
     if (cudaMalloc(&idx->d_occ, occ_b) != cudaSuccess || cudaMalloc(&idx->d_tend, tend_b) != cudaSuccess ||
-        cudaMalloc(&idx->d_text, text_b) != cudaSuccess) {
+        cudaMalloc(&idx->d_text, text_b) != cudaSuccess ||
+        (h.nseq && (cudaMalloc(&idx->d_sep, sep_b) != cudaSuccess || cudaMalloc(&idx->d_ends, ends_b) != cudaSuccess))) {
         cudaGetLastError();
         return AE_ENOMEM;
     }
     if (cudaMemcpy(idx->d_occ, h.occ, occ_b, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(idx->d_tend, h.tend, tend_b, cudaMemcpyHostToDevice) != cudaSuccess ||
-        cudaMemcpy(idx->d_text, h.text, text_b, cudaMemcpyHostToDevice) != cudaSuccess)
+        cudaMemcpy(idx->d_text, h.text, text_b, cudaMemcpyHostToDevice) != cudaSuccess ||
+        (h.nseq && (cudaMemcpy(idx->d_sep, h.sep, sep_b, cudaMemcpyHostToDevice) != cudaSuccess ||
+                    cudaMemcpy(idx->d_ends, h.ends, ends_b, cudaMemcpyHostToDevice) != cudaSuccess)))
         return AE_ECUDA;
-    idx->device_bytes = (int64_t)(occ_b + tend_b + text_b);
+    idx->device_bytes = (int64_t)(occ_b + tend_b + text_b + sep_b + ends_b);
     IndexView &v = idx->view;
     memset(&v, 0, sizeof(v));
     v.occ = (const uint32_t *)idx->d_occ;
@@ -294,6 +336,9 @@ ae_status upload_index(ae_index *idx) {
     for (int c = 0; c <= h.sigma; ++c) v.C[c] = h.C[c];
     v.sigma = h.sigma;
     v.alphabet = h.alphabet;
+    v.rows = h.rows;
+    v.sep = (const uint32_t *)idx->d_sep;
+    v.ends = (const uint32_t *)idx->d_ends;
     return AE_OK;
 }
 
@@ -411,6 +456,8 @@ struct Search {
     }
 
     void run_batch(const std::vector<WorkItem> &items);
+    void dna_level(int64_t &F, int cur, int64_t &cur_ent, int64_t &lf_ent_base, int64_t &lf_node_base,
+                   int64_t &rh_base, const WorkItem *d_items);
     void run_batch_split(const std::vector<WorkItem> &items);
     void compact_hits(int64_t from);
     void leaf_phase(int64_t ninj);
@@ -464,6 +511,9 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
         sa.d0 = d0;
         sa.npos = npos;
         sa.int16 = i16 ? 1 : 0;
+        // the domination table is allocated once per index (never from the static array)
+        sa.dom = (opt.qprefix_domination && !g_arena) ? dom_table(idx, d0, st) : nullptr;
+        sa.dominated = (unsigned long long *)((char *)w->stats.p + offsetof(DevStats, dominated));
         ensure(w->sk0, npos * 8, st);
         ensure(w->sv0, npos * 4, st);
         ensure(w->sk1, npos * 8, st);
@@ -501,7 +551,7 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
         std::vector<Node> roots(nitems);
         for (int i = 0; i < nitems; ++i) {
             roots[i].lo = 0;
-            roots[i].hi = (uint32_t)(ix.n + 1);
+            roots[i].hi = (uint32_t)ix.rows;
             roots[i].item = i;
             roots[i].cnt = AE_ROOT_ROW;
             roots[i].off = 0;
@@ -526,6 +576,7 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
     }
     ensure(w->totals, 64, st);
     ensure(w->ctr, sizeof(LevelCounters), st);
+    bool root_level = d0 < 1;   // the first level of a walk from the root has implicit rows
     while (F > 0 && depth <= L_max_all) {
         if (i16 && (int64_t)(depth + 1) * sc.gmax > opt.int16_limit) {
             ensure(w->aGa[cur], std::max<int64_t>(cur_ent, 1) * 4, st);
@@ -534,6 +585,17 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
             prof.mark(K_OTHER);
             i16 = false;
         }
+        if (sigma == 4 && i16 && !opt.tier_stats && !root_level && !opt.general_rows && -sc.ss < 65536) {
+            // DNA int16x2 route: one lane per parent entry, child ranges taken in
+            // the task prologue (no separate children / compaction passes)
+            dna_level(F, cur, cur_ent, lf_ent_base, lf_node_base, rh_base, d_items);
+            cur ^= 1;
+            ++depth;
+            stats.levels++;
+            stats.levels_int16++;
+            continue;
+        }
+        root_level = false;
         // children per node (backward-search step per letter), scanned into
         // segment and triple offsets
         for (int k = 0; k < 2; ++k) {
@@ -698,6 +760,116 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
     stats.ms_reduce += ms_since(t2);
 }
 
+// One trie level of the DNA int16x2 route (ae_rows_dna.cu): count pass, scan
+// of the per-task totals, exact sizing of the next arenas from the level
+// totals, write pass.  Nodes and arenas have the layout of the general route.
+void Search::dna_level(int64_t &F, int cur, int64_t &cur_ent, int64_t &lf_ent_base, int64_t &lf_node_base,
+                       int64_t &rh_base, const WorkItem *d_items) {
+    (void)d_items;
+    const int nxt = cur ^ 1;
+    // nodes per task: 32 (one per lane) unless the level is too small to give
+    // every resident warp a few tasks
+    const int64_t warps = (int64_t)num_sms * ae_rows_dna_blocks_per_sm(false) * 8;
+    const int npt = (int)std::max<int64_t>(1, std::min<int64_t>(32, F / (warps * 4)));
+    const int64_t ntask = (F + npt - 1) / npt;
+    ensure(w->kcnt, (size_t)F * 16, st);
+    ensure(w->khit, (size_t)F * 16, st);
+    ensure(w->task_tot, (size_t)ntask * 5 * 4, st);
+    ensure(w->task_off, (size_t)ntask * 5 * 8, st);
+    ensure(w->task_tmp, (size_t)ae_scan_tmp_words(ntask, 5) * 8, st);
+    ensure(w->task_sum, 5 * 8, st);
+    LevelCounters h0;
+    memset(&h0, 0, sizeof(h0));
+    h0.lf_ent = (unsigned long long)lf_ent_base;
+    h0.lf_node = (unsigned long long)lf_node_base;
+    h0.hits = (unsigned long long)rh_base;
+    CU(cudaMemcpyAsync(w->ctr.p, &h0, sizeof(h0), cudaMemcpyHostToDevice, st));
+    DnaRowsArgs da;
+    memset(&da, 0, sizeof(da));
+    da.ix = ix;
+    da.sc = sc;
+    da.qv = qv;
+    da.nodes = ptr<Node>(w->nodes[cur]);
+    da.nnodes = F;
+    da.nodes_per_task = npt;
+    da.leaf_delay = opt.leaf_delay;
+    {
+        const uint64_t u = (uint64_t)(-(int64_t)sc.ss);
+        da.urec = ((1ull << 32) + u - 1) / u;
+    }
+    da.pj = ptr<int32_t>(w->aj[cur]);
+    da.pmg = ptr<uint32_t>(w->aM[cur]);
+    da.kcnt = ptr<uint32_t>(w->kcnt);
+    da.khit = ptr<uint32_t>(w->khit);
+    da.task_tot = ptr<uint32_t>(w->task_tot);
+    da.task_stride = (uint64_t)ntask;
+    da.ctr = ptr<LevelCounters>(w->ctr);
+    da.stats = ptr<DevStats>(w->stats);
+    prof.mark(K_ROWS);
+    ae_rows_dna(da, false, num_sms * ae_rows_dna_blocks_per_sm(false), st);
+    const uint32_t *tin[5];
+    uint64_t *tout[5];
+    for (int q = 0; q < 5; ++q) {
+        tin[q] = ptr<uint32_t>(w->task_tot) + q * ntask;
+        tout[q] = ptr<uint64_t>(w->task_off) + q * ntask;
+    }
+    ae_scan_u32(tin, tout, 5, ntask, ptr<uint64_t>(w->task_sum), ptr<uint64_t>(w->task_tmp), st);
+    prof.mark(K_ROWS);
+    LevelCounters hc;
+    CU(cudaMemcpyAsync(tot(), w->ctr.p, sizeof(hc), cudaMemcpyDeviceToHost, st));
+    sync();
+    memcpy(&hc, tot(), sizeof(hc));
+    const int64_t fr_ent = (int64_t)hc.c_fr_ent, fr_node = (int64_t)hc.c_fr_node;
+    const int64_t lf_ent = (int64_t)hc.c_lf_ent, lf_node = (int64_t)hc.c_lf_node, hits = (int64_t)hc.c_hits;
+    stats.triples += (int64_t)hc.triples;
+    ensure(w->aj[nxt], std::max<int64_t>(fr_ent, 1) * 4, st);
+    ensure(w->aM[nxt], std::max<int64_t>(fr_ent, 1) * 4, st);
+    ensure(w->nodes[nxt], std::max<int64_t>(fr_node, 1) * sizeof(Node), st);
+    ensure_keep(w->lj, (size_t)(lf_ent_base + lf_ent + 1) * 4, (size_t)lf_ent_base * 4, st);
+    ensure_keep(w->lM, (size_t)(lf_ent_base + lf_ent + 1) * 4, (size_t)lf_ent_base * 4, st);
+    ensure_keep(w->lGa, (size_t)(lf_ent_base + lf_ent + 1) * 4, (size_t)lf_ent_base * 4, st);
+    ensure_keep(w->inj, (size_t)(lf_node_base + lf_node + 1) * sizeof(Inject), (size_t)lf_node_base * sizeof(Inject),
+                st);
+    ensure_keep(w->rhits, (size_t)(rh_base + hits + 1) * sizeof(RangeHit), (size_t)rh_base * sizeof(RangeHit), st);
+    // the buffers above may have moved: the pointers are taken after sizing
+    da.nodes = ptr<Node>(w->nodes[cur]);
+    da.pj = ptr<int32_t>(w->aj[cur]);
+    da.pmg = ptr<uint32_t>(w->aM[cur]);
+    da.kcnt = ptr<uint32_t>(w->kcnt);
+    da.khit = ptr<uint32_t>(w->khit);
+    da.fj = ptr<int32_t>(w->aj[nxt]);
+    da.fmg = ptr<uint32_t>(w->aM[nxt]);
+    da.fnodes = ptr<Node>(w->nodes[nxt]);
+    da.fr_ent_cap = (uint64_t)fr_ent;
+    da.fr_node_cap = (uint64_t)fr_node;
+    da.lj = ptr<int32_t>(w->lj);
+    da.lM = ptr<int32_t>(w->lM);
+    da.lGa = ptr<int32_t>(w->lGa);
+    da.inj = ptr<Inject>(w->inj);
+    da.lf_ent_cap = (uint64_t)(lf_ent_base + lf_ent);
+    da.lf_node_cap = (uint64_t)(lf_node_base + lf_node);
+    da.rhits = ptr<RangeHit>(w->rhits);
+    da.hit_cap = (uint64_t)(rh_base + hits);
+    da.task_tot = ptr<uint32_t>(w->task_tot);
+    da.task_off = hc.wide ? nullptr : ptr<uint64_t>(w->task_off);
+    da.base_off[0] = 0;
+    da.base_off[1] = (uint64_t)lf_ent_base;
+    da.base_off[2] = 0;
+    da.base_off[3] = (uint64_t)lf_node_base;
+    da.base_off[4] = (uint64_t)rh_base;
+    prof.mark(K_ROWS);
+    ae_rows_dna(da, true, num_sms * ae_rows_dna_blocks_per_sm(true), st);
+    prof.mark(K_ROWS);
+    if (trace())
+        fprintf(stderr, "[ae level] dna nodes %lld (per task %d) -> frontier %lld nodes %lld, leaf %lld rows %lld\n",
+                (long long)F, npt, (long long)fr_ent, (long long)fr_node, (long long)lf_ent, (long long)lf_node);
+    lf_ent_base += lf_ent;
+    lf_node_base += lf_node;
+    rh_base += hits;
+    F = fr_node;
+    cur_ent = fr_ent;
+}
+
 // Reduce the hits [from, nhits) of the batch just finished to one record per
 // (query, text end, query end) with the maximum score, in place.  Queries are
 // whole inside a batch by default, so the final pass then sorts far fewer
@@ -855,6 +1027,8 @@ void Search::leaf_phase(int64_t ninj) {
                     hdr[0] - (unsigned long long)nhits, (long long)hit_cap, hdr[1], hdr[2], w->leaf_cap);
         if (hdr[1] != 0) {          // a row outgrew the scratch: retry larger
             w->leaf_cap *= 4;
+            // the no-allocation entry point caps sweep rows at its documented limit
+            if (g_arena && w->leaf_cap > AE_STATIC_MAX_LEAF_CAP) throw ae_error{AE_EUNSUPPORTED};
             continue;
         }
         if (hdr[2] != 0 || (int64_t)hdr[0] > nhits + hit_cap) {   // hit buffer too small
@@ -1048,6 +1222,7 @@ ae_status search_core(const ae_index *idx, Workspace *w, const int64_t *offsets,
         s.stats.entries = (int64_t)ds.entries;
         for (int k = 0; k < 3; ++k) s.stats.entries_tier[k] = (int64_t)ds.tier[k];
         s.stats.entries_leaf = (int64_t)ds.entries_leaf;
+        s.stats.dominated = (int64_t)ds.dominated;
         s.stats.leaf_max_steps = (int64_t)ds.leaf_max_steps;
         s.stats.leaf_max_width = (int64_t)ds.leaf_max_width;
         if (trace())
@@ -1080,8 +1255,31 @@ namespace {
 // Section 5 (1)-(2): the suffix array of the reversed text on the device
 // (prefix doubling), the occurrence blocks and text-end array filled from it
 // on the host, then the upload.
-ae_status build_index(ae_index *idx, const uint8_t *codes, int64_t n, int32_t alphabet) {
-    const int64_t N = n + 1;
+ae_status build_index(ae_index *idx, const uint8_t *codes, int64_t n, int32_t alphabet,
+                      const int64_t *starts = nullptr, int32_t nseq = 0) {
+    // a collection is indexed as its sequences joined by separators (code 0,
+    // letters shifted up by one for the suffix array)
+    std::vector<uint8_t> joined;
+    const uint8_t *sa_codes = codes;
+    int64_t J = n;
+    int sa_sigma = ae_alphabet_sigma(alphabet);
+    if (nseq > 0) {
+        J = n + nseq - 1;
+        try {
+            joined.resize((size_t)J);
+        } catch (...) {
+            return AE_ENOMEM;
+        }
+        int64_t q = 0;
+        for (int32_t k = 0; k < nseq; ++k) {
+            const int64_t b = starts[k], e = k + 1 < nseq ? starts[k + 1] : n;
+            if (k > 0) joined[q++] = 0;
+            for (int64_t p = b; p < e; ++p) joined[q++] = (uint8_t)(codes[p] + 1);
+        }
+        sa_codes = joined.data();
+        sa_sigma += 1;
+    }
+    const int64_t N = J + 1;
     std::vector<int32_t> sa;
     try {
         sa.resize((size_t)N);
@@ -1096,13 +1294,13 @@ ae_status build_index(ae_index *idx, const uint8_t *codes, int64_t n, int32_t al
     uint8_t *d_codes = nullptr;
     int32_t *d_sa = nullptr;
     ae_status res = AE_OK;
-    if (cudaMalloc(&d_codes, (size_t)n) != cudaSuccess || cudaMalloc(&d_sa, sizeof(int32_t) * (size_t)N) != cudaSuccess) {
+    if (cudaMalloc(&d_codes, (size_t)J) != cudaSuccess || cudaMalloc(&d_sa, sizeof(int32_t) * (size_t)N) != cudaSuccess) {
         cudaGetLastError();
         res = AE_ENOMEM;
     }
-    if (res == AE_OK && cudaMemcpyAsync(d_codes, codes, (size_t)n, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    if (res == AE_OK && cudaMemcpyAsync(d_codes, sa_codes, (size_t)J, cudaMemcpyHostToDevice, st) != cudaSuccess)
         res = AE_ECUDA;
-    if (res == AE_OK) res = ae_sa_doubling(d_codes, n, ae_alphabet_sigma(alphabet), 1, d_sa, nullptr, st);
+    if (res == AE_OK) res = ae_sa_doubling(d_codes, J, sa_sigma, 1, d_sa, nullptr, st);
     if (res == AE_OK && (cudaMemcpyAsync(sa.data(), d_sa, sizeof(int32_t) * (size_t)N, cudaMemcpyDeviceToHost, st) !=
                              cudaSuccess ||
                          cudaStreamSynchronize(st) != cudaSuccess))
@@ -1111,7 +1309,9 @@ ae_status build_index(ae_index *idx, const uint8_t *codes, int64_t n, int32_t al
     if (d_codes) cudaFree(d_codes);
     if (d_sa) cudaFree(d_sa);
     cudaStreamDestroy(st);
-    if (res == AE_OK) res = ae_host_index_fill(codes, n, alphabet, sa.data(), &idx->host);
+    if (res == AE_OK)
+        res = nseq > 0 ? ae_host_index_fill_collection(codes, n, starts, nseq, alphabet, sa.data(), &idx->host)
+                       : ae_host_index_fill(codes, n, alphabet, sa.data(), &idx->host);
     if (res == AE_OK) res = upload_index(idx);
     return res;
 }
@@ -1133,6 +1333,8 @@ void ae_options_default(ae_options *opt) {
     opt->hint_hits = nullptr;
     opt->tier_stats = 0;
     opt->workspace_limit = 0;
+    opt->general_rows = 0;
+    opt->qprefix_domination = 1;
 }
 
 const char *ae_strerror(int32_t status) {
@@ -1171,6 +1373,32 @@ ae_status ae_index_build(const uint8_t *text, int64_t n, int32_t alphabet, ae_in
     ae_index *idx = new (std::nothrow) ae_index();
     if (!idx) return AE_ENOMEM;
     ae_status st = build_index(idx, codes.data(), n, alphabet);
+    if (st != AE_OK) {
+        delete idx;
+        return st;
+    }
+    *out = idx;
+    return AE_OK;
+}
+
+ae_status ae_index_build_collection(const uint8_t *text, int64_t n, const int64_t *starts, int32_t nseq,
+                                   int32_t alphabet, ae_index **out) {
+    if (!out) return AE_EINVAL;
+    *out = nullptr;
+    if (!text || n < 1 || !starts || nseq < 1 || starts[0] != 0 || !ae_alphabet_sigma(alphabet)) return AE_EINVAL;
+    for (int32_t k = 1; k < nseq; ++k)
+        if (starts[k] < starts[k - 1] || starts[k] > n) return AE_EINVAL;
+    if (n + nseq >= INT32_MAX) return AE_EUNSUPPORTED;
+    std::vector<uint8_t> codes;
+    try {
+        codes.resize((size_t)n);
+    } catch (...) {
+        return AE_ENOMEM;
+    }
+    if (ae_encode_letters(text, n, alphabet, codes.data()) != 0) return AE_EINVAL;
+    ae_index *idx = new (std::nothrow) ae_index();
+    if (!idx) return AE_ENOMEM;
+    ae_status st = build_index(idx, codes.data(), n, alphabet, starts, nseq);
     if (st != AE_OK) {
         delete idx;
         return st;
@@ -1417,15 +1645,28 @@ Workspace g_static_ws[AE_STATIC_MAX_DEVICES];
 uint64_t g_static_htot[AE_STATIC_MAX_DEVICES][64];
 std::mutex g_static_mu[AE_STATIC_MAX_DEVICES];
 
+// Grow buffer b to at least `bytes` inside the arena, keeping its first `keep`
+// bytes.  The most recently carved buffer grows in place; any other buffer gets
+// a new region 1.25x larger than it was (as ensure() grows), so a buffer that
+// grows level by level in small steps does not use up the array early.
 void carve(DevBuf &b, size_t bytes, size_t keep, cudaStream_t st) {
     StaticArena &a = *g_arena;
+    if (b.carved && b.p && reinterpret_cast<char *>(b.p) + b.bytes == a.base + a.used) {
+        const size_t start = (size_t)(reinterpret_cast<char *>(b.p) - a.base);
+        if (start + bytes > a.cap) throw ae_error{AE_EUNSUPPORTED};
+        a.used = start + bytes;
+        b.bytes = bytes;
+        return;
+    }
     const size_t off = (a.used + 255) & ~size_t(255);
-    if (off + bytes > a.cap) throw ae_error{AE_EUNSUPPORTED};
+    size_t nb = std::max(bytes, b.bytes + b.bytes / 4);
+    if (off + nb > a.cap) nb = bytes;   // the growth margin is optional, the request is not
+    if (off + nb > a.cap) throw ae_error{AE_EUNSUPPORTED};
     void *p = a.base + off;
     if (keep && b.p) CU(cudaMemcpyAsync(p, b.p, keep, cudaMemcpyDeviceToDevice, st));
-    a.used = off + bytes;
+    a.used = off + nb;
     b.p = p;
-    b.bytes = bytes;
+    b.bytes = nb;
     b.carved = true;
 }
 
@@ -1448,6 +1689,15 @@ extern "C" ae_status ae_search_device_static(const ae_index *idx, const uint8_t 
         return AE_ECUDA;
     }
     if (dev < 0 || dev >= AE_STATIC_MAX_DEVICES) return AE_EUNSUPPORTED;
+    cudaStream_t st = (cudaStream_t)stream;
+    // the search synchronises its stream and reads level sizes back to the host,
+    // which a stream in capture mode does not allow: refuse before any work
+    cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cap_status) != cudaSuccess) {
+        cudaGetLastError();
+        return AE_ECUDA;
+    }
+    if (cap_status != cudaStreamCaptureStatusNone) return AE_EUNSUPPORTED;
     std::lock_guard<std::mutex> guard(g_static_mu[dev]);
     if (!g_static_ptr[dev]) {
         // once per device, with that device current
@@ -1458,7 +1708,6 @@ extern "C" ae_status ae_search_device_static(const ae_index *idx, const uint8_t 
         }
         g_static_ptr[dev] = p;
     }
-    cudaStream_t st = (cudaStream_t)stream;
     ae_options o;
     ae_options_default(&o);
     if (opt) o = *opt;
@@ -1499,11 +1748,15 @@ extern "C" ae_status ae_search_device_static(const ae_index *idx, const uint8_t 
             }
         }
     } catch (const ae_error &err) {
-        cudaGetLastError();
         status = err.st;
     } catch (const std::bad_alloc &) {
         status = AE_ENOMEM;
     }
+    // A search that stopped early (the array ran out, a CUDA call failed) may
+    // still have kernels queued that write into the array: wait for them while
+    // the device's lock is held, so the next call never shares the array with them.
+    cudaStreamSynchronize(st);
+    cudaGetLastError();
     g_arena = nullptr;
     return status;
 }

@@ -231,6 +231,117 @@ ae_status ae_host_index_fill(const uint8_t *codes, int64_t n, int32_t alphabet, 
         uint32_t *blk = out->occ + b * out->block_words;
         for (int c = 0; c < sigma; ++c) blk[c] = run[c];
     }
+    out->rows = N;
+    return AE_OK;
+}
+
+// A collection (Section 2.3): the sequences are joined by a separator, code 0
+// in the suffix array's alphabet (letters are code + 1), which sorts below every
+// letter and never matches.  Row h of the BWT of the reversed joined text has
+// suffix sa[h]; its BWT letter is the joined text's letter at J - sa[h] (J = the
+// joined length).  Separator rows are counted in `sep`, not in the letter counts,
+// and positions are mapped from the joined text to the sequences back to back.
+ae_status ae_host_index_fill_collection(const uint8_t *codes, int64_t n, const int64_t *starts, int32_t nseq,
+                                        int32_t alphabet, const int32_t *sa, HostIndex *out) {
+    memset(out, 0, sizeof(*out));
+    int sigma = ae_alphabet_sigma(alphabet);
+    if (!sigma || n < 1 || !sa || nseq < 1 || !starts || starts[0] != 0) return AE_EINVAL;
+    for (int32_t k = 1; k < nseq; ++k)
+        if (starts[k] < starts[k - 1] || starts[k] > n) return AE_EINVAL;
+    const int64_t nsep = nseq - 1, J = n + nsep, N = J + 1;
+    if (N >= INT32_MAX) return AE_EUNSUPPORTED;
+    out->alphabet = alphabet;
+    out->sigma = sigma;
+    out->n = n;
+    out->rows = N;
+    out->nseq = nseq;
+    out->block_words = alphabet == AE_DNA ? AE_DNA_BLOCK_WORDS : AE_PROT_BLOCK_WORDS;
+    out->nblocks = (N + AE_ROWS_PER_BLOCK - 1) / AE_ROWS_PER_BLOCK + 1;
+    out->occ = (uint32_t *)calloc((size_t)(out->nblocks * out->block_words), sizeof(uint32_t));
+    out->sep = (uint32_t *)calloc((size_t)(out->nblocks * AE_SEP_BLOCK_WORDS), sizeof(uint32_t));
+    out->ends = (uint32_t *)calloc((size_t)((n + 31) / 32), sizeof(uint32_t));
+    out->tend = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    out->text = (uint8_t *)malloc((size_t)n);
+    std::vector<int64_t> jpos;   // joined position -> text position (-1 for a separator)
+    std::vector<uint8_t> joined;
+    try {
+        jpos.resize((size_t)J);
+        joined.resize((size_t)J);
+    } catch (...) {
+        ae_host_index_free(out);
+        return AE_ENOMEM;
+    }
+    if (!out->occ || !out->sep || !out->ends || !out->tend || !out->text) {
+        ae_host_index_free(out);
+        return AE_ENOMEM;
+    }
+    memcpy(out->text, codes, (size_t)n);
+    {
+        int64_t q = 0;
+        for (int32_t k = 0; k < nseq; ++k) {
+            const int64_t b = starts[k], e = k + 1 < nseq ? starts[k + 1] : n;
+            if (k > 0) {
+                joined[q] = 0xFF;
+                jpos[q++] = -1;
+            }
+            for (int64_t p = b; p < e; ++p) {
+                joined[q] = codes[p];
+                jpos[q++] = p;
+            }
+            if (e > b) out->ends[(e - 1) >> 5] |= 1u << ((e - 1) & 31);
+        }
+    }
+    std::vector<int64_t> cnt(sigma, 0);
+    for (int64_t i = 0; i < n; ++i) ++cnt[codes[i]];
+    out->C[0] = (uint32_t)(1 + nsep);
+    for (int c = 0; c < sigma; ++c) out->C[c + 1] = out->C[c] + (uint32_t)cnt[c];
+
+    std::vector<uint32_t> run(sigma, 0);
+    uint32_t seps = 0;
+    out->dollar_row = -1;
+    for (int64_t h = 0; h < N; ++h) {
+        const int64_t k = sa[h];
+        if (k < 0 || k > J) {
+            ae_host_index_free(out);
+            return AE_EINVAL;
+        }
+        // the substrings of row h end at joined position J - 1 - k
+        out->tend[h] = (k < J && jpos[J - 1 - k] >= 0) ? (int32_t)jpos[J - 1 - k] : -1;
+        int code = 0;
+        bool is_sep = false;
+        if (k == 0) {
+            out->dollar_row = h;
+        } else if (joined[J - k] == 0xFF) {
+            is_sep = true;
+        } else {
+            code = joined[J - k];
+        }
+        const int64_t b = h / AE_ROWS_PER_BLOCK, r = h % AE_ROWS_PER_BLOCK;
+        uint32_t *blk = out->occ + b * out->block_words;
+        uint32_t *sb = out->sep + b * AE_SEP_BLOCK_WORDS;
+        if (r == 0) {
+            for (int c = 0; c < sigma; ++c) blk[c] = run[c];
+            sb[0] = seps;
+        }
+        if (alphabet == AE_DNA) {
+            blk[4 + r / 16] |= (uint32_t)code << (2 * (r % 16));
+        } else {
+            uint64_t *planes = (uint64_t *)(blk + 22);
+            for (int t = 0; t < 5; ++t)
+                if ((code >> t) & 1) planes[t] |= 1ull << r;
+        }
+        if (is_sep) {
+            sb[1 + r / 32] |= 1u << (r % 32);
+            ++seps;
+        } else if (k != 0) {
+            ++run[code];
+        }
+    }
+    for (int64_t b = (N + AE_ROWS_PER_BLOCK - 1) / AE_ROWS_PER_BLOCK; b < out->nblocks; ++b) {
+        uint32_t *blk = out->occ + b * out->block_words;
+        for (int c = 0; c < sigma; ++c) blk[c] = run[c];
+        out->sep[b * AE_SEP_BLOCK_WORDS] = seps;
+    }
     return AE_OK;
 }
 
@@ -239,9 +350,13 @@ void ae_host_index_free(HostIndex *h) {
     free(h->occ);
     free(h->tend);
     free(h->text);
+    free(h->sep);
+    free(h->ends);
     h->occ = nullptr;
     h->tend = nullptr;
     h->text = nullptr;
+    h->sep = nullptr;
+    h->ends = nullptr;
 }
 
 // ------------------------------------------------------------------ file format
@@ -277,10 +392,15 @@ ae_status ae_host_index_save(const HostIndex *h, const char *path) {
     FILE *f = fopen(path, "wb");
     if (!f) return AE_EIO;
     Fnv fnv;
-    int64_t hdr[8] = {h->alphabet, h->sigma, h->n, h->dollar_row, h->nblocks, h->block_words, 0, 0};
+    // header words 6 and 7: sequences and BWT rows of a collection (0, 0 for one text)
+    int64_t hdr[8] = {h->alphabet, h->sigma, h->n, h->dollar_row, h->nblocks, h->block_words,
+                      h->nseq, h->nseq ? h->rows : 0};
     bool ok = wr(f, fnv, kMagic, 8) && wr(f, fnv, hdr, sizeof(hdr)) && wr(f, fnv, h->C, sizeof(h->C)) &&
               wr(f, fnv, h->occ, sizeof(uint32_t) * (size_t)(h->nblocks * h->block_words)) &&
-              wr(f, fnv, h->tend, sizeof(int32_t) * (size_t)(h->n + 1)) && wr(f, fnv, h->text, (size_t)h->n);
+              wr(f, fnv, h->tend, sizeof(int32_t) * (size_t)h->rows) && wr(f, fnv, h->text, (size_t)h->n);
+    if (h->nseq)
+        ok = ok && wr(f, fnv, h->sep, sizeof(uint32_t) * (size_t)(h->nblocks * AE_SEP_BLOCK_WORDS)) &&
+             wr(f, fnv, h->ends, sizeof(uint32_t) * (size_t)((h->n + 31) / 32));
     uint64_t sum = fnv.h;
     ok = ok && fwrite(&sum, 1, 8, f) == 8;
     ok = (fclose(f) == 0) && ok;
@@ -302,20 +422,30 @@ ae_status ae_host_index_load(const char *path, HostIndex *h) {
     h->dollar_row = hdr[3];
     h->nblocks = hdr[4];
     h->block_words = (int32_t)hdr[5];
-    if (ae_alphabet_sigma(h->alphabet) != h->sigma || h->n < 1 || h->n + 1 >= INT32_MAX ||
-        h->nblocks != (h->n + 1 + AE_ROWS_PER_BLOCK - 1) / AE_ROWS_PER_BLOCK + 1 ||
+    h->nseq = (int32_t)hdr[6];
+    h->rows = h->nseq ? hdr[7] : h->n + 1;
+    if (ae_alphabet_sigma(h->alphabet) != h->sigma || h->n < 1 || h->rows >= INT32_MAX || h->nseq < 0 ||
+        h->rows != h->n + (h->nseq ? h->nseq : 1) ||
+        h->nblocks != (h->rows + AE_ROWS_PER_BLOCK - 1) / AE_ROWS_PER_BLOCK + 1 ||
         h->block_words != (h->alphabet == AE_DNA ? AE_DNA_BLOCK_WORDS : AE_PROT_BLOCK_WORDS))
         goto done;
     if (!rd(f, fnv, h->C, sizeof(h->C))) goto done;
     h->occ = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(h->nblocks * h->block_words));
-    h->tend = (int32_t *)malloc(sizeof(int32_t) * (size_t)(h->n + 1));
+    h->tend = (int32_t *)malloc(sizeof(int32_t) * (size_t)h->rows);
     h->text = (uint8_t *)malloc((size_t)h->n);
-    if (!h->occ || !h->tend || !h->text) {
+    if (h->nseq) {
+        h->sep = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(h->nblocks * AE_SEP_BLOCK_WORDS));
+        h->ends = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)((h->n + 31) / 32));
+    }
+    if (!h->occ || !h->tend || !h->text || (h->nseq && (!h->sep || !h->ends))) {
         st = AE_ENOMEM;
         goto done;
     }
     if (!rd(f, fnv, h->occ, sizeof(uint32_t) * (size_t)(h->nblocks * h->block_words)) ||
-        !rd(f, fnv, h->tend, sizeof(int32_t) * (size_t)(h->n + 1)) || !rd(f, fnv, h->text, (size_t)h->n))
+        !rd(f, fnv, h->tend, sizeof(int32_t) * (size_t)h->rows) || !rd(f, fnv, h->text, (size_t)h->n))
+        goto done;
+    if (h->nseq && (!rd(f, fnv, h->sep, sizeof(uint32_t) * (size_t)(h->nblocks * AE_SEP_BLOCK_WORDS)) ||
+                    !rd(f, fnv, h->ends, sizeof(uint32_t) * (size_t)((h->n + 31) / 32))))
         goto done;
     {
         uint64_t want = fnv.h, got = 0;

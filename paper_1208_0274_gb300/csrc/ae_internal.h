@@ -32,15 +32,29 @@
 #define AE_PROT_BLOCK_WORDS 32
 #define AE_ROWS_PER_BLOCK 64
 
+// Collections (several sequences indexed as one text, Section 2.3): the BWT
+// is that of the sequences joined by a separator that sorts below every
+// letter.  A separator row stores letter code 0 in its block and is flagged in
+// `sep`: 4 words per occurrence block, the number of separator rows before the
+// block and a 64-bit mask of the block's separator rows (low word first); the
+// block's letter counts leave separators out, and Occ(0, k) subtracts the
+// flagged rows of k's own block.  Positions (tend, text, results) are those of the
+// sequences joined without separators; `ends` has bit p set where position p is
+// the last letter of a sequence, which no alignment may cross.
+#define AE_SEP_BLOCK_WORDS 4
+
 struct IndexView {
     const uint32_t *occ;    // blocks
     const int32_t *tend;    // per BWT row: end position in T of its substrings (-1 = sentinel row)
     const uint8_t *text;    // forward text, letter codes
-    int64_t n;              // text length
+    int64_t n;              // text length (letters, separators not counted)
     int64_t dollar_row;     // BWT row holding the sentinel
-    uint32_t C[AE_MAX_SIGMA + 1];  // C[c] = 1 + number of letters < c; C[sigma] = n + 1
+    uint32_t C[AE_MAX_SIGMA + 1];  // C[c] = 1 + separators + number of letters < c; C[sigma] = rows
     int32_t sigma;
     int32_t alphabet;
+    int64_t rows;           // BWT rows: n + separators + 1
+    const uint32_t *sep;    // collections: separator rows per block (NULL for one sequence)
+    const uint32_t *ends;   // collections: sequence-end bitmap over text positions (NULL for one sequence)
 };
 
 struct ScoreView {
@@ -104,7 +118,8 @@ struct DevStats {
     unsigned long long entries_leaf;
     unsigned long long leaf_max_steps, leaf_max_width;
     unsigned long long leaf_max_cycles;   // longest sweep task (SM clock cycles)
-    unsigned long long pad[2];
+    unsigned long long dominated;         // seed entries dropped by q-prefix domination (Lemma 1)
+    unsigned long long pad;
 };
 
 // ---------------------------------------------------------------- host index
@@ -116,14 +131,24 @@ struct HostIndex {
     int64_t nblocks;
     int32_t block_words;
     uint32_t *occ;     // nblocks * block_words
-    int32_t *tend;     // n + 1
+    int32_t *tend;     // rows
     uint8_t *text;     // n codes
+    int64_t rows;      // BWT rows (n + 1 + separators)
+    int32_t nseq;      // sequences of a collection (0: a single text)
+    uint32_t *sep;     // collections: nblocks * AE_SEP_BLOCK_WORDS
+    uint32_t *ends;    // collections: (n + 31) / 32 words
 };
 
 int ae_alphabet_sigma(int32_t alphabet);
 int ae_encode_letters(const uint8_t *ascii, int64_t n, int32_t alphabet, uint8_t *codes);
 void ae_letter_lut(int32_t alphabet, uint8_t lut[256]);
 ae_status ae_host_index_fill(const uint8_t *codes, int64_t n, int32_t alphabet, const int32_t *sa, HostIndex *out);
+// The index of a collection: codes[0..n) are the sequences back to back,
+// starts[0..nseq) their first positions (starts[0] = 0, non-decreasing); sa is
+// the suffix array of the reversed joined text (nseq - 1 separators of code 0,
+// letters shifted up by one) followed by the sentinel.
+ae_status ae_host_index_fill_collection(const uint8_t *codes, int64_t n, const int64_t *starts, int32_t nseq,
+                                        int32_t alphabet, const int32_t *sa, HostIndex *out);
 void ae_host_index_free(HostIndex *h);
 ae_status ae_host_index_save(const HostIndex *h, const char *path);
 ae_status ae_host_index_load(const char *path, HostIndex *h);

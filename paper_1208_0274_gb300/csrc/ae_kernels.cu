@@ -279,16 +279,31 @@ __global__ void k_seed_nodes(SeedArgs a, const uint64_t *keys, const uint32_t *v
     const uint64_t gmask = (1ull << (bits * a.d0)) - 1ull;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
         aj[t] = (int32_t)vals[t] + a.d0 - 1;
+        // q-prefix domination (Lemma 1): when every occurrence of the gram in T is
+        // preceded by the query letter before its start y, the fork starting at y
+        // is matched letter for letter, one better, by the fork starting at y - 1
+        // (the same text ends, one more match), so its entry starts dead
+        int32_t M0 = a.d0 * a.sc.sa;
+        bool dead = false;
+        if (a.dom && vals[t] > 0) {
+            const WorkItem it = a.items[(int32_t)(keys[t] >> (bits * a.d0))];
+            const int prev = a.qv.codes[a.qv.off[it.qid] + vals[t] - 1];
+            dead = __ldg(a.dom + (keys[t] & gmask)) == (1u << prev);
+        }
+        const unsigned dm = __ballot_sync(__activemask(), dead);
+        if (dead && a.dominated && (threadIdx.x & 31) == __ffs(dm) - 1)
+            atomicAdd(a.dominated, (unsigned long long)__popc(dm));
+        if (dead) M0 = AE_NEG;
         if (a.int16) {
-            reinterpret_cast<uint32_t *>(aM)[t] = pack_mg(a.d0 * a.sc.sa, AE_NEG);
+            reinterpret_cast<uint32_t *>(aM)[t] = pack_mg(M0, AE_NEG);
         } else {
-            aM[t] = a.d0 * a.sc.sa;
+            aM[t] = M0;
             aGa[t] = AE_NEG;
         }
         if (flags[t]) {
             uint64_t key = keys[t];
             uint64_t gram = key & gmask;
-            uint32_t lo = 0, hi = (uint32_t)(a.ix.n + 1);
+            uint32_t lo = 0, hi = (uint32_t)a.ix.rows;
             for (int i = a.d0 - 1; i >= 0; --i) {
                 int c = (int)((gram >> (bits * i)) & ((1u << bits) - 1u));
                 lo = a.ix.C[c] + occ_of<SIGMA>(a.ix, c, lo);
@@ -304,6 +319,37 @@ __global__ void k_seed_nodes(SeedArgs a, const uint64_t *keys, const uint32_t *v
             nd.off = (uint64_t)t;
             nodes[k] = nd;
         }
+    }
+}
+
+// Predecessor masks of the d0-grams of T.  A gram is an occurrence only if it
+// lies inside one sequence (collections); its predecessor is the letter before
+// it, or `sigma` when it starts a sequence.  Small tables are merged per block
+// in shared memory first (the grams of i.i.d. text hit every entry).
+__global__ void k_dom_table(IndexView ix, int d0, int bits, uint32_t *mask, int64_t ngram) {
+    extern __shared__ uint32_t sm_mask[];
+    const bool local = ngram <= 4096;
+    if (local) {
+        for (int64_t g = threadIdx.x; g < ngram; g += blockDim.x) sm_mask[g] = 0;
+        __syncthreads();
+    }
+    const int64_t last = ix.n - d0;   // last start position
+    for (int64_t p = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; p <= last; p += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t gram = 0;
+        bool inside = true;
+        for (int i = 0; i < d0; ++i) {
+            gram = (gram << bits) | ix.text[p + i];
+            if (i + 1 < d0 && seq_end(ix, p + i)) inside = false;
+        }
+        if (!inside) continue;
+        const int prev = (p > 0 && !seq_end(ix, p - 1)) ? (int)ix.text[p - 1] : ix.sigma;
+        if (local) atomicOr(&sm_mask[gram], 1u << prev);
+        else atomicOr(&mask[gram], 1u << prev);
+    }
+    if (local) {
+        __syncthreads();
+        for (int64_t g = threadIdx.x; g < ngram; g += blockDim.x)
+            if (sm_mask[g]) atomicOr(&mask[g], sm_mask[g]);
     }
 }
 
@@ -554,7 +600,7 @@ __global__ void __launch_bounds__(128, AE_LEAF_MINB) k_leaf(LeafArgs a) {
                     continue;
                 }
             }
-            if (rlen > 0 && inreg && p + 1 < a.ix.n) {
+            if (rlen > 0 && inreg && p + 1 < a.ix.n && !seq_end(a.ix, p)) {
                 const bool inj_next = nk_qid == qid && nk_e == p + 1;
                 if (!inj_next) {
                     // ---- fast step: gen + horizontal finish in registers
@@ -731,8 +777,13 @@ __global__ void __launch_bounds__(128, AE_LEAF_MINB) k_leaf(LeafArgs a) {
                     P = a.qv.codes + a.qv.off[qid];
                 }
             } else {
+                // the row ends with the text or its sequence: the walk goes on with
+                // the next injection
+                if (p + 1 >= a.ix.n || seq_end(a.ix, p)) {
+                    rlen = 0;
+                    continue;
+                }
                 ++p;
-                if (p >= a.ix.n) break;
                 if (p < tw_base || p >= tw_base + 32) {
                     tw_base = p;
                     tw = (p + lane < a.ix.n) ? a.ix.text[p + lane] : 0u;
@@ -1184,6 +1235,15 @@ void ae_seed_nodes(const SeedArgs &a, const uint64_t *keys, const uint32_t *vals
         k_seed_nodes<20><<<grid_for(npos, 256), 256, 0, st>>>(a, keys, vals, npos, flags, flag_off, nodes, aj, aM, aGa);
     ++g_launches;
     k_seed_fix<<<grid_for(npos, 256), 256, 0, st>>>(nodes, nnodes_dev, npos);
+}
+
+void ae_dom_table(const IndexView &ix, int d0, uint32_t *mask, cudaStream_t st) {
+    const int bits = ix.sigma == 4 ? 2 : 5;
+    const int64_t ngram = 1ll << (bits * d0);
+    if (ix.n < d0) return;
+    ++g_launches;
+    const size_t smem = ngram <= 4096 ? (size_t)ngram * 4 : 0;
+    k_dom_table<<<grid_for(ix.n, 256, 152 * 8), 256, smem, st>>>(ix, d0, bits, mask, ngram);
 }
 
 void ae_inject_keys(const Inject *inj, int64_t ninj, uint64_t *keys, uint32_t *vals, cudaStream_t st) {

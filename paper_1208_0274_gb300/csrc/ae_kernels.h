@@ -45,7 +45,16 @@ struct SeedArgs {
     int32_t d0;                // seed depth (>= 1)
     int64_t npos;
     int32_t int16;             // 1: write the seed rows as packed int16x2 pairs into aM
+    // q-prefix domination (Lemma 1): per d0-gram (packed as in the seed keys) the
+    // mask of letters that precede its occurrences in T (bit sigma: an occurrence
+    // starting a sequence); NULL = off.  `dominated` counts the dropped entries.
+    const uint32_t *dom;
+    unsigned long long *dominated;
 };
+// Predecessor masks of every d0-gram of the text (the table SeedArgs::dom reads):
+// mask[gram] |= 1 << (letter before the occurrence, or sigma at a sequence start).
+// mask must hold sigma_bits^d0 words and be zeroed.
+void ae_dom_table(const IndexView &ix, int d0, uint32_t *mask, cudaStream_t st);
 // keys = (item << 2*d0... packed gram), vals = query start column y.
 void ae_seed_keys(const SeedArgs &a, uint64_t *keys, uint32_t *vals, cudaStream_t st);
 // After sorting: one node per run of equal keys; writes nodes + level-0 arena.
@@ -96,6 +105,7 @@ struct LevelCounters {
     unsigned long long c_fr_ent, c_fr_node, c_lf_ent, c_lf_node, c_hits;
     unsigned long long fr_ent, fr_node, lf_ent, lf_node, hits;
     unsigned long long overflow, task_c, task_w, wide;   // wide: a task total passed 2^32 - 1
+    unsigned long long triples;   // DNA int16x2 route: (child, parent entry) pairs of the level
 };
 
 struct RowsArgs {
@@ -137,6 +147,42 @@ struct RowsArgs {
 void ae_rows(const RowsArgs &a, bool write, int blocks, cudaStream_t st);
 int ae_rows_blocks_per_sm(bool write);   // blocks per SM to launch a k_rows pass with (one full wave)
 void ae_mg_to_i32(int32_t *M, int32_t *Ga, int64_t n, cudaStream_t st);
+
+// ---- one trie level of the DNA int16x2 route, one lane per parent entry
+// (ae_rows_dna.cu).  Tasks are groups of nodes_per_task (<= 32) nodes whose
+// child ranges are taken in the task's prologue; kcnt/khit (4 per node, by
+// letter) carry each child's outputs and hits from the count to the write pass.
+// The output arguments are those of RowsArgs.
+struct DnaRowsArgs {
+    IndexView ix;
+    ScoreView sc;
+    QueryView qv;
+    const Node *nodes;
+    int64_t nnodes;
+    int32_t nodes_per_task;
+    int32_t leaf_delay;
+    uint64_t urec;                        // ceil(2^32 / u), u = -s_s: gap-run lengths without division
+    const int32_t *pj;                    // parent arena: column, packed (M | G_a << 16)
+    const uint32_t *pmg;
+    uint32_t *kcnt, *khit;                // per (node, letter): entries, hits
+    uint32_t *task_tot;                   // count pass: per arena kind and task, as in RowsArgs
+    const uint64_t *task_off;             // write pass: their exclusive scan (NULL: atomics)
+    uint64_t task_stride;
+    uint64_t base_off[5];
+    int32_t *fj;                          // next-level arena (packed rows)
+    uint32_t *fmg;
+    Node *fnodes;
+    uint64_t fr_ent_cap, fr_node_cap;
+    int32_t *lj, *lM, *lGa;               // leaf arena (int32 rows)
+    Inject *inj;
+    uint64_t lf_ent_cap, lf_node_cap;
+    RangeHit *rhits;
+    uint64_t hit_cap;
+    LevelCounters *ctr;
+    DevStats *stats;
+};
+void ae_rows_dna(const DnaRowsArgs &a, bool write, int blocks, cudaStream_t st);
+int ae_rows_dna_blocks_per_sm(bool write);
 struct LeafArgs {
     IndexView ix;
     ScoreView sc;

@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(FEAT_THREADS) k_features(IndexView ix, const u
     }
     float acc = 0.f;
     for (int64_t p = threadIdx.x; p + K <= m; p += blockDim.x) {
-        uint32_t lo = 0, hi = (uint32_t)(ix.n + 1);
+        uint32_t lo = 0, hi = (uint32_t)ix.rows;
         for (int s = 0; s < K && lo < hi; ++s) {
             const int c = dna_code(seq[b + p + s], bad);
             lo = ix.C[c] + aedev::occ_dna(ix, c, lo);

@@ -1,0 +1,596 @@
+// One trie level of the DNA int16x2 route (Section 5 (3) and Section 2.2),
+// organised around the parent entry.
+//
+// A task is a group of up to 32 frontier nodes, one per lane.  Its prologue
+// takes each node's child ranges for all four letters from one decode of the
+// occurrence block at each end of the node's SA range (Section 5 (3):
+// lo' = C[c] + Occ(c, lo), hi' = C[c] + Occ(c, hi)); a single occurrence has
+// only the child BWT[lo] (one LF step).  The rows of the task's nodes are then
+// laid end to end over the lanes, one parent entry per lane, 32 at a time, and
+// each lane computes the slots of that entry for every child of its node:
+// the vertical gap G_a (the same for all children) once, the diagonal terms per
+// child.  Horizontal gaps are a max-plus scan segmented by node, as in the
+// general kernel (ae_trie.cu).
+//
+//   count pass  per (node, child): output entries and hits; per task: totals
+//               per output arena (scanned on the device into task offsets).
+//   write pass  the same computation again, now writing child node records,
+//               injections, row entries and range hits at the scanned offsets.
+//
+// The general kernel (ae_trie.cu) handles protein, the int32 route, root rows
+// and cost-tier counting; both produce the same nodes and arenas.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ae_device.cuh"
+#include "ae_kernels.h"
+
+namespace {
+using namespace aedev;
+
+constexpr int DW = 8;   // warps per block
+// Resident blocks per SM the passes are compiled for and launched with (64
+// registers a thread; fewer registers spill in the row loop)
+#ifndef AE_DNA_MINB_COUNT
+#define AE_DNA_MINB_COUNT 4
+#endif
+#ifndef AE_DNA_MINB_WRITE
+#define AE_DNA_MINB_WRITE 4
+#endif
+
+// Occ(c, k) for c = A, C, G, T at once from one 32-byte block (layout in
+// ae_internal.h): counts before the block plus the codes of rows [64b, k).
+__device__ __forceinline__ void occ4(const IndexView &ix, uint32_t k, uint32_t (&o)[4], uint64_t &w0, uint64_t &w1) {
+    const uint32_t *blk = ix.occ + (size_t)(k >> 6) * AE_DNA_BLOCK_WORDS;
+    const uint4 cnt = __ldg(reinterpret_cast<const uint4 *>(blk));
+    const uint4 bits = __ldg(reinterpret_cast<const uint4 *>(blk + 4));
+    w0 = (uint64_t)bits.x | ((uint64_t)bits.y << 32);   // rows 0..31 of the block, 2 bits each
+    w1 = (uint64_t)bits.z | ((uint64_t)bits.w << 32);   // rows 32..63
+    const uint32_t r = k & 63;
+    const uint64_t EV = 0x5555555555555555ull;
+    const uint64_t m0 = r >= 32 ? EV : (((1ull << (2 * r)) - 1) & EV);
+    const uint64_t m1 = r <= 32 ? 0ull : (((1ull << (2 * (r - 32))) - 1) & EV);
+    const uint64_t l0 = w0 & EV, h0 = (w0 >> 1) & EV, l1 = w1 & EV, h1 = (w1 >> 1) & EV;
+    const uint32_t nC = __popcll(l0 & ~h0 & m0) + __popcll(l1 & ~h1 & m1);
+    const uint32_t nG = __popcll(~l0 & h0 & m0) + __popcll(~l1 & h1 & m1);
+    const uint32_t nT = __popcll(l0 & h0 & m0) + __popcll(l1 & h1 & m1);
+    uint32_t nA = r - nC - nG - nT;
+    if ((int64_t)(k >> 6) == (ix.dollar_row >> 6) && (uint32_t)(ix.dollar_row & 63) < r) nA -= 1;
+    if (ix.sep) nA -= sep_in_block(ix, k);   // collections: separator rows store code 0
+    o[0] = cnt.x + nA;
+    o[1] = cnt.y + nC;
+    o[2] = cnt.z + nG;
+    o[3] = cnt.w + nT;
+}
+
+// Child ranges of SA range [lo, hi) for the four letters; returns the mask of
+// non-empty children.
+__device__ __forceinline__ unsigned kids4(const IndexView &ix, uint32_t lo, uint32_t hi, uint32_t (&clo)[4],
+                                          uint32_t (&chi)[4]) {
+    uint32_t a[4], b[4];
+    uint64_t w0, w1;
+    occ4(ix, lo, a, w0, w1);
+    if (hi - lo == 1) {
+        if ((int64_t)lo == ix.dollar_row || sep_row(ix, lo)) return 0u;
+        const uint32_t r = lo & 63;
+        const int c = (int)(((r < 32 ? w0 : w1) >> (2 * (r & 31))) & 3ull);
+#pragma unroll
+        for (int x = 0; x < 4; ++x) {
+            clo[x] = ix.C[x] + a[x];
+            chi[x] = clo[x] + (x == c ? 1u : 0u);
+        }
+        return 1u << c;
+    }
+    occ4(ix, hi, b, w0, w1);
+    unsigned mask = 0;
+#pragma unroll
+    for (int x = 0; x < 4; ++x) {
+        clo[x] = ix.C[x] + a[x];
+        chi[x] = ix.C[x] + b[x];
+        if (chi[x] > clo[x]) mask |= 1u << x;
+    }
+    return mask;
+}
+
+// Per-warp shared state of a task: per (node lane, letter) the outputs and
+// hits counted so far (count pass), or the next output positions relative to
+// the task's arena bases and the child's SA range (write pass).
+struct WarpSmem {
+    uint32_t a[128];    // count: entries   write: next entry position
+    uint32_t h[128];    // count: hits      write: next hit position
+    uint32_t lo[128];   // write: child SA range
+    uint32_t hi[128];
+    int32_t carry[4];   // per child index: the G_b scan's carry into the next chunk
+    uint64_t base[3];   // write: the task's first slot in the frontier, leaf and hit arenas
+};
+
+// Length of a gap run (Section 2.2: a horizontal gap extended column by column)
+// without a division: the run after a lane's last slot starts at column rs with
+// G_b = V0 > 0 and loses u per column, so away from the query's last columns
+// (threshold 0) its live cells number floor((V0 - 1) / u) + 1.  The quotient is
+// taken as a product with the reciprocal rec = ceil(2^32 / u), exact for
+// numerators below 2^16 (the int16x2 route keeps every state below 2^15).
+__device__ __forceinline__ uint32_t div_small(uint32_t a, uint64_t rec) {
+    return (uint32_t)(((uint64_t)a * rec) >> 32);
+}
+
+__device__ __forceinline__ uint64_t reduce_add_u64(uint32_t v) {
+    const uint32_t hi = __reduce_add_sync(FULL, v >> 16), lo = __reduce_add_sync(FULL, v & 0xFFFFu);
+    return ((uint64_t)hi << 16) + lo;
+}
+
+__device__ __forceinline__ uint64_t excl_scan_u64(uint64_t v, uint64_t &total) {
+    const int lane = threadIdx.x & 31;
+    uint64_t x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint64_t y = __shfl_up_sync(FULL, x, d);
+        if (lane >= d) x += y;
+    }
+    total = __shfl_sync(FULL, x, 31);
+    return x - v;
+}
+
+template <bool WRITE>
+__global__ void __launch_bounds__(DW * 32, WRITE ? AE_DNA_MINB_WRITE : AE_DNA_MINB_COUNT) k_rows_dna(DnaRowsArgs a) {
+    __shared__ WarpSmem smem[DW];
+    const int lane = threadIdx.x & 31;
+    WarpSmem &sm = smem[threadIdx.x >> 5];
+    const unsigned le = (lane == 31) ? 0xffffffffu : ((1u << (lane + 1)) - 1u);
+    const ScoreView &sc = a.sc;
+    const int32_t u = -sc.ss, oe = sc.sg + sc.ss, g = sc.gmax, sa = sc.sa, sb = sc.sb;
+    const int32_t strong = -oe;   // a gap state from M' can be live only if M' > |s_g + s_s| (Eq. 3)
+    const int64_t nnodes = a.nnodes;
+    const int npt = a.nodes_per_task;
+    const uint64_t ntask = (uint64_t)((nnodes + npt - 1) / npt);
+    unsigned long long *task_ctr = WRITE ? &a.ctr->task_w : &a.ctr->task_c;
+    uint64_t tot_mine = 0;   // count pass: lane q < 5 sums this warp's level total of arena kind q, lane 5 the triples
+    if (!WRITE && a.stats && blockIdx.x == 0 && threadIdx.x == 0)
+        atomicAdd(&a.stats->nodes, (unsigned long long)nnodes);
+
+    for (uint64_t tb = 0;;) {
+        if (lane == 0) tb = atomicAdd(task_ctr, 4ull);
+        tb = __shfl_sync(FULL, tb, 0);
+        if (tb >= ntask) break;
+    for (uint64_t task = tb; task < tb + 4 && task < ntask; ++task) {
+        // ---- prologue: one node per lane
+        const int64_t v = (int64_t)task * npt + lane;
+        const bool own = lane < npt && v < nnodes;
+        Node nd;
+        nd.lo = nd.hi = 0;
+        nd.item = 0;
+        nd.cnt = 0;
+        nd.off = 0;
+        if (own) nd = a.nodes[v];
+        uint32_t clo[4] = {0, 0, 0, 0}, chi[4] = {0, 0, 0, 0};
+        unsigned kmask = own ? kids4(a.ix, nd.lo, nd.hi, clo, chi) : 0u;
+        const uint32_t len = own ? nd.cnt : 0u;
+        if (!len) kmask = 0;
+        const int32_t qid = nd.item & 0xFFFFFF;
+        const uint32_t pcnt = (uint32_t)nd.item >> 24;   // levels the node has been a single occurrence
+        // a child stays in the walk while it has several occurrences, or for the
+        // first leaf_delay levels after it became a single occurrence
+        unsigned smask = 0;   // children that stay in the trie walk
+        if (kmask) {
+            const bool young = (int)pcnt + 1 <= a.leaf_delay;
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (((kmask >> c) & 1u) && (young || chi[c] - clo[c] >= 2)) smask |= 1u << c;
+        }
+        int32_t qm = 1, qH = 1;
+        uint32_t qoff = 0;
+        if (kmask) {
+            qm = a.qv.m[qid];
+            qH = a.qv.H[qid];
+            qoff = (uint32_t)a.qv.off[qid];
+        }
+        const int32_t tbase = qH - 1 - (qm - 1) * g;   // thr(j) = max(tbase + j g, 0), Theorem 2
+        const uint32_t work = kmask ? len : 0u;
+        uint32_t woff = work;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(FULL, woff, d);
+            if (lane >= d) woff += y;
+        }
+        const uint32_t total = __shfl_sync(FULL, woff, 31);
+        woff -= work;
+        if (total == 0) {
+            if (!WRITE && lane < 5) a.task_tot[lane * a.task_stride + task] = 0u;
+            continue;
+        }
+
+        if (!WRITE) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                sm.a[lane * 4 + c] = 0;
+                sm.h[lane * 4 + c] = 0;
+            }
+        } else {
+            // per-child outputs from the count pass -> positions in the task's output ranges
+            uint32_t cn[4] = {0, 0, 0, 0}, ch[4] = {0, 0, 0, 0};
+            uint32_t s_fe = 0, s_le = 0, s_fn = 0, s_ln = 0, s_h = 0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                if ((kmask >> c) & 1u) {
+                    cn[c] = a.kcnt[v * 4 + c];
+                    ch[c] = a.khit[v * 4 + c];
+                    if ((smask >> c) & 1u) {
+                        s_fe += cn[c];
+                        s_fn += cn[c] ? 1u : 0u;
+                    } else {
+                        s_le += cn[c];
+                        s_ln += cn[c] ? 1u : 0u;
+                    }
+                    s_h += ch[c];
+                }
+            }
+            uint64_t tsum[5], base[5];
+            const uint64_t ex_fe = excl_scan_u64(s_fe, tsum[0]);
+            const uint64_t ex_le = excl_scan_u64(s_le, tsum[1]);
+            const uint64_t ex_fn = excl_scan_u64(s_fn, tsum[2]);
+            const uint64_t ex_ln = excl_scan_u64(s_ln, tsum[3]);
+            const uint64_t ex_h = excl_scan_u64(s_h, tsum[4]);
+            if (a.task_off) {
+#pragma unroll
+                for (int q = 0; q < 5; ++q) base[q] = a.base_off[q] + a.task_off[q * a.task_stride + task];
+            } else {
+                unsigned long long r[5] = {0, 0, 0, 0, 0};
+                if (lane == 0) {
+                    r[0] = atomicAdd(&a.ctr->fr_ent, (unsigned long long)tsum[0]);
+                    r[1] = atomicAdd(&a.ctr->lf_ent, (unsigned long long)tsum[1]);
+                    r[2] = atomicAdd(&a.ctr->fr_node, (unsigned long long)tsum[2]);
+                    r[3] = atomicAdd(&a.ctr->lf_node, (unsigned long long)tsum[3]);
+                    r[4] = atomicAdd(&a.ctr->hits, (unsigned long long)tsum[4]);
+                }
+#pragma unroll
+                for (int q = 0; q < 5; ++q) base[q] = __shfl_sync(FULL, r[q], 0);
+            }
+            // the count pass sized every range exactly; a reservation past the end
+            // means the passes disagreed, which is reported, never written
+            const bool ovf = base[0] + tsum[0] > a.fr_ent_cap || base[1] + tsum[1] > a.lf_ent_cap ||
+                             base[2] + tsum[2] > a.fr_node_cap || base[3] + tsum[3] > a.lf_node_cap ||
+                             base[4] + tsum[4] > a.hit_cap;
+            if (ovf) {
+                if (lane == 0) atomicExch(&a.ctr->overflow, 1ull);
+                continue;
+            }
+            if (lane == 0) {
+                sm.base[0] = base[0];
+                sm.base[1] = base[1];
+                sm.base[2] = base[4];
+            }
+            uint64_t efr = ex_fe, elf = ex_le, nfr = ex_fn, nlf = ex_ln, hh = ex_h;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                sm.lo[lane * 4 + c] = clo[c];
+                sm.hi[lane * 4 + c] = chi[c];
+                if (!((kmask >> c) & 1u)) continue;
+                const bool st = (smask >> c) & 1u;
+                const uint64_t e = st ? efr : elf;
+                sm.a[lane * 4 + c] = (uint32_t)e;
+                sm.h[lane * 4 + c] = (uint32_t)hh;
+                if (cn[c]) {
+                    if (st) {
+                        Node cn_;
+                        cn_.lo = clo[c];
+                        cn_.hi = chi[c];
+                        const uint32_t uq = (chi[c] - clo[c] == 1) ? pcnt + 1u : 0u;
+                        cn_.item = (int32_t)((uint32_t)qid | (uq << 24));
+                        cn_.cnt = cn[c];
+                        cn_.off = base[0] + e;
+                        a.fnodes[base[2] + nfr] = cn_;
+                        ++nfr;
+                    } else {
+                        Inject in;
+                        in.qid = qid;
+                        in.e = a.ix.tend[clo[c]];
+                        in.cnt = cn[c];
+                        in.pad = 0;
+                        in.off = base[1] + e;
+                        a.inj[base[3] + nlf] = in;
+                        ++nlf;
+                    }
+                }
+                if (st) efr += cn[c];
+                else elf += cn[c];
+                hh += ch[c];
+            }
+        }
+        __syncwarp();
+
+        // ---- the rows: parent entries laid end to end over the lanes
+        if (lane < 4) sm.carry[lane] = AE_KNEG;
+        __syncwarp();
+        for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+            const uint32_t t = t0 + lane;
+            const bool valid = t < total;
+            int L = 0;
+#pragma unroll
+            for (int step = 16; step > 0; step >>= 1) {
+                const uint32_t o = __shfl_sync(FULL, woff, L + step);
+                if (o <= t) L += step;
+            }
+            const uint32_t k = t - __shfl_sync(FULL, woff, L);
+            const uint32_t nlen = __shfl_sync(FULL, len, L);
+            const uint64_t off = __shfl_sync(FULL, nd.off, L);
+            const unsigned km = __shfl_sync(FULL, kmask, L);
+            const unsigned sm_ = __shfl_sync(FULL, smask, L);
+            const int32_t m = __shfl_sync(FULL, qm, L);
+            const int32_t H = __shfl_sync(FULL, qH, L);
+            const int32_t tb0 = __shfl_sync(FULL, tbase, L);
+            const uint32_t qo = __shfl_sync(FULL, qoff, L);
+            const int32_t eq = WRITE ? __shfl_sync(FULL, qid, L) : 0;   // query of the entry's node
+            const unsigned heads = __ballot_sync(FULL, !valid || k == 0 || lane == 0);
+            const int first_lane = 31 - __clz(heads & le);
+            const bool next_in = (lane < 31) && (((heads >> (lane + 1)) & 1u) == 0);
+            const bool is_last = valid && !next_in;
+            int32_t j = m;
+            uint32_t mg = 0;
+            if (valid) {
+                j = a.pj[off + k];
+                mg = a.pmg[off + k];
+            }
+            const int32_t M = (int32_t)(int16_t)(mg & 0xFFFFu);   // live iff > 0
+            int32_t jn = __shfl_down_sync(FULL, j, 1);
+            int32_t pjv = __shfl_up_sync(FULL, j, 1), pMv = __shfl_up_sync(FULL, M, 1);
+            if (valid) {
+                if (!next_in) jn = (k + 1 < nlen) ? a.pj[off + k + 1] : m;
+                if (lane == first_lane) {
+                    if (k > 0) {
+                        pjv = a.pj[off + k - 1];
+                        pMv = (int32_t)(int16_t)(a.pmg[off + k - 1] & 0xFFFFu);
+                    } else {
+                        pjv = -2;
+                        pMv = 0;
+                    }
+                }
+            }
+            const uint8_t *P = a.qv.codes + qo;
+            const bool adjA = valid && pjv + 1 == j && pMv > 0;
+            const bool hasB = valid && (j + 1 < m) && (j + 1 != jn);
+            const int pA = valid ? (int)P[j] : 255;
+            const int pB = hasB ? (int)P[j + 1] : 255;
+            const int32_t traw = tb0 + j * g;
+            const int32_t tA = max(traw, 0), tB = max(traw + g, 0);
+            int32_t Gap = valid ? gap_from_mg(mg, sc.ss, oe) : AE_NEG;
+            Gap = Gap > tA ? Gap : AE_NEG;
+            const int32_t ju = j * u;
+            // the node continuing from the previous chunk sits at lane 0
+            const uint32_t k_lane0 = __shfl_sync(FULL, k, 0);
+            const bool cont = first_lane == 0 && valid && k_lane0 > 0;
+            const bool goes_on = __shfl_sync(FULL, (int)(valid && k + 1 < nlen), 31) != 0;
+            unsigned rem = valid ? km : 0u;
+#pragma unroll 1
+            for (int i = 0; i < 4; ++i) {
+                const bool has_c = rem != 0;
+                if (!__any_sync(FULL, has_c)) {
+                    if (lane == 0) sm.carry[i] = AE_KNEG;
+                    __syncwarp();
+                    continue;
+                }
+                const int c = has_c ? __ffs(rem) - 1 : 0;
+                rem &= rem - 1;
+                int32_t MpA = AE_NEG, MpB = AE_NEG;
+                if (has_c) {
+                    int32_t DA = adjA ? pMv + (c == pA ? sa : sb) : AE_NEG;
+                    DA = DA > tA ? DA : AE_NEG;
+                    MpA = max(DA, Gap);
+                    int32_t DB = M + (c == pB ? sa : sb);
+                    MpB = (hasB && DB > tB) ? DB : AE_NEG;
+                }
+                const int32_t keyA = MpA > strong ? MpA + ju : AE_KNEG;
+                const int32_t keyB = MpB > strong ? MpB + ju + u : AE_KNEG;
+                int32_t incl = max(keyA, keyB);
+                int32_t excl = AE_KNEG;
+                const int32_t cin = sm.carry[i];
+                if (__any_sync(FULL, incl > AE_KNEG || (cont && cin > AE_KNEG))) {
+#pragma unroll
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const int32_t o = __shfl_up_sync(FULL, incl, d);
+                        if (lane - d >= first_lane) incl = max(incl, o);
+                    }
+                    if (cont) incl = max(incl, cin);
+                    excl = __shfl_up_sync(FULL, incl, 1);
+                    if (lane - 1 < first_lane) excl = cont ? cin : AE_KNEG;
+                }
+                __syncwarp();
+                if (lane == 31) sm.carry[i] = goes_on ? incl : AE_KNEG;
+                // finish: G_b at the slots, then the gap run after them
+                const int32_t GbA = excl > AE_KNEG / 2 ? sc.sg - ju + excl : AE_NEG;
+                const int32_t MA = max(MpA, GbA);
+                const bool aliveA = has_c && MA > tA;
+                int32_t MB = AE_NEG;
+                bool aliveB = false;
+                if (has_c && hasB) {
+                    const int32_t KB = max(excl, keyA);
+                    const int32_t GbB = KB > AE_KNEG / 2 ? sc.sg - ju - u + KB : AE_NEG;
+                    MB = max(MpB, GbB);
+                    aliveB = MB > tB;
+                }
+                // the gap run after the lane's slots: columns [run_start, jn) where only G_b
+                // can live, G_b(x) = V0 - (x - run_start) u
+                int32_t run_len = 0, run_hits = 0;
+                const int32_t run_start = hasB ? j + 2 : j + 1;
+                const int32_t V0 = sc.sg - run_start * u + incl;
+                if (has_c && incl > AE_KNEG / 2 && run_start < jn && V0 > 0) {
+                    const int32_t rl = min((int32_t)div_small((uint32_t)(V0 - 1), a.urec) + 1, jn - run_start);
+                    if (traw + (run_start + rl - 1) * g <= 0) {   // threshold 0 over the whole run
+                        run_len = rl;
+                        if (V0 >= H) run_hits = min(rl, (int32_t)div_small((uint32_t)(V0 - H), a.urec) + 1);
+                    } else {                                       // the query's last columns: exact form
+                        run_of(run_start, jn, incl, sc, m, H, u, run_len, run_hits);
+                    }
+                }
+                const bool st = has_c && ((sm_ >> c) & 1u);
+                const bool hA = st && aliveA && MA >= H, hB = st && aliveB && MB >= H;
+                const uint32_t cnt = (uint32_t)aliveA + (uint32_t)aliveB + (uint32_t)run_len;
+                const uint32_t hcnt = (uint32_t)hA + (uint32_t)hB + (st ? (uint32_t)run_hits : 0u);
+                const unsigned in_seg = le & ~((1u << first_lane) - 1u);
+                uint32_t ci, hi;
+                if (__any_sync(FULL, run_len > 0)) {
+                    ci = cnt;
+#pragma unroll
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const uint32_t x = __shfl_up_sync(FULL, ci, d);
+                        if (lane - d >= first_lane) ci += x;
+                    }
+                } else {
+                    ci = __popc(__ballot_sync(FULL, aliveA) & in_seg) + __popc(__ballot_sync(FULL, aliveB) & in_seg);
+                }
+                if (__any_sync(FULL, run_hits > 0)) {
+                    hi = hcnt;
+#pragma unroll
+                    for (int d = 1; d < 32; d <<= 1) {
+                        const uint32_t y = __shfl_up_sync(FULL, hi, d);
+                        if (lane - d >= first_lane) hi += y;
+                    }
+                } else {
+                    hi = __popc(__ballot_sync(FULL, hA) & in_seg) + __popc(__ballot_sync(FULL, hB) & in_seg);
+                }
+                const int slot = L * 4 + c;
+                if (!WRITE) {
+                    if (is_last && has_c) {
+                        sm.a[slot] += ci;
+                        sm.h[slot] += hi;
+                    }
+                    __syncwarp();
+                    continue;
+                }
+                // ---- write the entries (and the hits of children that stay)
+                uint64_t e0 = 0, h0 = 0;
+                if (has_c) {
+                    e0 = sm.base[st ? 0 : 1] + sm.a[slot] + (ci - cnt);
+                    h0 = sm.base[2] + sm.h[slot] + (hi - hcnt);
+                }
+                __syncwarp();
+                if (is_last && has_c) {
+                    sm.a[slot] += ci;
+                    sm.h[slot] += hi;
+                }
+                // the outputs stay inside their arenas even if the two passes ever
+                // disagreed: such a chunk is reported (overflow) and not written
+                const bool outside = has_c && (e0 + cnt > (st ? a.fr_ent_cap : a.lf_ent_cap) ||
+                                               h0 + hcnt > a.hit_cap);
+                if (__any_sync(FULL, outside)) {
+                    if (lane == 0) atomicExch(&a.ctr->overflow, 1ull);
+                    __syncwarp();
+                    continue;
+                }
+                if (aliveA) {
+                    if (st) {
+                        a.fj[e0] = j;
+                        a.fmg[e0] = pack_mg(MA, Gap);
+                    } else {
+                        a.lj[e0] = j;
+                        a.lM[e0] = MA;
+                        a.lGa[e0] = Gap;
+                    }
+                }
+                if (aliveB) {
+                    const uint64_t eb = e0 + (aliveA ? 1 : 0);
+                    if (st) {
+                        a.fj[eb] = j + 1;
+                        a.fmg[eb] = pack_mg(MB, AE_NEG);
+                    } else {
+                        a.lj[eb] = j + 1;
+                        a.lM[eb] = MB;
+                        a.lGa[eb] = AE_NEG;
+                    }
+                }
+                if (hA || hB) {
+                    const RangeHit base_hit = {sm.lo[slot], sm.hi[slot], eq, 0, 0, 0};
+                    uint64_t hp = h0;
+                    if (hA) {
+                        RangeHit r = base_hit;
+                        r.j = j;
+                        r.score = MA;
+                        a.rhits[hp++] = r;
+                    }
+                    if (hB) {
+                        RangeHit r = base_hit;
+                        r.j = j + 1;
+                        r.score = MB;
+                        a.rhits[hp] = r;
+                    }
+                }
+                if (run_len > 0) {   // each lane writes its own run (a few cells)
+                    const uint64_t er = e0 + (uint64_t)aliveA + (uint64_t)aliveB;
+                    const uint64_t hr = h0 + (uint64_t)hA + (uint64_t)hB;
+                    for (int32_t r = 0; r < run_len; ++r) {
+                        const int32_t col = run_start + r, val = V0 - r * u;
+                        if (st) {
+                            a.fj[er + r] = col;
+                            a.fmg[er + r] = pack_mg(val, AE_NEG);
+                        } else {
+                            a.lj[er + r] = col;
+                            a.lM[er + r] = val;
+                            a.lGa[er + r] = AE_NEG;
+                        }
+                        if (st && r < run_hits) {
+                            RangeHit rh = {sm.lo[slot], sm.hi[slot], eq, col, val, 0};
+                            a.rhits[hr + r] = rh;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        if (!WRITE) {
+            // ---- epilogue: per-child counts for the write pass, task totals per arena
+            uint32_t s_fe = 0, s_le = 0, s_fn = 0, s_ln = 0, s_h = 0;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                if (!((kmask >> c) & 1u)) continue;
+                const uint32_t cn = sm.a[lane * 4 + c], ch = sm.h[lane * 4 + c];
+                a.kcnt[v * 4 + c] = cn;
+                a.khit[v * 4 + c] = ch;
+                if ((smask >> c) & 1u) {
+                    s_fe += cn;
+                    s_fn += cn ? 1u : 0u;
+                } else {
+                    s_le += cn;
+                    s_ln += cn ? 1u : 0u;
+                }
+                s_h += ch;
+            }
+            const uint64_t trip = reduce_add_u64((uint32_t)__popc(kmask) * len);
+            if (lane == 5) tot_mine += trip;
+            uint64_t tt[5];
+            tt[0] = reduce_add_u64(s_fe);
+            tt[1] = reduce_add_u64(s_le);
+            tt[2] = reduce_add_u64(s_fn);
+            tt[3] = reduce_add_u64(s_ln);
+            tt[4] = reduce_add_u64(s_h);
+#pragma unroll
+            for (int q = 0; q < 5; ++q) {
+                if (lane == q) {
+                    tot_mine += tt[q];
+                    a.task_tot[q * a.task_stride + task] = (uint32_t)tt[q];
+                    if (tt[q] > 0xFFFFFFFFull) atomicExch(&a.ctr->wide, 1ull);
+                }
+            }
+        }
+        __syncwarp();
+    }
+    }
+    if (!WRITE && lane == 5 && tot_mine) atomicAdd(&a.ctr->triples, (unsigned long long)tot_mine);
+    if (!WRITE && lane < 5 && tot_mine) {
+        // kind q (fr_ent, lf_ent, fr_node, lf_node, hits) -> its LevelCounters field
+        const int field = (0x43120 >> (4 * lane)) & 0xF;
+        atomicAdd(&a.ctr->c_fr_ent + field, (unsigned long long)tot_mine);
+        if (a.stats && lane < 2) atomicAdd(&a.stats->entries, (unsigned long long)tot_mine);
+    }
+}
+
+}  // namespace
+
+int ae_rows_dna_blocks_per_sm(bool write) { return write ? AE_DNA_MINB_WRITE : AE_DNA_MINB_COUNT; }
+
+void ae_rows_dna(const DnaRowsArgs &a, bool write, int blocks, cudaStream_t st) {
+    if (a.nnodes <= 0) return;
+    ++g_launches;
+    if (write)
+        k_rows_dna<true><<<blocks, DW * 32, 0, st>>>(a);
+    else
+        k_rows_dna<false><<<blocks, DW * 32, 0, st>>>(a);
+}

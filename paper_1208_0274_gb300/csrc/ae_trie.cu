@@ -31,7 +31,7 @@ using namespace aedev;
 template <int SIGMA, typename F>
 __device__ __forceinline__ void for_children(const IndexView &ix, const Node &nd, F f) {
     if (nd.hi - nd.lo == 1) {
-        if ((int64_t)nd.lo == ix.dollar_row) return;
+        if ((int64_t)nd.lo == ix.dollar_row || sep_row(ix, nd.lo)) return;
         const int b = bwt_letter<SIGMA>(ix, nd.lo);
         const uint32_t lo = ix.C[b] + occ_of<SIGMA>(ix, b, nd.lo);
         f(b, lo, lo + 1);

@@ -15,9 +15,12 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 def test_every_declared_symbol_is_exported():
-    hdr = open(os.path.join(ROOT, "include", "ae.h")).read()
-    declared = set(re.findall(r"\b(ae_[a-z_]+)\s*\(", hdr))
-    assert {"ae_index_build", "ae_search", "ae_search_device"} <= declared
+    inc = os.path.join(ROOT, "include")
+    declared = set()
+    for h in sorted(os.listdir(inc)):
+        if h.endswith(".h"):
+            declared |= set(re.findall(r"\b(ae_[a-z0-9_]+)\s*\(", open(os.path.join(inc, h)).read()))
+    assert {"ae_index_build", "ae_search", "ae_search_device", "ae_mlp_forward", "ae_int_peak"} <= declared
     for name in declared:
         assert hasattr(ae.lib, name), name
 
@@ -116,3 +119,21 @@ def test_device_suffix_array_argument_errors_without_device():
                        ((1, 10, 256, 0, 1), ae.AE_EINVAL), ((1, 1 << 31, 4, 0, 1), ae.AE_EUNSUPPORTED)]:
         d_codes, n, sigma, rev, d_sa = args
         assert ae.lib.ae_suffix_array_device(d_codes or None, n, sigma, rev, d_sa or None, None) == want
+
+
+def test_collection_build_rejects_bad_arguments():
+    import ctypes
+    t = np.frombuffer(b"ACGTACGT", dtype=np.uint8)
+    out = ctypes.c_void_p(0)
+    for starts in ([1, 4], [0, 5, 3], [0, 9]):
+        s = np.asarray(starts, dtype=np.int64)
+        st = ae.lib.ae_index_build_collection(t.ctypes.data, t.size, s.ctypes.data, s.size, ae.AE_DNA,
+                                              ctypes.byref(out))
+        assert st == ae.AE_EINVAL, starts
+    s = np.asarray([0], dtype=np.int64)
+    assert ae.lib.ae_index_build_collection(t.ctypes.data, 0, s.ctypes.data, 1, ae.AE_DNA,
+                                            ctypes.byref(out)) == ae.AE_EINVAL
+    bad = np.frombuffer(b"ACGNACGT", dtype=np.uint8)
+    assert ae.lib.ae_index_build_collection(bad.ctypes.data, bad.size, s.ctypes.data, 1, ae.AE_DNA,
+                                            ctypes.byref(out)) == ae.AE_EINVAL
+

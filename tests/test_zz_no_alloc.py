@@ -1,8 +1,8 @@
 """The no-allocation search (ae_search_device_static) against ae_search_device.
 
 ae_search_device_static serves callers that cannot allocate device memory,
-for example code running while a CUDA stream is captured into a graph. Its
-working memory is a fixed array inside the library, shared by every call. The
+for example a process whose device memory is already handed out to another
+allocator. Its working memory is a fixed array inside the library, shared by every call. The
 results must be identical to those of ae_search_device: two different searches
 are run back to back, so the second one starts from the array the first one
 left behind. The file sorts last so a stop at the first failure has already
@@ -77,5 +77,52 @@ def test_static_search_rejects_inputs_beyond_its_limit():
     d_seq, offsets = _device_inputs([P])
     out = torch.empty(16, dtype=torch.uint8, device="cuda")
     st, _ = ae.ae_search_device_static(idx, d_seq.data_ptr(), offsets, Scheme(), [30], out.data_ptr(), 1)
+    assert st == ae.AE_EUNSUPPORTED
+    idx.close()
+
+
+def test_static_search_out_of_array_midway_then_next_call_is_clean():
+    # A one-letter text and query keep every trie node's row m entries wide and
+    # emit a range hit per entry from depth H on, so the hit arena outgrows the
+    # 64 MiB array after ~100 levels of queued kernels: the call must report
+    # AE_EUNSUPPORTED, and must have waited for those kernels before returning.
+    n = m = 20_000
+    T = np.full(n, ord("A"), dtype=np.uint8)
+    idx = ae.ae_index_build(T, ae.AE_DNA)
+    d_seq, offsets = _device_inputs([np.full(m, ord("A"), dtype=np.uint8)])
+    out = torch.empty(16, dtype=torch.uint8, device="cuda")
+    st, _ = ae.ae_search_device_static(idx, d_seq.data_ptr(), offsets, Scheme(1, -3, -5, -2), [20],
+                                       out.data_ptr(), 1)
+    assert st == ae.AE_EUNSUPPORTED
+    idx.close()
+    # the next call, on another stream, sees a clean array and matches ae_search_device
+    wl = dna_small()
+    idx = ae.ae_index_build(wl.text, ae.AE_DNA)
+    d_seq, offsets = _device_inputs(wl.queries)
+    cap = 1 << 17
+    ref = torch.empty(cap * 16, dtype=torch.uint8, device="cuda")
+    st, want = ae.ae_search_device(idx, d_seq.data_ptr(), offsets, wl.scheme, wl.H, ref.data_ptr(), cap)
+    assert st == ae.AE_OK
+    other = torch.cuda.Stream()
+    got_buf = torch.full((cap * 16,), 0xAB, dtype=torch.uint8, device="cuda")
+    torch.cuda.synchronize()
+    st, got = ae.ae_search_device_static(idx, d_seq.data_ptr(), offsets, wl.scheme, wl.H, got_buf.data_ptr(), cap,
+                                         stream=other)
+    assert st == ae.AE_OK and np.array_equal(got, want)
+    assert np.array_equal(_hits(got_buf, int(got.sum())), _hits(ref, int(want.sum())))
+    idx.close()
+
+
+def test_static_search_refuses_a_capturing_stream():
+    wl = dna_small()
+    idx = ae.ae_index_build(wl.text, ae.AE_DNA)
+    d_seq, offsets = _device_inputs(wl.queries)
+    out = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
+    s = torch.cuda.Stream()
+    g = torch.cuda.CUDAGraph()
+    torch.cuda.synchronize()
+    with torch.cuda.graph(g, stream=s):
+        st, _ = ae.ae_search_device_static(idx, d_seq.data_ptr(), offsets, wl.scheme, wl.H, out.data_ptr(),
+                                           out.numel() // 16, stream=s)
     assert st == ae.AE_EUNSUPPORTED
     idx.close()
