@@ -143,6 +143,17 @@ typedef struct {
                                  in T is preceded by the query letter before the fork's start (a table
                                  of the letters preceding each gram is built once per index and seed
                                  depth); 0: keep every fork.  The results are the same */
+    int32_t row_layout;       /* DNA int16x2 kernel: 0 (default) chooses per trie level, 1 walks each
+                                 parent row in one lane per (node, child), 2 spreads each row over the
+                                 lanes one entry per lane.  The results are the same */
+    /* A search split over ranks or devices: with fork_parts = R > 1 the search keeps only part
+     * fork_part (0 <= fork_part < R) of the forks -- the seed subtrees whose gram hashes to the
+     * part (q-prefix seeding), or the start columns j with j % R == fork_part (walks from the
+     * root).  The R parts together cover every fork once, so the per-cell maximum over their
+     * results (ae_hits_merge) is the full search's result set; one part alone may miss a result
+     * or report it with a lower score.  Defaults: 1 and 0 (the whole search). */
+    int32_t fork_parts;
+    int32_t fork_part;
 } ae_options;
 
 /* Fill *opt with the defaults. */
@@ -241,6 +252,22 @@ ae_status ae_search_device_static(const ae_index *idx, const uint8_t *d_seq, con
                                   int32_t nq, const ae_scoring *scoring, const int32_t *H,
                                   const ae_options *opt, ae_hit *d_hits, int64_t capacity,
                                   int64_t *counts, void *stream);
+
+/* Per-cell maximum over the results of several partial searches (Algorithm 1
+ * lines 6-10, the maximum over all forks of a cell, when the forks were split
+ * over searches with ae_options.fork_parts, e.g. over ranks or devices).
+ * d_hits (device, n records) holds results of queries 0..nq-1, d_qid (device,
+ * n int32) the query of each record; positions are < text_len and query ends
+ * < max_query_len.  d_out (device, capacity n) receives one record per
+ * distinct (query, text end, query end) with the largest score, grouped by
+ * query and sorted by (text_end, query_end) -- the order of ae_search --
+ * counts (host, nq) the records per query and *total their number.  The call
+ * allocates and frees its sort buffers and returns after `stream` finished.
+ * The paper has no counterpart (its search runs on one machine).
+ * Errors: AE_EINVAL, AE_EUNSUPPORTED (keys wider than 64 bits), AE_ENOMEM,
+ * AE_ECUDA. */
+ae_status ae_hits_merge(const ae_hit *d_hits, const int32_t *d_qid, int64_t n, int32_t nq, int64_t text_len,
+                        int64_t max_query_len, ae_hit *d_out, int64_t *counts, int64_t *total, void *stream);
 
 /* Working memory.  ae_search and ae_search_device keep one workspace per
  * (index, stream): device buffers that only grow, reused by the next search on

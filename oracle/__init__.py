@@ -15,6 +15,12 @@ Contents (each follows the passage it cites):
   column's V and F crossing between stripes. Pinned bit for bit against
   ``sw_hits`` (``tests/test_oracle_mt.py``); it times the CPU baseline and
   speeds up the large parity windows.
+* ``sw_hits_starts`` — the same problem restricted to alignments that start
+  at given query columns (no floor at 0, a fresh alignment begins only at an
+  allowed column): the share of one part of a search whose forks are split
+  over ranks. Pinned by ``local_bruteforce_starts`` (enumeration of every
+  alignment from an allowed start) and by its union over a partition, which
+  must equal ``sw_hits``.
 * ``sim_bruteforce`` / ``local_bruteforce`` — the similarity of Section 2.1
   taken literally: every global alignment of two strings is enumerated and
   scored (no dynamic programming), then maximised over all start pairs. Used
@@ -81,6 +87,10 @@ def _load():
         lib.ae_oracle_sw_hits_mt.argtypes = [P, ctypes.c_int64, P, ctypes.c_int64, P, ctypes.c_int32,
                                              ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                              ctypes.c_int64, ctypes.c_int32, P, P, P, ctypes.c_int64]
+        lib.ae_oracle_sw_hits_starts.restype = ctypes.c_int64
+        lib.ae_oracle_sw_hits_starts.argtypes = [P, ctypes.c_int64, P, ctypes.c_int64, P, ctypes.c_int32,
+                                                 ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P, P, P, P,
+                                                 ctypes.c_int64]
         lib.ae_oracle_sw_matrix.restype = ctypes.c_int
         lib.ae_oracle_sw_matrix.argtypes = [P, ctypes.c_int64, P, ctypes.c_int64, P, ctypes.c_int32,
                                             ctypes.c_int32, ctypes.c_int32, P]
@@ -177,6 +187,55 @@ def sw_hits_mt(text, query, scheme, H, alphabet=b"ACGT", row_lo=0, threads=None)
         if cnt <= cap:
             return oi[:cnt], oj[:cnt], os_[:cnt]
         cap = int(cnt)
+
+
+def sw_hits_starts(text, query, scheme, H, allowed, alphabet=b"ACGT"):
+    """Results of the alignments that start at query columns y with
+    allowed[y] (0-based): every (i, j, score >= H) of the largest similarity
+    of such an alignment ending at (i, j). The union of these over a partition
+    of the columns, maximised per cell, is sw_hits."""
+    lib = _load()
+    T = np.ascontiguousarray(encode(text, alphabet))
+    P = np.ascontiguousarray(encode(query, alphabet))
+    A = np.ascontiguousarray(np.asarray(allowed, dtype=np.uint8))
+    if A.size != P.size:
+        raise ValueError("one allowed flag per query column")
+    sub = subst_table(scheme, len(alphabet))
+    cap = max(1024, 4 * (T.size + P.size))
+    while True:
+        oi = np.empty(cap, dtype=np.int64)
+        oj = np.empty(cap, dtype=np.int32)
+        os_ = np.empty(cap, dtype=np.int32)
+        cnt = lib.ae_oracle_sw_hits_starts(T.ctypes.data, T.size, P.ctypes.data, P.size, sub.ctypes.data,
+                                           len(alphabet), int(scheme.gap_open), int(scheme.gap_extend), int(H),
+                                           A.ctypes.data, oi.ctypes.data, oj.ctypes.data, os_.ctypes.data, cap)
+        if cnt < 0:
+            raise RuntimeError("oracle failed")
+        if cnt <= cap:
+            return oi[:cnt], oj[:cnt], os_[:cnt]
+        cap = int(cnt)
+
+
+def local_bruteforce_starts(text, query, scheme, allowed, alphabet=b"ACGT"):
+    """S[i][j] = max over x <= i and allowed y <= j of sim(T[x..i], P[y..j])
+    (-inf where no such pair), by enumerating every alignment: the pin of
+    sw_hits_starts on small inputs."""
+    T = encode(text, alphabet).tolist()
+    P = encode(query, alphabet).tolist()
+    delta = subst_table(scheme, len(alphabet)).tolist()
+    n, m = len(T), len(P)
+    S = np.full((n, m), NEG, dtype=np.int64)
+    for i in range(n):
+        for j in range(m):
+            best = NEG
+            for x in range(i + 1):
+                for y in range(j + 1):
+                    if not allowed[y]:
+                        continue
+                    v = max(_alignment_scores(T[x:i + 1], P[y:j + 1], delta, scheme.gap_open, scheme.gap_extend))
+                    best = max(best, v)
+            S[i, j] = best
+    return S
 
 
 def sw_matrix(text, query, scheme, alphabet=b"ACGT"):

@@ -352,3 +352,65 @@ int64_t ae_oracle_sw_hits_mt(const uint8_t *T, int64_t n, const uint8_t *P, int6
     free(J.c0); free((void *)J.done); free(J.edgeV); free(J.edgeF); free(th); free(args);
     return result;
 }
+
+/* ---------------------------------------------------------------- restricted starts
+ *
+ * ae_oracle_sw_hits_starts: the largest similarity of alignments ending at
+ * (i, j) that START at a query column y with allowed[y] != 0 (0-based), for
+ * every cell, reported where it reaches H.  This is the result of the forks
+ * one part of a split search owns; the maximum over a partition of the query
+ * columns is the unrestricted value of ae_oracle_sw_hits at every cell >= H.
+ * Written as the Gotoh recurrence without the floor at 0 (a floor would
+ * re-start the alignment at any column): S = best restricted alignment ending
+ * at the cell, E / F its vertical / horizontal gap states, and a fresh
+ * alignment may begin only by pairing T[i] with an allowed P[j]:
+ *     D(i,j) = delta(T[i],P[j]) + max(S(i-1,j-1), allowed[j] ? 0 : -inf)
+ *     E(i,j) = max(E(i-1,j) + s_s, S(i-1,j) + s_g + s_s)
+ *     F(i,j) = max(F(i,j-1) + s_s, S(i,j-1) + s_g + s_s)
+ *     S(i,j) = max(D, E, F),   S = E = F = -inf outside the matrix.
+ * (An optimal alignment never starts with a gap.)  Same arguments and
+ * return convention as ae_oracle_sw_hits plus the allowed[0..m) mask.
+ */
+int64_t ae_oracle_sw_hits_starts(const uint8_t *T, int64_t n, const uint8_t *P, int64_t m,
+                                 const int32_t *subst, int32_t sigma,
+                                 int32_t gap_open, int32_t gap_extend, int32_t H,
+                                 const uint8_t *allowed,
+                                 int64_t *out_i, int32_t *out_j, int32_t *out_s, int64_t cap)
+{
+    if (n < 0 || m < 0 || sigma <= 0 || !subst || (m > 0 && !allowed)) return -1;
+    if (n == 0 || m == 0) return 0;
+    int64_t *Sp = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m + 1));
+    int64_t *Sc = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m + 1));
+    int64_t *E = (int64_t *)malloc(sizeof(int64_t) * (size_t)(m + 1));
+    if (!Sp || !Sc || !E) { free(Sp); free(Sc); free(E); return -1; }
+    const int64_t open_ext = (int64_t)gap_open + gap_extend;
+    for (int64_t j = 0; j <= m; ++j) { Sp[j] = ORACLE_NEG; E[j] = ORACLE_NEG; }
+    int64_t count = 0;
+    for (int64_t i = 1; i <= n; ++i) {
+        const int32_t *row = subst + (int64_t)T[i - 1] * sigma;
+        int64_t F = ORACLE_NEG;
+        Sc[0] = ORACLE_NEG;
+        for (int64_t j = 1; j <= m; ++j) {
+            E[j] = max2(E[j] + gap_extend, Sp[j] + open_ext);
+            F = max2(F + gap_extend, Sc[j - 1] + open_ext);
+            int64_t prev = Sp[j - 1];
+            if (allowed[j - 1]) prev = max2(prev, 0);
+            int64_t v = prev + row[P[j - 1]];
+            v = max2(v, E[j]);
+            v = max2(v, F);
+            if (v < ORACLE_NEG) v = ORACLE_NEG;   /* keep -inf from drifting */
+            Sc[j] = v;
+            if (v >= H) {
+                if (count < cap) {
+                    out_i[count] = i - 1;
+                    out_j[count] = (int32_t)(j - 1);
+                    out_s[count] = (int32_t)v;
+                }
+                ++count;
+            }
+        }
+        int64_t *t = Sp; Sp = Sc; Sc = t;
+    }
+    free(Sp); free(Sc); free(E);
+    return count;
+}

@@ -45,7 +45,8 @@ class ae_options(ctypes.Structure):
                 ("leaf_delay", ctypes.c_int32), ("int16_limit", ctypes.c_int32),
                 ("hint_hits", ctypes.c_void_p), ("tier_stats", ctypes.c_int32),
                 ("workspace_limit", ctypes.c_int64), ("general_rows", ctypes.c_int32),
-                ("qprefix_domination", ctypes.c_int32)]
+                ("qprefix_domination", ctypes.c_int32), ("row_layout", ctypes.c_int32),
+                ("fork_parts", ctypes.c_int32), ("fork_part", ctypes.c_int32)]
 
 
 class ae_stats(ctypes.Structure):
@@ -86,6 +87,7 @@ def _load():
         "ae_search_device": (I32, [V, V, V, I32, V, V, V, V, I64, V, V]),
         "ae_search_device_static": (I32, [V, V, V, I32, V, V, V, V, I64, V, V]),
         "ae_workspace_info": (I32, [V, V, V, V]),
+        "ae_hits_merge": (I32, [V, V, I64, I32, I64, I64, V, V, V, V]),
         "ae_mlp_create": (I32, [ctypes.c_uint64, V]),
         "ae_mlp_free": (None, [V]),
         "ae_mlp_set_params": (I32, [V, V]),
@@ -317,6 +319,19 @@ def ae_search_device_static(index, d_seq_ptr, offsets, scheme, H, d_hits_ptr, ca
     if st not in (AE_OK, AE_EOVERFLOW, AE_EUNSUPPORTED):
         _check(st, "ae_search_device_static")
     return st, counts[:nq].copy()
+
+
+def ae_hits_merge(d_hits_ptr, d_qid_ptr, n, nq, text_len, max_query_len, d_out_ptr, stream=None):
+    """Per-cell maximum of n device result records (with device query ids) from
+    partial searches. Returns (counts per query, total) of the records written
+    to d_out (device, capacity n), grouped by query and sorted like ae_search."""
+    counts = np.zeros(max(nq, 1), dtype=np.int64)
+    total = ctypes.c_int64(0)
+    _check(lib.ae_hits_merge(ctypes.c_void_p(int(d_hits_ptr)) if n else None,
+                             ctypes.c_void_p(int(d_qid_ptr)) if n else None, int(n), int(nq), int(text_len),
+                             int(max_query_len), ctypes.c_void_p(int(d_out_ptr)) if n else None,
+                             counts.ctypes.data, ctypes.byref(total), _stream_handle(stream)), "ae_hits_merge")
+    return counts[:nq].copy(), total.value
 
 
 def ae_workspace_info(index, stream=None):

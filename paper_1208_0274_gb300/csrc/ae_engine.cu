@@ -514,6 +514,8 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
         // the domination table is allocated once per index (never from the static array)
         sa.dom = (opt.qprefix_domination && !g_arena) ? dom_table(idx, d0, st) : nullptr;
         sa.dominated = (unsigned long long *)((char *)w->stats.p + offsetof(DevStats, dominated));
+        sa.parts = opt.fork_parts;
+        sa.part = opt.fork_part;
         ensure(w->sk0, npos * 8, st);
         ensure(w->sv0, npos * 4, st);
         ensure(w->sk1, npos * 8, st);
@@ -651,6 +653,8 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
         ra.leaf_delay = opt.leaf_delay;
         ra.int16 = i16 ? 1 : 0;
         ra.tiers = opt.tier_stats ? 1 : 0;
+        ra.parts = opt.fork_parts;
+        ra.part = opt.fork_part;
         // count pass: exact output sizes of this level
         LevelCounters h0;
         memset(&h0, 0, sizeof(h0));
@@ -760,6 +764,12 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
     stats.ms_reduce += ms_since(t2);
 }
 
+// Average parent-row length up to which a level's rows are walked one lane per
+// (node, child) rather than spread one entry per lane
+#ifndef AE_SEQ_ROW_AVG
+#define AE_SEQ_ROW_AVG 24
+#endif
+
 // One trie level of the DNA int16x2 route (ae_rows_dna.cu): count pass, scan
 // of the per-task totals, exact sizing of the next arenas from the level
 // totals, write pass.  Nodes and arenas have the layout of the general route.
@@ -797,6 +807,9 @@ void Search::dna_level(int64_t &F, int cur, int64_t &cur_ent, int64_t &lf_ent_ba
         const uint64_t u = (uint64_t)(-(int64_t)sc.ss);
         da.urec = ((1ull << 32) + u - 1) / u;
     }
+    // short parent rows are walked one lane per (node, child); long rows spread
+    // over the lanes (a lone long row would hold its warp alone)
+    da.sequential = (opt.row_layout == 1) || (opt.row_layout == 0 && cur_ent <= AE_SEQ_ROW_AVG * F) ? 1 : 0;
     da.pj = ptr<int32_t>(w->aj[cur]);
     da.pmg = ptr<uint32_t>(w->aM[cur]);
     da.kcnt = ptr<uint32_t>(w->kcnt);
@@ -1135,6 +1148,7 @@ ae_status search_core(const ae_index *idx, Workspace *w, const int64_t *offsets,
     memset(&s.stats, 0, sizeof(s.stats));
     ae_options_default(&s.opt);
     if (opt) s.opt = *opt;
+    if (s.opt.fork_parts < 1 || s.opt.fork_part < 0 || s.opt.fork_part >= s.opt.fork_parts) return AE_EINVAL;
     if (s.opt.item_columns < 1 || s.opt.batch_columns < 1 || s.opt.leaf_capacity < 64 || s.opt.leaf_segment < 0 ||
         s.opt.leaf_delay < 0 || s.opt.leaf_delay > 14 || s.opt.int16_limit < 0 || s.opt.int16_limit > 32000)
         return AE_EINVAL;
@@ -1335,6 +1349,9 @@ void ae_options_default(ae_options *opt) {
     opt->workspace_limit = 0;
     opt->general_rows = 0;
     opt->qprefix_domination = 1;
+    opt->row_layout = 0;
+    opt->fork_parts = 1;
+    opt->fork_part = 0;
 }
 
 const char *ae_strerror(int32_t status) {
@@ -1546,6 +1563,62 @@ ae_status ae_search_device(const ae_index *idx, const uint8_t *d_seq, const int6
         return AE_ENOMEM;
     }
     return AE_OK;
+}
+
+ae_status ae_hits_merge(const ae_hit *d_hits, const int32_t *d_qid, int64_t n, int32_t nq, int64_t text_len,
+                        int64_t max_query_len, ae_hit *d_out, int64_t *counts, int64_t *total, void *stream) {
+    if (n < 0 || nq < 1 || text_len < 1 || max_query_len < 1 || !counts || !total || (n > 0 && (!d_hits || !d_qid || !d_out)))
+        return AE_EINVAL;
+    const int be = bits_for(std::max<int64_t>(text_len - 1, 1)), bj = bits_for(std::max<int64_t>(max_query_len - 1, 1));
+    const int bq = bits_for(std::max(nq - 1, 1));
+    if (be + bj + bq > 64) return AE_EUNSUPPORTED;
+    for (int32_t q = 0; q < nq; ++q) counts[q] = 0;
+    *total = 0;
+    if (n == 0) return AE_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<void *> bufs;
+    auto alloc = [&](size_t bytes) -> void * {
+        void *p = nullptr;
+        if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+            cudaGetLastError();
+            throw ae_error{AE_ENOMEM};
+        }
+        bufs.push_back(p);
+        return p;
+    };
+    ae_status res = AE_OK;
+    try {
+        uint64_t *k0 = (uint64_t *)alloc(8 * (size_t)n), *k1 = (uint64_t *)alloc(8 * (size_t)n);
+        uint32_t *v0 = (uint32_t *)alloc(4 * (size_t)n), *v1 = (uint32_t *)alloc(4 * (size_t)n);
+        uint64_t *tmp = (uint64_t *)alloc(8 * (size_t)std::max(ae_sort_tmp_words(n), ae_scan_tmp_words(n, 1)));
+        uint32_t *flags = (uint32_t *)alloc(4 * (size_t)n);
+        uint64_t *off = (uint64_t *)alloc(8 * (size_t)n), *tot = (uint64_t *)alloc(64);
+        unsigned long long *qc = (unsigned long long *)alloc(8 * (size_t)nq);
+        CU(cudaMemsetAsync(qc, 0, 8 * (size_t)nq, st));
+        ae_merge_keys(d_hits, d_qid, n, be, bj, k0, v0, st);
+        const int which = ae_radix_sort(k0, v0, k1, v1, n, be + bj + bq, tmp, st);
+        const uint64_t *keys = which ? k1 : k0;
+        const int32_t *scores = (const int32_t *)(which ? v1 : v0);
+        ae_unique_flags(keys, n, flags, st);
+        const uint32_t *in[1] = {flags};
+        uint64_t *out[1] = {off};
+        ae_scan_u32(in, out, 1, n, tot, tmp, st);
+        ae_unique_write(keys, scores, n, off, be, bj, d_out, qc, st);
+        std::vector<unsigned long long> hq(nq);
+        uint64_t u = 0;
+        CU(cudaMemcpyAsync(&u, tot, 8, cudaMemcpyDeviceToHost, st));
+        CU(cudaMemcpyAsync(hq.data(), qc, 8 * (size_t)nq, cudaMemcpyDeviceToHost, st));
+        CU(cudaStreamSynchronize(st));
+        CU(cudaGetLastError());
+        for (int32_t q = 0; q < nq; ++q) counts[q] = (int64_t)hq[q];
+        *total = (int64_t)u;
+    } catch (const ae_error &e) {
+        cudaStreamSynchronize(st);
+        cudaGetLastError();
+        res = e.st;
+    }
+    for (void *p : bufs) cudaFree(p);
+    return res;
 }
 
 ae_status ae_workspace_info(const ae_index *idx, void *stream, int64_t *bytes, int64_t *process_bytes) {

@@ -247,6 +247,12 @@ __global__ void k_encode(const uint8_t *ascii, uint8_t *codes, int64_t total, in
 
 // ------------------------------------------------------------------ seed (Theorem 3)
 
+// The part of a seed subtree (its gram) when one search is split over ranks:
+// a multiplicative hash spreads neighbouring grams over the parts.
+__device__ __forceinline__ int fork_part(uint64_t gram, int parts) {
+    return (int)((uint32_t)((gram * 0x9E3779B97F4A7C15ull) >> 32) % (uint32_t)parts);
+}
+
 __global__ void k_seed_keys(SeedArgs a, uint64_t *keys, uint32_t *vals) {
     const int bits = a.ix.sigma == 4 ? 2 : 5;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < a.npos;
@@ -291,6 +297,8 @@ __global__ void k_seed_nodes(SeedArgs a, const uint64_t *keys, const uint32_t *v
             dead = __ldg(a.dom + (keys[t] & gmask)) == (1u << prev);
         }
         const unsigned dm = __ballot_sync(__activemask(), dead);
+        // a search split over ranks keeps the seed subtrees of its own part
+        if (a.parts > 1 && fork_part(keys[t] & gmask, a.parts) != a.part) dead = true;
         if (dead && a.dominated && (threadIdx.x & 31) == __ffs(dm) - 1)
             atomicAdd(a.dominated, (unsigned long long)__popc(dm));
         if (dead) M0 = AE_NEG;
@@ -1103,6 +1111,16 @@ __global__ void k_locate(const RangeHit *rh, int64_t n, const uint64_t *off, int
     }
 }
 
+// Keys (query, text end, query end) of result records to merge, their scores as values.
+__global__ void k_merge_keys(const ae_hit *hits, const int32_t *qid, int64_t N, int be, int bj, uint64_t *key,
+                             uint32_t *val) {
+    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
+        const ae_hit h = hits[t];
+        key[t] = ((uint64_t)(uint32_t)qid[t] << (be + bj)) | ((uint64_t)h.text_end << bj) | (uint64_t)(uint32_t)h.query_end;
+        val[t] = (uint32_t)h.score;
+    }
+}
+
 __global__ void k_unique_flags(const uint64_t *key, int64_t N, uint32_t *flags) {
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x)
         flags[t] = (t == 0 || key[t] != key[t - 1]) ? 1u : 0u;
@@ -1271,6 +1289,13 @@ void ae_locate(const RangeHit *rh, int64_t nrh, const uint64_t *off, int64_t tot
     if (total <= 0) return;
     ++g_launches;
     k_locate<<<grid_for(total, 256), 256, 0, st>>>(rh, nrh, off, total, tend, be, bj, key, score);
+}
+
+void ae_merge_keys(const ae_hit *hits, const int32_t *qid, int64_t N, int be, int bj, uint64_t *key, uint32_t *val,
+                   cudaStream_t st) {
+    if (N <= 0) return;
+    ++g_launches;
+    k_merge_keys<<<grid_for(N, 256), 256, 0, st>>>(hits, qid, N, be, bj, key, val);
 }
 
 void ae_unique_flags(const uint64_t *key, int64_t N, uint32_t *flags, cudaStream_t st) {

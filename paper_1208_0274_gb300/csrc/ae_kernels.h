@@ -50,6 +50,9 @@ struct SeedArgs {
     // starting a sequence); NULL = off.  `dominated` counts the dropped entries.
     const uint32_t *dom;
     unsigned long long *dominated;
+    // fork partition (one query's search split over ranks): with parts > 1 only
+    // the seed grams whose hash falls in part `part` start forks here
+    int32_t parts, part;
 };
 // Predecessor masks of every d0-gram of the text (the table SeedArgs::dom reads):
 // mask[gram] |= 1 << (letter before the occurrence, or sigma at a sequence start).
@@ -139,6 +142,8 @@ struct RowsArgs {
     uint64_t base_off[5];
     int32_t int16;                        // 1: parent and frontier rows are packed int16x2 (M | G_a << 16) in pM / fM
     int32_t tiers;                        // 1: count entries by cost tier (ae_stats.entries_tier)
+    int32_t parts, part;                  // root rows: with parts > 1 only start columns j with
+                                          // j % parts == part open forks (a search split over ranks)
     // int16x2 route without tier counting: per triple the final slot values of the count
     // pass (M_A | M_B << 16, 0 = dead) and the key K of its gap run (AE_KNEG: none)
     uint32_t *res;
@@ -162,6 +167,8 @@ struct DnaRowsArgs {
     int32_t nodes_per_task;
     int32_t leaf_delay;
     uint64_t urec;                        // ceil(2^32 / u), u = -s_s: gap-run lengths without division
+    int32_t sequential;                   // 1: one lane per (node, child) walking the parent row in order
+                                          // (short rows); 0: one lane per parent entry (long rows)
     const int32_t *pj;                    // parent arena: column, packed (M | G_a << 16)
     const uint32_t *pmg;
     uint32_t *kcnt, *khit;                // per (node, letter): entries, hits
@@ -213,6 +220,10 @@ int64_t ae_leaf_scratch_words(int32_t cap, int32_t nwarps);
 void ae_locate_counts(const RangeHit *rh, int64_t nrh, uint32_t *cnt, cudaStream_t st);
 void ae_locate(const RangeHit *rh, int64_t nrh, const uint64_t *off, int64_t total, const int32_t *tend, int be,
                int bj, uint64_t *key, int32_t *score, cudaStream_t st);
+
+// Result records (with per-record query ids) -> sort keys (query, text end, query end) and scores.
+void ae_merge_keys(const ae_hit *hits, const int32_t *qid, int64_t N, int be, int bj, uint64_t *key, uint32_t *val,
+                   cudaStream_t st);
 
 // Sorted (key, score) -> unique keys with max score.
 void ae_unique_flags(const uint64_t *key, int64_t N, uint32_t *flags, cudaStream_t st);

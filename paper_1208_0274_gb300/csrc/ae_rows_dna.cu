@@ -131,7 +131,176 @@ __device__ __forceinline__ uint64_t excl_scan_u64(uint64_t v, uint64_t &total) {
     return x - v;
 }
 
+// Rows of short parent rows, one lane per (node, child): the lane walks the
+// parent row entry by entry in column order and carries the horizontal gap as
+// a running key (the recurrence of Section 2.2 in its sequential form), so no
+// scan, vote or compaction is needed; siblings sit in adjacent lanes and read
+// the same parent entries.  Count pass: the pair's entries and hits go to its
+// (node, letter) slot.  Write pass: the pair writes its child row from the
+// slot's position on.  The values equal those of the lane-per-entry form.
 template <bool WRITE>
+__device__ __forceinline__ void rows_seq(const DnaRowsArgs &a, WarpSmem &sm, int lane, unsigned kmask, unsigned smask,
+                                         uint32_t len, uint64_t noff, int32_t qm, int32_t qH, int32_t tbase,
+                                         uint32_t qoff, int32_t qid) {
+    const ScoreView &sc = a.sc;
+    const int32_t u = -sc.ss, oe = sc.sg + sc.ss, g = sc.gmax, sa = sc.sa, sb = sc.sb;
+    const int32_t strong = -oe;
+    const uint32_t np = __popc(kmask);   // pairs of this node lane
+    uint32_t poff = np;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, poff, d);
+        if (lane >= d) poff += y;
+    }
+    const uint32_t npairs = __shfl_sync(FULL, poff, 31);
+    poff -= np;
+    for (uint32_t p0 = 0; p0 < npairs; p0 += 32) {
+        const uint32_t p = p0 + lane;
+        const bool valid = p < npairs;
+        int L = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const uint32_t o = __shfl_sync(FULL, poff, L + step);
+            if (o <= p) L += step;
+        }
+        const uint32_t i = p - __shfl_sync(FULL, poff, L);
+        unsigned km = __shfl_sync(FULL, kmask, L);
+        const unsigned smL = __shfl_sync(FULL, smask, L);
+        const uint32_t nlen = __shfl_sync(FULL, len, L);
+        const uint64_t off = __shfl_sync(FULL, noff, L);
+        const int32_t m = __shfl_sync(FULL, qm, L), H = __shfl_sync(FULL, qH, L);
+        const int32_t tb0 = __shfl_sync(FULL, tbase, L);
+        const uint32_t qo = __shfl_sync(FULL, qoff, L);
+        const int32_t eq = __shfl_sync(FULL, qid, L);
+        if (!valid) continue;
+        for (uint32_t x = 0; x < i; ++x) km &= km - 1;   // the i-th child letter of the node
+        const int c = __ffs(km) - 1;
+        const bool st = (smL >> c) & 1u;
+        const int slot = L * 4 + c;
+        const uint8_t *P = a.qv.codes + qo;
+        uint64_t eout = 0, hout = 0, ecap = 0;
+        uint32_t clo = 0, chi = 0;
+        if (WRITE) {
+            eout = sm.base[st ? 0 : 1] + sm.a[slot];
+            hout = sm.base[2] + sm.h[slot];
+            ecap = st ? a.fr_ent_cap : a.lf_ent_cap;
+            clo = sm.lo[slot];
+            chi = sm.hi[slot];
+        }
+        uint32_t cnt = 0, hcnt = 0;
+        bool bad = false;
+        int32_t K = AE_KNEG, prev_j = -2, prev_M = 0;
+        int32_t jn = a.pj[off];
+        uint32_t mgn = a.pmg[off];
+        for (uint32_t k = 0; k < nlen; ++k) {
+            const int32_t j = jn;
+            const uint32_t mg = mgn;
+            if (k + 1 < nlen) {
+                jn = a.pj[off + k + 1];
+                mgn = a.pmg[off + k + 1];
+            } else {
+                jn = m;
+            }
+            const int32_t M = (int32_t)(int16_t)(mg & 0xFFFFu);
+            const int32_t traw = tb0 + j * g;
+            const int32_t tA = max(traw, 0), tB = max(traw + g, 0);
+            const int32_t ju = j * u;
+            int32_t Gap = gap_from_mg(mg, sc.ss, oe);
+            Gap = Gap > tA ? Gap : AE_NEG;
+            int32_t DA = (prev_j + 1 == j && prev_M > 0) ? prev_M + (c == (int)P[j] ? sa : sb) : AE_NEG;
+            DA = DA > tA ? DA : AE_NEG;
+            const int32_t MpA = max(DA, Gap);
+            const int32_t MA = max(MpA, K > AE_KNEG / 2 ? sc.sg - ju + K : AE_NEG);
+            const bool aliveA = MA > tA;
+            if (MpA > strong) K = max(K, MpA + ju);
+            const bool hasB = (j + 1 < m) && (j + 1 != jn);
+            int32_t MB = AE_NEG;
+            bool aliveB = false;
+            if (hasB) {
+                const int32_t DB = M + (c == (int)P[j + 1] ? sa : sb);
+                const int32_t MpB = DB > tB ? DB : AE_NEG;
+                MB = max(MpB, K > AE_KNEG / 2 ? sc.sg - ju - u + K : AE_NEG);
+                aliveB = MB > tB;
+                if (MpB > strong) K = max(K, MpB + ju + u);
+            }
+            // the gap run after the slots: columns [rs, jn) where only G_b lives
+            int32_t run_len = 0, run_hits = 0;
+            const int32_t rs = hasB ? j + 2 : j + 1;
+            const int32_t V0 = sc.sg - rs * u + K;
+            if (K > AE_KNEG / 2 && rs < jn && V0 > 0) {
+                const int32_t rl = min((int32_t)div_small((uint32_t)(V0 - 1), a.urec) + 1, jn - rs);
+                if (traw + (rs + rl - 1) * g <= 0) {
+                    run_len = rl;
+                    if (V0 >= H) run_hits = min(rl, (int32_t)div_small((uint32_t)(V0 - H), a.urec) + 1);
+                } else {
+                    run_of(rs, jn, K, sc, m, H, u, run_len, run_hits);
+                }
+            }
+            const bool hA = st && aliveA && MA >= H, hB = st && aliveB && MB >= H;
+            if (!WRITE) {
+                cnt += (uint32_t)aliveA + (uint32_t)aliveB + (uint32_t)run_len;
+                hcnt += (uint32_t)hA + (uint32_t)hB + (st ? (uint32_t)run_hits : 0u);
+            } else if (!bad) {
+                if (eout + cnt + (uint32_t)aliveA + (uint32_t)aliveB + (uint32_t)run_len > ecap) {
+                    bad = true;   // the passes disagree: reported, not written
+                } else {
+                    if (aliveA) {
+                        if (st) {
+                            a.fj[eout + cnt] = j;
+                            a.fmg[eout + cnt] = pack_mg(MA, Gap);
+                        } else {
+                            a.lj[eout + cnt] = j;
+                            a.lM[eout + cnt] = MA;
+                            a.lGa[eout + cnt] = Gap;
+                        }
+                        ++cnt;
+                        if (hA && hout + hcnt < a.hit_cap) a.rhits[hout + hcnt++] = RangeHit{clo, chi, eq, j, MA, 0};
+                        else if (hA) bad = true;
+                    }
+                    if (aliveB) {
+                        if (st) {
+                            a.fj[eout + cnt] = j + 1;
+                            a.fmg[eout + cnt] = pack_mg(MB, AE_NEG);
+                        } else {
+                            a.lj[eout + cnt] = j + 1;
+                            a.lM[eout + cnt] = MB;
+                            a.lGa[eout + cnt] = AE_NEG;
+                        }
+                        ++cnt;
+                        if (hB && hout + hcnt < a.hit_cap) a.rhits[hout + hcnt++] = RangeHit{clo, chi, eq, j + 1, MB, 0};
+                        else if (hB) bad = true;
+                    }
+                    for (int32_t r = 0; r < run_len; ++r) {
+                        const int32_t col = rs + r, val = V0 - r * u;
+                        if (st) {
+                            a.fj[eout + cnt] = col;
+                            a.fmg[eout + cnt] = pack_mg(val, AE_NEG);
+                        } else {
+                            a.lj[eout + cnt] = col;
+                            a.lM[eout + cnt] = val;
+                            a.lGa[eout + cnt] = AE_NEG;
+                        }
+                        ++cnt;
+                        if (st && r < run_hits) {
+                            if (hout + hcnt < a.hit_cap) a.rhits[hout + hcnt++] = RangeHit{clo, chi, eq, col, val, 0};
+                            else bad = true;
+                        }
+                    }
+                }
+            }
+            prev_j = j;
+            prev_M = M;
+        }
+        if (!WRITE) {
+            sm.a[slot] = cnt;
+            sm.h[slot] = hcnt;
+        } else if (bad) {
+            atomicExch(&a.ctr->overflow, 1ull);
+        }
+    }
+}
+
+template <bool WRITE, bool SEQ>
 __global__ void __launch_bounds__(DW * 32, WRITE ? AE_DNA_MINB_WRITE : AE_DNA_MINB_COUNT) k_rows_dna(DnaRowsArgs a) {
     __shared__ WarpSmem smem[DW];
     const int lane = threadIdx.x & 31;
@@ -298,10 +467,14 @@ __global__ void __launch_bounds__(DW * 32, WRITE ? AE_DNA_MINB_WRITE : AE_DNA_MI
         }
         __syncwarp();
 
+        if (SEQ) {
+            rows_seq<WRITE>(a, sm, lane, kmask, smask, len, nd.off, qm, qH, tbase, qoff, qid);
+            __syncwarp();
+        }
         // ---- the rows: parent entries laid end to end over the lanes
         if (lane < 4) sm.carry[lane] = AE_KNEG;
         __syncwarp();
-        for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+        for (uint32_t t0 = 0; t0 < (SEQ ? 0u : total); t0 += 32) {
             const uint32_t t = t0 + lane;
             const bool valid = t < total;
             int L = 0;
@@ -589,8 +762,15 @@ int ae_rows_dna_blocks_per_sm(bool write) { return write ? AE_DNA_MINB_WRITE : A
 void ae_rows_dna(const DnaRowsArgs &a, bool write, int blocks, cudaStream_t st) {
     if (a.nnodes <= 0) return;
     ++g_launches;
-    if (write)
-        k_rows_dna<true><<<blocks, DW * 32, 0, st>>>(a);
-    else
-        k_rows_dna<false><<<blocks, DW * 32, 0, st>>>(a);
+    if (a.sequential) {
+        if (write)
+            k_rows_dna<true, true><<<blocks, DW * 32, 0, st>>>(a);
+        else
+            k_rows_dna<false, true><<<blocks, DW * 32, 0, st>>>(a);
+    } else {
+        if (write)
+            k_rows_dna<true, false><<<blocks, DW * 32, 0, st>>>(a);
+        else
+            k_rows_dna<false, false><<<blocks, DW * 32, 0, st>>>(a);
+    }
 }

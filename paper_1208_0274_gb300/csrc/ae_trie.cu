@@ -245,7 +245,9 @@ __device__ void run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, ui
                 const int32_t c0 = (int32_t)(uint32_t)sg.poff, c1 = (int32_t)(uint32_t)(sg.poff >> 32);
                 colA = c0 + (int32_t)k;
                 const int32_t D = delta_of(sc, smat, c, P[colA]);
-                Dprev = D > thr_of(colA, m, H, g) ? D : AE_NEG;
+                // a search split over ranks opens forks only at its own start columns
+                const bool mine = a.parts <= 1 || colA % a.parts == a.part;
+                Dprev = (mine && D > thr_of(colA, m, H, g)) ? D : AE_NEG;
                 MpA = Dprev;
                 next_col = (colA + 1 < c1) ? colA + 1 : m;
             } else {

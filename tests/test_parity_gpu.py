@@ -111,14 +111,16 @@ def test_random_planted_cases(si):
                                        item_columns=int(rng.integers(3, 500)),
                                        leaf_delay=int(rng.integers(0, 15)),
                                        int16_limit=int(rng.choice([0, 5, 9, 32000])),
-                                       general_rows=int(rng.integers(0, 2)))
+                                       general_rows=int(rng.integers(0, 2)),
+                                       row_layout=int(rng.integers(0, 3)))
                 hits, _ = ae.ae_search(idx, [P], scheme, [H], options=opts)
                 assert_same(hits, want_hits(T, P, scheme, H), f"case {case} H {H} seed {seed_on}")
         idx.close()
 
 
 def test_row_kernels_agree_entry_for_entry():
-    """The DNA int16x2 row kernel (one lane per parent entry, all children) and
+    """The DNA int16x2 row kernel in both layouts (one lane per parent entry
+    with all children; one lane per (node, child) walking the parent row) and
     the general one (one lane per (child, parent entry)) compute the same trie
     levels: identical results, DP entries, triples and nodes, on a 1 Mbp text
     with planted homologs of several lengths and at several leaf delays."""
@@ -140,14 +142,16 @@ def test_row_kernels_agree_entry_for_entry():
     idx = ae.ae_index_build(T, ae.AE_DNA)
     for delay in (0, 8, 14):
         got = {}
-        for general in (0, 1):
-            hits, counts = ae.ae_search(idx, qs, scheme, Hs,
-                                        options=ae.make_options(leaf_delay=delay, general_rows=general))
+        for kind, opts in (("general", dict(general_rows=1)), ("auto", dict()),
+                           ("walk", dict(row_layout=1)), ("spread", dict(row_layout=2))):
+            hits, counts = ae.ae_search(idx, qs, scheme, Hs, options=ae.make_options(leaf_delay=delay, **opts))
             st = ae.ae_last_stats()
-            got[general] = (hits, counts, st["entries"], st["triples"], st["nodes"], st["injections"])
-        assert np.array_equal(got[0][0], got[1][0]) and np.array_equal(got[0][1], got[1][1])
-        assert got[0][0].size > 1_000
-        assert got[0][2:] == got[1][2:], (delay, got[0][2:], got[1][2:])
+            got[kind] = (hits, counts, st["entries"], st["triples"], st["nodes"], st["injections"])
+        ref = got["general"]
+        assert ref[0].size > 1_000
+        for kind, g in got.items():
+            assert np.array_equal(g[0], ref[0]) and np.array_equal(g[1], ref[1]), (delay, kind)
+            assert g[2:] == ref[2:], (delay, kind, g[2:], ref[2:])
     idx.close()
 
 
