@@ -109,6 +109,19 @@ typedef struct {
     int64_t dominated;        /* forks dropped at the seed depth by q-prefix domination (Lemma 1):
                                  the text letter before every occurrence of the seed gram equals
                                  the query letter before the fork's start */
+    /* Filtering and reuse (Section 7.2, Eq. 5 and Eq. 6, in this engine's units).  With
+     * ae_options.tier_stats, `candidates` counts the DP cells the trie levels evaluated (the
+     * diagonal and vertical-gap slots of every (child, parent entry) pair), `pruned_nonpos`
+     * those dropped with a value <= 0 (Theorem 2 (i)) and `pruned_reach` those dropped with
+     * 0 < value <= thr(j), unable to reach H (Theorem 2 (ii)); the filtering ratio is
+     * (pruned_nonpos + pruned_reach) / candidates.  `reused` (always counted) is the number of
+     * entries of rows handed to the text-position sweep that a row already walking through
+     * the same text position absorbed -- computed once for both from there on; the reusing
+     * ratio is reused / (reused + entries). */
+    int64_t candidates, pruned_nonpos, pruned_reach;
+    int64_t reused;
+    int64_t reroutes;         /* engine batches whose frontier left the int16x2 route for int32 (a
+                                 state could pass the int16 range; nothing is recomputed) */
 } ae_stats;
 
 /* Engine knobs (NULL = defaults).  None of them changes the result set. */

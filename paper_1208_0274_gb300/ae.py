@@ -64,7 +64,9 @@ class ae_stats(ctypes.Structure):
                 ("leaf_max_width", ctypes.c_int64), ("ws_bytes", ctypes.c_int64),
                 ("leaf_sweeps", ctypes.c_int64), ("leaf_raw_hits", ctypes.c_int64),
                 ("triples", ctypes.c_int64), ("batch_splits", ctypes.c_int64),
-                ("dominated", ctypes.c_int64)]
+                ("dominated", ctypes.c_int64), ("candidates", ctypes.c_int64),
+                ("pruned_nonpos", ctypes.c_int64), ("pruned_reach", ctypes.c_int64),
+                ("reused", ctypes.c_int64), ("reroutes", ctypes.c_int64)]
 
 
 def _load():

@@ -586,6 +586,7 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
             ae_mg_to_i32(ptr<int32_t>(w->aM[cur]), ptr<int32_t>(w->aGa[cur]), cur_ent, st);
             prof.mark(K_OTHER);
             i16 = false;
+            ++stats.reroutes;
         }
         if (sigma == 4 && i16 && !opt.tier_stats && !root_level && !opt.general_rows && -sc.ss < 65536) {
             // DNA int16x2 route: one lane per parent entry, child ranges taken in
@@ -818,6 +819,7 @@ void Search::dna_level(int64_t &F, int cur, int64_t &cur_ent, int64_t &lf_ent_ba
     da.task_stride = (uint64_t)ntask;
     da.ctr = ptr<LevelCounters>(w->ctr);
     da.stats = ptr<DevStats>(w->stats);
+    const auto t_level = std::chrono::steady_clock::now();
     prof.mark(K_ROWS);
     ae_rows_dna(da, false, num_sms * ae_rows_dna_blocks_per_sm(false), st);
     const uint32_t *tin[5];
@@ -873,9 +875,13 @@ void Search::dna_level(int64_t &F, int cur, int64_t &cur_ent, int64_t &lf_ent_ba
     prof.mark(K_ROWS);
     ae_rows_dna(da, true, num_sms * ae_rows_dna_blocks_per_sm(true), st);
     prof.mark(K_ROWS);
-    if (trace())
-        fprintf(stderr, "[ae level] dna nodes %lld (per task %d) -> frontier %lld nodes %lld, leaf %lld rows %lld\n",
-                (long long)F, npt, (long long)fr_ent, (long long)fr_node, (long long)lf_ent, (long long)lf_node);
+    if (trace()) {
+        sync();   // trace mode only: the level's own wall time
+        fprintf(stderr, "[ae level] dna %s nodes %lld (per task %d) entries %lld triples %lld -> frontier %lld nodes %lld, "
+                        "leaf %lld rows %lld; %.3f ms\n",
+                da.sequential ? "walk" : "spread", (long long)F, npt, (long long)cur_ent, (long long)hc.triples,
+                (long long)fr_ent, (long long)fr_node, (long long)lf_ent, (long long)lf_node, ms_since(t_level));
+    }
     lf_ent_base += lf_ent;
     lf_node_base += lf_node;
     rh_base += hits;
@@ -1237,6 +1243,10 @@ ae_status search_core(const ae_index *idx, Workspace *w, const int64_t *offsets,
         for (int k = 0; k < 3; ++k) s.stats.entries_tier[k] = (int64_t)ds.tier[k];
         s.stats.entries_leaf = (int64_t)ds.entries_leaf;
         s.stats.dominated = (int64_t)ds.dominated;
+        s.stats.reused = (int64_t)ds.reused;
+        s.stats.candidates = (int64_t)ds.cand;
+        s.stats.pruned_nonpos = (int64_t)ds.pruned_nonpos;
+        s.stats.pruned_reach = (int64_t)ds.pruned_reach;
         s.stats.leaf_max_steps = (int64_t)ds.leaf_max_steps;
         s.stats.leaf_max_width = (int64_t)ds.leaf_max_width;
         if (trace())

@@ -119,6 +119,9 @@ struct DevStats {
     unsigned long long leaf_max_steps, leaf_max_width;
     unsigned long long leaf_max_cycles;   // longest sweep task (SM clock cycles)
     unsigned long long dominated;         // seed entries dropped by q-prefix domination (Lemma 1)
+    unsigned long long reused;            // sweep: injected entries absorbed by a walked row at their position
+    unsigned long long cand, pruned_nonpos, pruned_reach;   // tier_stats: slot candidates of the trie
+                                                            // levels and those the filters dropped
     unsigned long long pad;
 };
 

@@ -531,7 +531,7 @@ __global__ void __launch_bounds__(128, AE_LEAF_MINB) k_leaf(LeafArgs a) {
     Buf Cb = {wb + 6 * cap, wb + 7 * cap, wb + 8 * cap};
     Buf C2 = {wb + 9 * cap, wb + 10 * cap, wb + 11 * cap};
     const uint64_t jmask = (1ull << a.bj) - 1ull;
-    unsigned long long st_rows = 0, st_ent = 0, st_t0 = 0, st_t1 = 0, st_t2 = 0;
+    unsigned long long st_rows = 0, st_ent = 0, st_t0 = 0, st_t1 = 0, st_t2 = 0, st_reused = 0;
     bool overflow = false;
 
     while (!overflow) {
@@ -957,7 +957,10 @@ __global__ void __launch_bounds__(128, AE_LEAF_MINB) k_leaf(LeafArgs a) {
                     }
                     dominated = __all_sync(FULL, ok);
                 }
-                if (dominated) continue;
+                if (dominated) {
+                    st_reused += (unsigned long long)icnt;   // the whole row rides on the walked one
+                    continue;
+                }
                 if (nlen + icnt > cap) {
                     overflow = true;
                     break;
@@ -1032,6 +1035,7 @@ __global__ void __launch_bounds__(128, AE_LEAF_MINB) k_leaf(LeafArgs a) {
                 }
                 __syncwarp();
                 st_ent += (unsigned long long)(out - nlen);
+                st_reused += (unsigned long long)(nlen + icnt - out);   // columns both rows had
                 Buf t = Rn;
                 Rn = Cb;
                 Cb = t;
@@ -1084,6 +1088,7 @@ __global__ void __launch_bounds__(128, AE_LEAF_MINB) k_leaf(LeafArgs a) {
         if (t0) atomicAdd(&a.stats->tier[0], t0);
         if (t1) atomicAdd(&a.stats->tier[1], t1);
         if (t2) atomicAdd(&a.stats->tier[2], t2);
+        if (st_reused) atomicAdd(&a.stats->reused, st_reused);
     }
 }
 

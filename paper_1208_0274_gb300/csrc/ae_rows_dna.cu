@@ -145,7 +145,22 @@ __device__ __forceinline__ void rows_seq(const DnaRowsArgs &a, WarpSmem &sm, int
     const ScoreView &sc = a.sc;
     const int32_t u = -sc.ss, oe = sc.sg + sc.ss, g = sc.gmax, sa = sc.sa, sb = sc.sb;
     const int32_t strong = -oe;
-    const uint32_t np = __popc(kmask);   // pairs of this node lane
+    // pairs are handed out in rounds of 32 in order of decreasing row length (a
+    // bitonic sort of the node lanes by length), so that the lanes of a round walk
+    // rows of similar length
+    uint32_t key = (kmask ? min(len, (1u << 26) - 1u) : 0u) << 5 | (uint32_t)(31 - lane);   // distinct per lane
+#pragma unroll
+    for (int k = 2; k <= 32; k <<= 1) {
+#pragma unroll
+        for (int jj = k >> 1; jj > 0; jj >>= 1) {
+            const uint32_t other = __shfl_xor_sync(FULL, key, jj);
+            const bool up = ((lane & k) == 0);          // this block sorts descending
+            const bool low = (lane & jj) == 0;
+            key = (low == up) ? max(key, other) : min(key, other);
+        }
+    }
+    const int sorted_lane = 31 - (int)(key & 31u);      // the node lane at this sorted position
+    const uint32_t np = __popc(__shfl_sync(FULL, kmask, sorted_lane));   // its pairs
     uint32_t poff = np;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -157,13 +172,14 @@ __device__ __forceinline__ void rows_seq(const DnaRowsArgs &a, WarpSmem &sm, int
     for (uint32_t p0 = 0; p0 < npairs; p0 += 32) {
         const uint32_t p = p0 + lane;
         const bool valid = p < npairs;
-        int L = 0;
+        int S = 0;
 #pragma unroll
         for (int step = 16; step > 0; step >>= 1) {
-            const uint32_t o = __shfl_sync(FULL, poff, L + step);
-            if (o <= p) L += step;
+            const uint32_t o = __shfl_sync(FULL, poff, S + step);
+            if (o <= p) S += step;
         }
-        const uint32_t i = p - __shfl_sync(FULL, poff, L);
+        const uint32_t i = p - __shfl_sync(FULL, poff, S);
+        const int L = __shfl_sync(FULL, sorted_lane, S);
         unsigned km = __shfl_sync(FULL, kmask, L);
         const unsigned smL = __shfl_sync(FULL, smask, L);
         const uint32_t nlen = __shfl_sync(FULL, len, L);
@@ -368,6 +384,7 @@ __global__ void __launch_bounds__(DW * 32, WRITE ? AE_DNA_MINB_WRITE : AE_DNA_MI
             continue;
         }
 
+        unsigned wmask = kmask;   // write pass: the children with any output (the others need no walk)
         if (!WRITE) {
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
@@ -383,6 +400,7 @@ __global__ void __launch_bounds__(DW * 32, WRITE ? AE_DNA_MINB_WRITE : AE_DNA_MI
                 if ((kmask >> c) & 1u) {
                     cn[c] = a.kcnt[v * 4 + c];
                     ch[c] = a.khit[v * 4 + c];
+                    if (cn[c] == 0 && ch[c] == 0) wmask &= ~(1u << c);
                     if ((smask >> c) & 1u) {
                         s_fe += cn[c];
                         s_fn += cn[c] ? 1u : 0u;
@@ -468,7 +486,7 @@ __global__ void __launch_bounds__(DW * 32, WRITE ? AE_DNA_MINB_WRITE : AE_DNA_MI
         __syncwarp();
 
         if (SEQ) {
-            rows_seq<WRITE>(a, sm, lane, kmask, smask, len, nd.off, qm, qH, tbase, qoff, qid);
+            rows_seq<WRITE>(a, sm, lane, WRITE ? wmask : kmask, smask, len, nd.off, qm, qH, tbase, qoff, qid);
             __syncwarp();
         }
         // ---- the rows: parent entries laid end to end over the lanes
@@ -486,7 +504,7 @@ __global__ void __launch_bounds__(DW * 32, WRITE ? AE_DNA_MINB_WRITE : AE_DNA_MI
             const uint32_t k = t - __shfl_sync(FULL, woff, L);
             const uint32_t nlen = __shfl_sync(FULL, len, L);
             const uint64_t off = __shfl_sync(FULL, nd.off, L);
-            const unsigned km = __shfl_sync(FULL, kmask, L);
+            const unsigned km = __shfl_sync(FULL, WRITE ? wmask : kmask, L);
             const unsigned sm_ = __shfl_sync(FULL, smask, L);
             const int32_t m = __shfl_sync(FULL, qm, L);
             const int32_t H = __shfl_sync(FULL, qH, L);

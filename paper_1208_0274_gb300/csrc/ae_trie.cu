@@ -162,7 +162,8 @@ struct TaskSmem {
 template <int SIGMA, bool WRITE, bool I16>
 __device__ void run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, uint64_t s_first, uint64_t s_last,
                          uint64_t t_beg, uint64_t t_end, unsigned long long &st0, unsigned long long &st1,
-                         unsigned long long &st2) {
+                         unsigned long long &st2, unsigned long long &st_cand, unsigned long long &st_np,
+                         unsigned long long &st_nr) {
     const int lane = threadIdx.x & 31;
     const unsigned le = (lane == 31) ? 0xffffffffu : ((1u << (lane + 1)) - 1u);
     const ScoreView &sc = a.sc;
@@ -207,7 +208,7 @@ __device__ void run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, ui
         }
         // ---- slots of this lane (see slot_finish)
         int32_t colA = m, MpA = AE_NEG, GaA = AE_NEG, MpB = AE_NEG, next_col = m;
-        int32_t Dprev = AE_NEG, Gap = AE_NEG, Dk = AE_NEG;
+        int32_t Dprev = AE_NEG, Gap = AE_NEG, Dk = AE_NEG, Gap_raw = AE_NEG;
         bool hasB = false;
         const unsigned heads = __ballot_sync(FULL, !valid || k == 0 || lane == 0);
         const int first_lane = 31 - __clz(heads & le);
@@ -258,6 +259,7 @@ __device__ void run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, ui
                     Dprev = D > tA ? D : AE_NEG;
                 }
                 const int32_t gap = I16 ? gap_from_mg(mg, sc.ss, oe) : gap_from_i32(M, Ga, sc.ss, oe);
+                Gap_raw = gap;
                 Gap = gap > tA ? gap : AE_NEG;
                 MpA = max(Dprev, Gap);
                 GaA = Gap;
@@ -393,7 +395,27 @@ __device__ void run_task(const RowsArgs &a, const int8_t *smat, TaskSmem &sm, ui
                 st1 += tier == 2;
             }
         }
-        if (a.tiers) st0 += nR;
+        if (a.tiers) {
+            st0 += nR;
+            // filter statistics (Theorem 2): the slot candidates of this triple and
+            // those dropped as non-positive or as unable to reach H
+            if (valid) {
+                const int32_t tA = thr_of(colA, m, H, g);
+                int32_t vA = max(Gap_raw, o.GbA);
+                if (!root && pjv + 1 == j && pMv > AE_NEG) vA = max(vA, pMv + delta_of(sc, smat, c, P[j]));
+                if (root) vA = max(vA, delta_of(sc, smat, c, P[colA]));
+                unsigned long long cand = 1, np = vA <= 0, nr = vA > 0 && vA <= tA;
+                if (hasB) {
+                    const int32_t vB = max(M + delta_of(sc, smat, c, P[j + 1]), o.GbB);
+                    cand += 1;
+                    np += vB <= 0;
+                    nr += vB > 0 && vB <= thr_of(colA + 1, m, H, g);
+                }
+                st_cand += cand;
+                st_np += np;
+                st_nr += nr;
+            }
+        }
         if (kind1) {
             uint64_t hp = h0;
             if (hA) {
@@ -660,6 +682,7 @@ __global__ void __launch_bounds__(RW_WARPS * 32, WRITE ? RW_MINB_WRITE : RW_MINB
     const uint64_t W = RW_TASK;
     const uint64_t ntask = (T + W - 1) / W;
     unsigned long long st0 = 0, st1 = 0, st2 = 0;
+    unsigned long long st_cand = 0, st_np = 0, st_nr = 0;
     unsigned long long st_ent = 0;
     unsigned long long *task_ctr = WRITE ? &a.ctr->task_w : &a.ctr->task_c;
     uint64_t tot_c[5] = {0, 0, 0, 0, 0};    // count pass: this warp's level totals
@@ -684,7 +707,8 @@ __global__ void __launch_bounds__(RW_WARPS * 32, WRITE ? RW_MINB_WRITE : RW_MINB
                 sm.hit[r] = 0;
             }
             __syncwarp();
-            run_task<SIGMA, false, I16>(a, smat, sm, s_first, s_last, t_beg, t_end, st0, st1, st2);
+            run_task<SIGMA, false, I16>(a, smat, sm, s_first, s_last, t_beg, t_end, st0, st1, st2, st_cand, st_np,
+                                        st_nr);
             __syncwarp();
         } else {
             for (uint64_t r = lane; r < nsg; r += 32) {
@@ -833,7 +857,8 @@ __global__ void __launch_bounds__(RW_WARPS * 32, WRITE ? RW_MINB_WRITE : RW_MINB
         if (I16 && a.res)
             run_task_stored<SIGMA>(a, sm, s_first, s_last, t_beg, t_end);
         else
-            run_task<SIGMA, true, I16>(a, smat, sm, s_first, s_last, t_beg, t_end, st0, st1, st2);
+            run_task<SIGMA, true, I16>(a, smat, sm, s_first, s_last, t_beg, t_end, st0, st1, st2, st_cand, st_np,
+                                       st_nr);
         __syncwarp();
     }
     }
@@ -845,17 +870,23 @@ __global__ void __launch_bounds__(RW_WARPS * 32, WRITE ? RW_MINB_WRITE : RW_MINB
         if (tot_c[4]) atomicAdd(&a.ctr->c_hits, (unsigned long long)tot_c[4]);
     }
     if (a.stats) {
-        unsigned long long t0 = st0, t1 = st1, t2 = st2;
+        unsigned long long t0 = st0, t1 = st1, t2 = st2, tc = st_cand, tn = st_np, tr = st_nr;
         for (int d = 16; d > 0; d >>= 1) {
             t0 += __shfl_down_sync(FULL, t0, d);
             t1 += __shfl_down_sync(FULL, t1, d);
             t2 += __shfl_down_sync(FULL, t2, d);
+            tc += __shfl_down_sync(FULL, tc, d);
+            tn += __shfl_down_sync(FULL, tn, d);
+            tr += __shfl_down_sync(FULL, tr, d);
         }
         if (lane == 0) {
             if (st_ent) atomicAdd(&a.stats->entries, st_ent);
             if (t0) atomicAdd(&a.stats->tier[0], t0);
             if (t1) atomicAdd(&a.stats->tier[1], t1);
             if (t2) atomicAdd(&a.stats->tier[2], t2);
+            if (tc) atomicAdd(&a.stats->cand, tc);
+            if (tn) atomicAdd(&a.stats->pruned_nonpos, tn);
+            if (tr) atomicAdd(&a.stats->pruned_reach, tr);
         }
     }
 }

@@ -78,6 +78,17 @@ def test_dna_small_workload_full_parity(small):
     assert np.array_equal(hits2, hits)
     st2 = ae.ae_last_stats()
     assert sum(st2["entries_tier"]) == st2["entries"] and st2["entries_tier"][0] > 0
+    # filter statistics (Eq. 5): slot candidates of the trie levels, those the filters
+    # dropped, and the kept ones, which with the gap-run cells are the trie's entries
+    cand, npos, nreach = st2["candidates"], st2["pruned_nonpos"], st2["pruned_reach"]
+    assert cand > 0 and npos > 0 and nreach > 0 and npos + nreach < cand
+    assert cand - npos - nreach <= st2["entries"] - st2["entries_leaf"]
+    assert st["candidates"] == 0        # counted only with tier_stats
+    # reuse at text positions (Eq. 6): rows of different starts meet along the homologs
+    assert st["reused"] > 0 and st2["reused"] > 0
+    assert st["reroutes"] == 0
+    ae.ae_search(idx, wl.queries, wl.scheme, wl.H, options=ae.make_options(int16_limit=6))
+    assert ae.ae_last_stats()["reroutes"] >= 1
 
 
 @pytest.mark.parametrize("opts", [dict(qprefix_seed=0), dict(leaf_segment=1), dict(leaf_segment=7),
