@@ -145,6 +145,16 @@ T *ptr(DevBuf &b) {
     return reinterpret_cast<T *>(b.p);
 }
 
+// Upload a level's starting counters, leaving the device's overflow flag as it
+// is: a disagreement reported by any earlier pass of the batch stays visible.
+void upload_level_counters(LevelCounters *d, const LevelCounters &h, cudaStream_t st) {
+    const size_t ov = offsetof(LevelCounters, overflow);
+    CU(cudaMemcpyAsync(d, &h, ov, cudaMemcpyHostToDevice, st));
+    CU(cudaMemcpyAsync((char *)d + ov + 8, (const char *)&h + ov + 8, sizeof(LevelCounters) - ov - 8,
+                       cudaMemcpyHostToDevice, st));
+}
+
+
 struct Workspace {
     cudaStream_t stream = nullptr;
     // queries
@@ -578,6 +588,7 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
     }
     ensure(w->totals, 64, st);
     ensure(w->ctr, sizeof(LevelCounters), st);
+    CU(cudaMemsetAsync(w->ctr.p, 0, sizeof(LevelCounters), st));   // clears the sticky overflow flag
     bool root_level = d0 < 1;   // the first level of a walk from the root has implicit rows
     while (F > 0 && depth <= L_max_all) {
         if (i16 && (int64_t)(depth + 1) * sc.gmax > opt.int16_limit) {
@@ -662,7 +673,7 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
         h0.lf_ent = (unsigned long long)lf_ent_base;
         h0.lf_node = (unsigned long long)lf_node_base;
         h0.hits = (unsigned long long)rh_base;
-        CU(cudaMemcpyAsync(w->ctr.p, &h0, sizeof(h0), cudaMemcpyHostToDevice, st));
+        upload_level_counters(ptr<LevelCounters>(w->ctr), h0, st);
         const int64_t ntask = (ntrip + AE_ROW_TASK - 1) / AE_ROW_TASK;
         ensure(w->task_tot, (size_t)std::max<int64_t>(ntask, 1) * 5 * 4, st);
         ensure(w->task_off, (size_t)std::max<int64_t>(ntask, 1) * 5 * 8, st);
@@ -693,6 +704,7 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
         CU(cudaMemcpyAsync(tot(), w->ctr.p, sizeof(hc), cudaMemcpyDeviceToHost, st));
         sync();
         memcpy(&hc, tot(), sizeof(hc));
+        if (hc.overflow) throw ae_error{AE_ECUDA};
         const int64_t fr_ent = (int64_t)hc.c_fr_ent, fr_node = (int64_t)hc.c_fr_node;
         const int64_t lf_ent = (int64_t)hc.c_lf_ent, lf_node = (int64_t)hc.c_lf_node, hits = (int64_t)hc.c_hits;
         ensure(w->aj[nxt], std::max<int64_t>(fr_ent, 1) * 4, st);
@@ -794,7 +806,7 @@ void Search::dna_level(int64_t &F, int cur, int64_t &cur_ent, int64_t &lf_ent_ba
     h0.lf_ent = (unsigned long long)lf_ent_base;
     h0.lf_node = (unsigned long long)lf_node_base;
     h0.hits = (unsigned long long)rh_base;
-    CU(cudaMemcpyAsync(w->ctr.p, &h0, sizeof(h0), cudaMemcpyHostToDevice, st));
+    upload_level_counters(ptr<LevelCounters>(w->ctr), h0, st);
     DnaRowsArgs da;
     memset(&da, 0, sizeof(da));
     da.ix = ix;
@@ -834,6 +846,7 @@ void Search::dna_level(int64_t &F, int cur, int64_t &cur_ent, int64_t &lf_ent_ba
     CU(cudaMemcpyAsync(tot(), w->ctr.p, sizeof(hc), cudaMemcpyDeviceToHost, st));
     sync();
     memcpy(&hc, tot(), sizeof(hc));
+    if (hc.overflow) throw ae_error{AE_ECUDA};   // an earlier pass found its sizes inconsistent
     const int64_t fr_ent = (int64_t)hc.c_fr_ent, fr_node = (int64_t)hc.c_fr_node;
     const int64_t lf_ent = (int64_t)hc.c_lf_ent, lf_node = (int64_t)hc.c_lf_node, hits = (int64_t)hc.c_hits;
     stats.triples += (int64_t)hc.triples;
@@ -1045,6 +1058,9 @@ void Search::leaf_phase(int64_t ninj) {
                     (long long)ninj, (long long)la.nseg, la.seg, attempt, ms_since(t_sweep),
                     hdr[0] - (unsigned long long)nhits, (long long)hit_cap, hdr[1], hdr[2], w->leaf_cap);
         if (hdr[1] != 0) {          // a row outgrew the scratch: retry larger
+            // a sweep row holds at most two entries per query column plus gap runs, so
+            // a capacity past 2^28 entries means something else is wrong: stop
+            if (w->leaf_cap >= (1 << 28)) throw ae_error{AE_ENOMEM};
             w->leaf_cap *= 4;
             // the no-allocation entry point caps sweep rows at its documented limit
             if (g_arena && w->leaf_cap > AE_STATIC_MAX_LEAF_CAP) throw ae_error{AE_EUNSUPPORTED};

@@ -141,7 +141,7 @@ __device__ __forceinline__ uint64_t excl_scan_u64(uint64_t v, uint64_t &total) {
 template <bool WRITE>
 __device__ __forceinline__ void rows_seq(const DnaRowsArgs &a, WarpSmem &sm, int lane, unsigned kmask, unsigned smask,
                                          uint32_t len, uint64_t noff, int32_t qm, int32_t qH, int32_t tbase,
-                                         uint32_t qoff, int32_t qid) {
+                                         uint32_t qoff, int32_t qid, int64_t vbase) {
     const ScoreView &sc = a.sc;
     const int32_t u = -sc.ss, oe = sc.sg + sc.ss, g = sc.gmax, sa = sc.sa, sb = sc.sb;
     const int32_t strong = -oe;
@@ -194,14 +194,15 @@ __device__ __forceinline__ void rows_seq(const DnaRowsArgs &a, WarpSmem &sm, int
         const bool st = (smL >> c) & 1u;
         const int slot = L * 4 + c;
         const uint8_t *P = a.qv.codes + qo;
-        uint64_t eout = 0, hout = 0, ecap = 0;
-        uint32_t clo = 0, chi = 0;
+        uint64_t eout = 0, hout = 0;
+        uint32_t clo = 0, chi = 0, ebud = 0, hbud = 0;   // write pass: the child's outputs as counted
         if (WRITE) {
             eout = sm.base[st ? 0 : 1] + sm.a[slot];
             hout = sm.base[2] + sm.h[slot];
-            ecap = st ? a.fr_ent_cap : a.lf_ent_cap;
             clo = sm.lo[slot];
             chi = sm.hi[slot];
+            ebud = a.kcnt[(vbase + L) * 4 + c];
+            hbud = a.khit[(vbase + L) * 4 + c];
         }
         uint32_t cnt = 0, hcnt = 0;
         bool bad = false;
@@ -216,6 +217,12 @@ __device__ __forceinline__ void rows_seq(const DnaRowsArgs &a, WarpSmem &sm, int
                 mgn = a.pmg[off + k + 1];
             } else {
                 jn = m;
+            }
+            // a parent row is sorted by column inside [0, m); anything else is
+            // reported, and no column past the query is read
+            if ((uint32_t)j >= (uint32_t)m || jn <= j || jn > m) {
+                bad = true;
+                break;
             }
             const int32_t M = (int32_t)(int16_t)(mg & 0xFFFFu);
             const int32_t traw = tb0 + j * g;
@@ -257,7 +264,9 @@ __device__ __forceinline__ void rows_seq(const DnaRowsArgs &a, WarpSmem &sm, int
                 cnt += (uint32_t)aliveA + (uint32_t)aliveB + (uint32_t)run_len;
                 hcnt += (uint32_t)hA + (uint32_t)hB + (st ? (uint32_t)run_hits : 0u);
             } else if (!bad) {
-                if (eout + cnt + (uint32_t)aliveA + (uint32_t)aliveB + (uint32_t)run_len > ecap) {
+                // every write stays inside the child's own range, as the count pass sized it
+                if (cnt + (uint32_t)aliveA + (uint32_t)aliveB + (uint32_t)run_len > ebud ||
+                    hcnt + (uint32_t)hA + (uint32_t)hB + (st ? (uint32_t)run_hits : 0u) > hbud) {
                     bad = true;   // the passes disagree: reported, not written
                 } else {
                     if (aliveA) {
@@ -270,8 +279,7 @@ __device__ __forceinline__ void rows_seq(const DnaRowsArgs &a, WarpSmem &sm, int
                             a.lGa[eout + cnt] = Gap;
                         }
                         ++cnt;
-                        if (hA && hout + hcnt < a.hit_cap) a.rhits[hout + hcnt++] = RangeHit{clo, chi, eq, j, MA, 0};
-                        else if (hA) bad = true;
+                        if (hA) a.rhits[hout + hcnt++] = RangeHit{clo, chi, eq, j, MA, 0};
                     }
                     if (aliveB) {
                         if (st) {
@@ -283,8 +291,7 @@ __device__ __forceinline__ void rows_seq(const DnaRowsArgs &a, WarpSmem &sm, int
                             a.lGa[eout + cnt] = AE_NEG;
                         }
                         ++cnt;
-                        if (hB && hout + hcnt < a.hit_cap) a.rhits[hout + hcnt++] = RangeHit{clo, chi, eq, j + 1, MB, 0};
-                        else if (hB) bad = true;
+                        if (hB) a.rhits[hout + hcnt++] = RangeHit{clo, chi, eq, j + 1, MB, 0};
                     }
                     for (int32_t r = 0; r < run_len; ++r) {
                         const int32_t col = rs + r, val = V0 - r * u;
@@ -297,10 +304,7 @@ __device__ __forceinline__ void rows_seq(const DnaRowsArgs &a, WarpSmem &sm, int
                             a.lGa[eout + cnt] = AE_NEG;
                         }
                         ++cnt;
-                        if (st && r < run_hits) {
-                            if (hout + hcnt < a.hit_cap) a.rhits[hout + hcnt++] = RangeHit{clo, chi, eq, col, val, 0};
-                            else bad = true;
-                        }
+                        if (st && r < run_hits) a.rhits[hout + hcnt++] = RangeHit{clo, chi, eq, col, val, 0};
                     }
                 }
             }
@@ -310,9 +314,8 @@ __device__ __forceinline__ void rows_seq(const DnaRowsArgs &a, WarpSmem &sm, int
         if (!WRITE) {
             sm.a[slot] = cnt;
             sm.h[slot] = hcnt;
-        } else if (bad) {
-            atomicExch(&a.ctr->overflow, 1ull);
         }
+        if (bad) atomicExch(&a.ctr->overflow, 1ull);
     }
 }
 
@@ -486,7 +489,8 @@ __global__ void __launch_bounds__(DW * 32, WRITE ? AE_DNA_MINB_WRITE : AE_DNA_MI
         __syncwarp();
 
         if (SEQ) {
-            rows_seq<WRITE>(a, sm, lane, WRITE ? wmask : kmask, smask, len, nd.off, qm, qH, tbase, qoff, qid);
+            rows_seq<WRITE>(a, sm, lane, WRITE ? wmask : kmask, smask, len, nd.off, qm, qH, tbase, qoff, qid,
+                            (int64_t)task * npt);
             __syncwarp();
         }
         // ---- the rows: parent entries laid end to end over the lanes
@@ -539,7 +543,7 @@ __global__ void __launch_bounds__(DW * 32, WRITE ? AE_DNA_MINB_WRITE : AE_DNA_MI
             const uint8_t *P = a.qv.codes + qo;
             const bool adjA = valid && pjv + 1 == j && pMv > 0;
             const bool hasB = valid && (j + 1 < m) && (j + 1 != jn);
-            const int pA = valid ? (int)P[j] : 255;
+            const int pA = (valid && (uint32_t)j < (uint32_t)m) ? (int)P[j] : 255;   // never past the query
             const int pB = hasB ? (int)P[j + 1] : 255;
             const int32_t traw = tb0 + j * g;
             const int32_t tA = max(traw, 0), tB = max(traw + g, 0);

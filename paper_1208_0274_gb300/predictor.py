@@ -2,8 +2,11 @@
 
 For a query it estimates log1p(DP entries) and log1p(sweep hit records) of
 its search from 66 features (3-mer spectrum, length, mean FM-interval size of
-its windows; see include/ae_mlp.h).  Everything numeric runs in libae's kernels: features,
-forward pass, backward pass and Adam.  This module only moves arrays.
+its windows; see include/ae_mlp.h).  The network runs in libae's kernels: the
+features, the forward pass, the backward pass and Adam.  This module computes
+on the host only the training set's normalisation (per-feature mean and spread
+handed to ae_mlp_set_norm) and the hit-hint margin (a quantile of held-out
+residuals), and moves arrays.
 
 Uses (none changes a result):
   * hint_hits(queries): per-query expected sweep hit records for

@@ -300,3 +300,20 @@ def test_oracle_suffix_array_inverts_through_bwt(kind):
     bad = sa.copy()
     bad[[p, p + 1]] = bad[[p + 1, p]]
     assert not np.array_equal(_bwt_inverse(codes, bad), codes)
+
+
+def test_sweep_thresholds_are_the_fits_frozen_values():
+    # the scheme and E-value sweeps' thresholds (workloads.SWEEP_H) are what the
+    # oracle-only fitting script gives for each scheme and E
+    from oracle import evalue_fit
+    from workloads import SWEEP_H
+    got = evalue_fit.sweep_thresholds()
+    assert set(got) == set(SWEEP_H)
+    for sc, (lam, K, H) in got.items():
+        assert H == SWEEP_H[sc], sc
+        assert 0.5 < lam < 2.0 and 0.01 < K < 1.0
+    # stricter E, higher threshold; a smaller |s_b| spreads scores, lowering lambda
+    for sc in SWEEP_H:
+        h = SWEEP_H[sc]
+        assert h[1e-15][100_000] > h[1e-5][100_000] > h[10.0][100_000]
+    assert got[(1, -1, -5, -2)][0] < got[(1, -3, -5, -2)][0]

@@ -145,3 +145,35 @@ def test_one_megabase_query_tail_where_threshold_bites():
     # results do land in the columns where the threshold is positive
     assert tail_hits > 0
     idx.close()
+
+
+def test_protein_match_mismatch_scheme_of_the_index_experiments():
+    # Section 7.5 pairs protein texts with <1,-3,-11,-1>: a match/mismatch scheme over
+    # 20 letters, so q-prefix seeding (Eq. 2: q = 4) and the domination filter are on,
+    # unlike BLOSUM62.  Full oracle on 300 k residues.
+    from workloads import PROTEIN_BG
+    rng = np.random.default_rng(17)
+    T = iid_text(300_000, PROTEIN, PROTEIN_BG, rng)
+    scheme = Scheme(1, -3, -11, -1)
+    idx = ae.ae_index_build(T, ae.AE_PROTEIN)
+    qs, Hs = [], []
+    for k, m in enumerate((300, 1_000, 2_500)):
+        P = iid_text(m, PROTEIN, PROTEIN_BG, rng)
+        L = m // 3
+        x = int(rng.integers(0, T.size - L))
+        seg = T[x:x + L].copy()
+        flip = rng.random(L) < 0.15
+        seg[flip] = iid_text(int(flip.sum()), PROTEIN, PROTEIN_BG, rng)
+        P[m // 4:m // 4 + L] = seg
+        qs.append(P)
+        Hs.append(12 + 3 * k)
+    assert ae.ae_plan(1_000, scheme, 12, ae.AE_PROTEIN)[0] == 4
+    hits, counts = ae.ae_search(idx, qs, scheme, Hs)
+    parts = np.split(hits, np.cumsum(counts)[:-1])
+    for k, (P, H) in enumerate(zip(qs, Hs)):
+        want = _as_hits(*oracle.sw_hits_mt(T, P, scheme, H, alphabet=PROTEIN))
+        assert want.size > 0
+        _compare(parts[k], want, f"protein <1,-3,-11,-1> query {k}")
+    st = ae.ae_last_stats()
+    assert st["seed_depth"] == 3
+    idx.close()

@@ -217,6 +217,18 @@ def dna_small(seed=20120801, n=100_000, m=1_000, copies=5):
 # the test suite).
 DNA_SCALE_H = {10_000: 19, 100_000: 21, 1_000_000: 23}
 
+# Thresholds of the scheme sweep (Section 7.4, Fig. 9: four BLAST schemes, E = 10,
+# m = 100 kbp) and of the E-value sweep (Section 7.3, Fig. 8: E = 1e-15, 1e-5, 10),
+# for the 10^8-letter text at 41% GC: a Gumbel fit of the oracle's best scores on
+# random pairs per scheme, frozen from `python -m oracle.evalue_fit sweep`
+# (lambda, K: 1.2892, 0.2187 / 1.3044, 0.2416 / 1.0639, 0.1778 / 1.2957, 0.2394).
+SWEEP_H = {
+    (1, -3, -5, -2): {1e-15: {10_000: 48, 100_000: 49}, 1e-5: {10_000: 30, 100_000: 31}, 10.0: {10_000: 19, 100_000: 21}},
+    (1, -4, -5, -2): {1e-15: {10_000: 47, 100_000: 49}, 1e-5: {10_000: 29, 100_000: 31}, 10.0: {10_000: 19, 100_000: 21}},
+    (1, -1, -5, -2): {1e-15: {10_000: 57, 100_000: 59}, 1e-5: {10_000: 36, 100_000: 38}, 10.0: {10_000: 23, 100_000: 25}},
+    (1, -3, -2, -2): {1e-15: {10_000: 47, 100_000: 49}, 1e-5: {10_000: 30, 100_000: 31}, 10.0: {10_000: 19, 100_000: 21}},
+}
+
 
 def dna_scale_text(seed=20120802, n=100_000_000, gc=0.41):
     rng = np.random.default_rng(seed)
