@@ -174,7 +174,6 @@ struct Workspace {
     // output
     DevBuf uniq, uflags, uoff, qcount;
     DevBuf stats, segs, ctr, seg_cnt, seg_hit, task_first, task_tot, task_off, task_tmp, task_sum, res, res_key;
-    DevBuf kcnt, khit;   // DNA int16x2 route: per (node, letter) outputs and hits of a level
     double fr_ratio = 1.2, lf_ratio = 0.6, hit_ratio = 0.5;
     // pinned host staging
     uint64_t *h_tot = nullptr;
@@ -197,7 +196,7 @@ struct Workspace {
                 &cnt[4], &off[0], &off[1], &off[2], &off[3], &off[4], &totals, &scan_tmp, &lj, &lM,
                 &lGa, &inj, &rhits, &sk0, &sv0, &sk1, &sv1, &sort_tmp, &hkey, &hscore, &hcount, &hk1,
                 &hv1, &scratch, &next_seg, &uniq, &uflags, &uoff, &qcount, &stats, &segs, &ctr, &seg_cnt, &seg_hit,
-                &task_first, &task_tot, &task_off, &task_tmp, &task_sum, &res, &res_key, &kcnt, &khit};
+                &task_first, &task_tot, &task_off, &task_tmp, &task_sum, &res, &res_key};
     }
 
     ~Workspace() {
@@ -217,7 +216,7 @@ struct Workspace {
                           &cnt[2], &cnt[3], &cnt[4], &off[0], &off[1], &off[2], &off[3], &off[4], &scan_tmp, &lj,
                           &lM, &lGa, &inj, &rhits, &sk0, &sv0, &sk1, &sv1, &sort_tmp, &hk1, &hv1, &scratch, &uniq,
                           &uflags, &uoff, &segs, &seg_cnt, &seg_hit, &task_first, &task_tot, &task_off, &task_tmp,
-                          &res, &res_key, &kcnt, &khit};
+                          &res, &res_key};
         for (DevBuf *b : drop)
             if (b->p && !b->carved) {
                 cudaFree(b->p);
@@ -451,6 +450,9 @@ struct Search {
     int64_t nhits = 0;        // point hits accumulated in w->hkey/hscore
     double batch_hint = -1;   // expected sweep hit records of the current batch (< 0: no hints)
     ae_stats stats;
+    int64_t dna_nodes = 0, dna_entries = 0, dna_retries = 0;   // DNA int16x2 route (counted on the host)
+    double dna_ratio[5] = {0, 0, 0, 0, 0};   // the last DNA level's outputs per input, by arena kind
+    bool dna_ratio_ok = false;
     int num_sms = 152;
     Prof prof;
 
@@ -582,6 +584,7 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
     // ---- trie levels
     int64_t lf_ent_base = 0, lf_node_base = 0, rh_base = 0;
     int64_t L_max_all = 0;
+    dna_ratio_ok = false;   // the batch's first DNA level sizes its arenas from the first-level ratios
     for (int q = 0; q < nq; ++q) {
         int64_t Lm = std::max<int64_t>(m[q], m[q] + (int64_t)floor((double)(H[q] - ((int64_t)sc.sa * m[q] + sc.sg)) / sc.ss));
         L_max_all = std::max(L_max_all, Lm);
@@ -783,36 +786,70 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
 #define AE_SEQ_ROW_AVG 24
 #endif
 
-// One trie level of the DNA int16x2 route (ae_rows_dna.cu): count pass, scan
-// of the per-task totals, exact sizing of the next arenas from the level
-// totals, write pass.  Nodes and arenas have the layout of the general route.
+// One trie level of the DNA int16x2 route (ae_rows_dna.cu) in one launch.
+// The output arenas are sized ahead from the previous level's output per input
+// (with headroom); the kernel reserves every task's ranges on the level
+// cursors, which end at the level's exact totals.  If a reservation passed a
+// capacity the arenas are grown to those totals and the level is run again.
+// Nodes and arenas have the layout of the general route.
 void Search::dna_level(int64_t &F, int cur, int64_t &cur_ent, int64_t &lf_ent_base, int64_t &lf_node_base,
                        int64_t &rh_base, const WorkItem *d_items) {
     (void)d_items;
     const int nxt = cur ^ 1;
     // nodes per task: 32 (one per lane) unless the level is too small to give
     // every resident warp a few tasks
-    const int64_t warps = (int64_t)num_sms * ae_rows_dna_blocks_per_sm(false) * 8;
+    const int64_t warps = (int64_t)num_sms * ae_rows_dna_blocks_per_sm() * ae_rows_dna_warps_per_block();
     const int npt = (int)std::max<int64_t>(1, std::min<int64_t>(32, F / (warps * 4)));
-    const int64_t ntask = (F + npt - 1) / npt;
-    ensure(w->kcnt, (size_t)F * 16, st);
-    ensure(w->khit, (size_t)F * 16, st);
-    ensure(w->task_tot, (size_t)ntask * 5 * 4, st);
-    ensure(w->task_off, (size_t)ntask * 5 * 8, st);
-    ensure(w->task_tmp, (size_t)ae_scan_tmp_words(ntask, 5) * 8, st);
-    ensure(w->task_sum, 5 * 8, st);
-    LevelCounters h0;
-    memset(&h0, 0, sizeof(h0));
-    h0.lf_ent = (unsigned long long)lf_ent_base;
-    h0.lf_node = (unsigned long long)lf_node_base;
-    h0.hits = (unsigned long long)rh_base;
-    upload_level_counters(ptr<LevelCounters>(w->ctr), h0, st);
+
+    // expected outputs: per kind (frontier entries, leaf entries, frontier
+    // nodes, leaf nodes, hits) the previous level's ratio to its input, plus a
+    // fifth; the first level of a batch assumes four children per node
+    static const double first_ratio[5] = {8.0, 1.0, 4.0, 1.0, 0.25};
+    const double in[5] = {(double)cur_ent, (double)cur_ent, (double)F, (double)F, (double)cur_ent};
+    int64_t want[5];
+    for (int q = 0; q < 5; ++q) {
+        const double r = dna_ratio_ok ? dna_ratio[q] * 1.2 : first_ratio[q];
+        want[q] = (int64_t)(r * in[q]) + 256;
+    }
+    want[2] = std::min<int64_t>(want[2], 4 * F);   // a node has at most four children
+    want[3] = std::min<int64_t>(want[3], 4 * F);
+    // grow ahead only outside the fixed arena, and only as far as memory allows:
+    // a capacity that falls short costs one more run of the level
+    auto grow = [&](int64_t fe, int64_t le, int64_t fn, int64_t ln, int64_t h, bool exact) {
+        auto one = [&](auto fn_) {
+            if (exact) {
+                fn_();
+                return;
+            }
+            if (g_arena) return;
+            try {
+                fn_();
+            } catch (const ae_error &e) {
+                if (e.st != AE_ENOMEM) throw;
+            }
+        };
+        one([&] { ensure(w->aj[nxt], (size_t)std::max<int64_t>(fe, 1) * 4, st); });
+        one([&] { ensure(w->aM[nxt], (size_t)std::max<int64_t>(fe, 1) * 4, st); });
+        one([&] { ensure(w->nodes[nxt], (size_t)std::max<int64_t>(fn, 1) * sizeof(Node), st); });
+        one([&] { ensure_keep(w->lj, (size_t)(lf_ent_base + le + 1) * 4, (size_t)lf_ent_base * 4, st); });
+        one([&] { ensure_keep(w->lM, (size_t)(lf_ent_base + le + 1) * 4, (size_t)lf_ent_base * 4, st); });
+        one([&] { ensure_keep(w->lGa, (size_t)(lf_ent_base + le + 1) * 4, (size_t)lf_ent_base * 4, st); });
+        one([&] {
+            ensure_keep(w->inj, (size_t)(lf_node_base + ln + 1) * sizeof(Inject), (size_t)lf_node_base * sizeof(Inject),
+                        st);
+        });
+        one([&] {
+            ensure_keep(w->rhits, (size_t)(rh_base + h + 1) * sizeof(RangeHit), (size_t)rh_base * sizeof(RangeHit),
+                        st);
+        });
+    };
+    grow(want[0], want[1], want[2], want[3], want[4], false);
+
     DnaRowsArgs da;
     memset(&da, 0, sizeof(da));
     da.ix = ix;
     da.sc = sc;
     da.qv = qv;
-    da.nodes = ptr<Node>(w->nodes[cur]);
     da.nnodes = F;
     da.nodes_per_task = npt;
     da.leaf_delay = opt.leaf_delay;
@@ -823,77 +860,72 @@ void Search::dna_level(int64_t &F, int cur, int64_t &cur_ent, int64_t &lf_ent_ba
     // short parent rows are walked one lane per (node, child); long rows spread
     // over the lanes (a lone long row would hold its warp alone)
     da.sequential = (opt.row_layout == 1) || (opt.row_layout == 0 && cur_ent <= AE_SEQ_ROW_AVG * F) ? 1 : 0;
-    da.pj = ptr<int32_t>(w->aj[cur]);
-    da.pmg = ptr<uint32_t>(w->aM[cur]);
-    da.kcnt = ptr<uint32_t>(w->kcnt);
-    da.khit = ptr<uint32_t>(w->khit);
-    da.task_tot = ptr<uint32_t>(w->task_tot);
-    da.task_stride = (uint64_t)ntask;
-    da.ctr = ptr<LevelCounters>(w->ctr);
-    da.stats = ptr<DevStats>(w->stats);
     const auto t_level = std::chrono::steady_clock::now();
-    prof.mark(K_ROWS);
-    ae_rows_dna(da, false, num_sms * ae_rows_dna_blocks_per_sm(false), st);
-    const uint32_t *tin[5];
-    uint64_t *tout[5];
-    for (int q = 0; q < 5; ++q) {
-        tin[q] = ptr<uint32_t>(w->task_tot) + q * ntask;
-        tout[q] = ptr<uint64_t>(w->task_off) + q * ntask;
-    }
-    ae_scan_u32(tin, tout, 5, ntask, ptr<uint64_t>(w->task_sum), ptr<uint64_t>(w->task_tmp), st);
-    prof.mark(K_ROWS);
     LevelCounters hc;
-    CU(cudaMemcpyAsync(tot(), w->ctr.p, sizeof(hc), cudaMemcpyDeviceToHost, st));
-    sync();
-    memcpy(&hc, tot(), sizeof(hc));
-    if (hc.overflow) throw ae_error{AE_ECUDA};   // an earlier pass found its sizes inconsistent
-    const int64_t fr_ent = (int64_t)hc.c_fr_ent, fr_node = (int64_t)hc.c_fr_node;
-    const int64_t lf_ent = (int64_t)hc.c_lf_ent, lf_node = (int64_t)hc.c_lf_node, hits = (int64_t)hc.c_hits;
+    auto run = [&]() {
+        LevelCounters h0;
+        memset(&h0, 0, sizeof(h0));
+        h0.lf_ent = (unsigned long long)lf_ent_base;
+        h0.lf_node = (unsigned long long)lf_node_base;
+        h0.hits = (unsigned long long)rh_base;
+        upload_level_counters(ptr<LevelCounters>(w->ctr), h0, st);
+        // capacities are the buffers' sizes (the leaf and hit arenas keep one spare slot)
+        auto cap = [](const DevBuf &b, size_t elem, int64_t spare) {
+            return (uint64_t)std::max<int64_t>((int64_t)(b.bytes / elem) - spare, 0);
+        };
+        da.nodes = ptr<Node>(w->nodes[cur]);
+        da.pj = ptr<int32_t>(w->aj[cur]);
+        da.pmg = ptr<uint32_t>(w->aM[cur]);
+        da.fj = ptr<int32_t>(w->aj[nxt]);
+        da.fmg = ptr<uint32_t>(w->aM[nxt]);
+        da.fnodes = ptr<Node>(w->nodes[nxt]);
+        da.fr_ent_cap = std::min(cap(w->aj[nxt], 4, 0), cap(w->aM[nxt], 4, 0));
+        da.fr_node_cap = cap(w->nodes[nxt], sizeof(Node), 0);
+        da.lj = ptr<int32_t>(w->lj);
+        da.lM = ptr<int32_t>(w->lM);
+        da.lGa = ptr<int32_t>(w->lGa);
+        da.inj = ptr<Inject>(w->inj);
+        da.lf_ent_cap = std::min({cap(w->lj, 4, 1), cap(w->lM, 4, 1), cap(w->lGa, 4, 1)});
+        da.lf_node_cap = cap(w->inj, sizeof(Inject), 1);
+        da.rhits = ptr<RangeHit>(w->rhits);
+        da.hit_cap = cap(w->rhits, sizeof(RangeHit), 1);
+        da.ctr = ptr<LevelCounters>(w->ctr);
+        prof.mark(K_ROWS);
+        ae_rows_dna(da, num_sms * ae_rows_dna_blocks_per_sm(), st);
+        prof.mark(K_ROWS);
+        CU(cudaMemcpyAsync(tot(), w->ctr.p, sizeof(hc), cudaMemcpyDeviceToHost, st));
+        sync();
+        memcpy(&hc, tot(), sizeof(hc));
+        if (hc.overflow) throw ae_error{AE_ECUDA};   // the two phases of a task disagreed
+    };
+    run();
+    int64_t fr_ent = (int64_t)hc.fr_ent, fr_node = (int64_t)hc.fr_node;
+    int64_t lf_ent = (int64_t)hc.lf_ent - lf_ent_base, lf_node = (int64_t)hc.lf_node - lf_node_base;
+    int64_t hits = (int64_t)hc.hits - rh_base;
+    const bool retried = hc.retry != 0;
+    if (retried) {
+        ++dna_retries;
+        grow(fr_ent, lf_ent, fr_node, lf_node, hits, true);
+        run();
+        if (hc.retry || (int64_t)hc.fr_ent != fr_ent || (int64_t)hc.fr_node != fr_node ||
+            (int64_t)hc.lf_ent - lf_ent_base != lf_ent || (int64_t)hc.lf_node - lf_node_base != lf_node ||
+            (int64_t)hc.hits - rh_base != hits)
+            throw ae_error{AE_ECUDA};   // the same level gave other totals
+    }
     stats.triples += (int64_t)hc.triples;
-    ensure(w->aj[nxt], std::max<int64_t>(fr_ent, 1) * 4, st);
-    ensure(w->aM[nxt], std::max<int64_t>(fr_ent, 1) * 4, st);
-    ensure(w->nodes[nxt], std::max<int64_t>(fr_node, 1) * sizeof(Node), st);
-    ensure_keep(w->lj, (size_t)(lf_ent_base + lf_ent + 1) * 4, (size_t)lf_ent_base * 4, st);
-    ensure_keep(w->lM, (size_t)(lf_ent_base + lf_ent + 1) * 4, (size_t)lf_ent_base * 4, st);
-    ensure_keep(w->lGa, (size_t)(lf_ent_base + lf_ent + 1) * 4, (size_t)lf_ent_base * 4, st);
-    ensure_keep(w->inj, (size_t)(lf_node_base + lf_node + 1) * sizeof(Inject), (size_t)lf_node_base * sizeof(Inject),
-                st);
-    ensure_keep(w->rhits, (size_t)(rh_base + hits + 1) * sizeof(RangeHit), (size_t)rh_base * sizeof(RangeHit), st);
-    // the buffers above may have moved: the pointers are taken after sizing
-    da.nodes = ptr<Node>(w->nodes[cur]);
-    da.pj = ptr<int32_t>(w->aj[cur]);
-    da.pmg = ptr<uint32_t>(w->aM[cur]);
-    da.kcnt = ptr<uint32_t>(w->kcnt);
-    da.khit = ptr<uint32_t>(w->khit);
-    da.fj = ptr<int32_t>(w->aj[nxt]);
-    da.fmg = ptr<uint32_t>(w->aM[nxt]);
-    da.fnodes = ptr<Node>(w->nodes[nxt]);
-    da.fr_ent_cap = (uint64_t)fr_ent;
-    da.fr_node_cap = (uint64_t)fr_node;
-    da.lj = ptr<int32_t>(w->lj);
-    da.lM = ptr<int32_t>(w->lM);
-    da.lGa = ptr<int32_t>(w->lGa);
-    da.inj = ptr<Inject>(w->inj);
-    da.lf_ent_cap = (uint64_t)(lf_ent_base + lf_ent);
-    da.lf_node_cap = (uint64_t)(lf_node_base + lf_node);
-    da.rhits = ptr<RangeHit>(w->rhits);
-    da.hit_cap = (uint64_t)(rh_base + hits);
-    da.task_tot = ptr<uint32_t>(w->task_tot);
-    da.task_off = hc.wide ? nullptr : ptr<uint64_t>(w->task_off);
-    da.base_off[0] = 0;
-    da.base_off[1] = (uint64_t)lf_ent_base;
-    da.base_off[2] = 0;
-    da.base_off[3] = (uint64_t)lf_node_base;
-    da.base_off[4] = (uint64_t)rh_base;
-    prof.mark(K_ROWS);
-    ae_rows_dna(da, true, num_sms * ae_rows_dna_blocks_per_sm(true), st);
-    prof.mark(K_ROWS);
+    dna_nodes += F;
+    dna_entries += fr_ent + lf_ent;
+    {
+        const double out[5] = {(double)fr_ent, (double)lf_ent, (double)fr_node, (double)lf_node, (double)hits};
+        for (int q = 0; q < 5; ++q) dna_ratio[q] = in[q] > 0 ? out[q] / in[q] : 0.0;
+        dna_ratio_ok = true;
+    }
     if (trace()) {
-        sync();   // trace mode only: the level's own wall time
         fprintf(stderr, "[ae level] dna %s nodes %lld (per task %d) entries %lld triples %lld -> frontier %lld nodes %lld, "
-                        "leaf %lld rows %lld; %.3f ms\n",
+                        "leaf %lld rows %lld%s; %.3f ms\n",
                 da.sequential ? "walk" : "spread", (long long)F, npt, (long long)cur_ent, (long long)hc.triples,
-                (long long)fr_ent, (long long)fr_node, (long long)lf_ent, (long long)lf_node, ms_since(t_level));
+                (long long)fr_ent, (long long)fr_node, (long long)lf_ent, (long long)lf_node,
+                retried ? " (run again at exact sizes)" : "", ms_since(t_level));
     }
     lf_ent_base += lf_ent;
     lf_node_base += lf_node;
@@ -1253,9 +1285,9 @@ ae_status search_core(const ae_index *idx, Workspace *w, const int64_t *offsets,
         DevStats ds;
         CU(cudaMemcpyAsync(&ds, w->stats.p, sizeof(ds), cudaMemcpyDeviceToHost, st));
         CU(cudaStreamSynchronize(st));
-        s.stats.nodes = (int64_t)ds.nodes;
+        s.stats.nodes = (int64_t)ds.nodes + s.dna_nodes;
         s.stats.leaf_rows = (int64_t)ds.leaf_rows;
-        s.stats.entries = (int64_t)ds.entries;
+        s.stats.entries = (int64_t)ds.entries + s.dna_entries;
         for (int k = 0; k < 3; ++k) s.stats.entries_tier[k] = (int64_t)ds.tier[k];
         s.stats.entries_leaf = (int64_t)ds.entries_leaf;
         s.stats.dominated = (int64_t)ds.dominated;

@@ -109,6 +109,7 @@ struct LevelCounters {
     unsigned long long fr_ent, fr_node, lf_ent, lf_node, hits;
     unsigned long long overflow, task_c, task_w, wide;   // wide: a task total passed 2^32 - 1
     unsigned long long triples;   // DNA int16x2 route: (child, parent entry) pairs of the level
+    unsigned long long retry;     // DNA int16x2 route: a reservation passed an arena's capacity
 };
 
 struct RowsArgs {
@@ -153,11 +154,14 @@ void ae_rows(const RowsArgs &a, bool write, int blocks, cudaStream_t st);
 int ae_rows_blocks_per_sm(bool write);   // blocks per SM to launch a k_rows pass with (one full wave)
 void ae_mg_to_i32(int32_t *M, int32_t *Ga, int64_t n, cudaStream_t st);
 
-// ---- one trie level of the DNA int16x2 route, one lane per parent entry
-// (ae_rows_dna.cu).  Tasks are groups of nodes_per_task (<= 32) nodes whose
-// child ranges are taken in the task's prologue; kcnt/khit (4 per node, by
-// letter) carry each child's outputs and hits from the count to the write pass.
-// The output arguments are those of RowsArgs.
+// ---- one trie level of the DNA int16x2 route in one launch (ae_rows_dna.cu).
+// Tasks are groups of nodes_per_task (<= 32) nodes whose child ranges are
+// taken in the task's prologue; each task counts its outputs, reserves its
+// ranges on the level cursors of `ctr` (fr_ent, lf_ent, fr_node, lf_node,
+// hits, uploaded at the arenas' bases) and writes them.  A reservation past a
+// capacity raises ctr->retry and leaves the task unwritten; the cursors end at
+// the level's exact totals either way.  The output arguments are those of
+// RowsArgs.
 struct DnaRowsArgs {
     IndexView ix;
     ScoreView sc;
@@ -171,25 +175,20 @@ struct DnaRowsArgs {
                                           // (short rows); 0: one lane per parent entry (long rows)
     const int32_t *pj;                    // parent arena: column, packed (M | G_a << 16)
     const uint32_t *pmg;
-    uint32_t *kcnt, *khit;                // per (node, letter): entries, hits
-    uint32_t *task_tot;                   // count pass: per arena kind and task, as in RowsArgs
-    const uint64_t *task_off;             // write pass: their exclusive scan (NULL: atomics)
-    uint64_t task_stride;
-    uint64_t base_off[5];
     int32_t *fj;                          // next-level arena (packed rows)
     uint32_t *fmg;
     Node *fnodes;
     uint64_t fr_ent_cap, fr_node_cap;
     int32_t *lj, *lM, *lGa;               // leaf arena (int32 rows)
     Inject *inj;
-    uint64_t lf_ent_cap, lf_node_cap;
+    uint64_t lf_ent_cap, lf_node_cap;     // absolute: the leaf arenas accumulate over levels
     RangeHit *rhits;
     uint64_t hit_cap;
     LevelCounters *ctr;
-    DevStats *stats;
 };
-void ae_rows_dna(const DnaRowsArgs &a, bool write, int blocks, cudaStream_t st);
-int ae_rows_dna_blocks_per_sm(bool write);
+void ae_rows_dna(const DnaRowsArgs &a, int blocks, cudaStream_t st);
+int ae_rows_dna_blocks_per_sm();
+int ae_rows_dna_warps_per_block();
 struct LeafArgs {
     IndexView ix;
     ScoreView sc;

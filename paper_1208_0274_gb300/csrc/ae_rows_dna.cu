@@ -1,24 +1,25 @@
 // One trie level of the DNA int16x2 route (Section 5 (3) and Section 2.2),
-// organised around the parent entry.
+// organised around the parent entry, in one launch.
 //
 // A task is a group of up to 32 frontier nodes, one per lane.  Its prologue
 // takes each node's child ranges for all four letters from one decode of the
 // occurrence block at each end of the node's SA range (Section 5 (3):
 // lo' = C[c] + Occ(c, lo), hi' = C[c] + Occ(c, hi)); a single occurrence has
-// only the child BWT[lo] (one LF step).  The rows of the task's nodes are then
-// laid end to end over the lanes, one parent entry per lane, 32 at a time, and
-// each lane computes the slots of that entry for every child of its node:
-// the vertical gap G_a (the same for all children) once, the diagonal terms per
-// child.  Horizontal gaps are a max-plus scan segmented by node, as in the
-// general kernel (ae_trie.cu).
+// only the child BWT[lo] (one LF step).  The task then
 //
-//   count pass  per (node, child): output entries and hits; per task: totals
-//               per output arena (scanned on the device into task offsets).
-//   write pass  the same computation again, now writing child node records,
-//               injections, row entries and range hits at the scanned offsets.
+//   counts    per (node, child) the output entries and hits of the child rows,
+//   reserves  its ranges in the five output arenas (frontier rows, leaf rows,
+//             frontier nodes, leaf injections, range hits) with one atomic
+//             per arena on the level's cursors, and
+//   writes    the child node records, injections, row entries and range hits,
+//             computing the rows a second time.
 //
-// The general kernel (ae_trie.cu) handles protein, the int32 route, root rows
-// and cost-tier counting; both produce the same nodes and arenas.
+// Rows are computed in one of two layouts chosen per level: short parent rows
+// walked one lane per (node, child) in column order (the horizontal gap as a
+// running key), long rows spread one parent entry per lane with the horizontal
+// gap as a segmented max-plus scan.  The general kernel (ae_trie.cu) handles
+// protein, the int32 route, root rows and cost-tier counting; both produce the
+// same nodes and arenas.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -29,13 +30,10 @@ namespace {
 using namespace aedev;
 
 constexpr int DW = 8;   // warps per block
-// Resident blocks per SM the passes are compiled for and launched with (64
-// registers a thread; fewer registers spill in the row loop)
-#ifndef AE_DNA_MINB_COUNT
-#define AE_DNA_MINB_COUNT 4
-#endif
-#ifndef AE_DNA_MINB_WRITE
-#define AE_DNA_MINB_WRITE 4
+// Resident blocks per SM the kernel is compiled for and launched with (64
+// registers a thread)
+#ifndef AE_DNA_MINB
+#define AE_DNA_MINB 4
 #endif
 
 // Occ(c, k) for c = A, C, G, T at once from one 32-byte block (layout in
@@ -92,13 +90,16 @@ __device__ __forceinline__ unsigned kids4(const IndexView &ix, uint32_t lo, uint
     return mask;
 }
 
-// Per-warp shared state of a task: per (node lane, letter) the outputs and
-// hits counted so far (count pass), or the next output positions relative to
-// the task's arena bases and the child's SA range (write pass).
+// Per-warp shared state of a task, per (node lane, letter): the outputs and
+// hits counted so far (count phase) or the next output positions relative to
+// the task's arena bases (write phase), the counted totals (the write phase's
+// bounds) and the child's SA range.
 struct WarpSmem {
     uint32_t a[128];    // count: entries   write: next entry position
     uint32_t h[128];    // count: hits      write: next hit position
-    uint32_t lo[128];   // write: child SA range
+    uint32_t be[128];   // write: the child's counted entries
+    uint32_t bh[128];   // write: the child's counted hits
+    uint32_t lo[128];   // child SA range
     uint32_t hi[128];
     int32_t carry[4];   // per child index: the G_b scan's carry into the next chunk
     uint64_t base[3];   // write: the task's first slot in the frontier, leaf and hit arenas
@@ -135,13 +136,13 @@ __device__ __forceinline__ uint64_t excl_scan_u64(uint64_t v, uint64_t &total) {
 // parent row entry by entry in column order and carries the horizontal gap as
 // a running key (the recurrence of Section 2.2 in its sequential form), so no
 // scan, vote or compaction is needed; siblings sit in adjacent lanes and read
-// the same parent entries.  Count pass: the pair's entries and hits go to its
-// (node, letter) slot.  Write pass: the pair writes its child row from the
+// the same parent entries.  Count phase: the pair's entries and hits go to its
+// (node, letter) slot.  Write phase: the pair writes its child row from the
 // slot's position on.  The values equal those of the lane-per-entry form.
 template <bool WRITE>
 __device__ __forceinline__ void rows_seq(const DnaRowsArgs &a, WarpSmem &sm, int lane, unsigned kmask, unsigned smask,
                                          uint32_t len, uint64_t noff, int32_t qm, int32_t qH, int32_t tbase,
-                                         uint32_t qoff, int32_t qid, int64_t vbase) {
+                                         uint32_t qoff, int32_t qid) {
     const ScoreView &sc = a.sc;
     const int32_t u = -sc.ss, oe = sc.sg + sc.ss, g = sc.gmax, sa = sc.sa, sb = sc.sb;
     const int32_t strong = -oe;
@@ -195,14 +196,14 @@ __device__ __forceinline__ void rows_seq(const DnaRowsArgs &a, WarpSmem &sm, int
         const int slot = L * 4 + c;
         const uint8_t *P = a.qv.codes + qo;
         uint64_t eout = 0, hout = 0;
-        uint32_t clo = 0, chi = 0, ebud = 0, hbud = 0;   // write pass: the child's outputs as counted
+        uint32_t clo = 0, chi = 0, ebud = 0, hbud = 0;   // write phase: the child's outputs as counted
         if (WRITE) {
             eout = sm.base[st ? 0 : 1] + sm.a[slot];
             hout = sm.base[2] + sm.h[slot];
             clo = sm.lo[slot];
             chi = sm.hi[slot];
-            ebud = a.kcnt[(vbase + L) * 4 + c];
-            hbud = a.khit[(vbase + L) * 4 + c];
+            ebud = sm.be[slot];
+            hbud = sm.bh[slot];
         }
         uint32_t cnt = 0, hcnt = 0;
         bool bad = false;
@@ -264,10 +265,10 @@ __device__ __forceinline__ void rows_seq(const DnaRowsArgs &a, WarpSmem &sm, int
                 cnt += (uint32_t)aliveA + (uint32_t)aliveB + (uint32_t)run_len;
                 hcnt += (uint32_t)hA + (uint32_t)hB + (st ? (uint32_t)run_hits : 0u);
             } else if (!bad) {
-                // every write stays inside the child's own range, as the count pass sized it
+                // every write stays inside the child's own range, as the count phase sized it
                 if (cnt + (uint32_t)aliveA + (uint32_t)aliveB + (uint32_t)run_len > ebud ||
                     hcnt + (uint32_t)hA + (uint32_t)hB + (st ? (uint32_t)run_hits : 0u) > hbud) {
-                    bad = true;   // the passes disagree: reported, not written
+                    bad = true;   // the phases disagree: reported, not written
                 } else {
                     if (aliveA) {
                         if (st) {
@@ -319,25 +320,292 @@ __device__ __forceinline__ void rows_seq(const DnaRowsArgs &a, WarpSmem &sm, int
     }
 }
 
-template <bool WRITE, bool SEQ>
-__global__ void __launch_bounds__(DW * 32, WRITE ? AE_DNA_MINB_WRITE : AE_DNA_MINB_COUNT) k_rows_dna(DnaRowsArgs a) {
-    __shared__ WarpSmem smem[DW];
-    const int lane = threadIdx.x & 31;
-    WarpSmem &sm = smem[threadIdx.x >> 5];
-    const unsigned le = (lane == 31) ? 0xffffffffu : ((1u << (lane + 1)) - 1u);
+// Rows of long parent rows: the task's parent entries laid end to end over the
+// lanes, 32 at a time, one entry per lane; each lane computes the slots of its
+// entry for every child of its node (G_a once, the diagonal terms per child)
+// and the horizontal gaps are a max-plus scan segmented by node.  `woff` is
+// the lane's node's first entry in the task, `total` the task's entries.
+template <bool WRITE>
+__device__ __forceinline__ void rows_spread(const DnaRowsArgs &a, WarpSmem &sm, int lane, unsigned kmask,
+                                            unsigned smask, uint32_t len, uint64_t noff, int32_t qm, int32_t qH,
+                                            int32_t tbase, uint32_t qoff, int32_t qid, uint32_t woff,
+                                            uint32_t total) {
     const ScoreView &sc = a.sc;
     const int32_t u = -sc.ss, oe = sc.sg + sc.ss, g = sc.gmax, sa = sc.sa, sb = sc.sb;
     const int32_t strong = -oe;   // a gap state from M' can be live only if M' > |s_g + s_s| (Eq. 3)
+    const unsigned le = (lane == 31) ? 0xffffffffu : ((1u << (lane + 1)) - 1u);
+    // ---- the rows: parent entries laid end to end over the lanes
+    if (lane < 4) sm.carry[lane] = AE_KNEG;
+    __syncwarp();
+    for (uint32_t t0 = 0; t0 < total; t0 += 32) {
+        const uint32_t t = t0 + lane;
+        const bool valid = t < total;
+        int L = 0;
+#pragma unroll
+        for (int step = 16; step > 0; step >>= 1) {
+            const uint32_t o = __shfl_sync(FULL, woff, L + step);
+            if (o <= t) L += step;
+        }
+        const uint32_t k = t - __shfl_sync(FULL, woff, L);
+        const uint32_t nlen = __shfl_sync(FULL, len, L);
+        const uint64_t off = __shfl_sync(FULL, noff, L);
+        const unsigned km = __shfl_sync(FULL, kmask, L);
+        const unsigned sm_ = __shfl_sync(FULL, smask, L);
+        const int32_t m = __shfl_sync(FULL, qm, L);
+        const int32_t H = __shfl_sync(FULL, qH, L);
+        const int32_t tb0 = __shfl_sync(FULL, tbase, L);
+        const uint32_t qo = __shfl_sync(FULL, qoff, L);
+        const int32_t eq = WRITE ? __shfl_sync(FULL, qid, L) : 0;   // query of the entry's node
+        const unsigned heads = __ballot_sync(FULL, !valid || k == 0 || lane == 0);
+        const int first_lane = 31 - __clz(heads & le);
+        const bool next_in = (lane < 31) && (((heads >> (lane + 1)) & 1u) == 0);
+        const bool is_last = valid && !next_in;
+        int32_t j = m;
+        uint32_t mg = 0;
+        if (valid) {
+            j = a.pj[off + k];
+            mg = a.pmg[off + k];
+        }
+        const int32_t M = (int32_t)(int16_t)(mg & 0xFFFFu);   // live iff > 0
+        int32_t jn = __shfl_down_sync(FULL, j, 1);
+        int32_t pjv = __shfl_up_sync(FULL, j, 1), pMv = __shfl_up_sync(FULL, M, 1);
+        if (valid) {
+            if (!next_in) jn = (k + 1 < nlen) ? a.pj[off + k + 1] : m;
+            if (lane == first_lane) {
+                if (k > 0) {
+                    pjv = a.pj[off + k - 1];
+                    pMv = (int32_t)(int16_t)(a.pmg[off + k - 1] & 0xFFFFu);
+                } else {
+                    pjv = -2;
+                    pMv = 0;
+                }
+            }
+        }
+        const uint8_t *P = a.qv.codes + qo;
+        const bool adjA = valid && pjv + 1 == j && pMv > 0;
+        const bool hasB = valid && (j + 1 < m) && (j + 1 != jn);
+        const int pA = (valid && (uint32_t)j < (uint32_t)m) ? (int)P[j] : 255;   // never past the query
+        const int pB = hasB ? (int)P[j + 1] : 255;
+        const int32_t traw = tb0 + j * g;
+        const int32_t tA = max(traw, 0), tB = max(traw + g, 0);
+        int32_t Gap = valid ? gap_from_mg(mg, sc.ss, oe) : AE_NEG;
+        Gap = Gap > tA ? Gap : AE_NEG;
+        const int32_t ju = j * u;
+        // the node continuing from the previous chunk sits at lane 0
+        const uint32_t k_lane0 = __shfl_sync(FULL, k, 0);
+        const bool cont = first_lane == 0 && valid && k_lane0 > 0;
+        const bool goes_on = __shfl_sync(FULL, (int)(valid && k + 1 < nlen), 31) != 0;
+        unsigned rem = valid ? km : 0u;
+#pragma unroll 1
+        for (int i = 0; i < 4; ++i) {
+            const bool has_c = rem != 0;
+            if (!__any_sync(FULL, has_c)) {
+                if (lane == 0) sm.carry[i] = AE_KNEG;
+                __syncwarp();
+                continue;
+            }
+            const int c = has_c ? __ffs(rem) - 1 : 0;
+            rem &= rem - 1;
+            int32_t MpA = AE_NEG, MpB = AE_NEG;
+            if (has_c) {
+                int32_t DA = adjA ? pMv + (c == pA ? sa : sb) : AE_NEG;
+                DA = DA > tA ? DA : AE_NEG;
+                MpA = max(DA, Gap);
+                int32_t DB = M + (c == pB ? sa : sb);
+                MpB = (hasB && DB > tB) ? DB : AE_NEG;
+            }
+            const int32_t keyA = MpA > strong ? MpA + ju : AE_KNEG;
+            const int32_t keyB = MpB > strong ? MpB + ju + u : AE_KNEG;
+            int32_t incl = max(keyA, keyB);
+            int32_t excl = AE_KNEG;
+            const int32_t cin = sm.carry[i];
+            if (__any_sync(FULL, incl > AE_KNEG || (cont && cin > AE_KNEG))) {
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const int32_t o = __shfl_up_sync(FULL, incl, d);
+                    if (lane - d >= first_lane) incl = max(incl, o);
+                }
+                if (cont) incl = max(incl, cin);
+                excl = __shfl_up_sync(FULL, incl, 1);
+                if (lane - 1 < first_lane) excl = cont ? cin : AE_KNEG;
+            }
+            __syncwarp();
+            if (lane == 31) sm.carry[i] = goes_on ? incl : AE_KNEG;
+            // finish: G_b at the slots, then the gap run after them
+            const int32_t GbA = excl > AE_KNEG / 2 ? sc.sg - ju + excl : AE_NEG;
+            const int32_t MA = max(MpA, GbA);
+            const bool aliveA = has_c && MA > tA;
+            int32_t MB = AE_NEG;
+            bool aliveB = false;
+            if (has_c && hasB) {
+                const int32_t KB = max(excl, keyA);
+                const int32_t GbB = KB > AE_KNEG / 2 ? sc.sg - ju - u + KB : AE_NEG;
+                MB = max(MpB, GbB);
+                aliveB = MB > tB;
+            }
+            // the gap run after the lane's slots: columns [run_start, jn) where only G_b
+            // can live, G_b(x) = V0 - (x - run_start) u
+            int32_t run_len = 0, run_hits = 0;
+            const int32_t run_start = hasB ? j + 2 : j + 1;
+            const int32_t V0 = sc.sg - run_start * u + incl;
+            if (has_c && incl > AE_KNEG / 2 && run_start < jn && V0 > 0) {
+                const int32_t rl = min((int32_t)div_small((uint32_t)(V0 - 1), a.urec) + 1, jn - run_start);
+                if (traw + (run_start + rl - 1) * g <= 0) {   // threshold 0 over the whole run
+                    run_len = rl;
+                    if (V0 >= H) run_hits = min(rl, (int32_t)div_small((uint32_t)(V0 - H), a.urec) + 1);
+                } else {                                       // the query's last columns: exact form
+                    run_of(run_start, jn, incl, sc, m, H, u, run_len, run_hits);
+                }
+            }
+            const bool st = has_c && ((sm_ >> c) & 1u);
+            const bool hA = st && aliveA && MA >= H, hB = st && aliveB && MB >= H;
+            const uint32_t cnt = (uint32_t)aliveA + (uint32_t)aliveB + (uint32_t)run_len;
+            const uint32_t hcnt = (uint32_t)hA + (uint32_t)hB + (st ? (uint32_t)run_hits : 0u);
+            const unsigned in_seg = le & ~((1u << first_lane) - 1u);
+            uint32_t ci, hi;
+            if (__any_sync(FULL, run_len > 0)) {
+                ci = cnt;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const uint32_t x = __shfl_up_sync(FULL, ci, d);
+                    if (lane - d >= first_lane) ci += x;
+                }
+            } else {
+                ci = __popc(__ballot_sync(FULL, aliveA) & in_seg) + __popc(__ballot_sync(FULL, aliveB) & in_seg);
+            }
+            if (__any_sync(FULL, run_hits > 0)) {
+                hi = hcnt;
+#pragma unroll
+                for (int d = 1; d < 32; d <<= 1) {
+                    const uint32_t y = __shfl_up_sync(FULL, hi, d);
+                    if (lane - d >= first_lane) hi += y;
+                }
+            } else {
+                hi = __popc(__ballot_sync(FULL, hA) & in_seg) + __popc(__ballot_sync(FULL, hB) & in_seg);
+            }
+            const int slot = L * 4 + c;
+            if (!WRITE) {
+                if (is_last && has_c) {
+                    sm.a[slot] += ci;
+                    sm.h[slot] += hi;
+                }
+                __syncwarp();
+                continue;
+            }
+            // ---- write the entries (and the hits of children that stay)
+            uint64_t e0 = 0, h0 = 0;
+            if (has_c) {
+                e0 = sm.base[st ? 0 : 1] + sm.a[slot] + (ci - cnt);
+                h0 = sm.base[2] + sm.h[slot] + (hi - hcnt);
+            }
+            __syncwarp();
+            if (is_last && has_c) {
+                sm.a[slot] += ci;
+                sm.h[slot] += hi;
+            }
+            // the outputs stay inside their arenas even if the two phases ever
+            // disagreed: such a chunk is reported (overflow) and not written
+            const bool outside = has_c && (e0 + cnt > (st ? a.fr_ent_cap : a.lf_ent_cap) ||
+                                           h0 + hcnt > a.hit_cap);
+            if (__any_sync(FULL, outside)) {
+                if (lane == 0) atomicExch(&a.ctr->overflow, 1ull);
+                __syncwarp();
+                continue;
+            }
+            if (aliveA) {
+                if (st) {
+                    a.fj[e0] = j;
+                    a.fmg[e0] = pack_mg(MA, Gap);
+                } else {
+                    a.lj[e0] = j;
+                    a.lM[e0] = MA;
+                    a.lGa[e0] = Gap;
+                }
+            }
+            if (aliveB) {
+                const uint64_t eb = e0 + (aliveA ? 1 : 0);
+                if (st) {
+                    a.fj[eb] = j + 1;
+                    a.fmg[eb] = pack_mg(MB, AE_NEG);
+                } else {
+                    a.lj[eb] = j + 1;
+                    a.lM[eb] = MB;
+                    a.lGa[eb] = AE_NEG;
+                }
+            }
+            if (hA || hB) {
+                const RangeHit base_hit = {sm.lo[slot], sm.hi[slot], eq, 0, 0, 0};
+                uint64_t hp = h0;
+                if (hA) {
+                    RangeHit r = base_hit;
+                    r.j = j;
+                    r.score = MA;
+                    a.rhits[hp++] = r;
+                }
+                if (hB) {
+                    RangeHit r = base_hit;
+                    r.j = j + 1;
+                    r.score = MB;
+                    a.rhits[hp] = r;
+                }
+            }
+            if (run_len > 0) {   // each lane writes its own run (a few cells)
+                const uint64_t er = e0 + (uint64_t)aliveA + (uint64_t)aliveB;
+                const uint64_t hr = h0 + (uint64_t)hA + (uint64_t)hB;
+                for (int32_t r = 0; r < run_len; ++r) {
+                    const int32_t col = run_start + r, val = V0 - r * u;
+                    if (st) {
+                        a.fj[er + r] = col;
+                        a.fmg[er + r] = pack_mg(val, AE_NEG);
+                    } else {
+                        a.lj[er + r] = col;
+                        a.lM[er + r] = val;
+                        a.lGa[er + r] = AE_NEG;
+                    }
+                    if (st && r < run_hits) {
+                        RangeHit rh = {sm.lo[slot], sm.hi[slot], eq, col, val, 0};
+                        a.rhits[hr + r] = rh;
+                    }
+                }
+            }
+            __syncwarp();
+        }
+    }
+}
+
+template <bool SEQ>
+__device__ __forceinline__ void rows_phase(bool write, const DnaRowsArgs &a, WarpSmem &sm, int lane,
+                                           unsigned kmask, unsigned smask, uint32_t len, uint64_t noff,
+                                           int32_t qm, int32_t qH, int32_t tbase, uint32_t qoff, int32_t qid,
+                                           uint32_t woff, uint32_t total) {
+    if (SEQ) {
+        if (write) rows_seq<true>(a, sm, lane, kmask, smask, len, noff, qm, qH, tbase, qoff, qid);
+        else rows_seq<false>(a, sm, lane, kmask, smask, len, noff, qm, qH, tbase, qoff, qid);
+    } else {
+        if (write) rows_spread<true>(a, sm, lane, kmask, smask, len, noff, qm, qH, tbase, qoff, qid, woff, total);
+        else rows_spread<false>(a, sm, lane, kmask, smask, len, noff, qm, qH, tbase, qoff, qid, woff, total);
+    }
+    __syncwarp();
+}
+
+// One launch per level.  Per task: prologue, count phase, reservation of the
+// task's output ranges (one atomic per arena on the level's cursors), write
+// phase.  A reservation past an arena's capacity leaves the task unwritten and
+// raises `retry`; the cursors still advance by every task's totals, so after
+// the launch they hold the level's exact sizes either way.
+template <bool SEQ>
+__global__ void __launch_bounds__(DW * 32, AE_DNA_MINB) k_rows_dna(DnaRowsArgs a) {
+    __shared__ WarpSmem smem[DW];
+    const int lane = threadIdx.x & 31;
+    WarpSmem &sm = smem[threadIdx.x >> 5];
+    const int32_t g = a.sc.gmax;
     const int64_t nnodes = a.nnodes;
     const int npt = a.nodes_per_task;
     const uint64_t ntask = (uint64_t)((nnodes + npt - 1) / npt);
-    unsigned long long *task_ctr = WRITE ? &a.ctr->task_w : &a.ctr->task_c;
-    uint64_t tot_mine = 0;   // count pass: lane q < 5 sums this warp's level total of arena kind q, lane 5 the triples
-    if (!WRITE && a.stats && blockIdx.x == 0 && threadIdx.x == 0)
-        atomicAdd(&a.stats->nodes, (unsigned long long)nnodes);
+    uint64_t trip_mine = 0;   // the (child, parent entry) pairs of this warp's tasks
 
     for (uint64_t tb = 0;;) {
-        if (lane == 0) tb = atomicAdd(task_ctr, 4ull);
+        if (lane == 0) tb = atomicAdd(&a.ctr->task_c, 4ull);
         tb = __shfl_sync(FULL, tb, 0);
         if (tb >= ntask) break;
     for (uint64_t task = tb; task < tb + 4 && task < ntask; ++task) {
@@ -382,417 +650,132 @@ __global__ void __launch_bounds__(DW * 32, WRITE ? AE_DNA_MINB_WRITE : AE_DNA_MI
         }
         const uint32_t total = __shfl_sync(FULL, woff, 31);
         woff -= work;
-        if (total == 0) {
-            if (!WRITE && lane < 5) a.task_tot[lane * a.task_stride + task] = 0u;
+        if (total == 0) continue;
+        trip_mine += reduce_add_u64((uint32_t)__popc(kmask) * len);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            sm.a[lane * 4 + c] = 0;
+            sm.h[lane * 4 + c] = 0;
+            sm.lo[lane * 4 + c] = clo[c];
+            sm.hi[lane * 4 + c] = chi[c];
+        }
+        __syncwarp();
+
+        // ---- count phase: per (node, child) outputs and hits
+        rows_phase<SEQ>(false, a, sm, lane, kmask, smask, len, nd.off, qm, qH, tbase, qoff, qid, woff, total);
+
+        // ---- reservation: the task's ranges in the five arenas
+        unsigned wmask = kmask;   // the children with any output (the others need no write walk)
+        uint32_t cn[4] = {0, 0, 0, 0}, ch[4] = {0, 0, 0, 0};
+        uint32_t s_fe = 0, s_le = 0, s_fn = 0, s_ln = 0, s_h = 0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            if ((kmask >> c) & 1u) {
+                cn[c] = sm.a[lane * 4 + c];
+                ch[c] = sm.h[lane * 4 + c];
+                if (cn[c] == 0 && ch[c] == 0) wmask &= ~(1u << c);
+                if ((smask >> c) & 1u) {
+                    s_fe += cn[c];
+                    s_fn += cn[c] ? 1u : 0u;
+                } else {
+                    s_le += cn[c];
+                    s_ln += cn[c] ? 1u : 0u;
+                }
+                s_h += ch[c];
+            }
+            sm.be[lane * 4 + c] = cn[c];
+            sm.bh[lane * 4 + c] = ch[c];
+        }
+        uint64_t tsum[5], base[5];
+        const uint64_t ex_fe = excl_scan_u64(s_fe, tsum[0]);
+        const uint64_t ex_le = excl_scan_u64(s_le, tsum[1]);
+        const uint64_t ex_fn = excl_scan_u64(s_fn, tsum[2]);
+        const uint64_t ex_ln = excl_scan_u64(s_ln, tsum[3]);
+        const uint64_t ex_h = excl_scan_u64(s_h, tsum[4]);
+        {
+            unsigned long long r[5] = {0, 0, 0, 0, 0};
+            if (lane == 0) {
+                if (tsum[0]) r[0] = atomicAdd(&a.ctr->fr_ent, (unsigned long long)tsum[0]);
+                if (tsum[1]) r[1] = atomicAdd(&a.ctr->lf_ent, (unsigned long long)tsum[1]);
+                if (tsum[2]) r[2] = atomicAdd(&a.ctr->fr_node, (unsigned long long)tsum[2]);
+                if (tsum[3]) r[3] = atomicAdd(&a.ctr->lf_node, (unsigned long long)tsum[3]);
+                if (tsum[4]) r[4] = atomicAdd(&a.ctr->hits, (unsigned long long)tsum[4]);
+            }
+#pragma unroll
+            for (int q = 0; q < 5; ++q) base[q] = __shfl_sync(FULL, r[q], 0);
+        }
+        if (tsum[0] + tsum[1] + tsum[4] == 0) {   // no child kept anything
+            __syncwarp();
             continue;
         }
-
-        unsigned wmask = kmask;   // write pass: the children with any output (the others need no walk)
-        if (!WRITE) {
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                sm.a[lane * 4 + c] = 0;
-                sm.h[lane * 4 + c] = 0;
-            }
-        } else {
-            // per-child outputs from the count pass -> positions in the task's output ranges
-            uint32_t cn[4] = {0, 0, 0, 0}, ch[4] = {0, 0, 0, 0};
-            uint32_t s_fe = 0, s_le = 0, s_fn = 0, s_ln = 0, s_h = 0;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                if ((kmask >> c) & 1u) {
-                    cn[c] = a.kcnt[v * 4 + c];
-                    ch[c] = a.khit[v * 4 + c];
-                    if (cn[c] == 0 && ch[c] == 0) wmask &= ~(1u << c);
-                    if ((smask >> c) & 1u) {
-                        s_fe += cn[c];
-                        s_fn += cn[c] ? 1u : 0u;
-                    } else {
-                        s_le += cn[c];
-                        s_ln += cn[c] ? 1u : 0u;
-                    }
-                    s_h += ch[c];
-                }
-            }
-            uint64_t tsum[5], base[5];
-            const uint64_t ex_fe = excl_scan_u64(s_fe, tsum[0]);
-            const uint64_t ex_le = excl_scan_u64(s_le, tsum[1]);
-            const uint64_t ex_fn = excl_scan_u64(s_fn, tsum[2]);
-            const uint64_t ex_ln = excl_scan_u64(s_ln, tsum[3]);
-            const uint64_t ex_h = excl_scan_u64(s_h, tsum[4]);
-            if (a.task_off) {
-#pragma unroll
-                for (int q = 0; q < 5; ++q) base[q] = a.base_off[q] + a.task_off[q * a.task_stride + task];
-            } else {
-                unsigned long long r[5] = {0, 0, 0, 0, 0};
-                if (lane == 0) {
-                    r[0] = atomicAdd(&a.ctr->fr_ent, (unsigned long long)tsum[0]);
-                    r[1] = atomicAdd(&a.ctr->lf_ent, (unsigned long long)tsum[1]);
-                    r[2] = atomicAdd(&a.ctr->fr_node, (unsigned long long)tsum[2]);
-                    r[3] = atomicAdd(&a.ctr->lf_node, (unsigned long long)tsum[3]);
-                    r[4] = atomicAdd(&a.ctr->hits, (unsigned long long)tsum[4]);
-                }
-#pragma unroll
-                for (int q = 0; q < 5; ++q) base[q] = __shfl_sync(FULL, r[q], 0);
-            }
-            // the count pass sized every range exactly; a reservation past the end
-            // means the passes disagreed, which is reported, never written
-            const bool ovf = base[0] + tsum[0] > a.fr_ent_cap || base[1] + tsum[1] > a.lf_ent_cap ||
-                             base[2] + tsum[2] > a.fr_node_cap || base[3] + tsum[3] > a.lf_node_cap ||
-                             base[4] + tsum[4] > a.hit_cap;
-            if (ovf) {
-                if (lane == 0) atomicExch(&a.ctr->overflow, 1ull);
-                continue;
-            }
-            if (lane == 0) {
-                sm.base[0] = base[0];
-                sm.base[1] = base[1];
-                sm.base[2] = base[4];
-            }
-            uint64_t efr = ex_fe, elf = ex_le, nfr = ex_fn, nlf = ex_ln, hh = ex_h;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                sm.lo[lane * 4 + c] = clo[c];
-                sm.hi[lane * 4 + c] = chi[c];
-                if (!((kmask >> c) & 1u)) continue;
-                const bool st = (smask >> c) & 1u;
-                const uint64_t e = st ? efr : elf;
-                sm.a[lane * 4 + c] = (uint32_t)e;
-                sm.h[lane * 4 + c] = (uint32_t)hh;
-                if (cn[c]) {
-                    if (st) {
-                        Node cn_;
-                        cn_.lo = clo[c];
-                        cn_.hi = chi[c];
-                        const uint32_t uq = (chi[c] - clo[c] == 1) ? pcnt + 1u : 0u;
-                        cn_.item = (int32_t)((uint32_t)qid | (uq << 24));
-                        cn_.cnt = cn[c];
-                        cn_.off = base[0] + e;
-                        a.fnodes[base[2] + nfr] = cn_;
-                        ++nfr;
-                    } else {
-                        Inject in;
-                        in.qid = qid;
-                        in.e = a.ix.tend[clo[c]];
-                        in.cnt = cn[c];
-                        in.pad = 0;
-                        in.off = base[1] + e;
-                        a.inj[base[3] + nlf] = in;
-                        ++nlf;
-                    }
-                }
-                if (st) efr += cn[c];
-                else elf += cn[c];
-                hh += ch[c];
-            }
-        }
-        __syncwarp();
-
-        if (SEQ) {
-            rows_seq<WRITE>(a, sm, lane, WRITE ? wmask : kmask, smask, len, nd.off, qm, qH, tbase, qoff, qid,
-                            (int64_t)task * npt);
+        // a range past an arena's capacity: the task is not written, the level is
+        // run again with arenas of the exact sizes the cursors then hold
+        const bool full = base[0] + tsum[0] > a.fr_ent_cap || base[1] + tsum[1] > a.lf_ent_cap ||
+                          base[2] + tsum[2] > a.fr_node_cap || base[3] + tsum[3] > a.lf_node_cap ||
+                          base[4] + tsum[4] > a.hit_cap;
+        if (full) {
+            if (lane == 0) atomicExch(&a.ctr->retry, 1ull);
             __syncwarp();
+            continue;
         }
-        // ---- the rows: parent entries laid end to end over the lanes
-        if (lane < 4) sm.carry[lane] = AE_KNEG;
-        __syncwarp();
-        for (uint32_t t0 = 0; t0 < (SEQ ? 0u : total); t0 += 32) {
-            const uint32_t t = t0 + lane;
-            const bool valid = t < total;
-            int L = 0;
-#pragma unroll
-            for (int step = 16; step > 0; step >>= 1) {
-                const uint32_t o = __shfl_sync(FULL, woff, L + step);
-                if (o <= t) L += step;
-            }
-            const uint32_t k = t - __shfl_sync(FULL, woff, L);
-            const uint32_t nlen = __shfl_sync(FULL, len, L);
-            const uint64_t off = __shfl_sync(FULL, nd.off, L);
-            const unsigned km = __shfl_sync(FULL, WRITE ? wmask : kmask, L);
-            const unsigned sm_ = __shfl_sync(FULL, smask, L);
-            const int32_t m = __shfl_sync(FULL, qm, L);
-            const int32_t H = __shfl_sync(FULL, qH, L);
-            const int32_t tb0 = __shfl_sync(FULL, tbase, L);
-            const uint32_t qo = __shfl_sync(FULL, qoff, L);
-            const int32_t eq = WRITE ? __shfl_sync(FULL, qid, L) : 0;   // query of the entry's node
-            const unsigned heads = __ballot_sync(FULL, !valid || k == 0 || lane == 0);
-            const int first_lane = 31 - __clz(heads & le);
-            const bool next_in = (lane < 31) && (((heads >> (lane + 1)) & 1u) == 0);
-            const bool is_last = valid && !next_in;
-            int32_t j = m;
-            uint32_t mg = 0;
-            if (valid) {
-                j = a.pj[off + k];
-                mg = a.pmg[off + k];
-            }
-            const int32_t M = (int32_t)(int16_t)(mg & 0xFFFFu);   // live iff > 0
-            int32_t jn = __shfl_down_sync(FULL, j, 1);
-            int32_t pjv = __shfl_up_sync(FULL, j, 1), pMv = __shfl_up_sync(FULL, M, 1);
-            if (valid) {
-                if (!next_in) jn = (k + 1 < nlen) ? a.pj[off + k + 1] : m;
-                if (lane == first_lane) {
-                    if (k > 0) {
-                        pjv = a.pj[off + k - 1];
-                        pMv = (int32_t)(int16_t)(a.pmg[off + k - 1] & 0xFFFFu);
-                    } else {
-                        pjv = -2;
-                        pMv = 0;
-                    }
-                }
-            }
-            const uint8_t *P = a.qv.codes + qo;
-            const bool adjA = valid && pjv + 1 == j && pMv > 0;
-            const bool hasB = valid && (j + 1 < m) && (j + 1 != jn);
-            const int pA = (valid && (uint32_t)j < (uint32_t)m) ? (int)P[j] : 255;   // never past the query
-            const int pB = hasB ? (int)P[j + 1] : 255;
-            const int32_t traw = tb0 + j * g;
-            const int32_t tA = max(traw, 0), tB = max(traw + g, 0);
-            int32_t Gap = valid ? gap_from_mg(mg, sc.ss, oe) : AE_NEG;
-            Gap = Gap > tA ? Gap : AE_NEG;
-            const int32_t ju = j * u;
-            // the node continuing from the previous chunk sits at lane 0
-            const uint32_t k_lane0 = __shfl_sync(FULL, k, 0);
-            const bool cont = first_lane == 0 && valid && k_lane0 > 0;
-            const bool goes_on = __shfl_sync(FULL, (int)(valid && k + 1 < nlen), 31) != 0;
-            unsigned rem = valid ? km : 0u;
-#pragma unroll 1
-            for (int i = 0; i < 4; ++i) {
-                const bool has_c = rem != 0;
-                if (!__any_sync(FULL, has_c)) {
-                    if (lane == 0) sm.carry[i] = AE_KNEG;
-                    __syncwarp();
-                    continue;
-                }
-                const int c = has_c ? __ffs(rem) - 1 : 0;
-                rem &= rem - 1;
-                int32_t MpA = AE_NEG, MpB = AE_NEG;
-                if (has_c) {
-                    int32_t DA = adjA ? pMv + (c == pA ? sa : sb) : AE_NEG;
-                    DA = DA > tA ? DA : AE_NEG;
-                    MpA = max(DA, Gap);
-                    int32_t DB = M + (c == pB ? sa : sb);
-                    MpB = (hasB && DB > tB) ? DB : AE_NEG;
-                }
-                const int32_t keyA = MpA > strong ? MpA + ju : AE_KNEG;
-                const int32_t keyB = MpB > strong ? MpB + ju + u : AE_KNEG;
-                int32_t incl = max(keyA, keyB);
-                int32_t excl = AE_KNEG;
-                const int32_t cin = sm.carry[i];
-                if (__any_sync(FULL, incl > AE_KNEG || (cont && cin > AE_KNEG))) {
-#pragma unroll
-                    for (int d = 1; d < 32; d <<= 1) {
-                        const int32_t o = __shfl_up_sync(FULL, incl, d);
-                        if (lane - d >= first_lane) incl = max(incl, o);
-                    }
-                    if (cont) incl = max(incl, cin);
-                    excl = __shfl_up_sync(FULL, incl, 1);
-                    if (lane - 1 < first_lane) excl = cont ? cin : AE_KNEG;
-                }
-                __syncwarp();
-                if (lane == 31) sm.carry[i] = goes_on ? incl : AE_KNEG;
-                // finish: G_b at the slots, then the gap run after them
-                const int32_t GbA = excl > AE_KNEG / 2 ? sc.sg - ju + excl : AE_NEG;
-                const int32_t MA = max(MpA, GbA);
-                const bool aliveA = has_c && MA > tA;
-                int32_t MB = AE_NEG;
-                bool aliveB = false;
-                if (has_c && hasB) {
-                    const int32_t KB = max(excl, keyA);
-                    const int32_t GbB = KB > AE_KNEG / 2 ? sc.sg - ju - u + KB : AE_NEG;
-                    MB = max(MpB, GbB);
-                    aliveB = MB > tB;
-                }
-                // the gap run after the lane's slots: columns [run_start, jn) where only G_b
-                // can live, G_b(x) = V0 - (x - run_start) u
-                int32_t run_len = 0, run_hits = 0;
-                const int32_t run_start = hasB ? j + 2 : j + 1;
-                const int32_t V0 = sc.sg - run_start * u + incl;
-                if (has_c && incl > AE_KNEG / 2 && run_start < jn && V0 > 0) {
-                    const int32_t rl = min((int32_t)div_small((uint32_t)(V0 - 1), a.urec) + 1, jn - run_start);
-                    if (traw + (run_start + rl - 1) * g <= 0) {   // threshold 0 over the whole run
-                        run_len = rl;
-                        if (V0 >= H) run_hits = min(rl, (int32_t)div_small((uint32_t)(V0 - H), a.urec) + 1);
-                    } else {                                       // the query's last columns: exact form
-                        run_of(run_start, jn, incl, sc, m, H, u, run_len, run_hits);
-                    }
-                }
-                const bool st = has_c && ((sm_ >> c) & 1u);
-                const bool hA = st && aliveA && MA >= H, hB = st && aliveB && MB >= H;
-                const uint32_t cnt = (uint32_t)aliveA + (uint32_t)aliveB + (uint32_t)run_len;
-                const uint32_t hcnt = (uint32_t)hA + (uint32_t)hB + (st ? (uint32_t)run_hits : 0u);
-                const unsigned in_seg = le & ~((1u << first_lane) - 1u);
-                uint32_t ci, hi;
-                if (__any_sync(FULL, run_len > 0)) {
-                    ci = cnt;
-#pragma unroll
-                    for (int d = 1; d < 32; d <<= 1) {
-                        const uint32_t x = __shfl_up_sync(FULL, ci, d);
-                        if (lane - d >= first_lane) ci += x;
-                    }
-                } else {
-                    ci = __popc(__ballot_sync(FULL, aliveA) & in_seg) + __popc(__ballot_sync(FULL, aliveB) & in_seg);
-                }
-                if (__any_sync(FULL, run_hits > 0)) {
-                    hi = hcnt;
-#pragma unroll
-                    for (int d = 1; d < 32; d <<= 1) {
-                        const uint32_t y = __shfl_up_sync(FULL, hi, d);
-                        if (lane - d >= first_lane) hi += y;
-                    }
-                } else {
-                    hi = __popc(__ballot_sync(FULL, hA) & in_seg) + __popc(__ballot_sync(FULL, hB) & in_seg);
-                }
-                const int slot = L * 4 + c;
-                if (!WRITE) {
-                    if (is_last && has_c) {
-                        sm.a[slot] += ci;
-                        sm.h[slot] += hi;
-                    }
-                    __syncwarp();
-                    continue;
-                }
-                // ---- write the entries (and the hits of children that stay)
-                uint64_t e0 = 0, h0 = 0;
-                if (has_c) {
-                    e0 = sm.base[st ? 0 : 1] + sm.a[slot] + (ci - cnt);
-                    h0 = sm.base[2] + sm.h[slot] + (hi - hcnt);
-                }
-                __syncwarp();
-                if (is_last && has_c) {
-                    sm.a[slot] += ci;
-                    sm.h[slot] += hi;
-                }
-                // the outputs stay inside their arenas even if the two passes ever
-                // disagreed: such a chunk is reported (overflow) and not written
-                const bool outside = has_c && (e0 + cnt > (st ? a.fr_ent_cap : a.lf_ent_cap) ||
-                                               h0 + hcnt > a.hit_cap);
-                if (__any_sync(FULL, outside)) {
-                    if (lane == 0) atomicExch(&a.ctr->overflow, 1ull);
-                    __syncwarp();
-                    continue;
-                }
-                if (aliveA) {
-                    if (st) {
-                        a.fj[e0] = j;
-                        a.fmg[e0] = pack_mg(MA, Gap);
-                    } else {
-                        a.lj[e0] = j;
-                        a.lM[e0] = MA;
-                        a.lGa[e0] = Gap;
-                    }
-                }
-                if (aliveB) {
-                    const uint64_t eb = e0 + (aliveA ? 1 : 0);
-                    if (st) {
-                        a.fj[eb] = j + 1;
-                        a.fmg[eb] = pack_mg(MB, AE_NEG);
-                    } else {
-                        a.lj[eb] = j + 1;
-                        a.lM[eb] = MB;
-                        a.lGa[eb] = AE_NEG;
-                    }
-                }
-                if (hA || hB) {
-                    const RangeHit base_hit = {sm.lo[slot], sm.hi[slot], eq, 0, 0, 0};
-                    uint64_t hp = h0;
-                    if (hA) {
-                        RangeHit r = base_hit;
-                        r.j = j;
-                        r.score = MA;
-                        a.rhits[hp++] = r;
-                    }
-                    if (hB) {
-                        RangeHit r = base_hit;
-                        r.j = j + 1;
-                        r.score = MB;
-                        a.rhits[hp] = r;
-                    }
-                }
-                if (run_len > 0) {   // each lane writes its own run (a few cells)
-                    const uint64_t er = e0 + (uint64_t)aliveA + (uint64_t)aliveB;
-                    const uint64_t hr = h0 + (uint64_t)hA + (uint64_t)hB;
-                    for (int32_t r = 0; r < run_len; ++r) {
-                        const int32_t col = run_start + r, val = V0 - r * u;
-                        if (st) {
-                            a.fj[er + r] = col;
-                            a.fmg[er + r] = pack_mg(val, AE_NEG);
-                        } else {
-                            a.lj[er + r] = col;
-                            a.lM[er + r] = val;
-                            a.lGa[er + r] = AE_NEG;
-                        }
-                        if (st && r < run_hits) {
-                            RangeHit rh = {sm.lo[slot], sm.hi[slot], eq, col, val, 0};
-                            a.rhits[hr + r] = rh;
-                        }
-                    }
-                }
-                __syncwarp();
-            }
+        if (lane == 0) {
+            sm.base[0] = base[0];
+            sm.base[1] = base[1];
+            sm.base[2] = base[4];
         }
-        if (!WRITE) {
-            // ---- epilogue: per-child counts for the write pass, task totals per arena
-            uint32_t s_fe = 0, s_le = 0, s_fn = 0, s_ln = 0, s_h = 0;
+        uint64_t efr = ex_fe, elf = ex_le, nfr = ex_fn, nlf = ex_ln, hh = ex_h;
 #pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                if (!((kmask >> c) & 1u)) continue;
-                const uint32_t cn = sm.a[lane * 4 + c], ch = sm.h[lane * 4 + c];
-                a.kcnt[v * 4 + c] = cn;
-                a.khit[v * 4 + c] = ch;
-                if ((smask >> c) & 1u) {
-                    s_fe += cn;
-                    s_fn += cn ? 1u : 0u;
+        for (int c = 0; c < 4; ++c) {
+            if (!((kmask >> c) & 1u)) continue;
+            const bool st = (smask >> c) & 1u;
+            const uint64_t e = st ? efr : elf;
+            sm.a[lane * 4 + c] = (uint32_t)e;
+            sm.h[lane * 4 + c] = (uint32_t)hh;
+            if (cn[c]) {
+                if (st) {
+                    Node cn_;
+                    cn_.lo = clo[c];
+                    cn_.hi = chi[c];
+                    const uint32_t uq = (chi[c] - clo[c] == 1) ? pcnt + 1u : 0u;
+                    cn_.item = (int32_t)((uint32_t)qid | (uq << 24));
+                    cn_.cnt = cn[c];
+                    cn_.off = base[0] + e;
+                    a.fnodes[base[2] + nfr] = cn_;
+                    ++nfr;
                 } else {
-                    s_le += cn;
-                    s_ln += cn ? 1u : 0u;
-                }
-                s_h += ch;
-            }
-            const uint64_t trip = reduce_add_u64((uint32_t)__popc(kmask) * len);
-            if (lane == 5) tot_mine += trip;
-            uint64_t tt[5];
-            tt[0] = reduce_add_u64(s_fe);
-            tt[1] = reduce_add_u64(s_le);
-            tt[2] = reduce_add_u64(s_fn);
-            tt[3] = reduce_add_u64(s_ln);
-            tt[4] = reduce_add_u64(s_h);
-#pragma unroll
-            for (int q = 0; q < 5; ++q) {
-                if (lane == q) {
-                    tot_mine += tt[q];
-                    a.task_tot[q * a.task_stride + task] = (uint32_t)tt[q];
-                    if (tt[q] > 0xFFFFFFFFull) atomicExch(&a.ctr->wide, 1ull);
+                    Inject in;
+                    in.qid = qid;
+                    in.e = a.ix.tend[clo[c]];
+                    in.cnt = cn[c];
+                    in.pad = 0;
+                    in.off = base[1] + e;
+                    a.inj[base[3] + nlf] = in;
+                    ++nlf;
                 }
             }
+            if (st) efr += cn[c];
+            else elf += cn[c];
+            hh += ch[c];
         }
         __syncwarp();
+
+        // ---- write phase: the same rows again, written at the reserved positions
+        rows_phase<SEQ>(true, a, sm, lane, wmask, smask, len, nd.off, qm, qH, tbase, qoff, qid, woff, total);
     }
     }
-    if (!WRITE && lane == 5 && tot_mine) atomicAdd(&a.ctr->triples, (unsigned long long)tot_mine);
-    if (!WRITE && lane < 5 && tot_mine) {
-        // kind q (fr_ent, lf_ent, fr_node, lf_node, hits) -> its LevelCounters field
-        const int field = (0x43120 >> (4 * lane)) & 0xF;
-        atomicAdd(&a.ctr->c_fr_ent + field, (unsigned long long)tot_mine);
-        if (a.stats && lane < 2) atomicAdd(&a.stats->entries, (unsigned long long)tot_mine);
-    }
+    if (lane == 0 && trip_mine) atomicAdd(&a.ctr->triples, (unsigned long long)trip_mine);
 }
 
 }  // namespace
 
-int ae_rows_dna_blocks_per_sm(bool write) { return write ? AE_DNA_MINB_WRITE : AE_DNA_MINB_COUNT; }
+int ae_rows_dna_blocks_per_sm() { return AE_DNA_MINB; }
+int ae_rows_dna_warps_per_block() { return DW; }
 
-void ae_rows_dna(const DnaRowsArgs &a, bool write, int blocks, cudaStream_t st) {
+void ae_rows_dna(const DnaRowsArgs &a, int blocks, cudaStream_t st) {
     if (a.nnodes <= 0) return;
     ++g_launches;
-    if (a.sequential) {
-        if (write)
-            k_rows_dna<true, true><<<blocks, DW * 32, 0, st>>>(a);
-        else
-            k_rows_dna<false, true><<<blocks, DW * 32, 0, st>>>(a);
-    } else {
-        if (write)
-            k_rows_dna<true, false><<<blocks, DW * 32, 0, st>>>(a);
-        else
-            k_rows_dna<false, false><<<blocks, DW * 32, 0, st>>>(a);
-    }
+    if (a.sequential)
+        k_rows_dna<true><<<blocks, DW * 32, 0, st>>>(a);
+    else
+        k_rows_dna<false><<<blocks, DW * 32, 0, st>>>(a);
 }
