@@ -208,16 +208,23 @@ __device__ __forceinline__ void rows_seq(const DnaRowsArgs &a, WarpSmem &sm, int
         uint32_t cnt = 0, hcnt = 0;
         bool bad = false;
         int32_t K = AE_KNEG, prev_j = -2, prev_M = 0;
-        int32_t jn = a.pj[off];
-        uint32_t mgn = a.pmg[off];
+        // loads run ahead of their use: the next entry and its query letters, and
+        // the column of the entry after it
+        int32_t j_c = a.pj[off];
+        uint32_t mg_c = a.pmg[off];
+        int32_t j_n = nlen > 1 ? a.pj[off + 1] : m;
+        int pa_c = (uint32_t)j_c < (uint32_t)m ? (int)P[j_c] : 255;
+        int pb_c = (uint32_t)(j_c + 1) < (uint32_t)m ? (int)P[j_c + 1] : 255;
         for (uint32_t k = 0; k < nlen; ++k) {
-            const int32_t j = jn;
-            const uint32_t mg = mgn;
+            const int32_t j = j_c, jn = j_n;
+            const uint32_t mg = mg_c;
+            const int pA = pa_c, pB = pb_c;
             if (k + 1 < nlen) {
-                jn = a.pj[off + k + 1];
-                mgn = a.pmg[off + k + 1];
-            } else {
-                jn = m;
+                mg_c = a.pmg[off + k + 1];
+                j_c = jn;
+                j_n = (k + 2 < nlen) ? a.pj[off + k + 2] : m;
+                pa_c = (uint32_t)jn < (uint32_t)m ? (int)P[jn] : 255;
+                pb_c = (uint32_t)(jn + 1) < (uint32_t)m ? (int)P[jn + 1] : 255;
             }
             // a parent row is sorted by column inside [0, m); anything else is
             // reported, and no column past the query is read
@@ -231,7 +238,7 @@ __device__ __forceinline__ void rows_seq(const DnaRowsArgs &a, WarpSmem &sm, int
             const int32_t ju = j * u;
             int32_t Gap = gap_from_mg(mg, sc.ss, oe);
             Gap = Gap > tA ? Gap : AE_NEG;
-            int32_t DA = (prev_j + 1 == j && prev_M > 0) ? prev_M + (c == (int)P[j] ? sa : sb) : AE_NEG;
+            int32_t DA = (prev_j + 1 == j && prev_M > 0) ? prev_M + (c == pA ? sa : sb) : AE_NEG;
             DA = DA > tA ? DA : AE_NEG;
             const int32_t MpA = max(DA, Gap);
             const int32_t MA = max(MpA, K > AE_KNEG / 2 ? sc.sg - ju + K : AE_NEG);
@@ -241,7 +248,7 @@ __device__ __forceinline__ void rows_seq(const DnaRowsArgs &a, WarpSmem &sm, int
             int32_t MB = AE_NEG;
             bool aliveB = false;
             if (hasB) {
-                const int32_t DB = M + (c == (int)P[j + 1] ? sa : sb);
+                const int32_t DB = M + (c == pB ? sa : sb);
                 const int32_t MpB = DB > tB ? DB : AE_NEG;
                 MB = max(MpB, K > AE_KNEG / 2 ? sc.sg - ju - u + K : AE_NEG);
                 aliveB = MB > tB;
