@@ -781,9 +781,11 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
 }
 
 // Average parent-row length up to which a level's rows are walked one lane per
-// (node, child) rather than spread one entry per lane
+// (node, child) rather than spread one entry per lane (per level on the 100 Mbp
+// text with queries of 10 kbp to 1 Mbp, the walk was the faster layout up to
+// rows of about 250 entries and the spread one from about 270)
 #ifndef AE_SEQ_ROW_AVG
-#define AE_SEQ_ROW_AVG 24
+#define AE_SEQ_ROW_AVG 256
 #endif
 
 // One trie level of the DNA int16x2 route (ae_rows_dna.cu) in one launch.

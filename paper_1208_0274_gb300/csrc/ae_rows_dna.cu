@@ -120,6 +120,17 @@ __device__ __forceinline__ uint64_t reduce_add_u64(uint32_t v) {
     return ((uint64_t)hi << 16) + lo;
 }
 
+__device__ __forceinline__ uint32_t excl_scan_u32(uint32_t v) {
+    const int lane = threadIdx.x & 31;
+    uint32_t x = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const uint32_t y = __shfl_up_sync(FULL, x, d);
+        if (lane >= d) x += y;
+    }
+    return x - v;
+}
+
 __device__ __forceinline__ uint64_t excl_scan_u64(uint64_t v, uint64_t &total) {
     const int lane = threadIdx.x & 31;
     uint64_t x = v;
@@ -694,11 +705,28 @@ __global__ void __launch_bounds__(DW * 32, AE_DNA_MINB) k_rows_dna(DnaRowsArgs a
             sm.bh[lane * 4 + c] = ch[c];
         }
         uint64_t tsum[5], base[5];
-        const uint64_t ex_fe = excl_scan_u64(s_fe, tsum[0]);
-        const uint64_t ex_le = excl_scan_u64(s_le, tsum[1]);
-        const uint64_t ex_fn = excl_scan_u64(s_fn, tsum[2]);
-        const uint64_t ex_ln = excl_scan_u64(s_ln, tsum[3]);
-        const uint64_t ex_h = excl_scan_u64(s_h, tsum[4]);
+        uint64_t ex_fe, ex_le, ex_fn, ex_ln, ex_h;
+        tsum[0] = reduce_add_u64(s_fe);
+        tsum[1] = reduce_add_u64(s_le);
+        tsum[4] = reduce_add_u64(s_h);
+        {   // node counts: at most 128 a task, both in one scan
+            const uint32_t nn = s_fn | (s_ln << 16);
+            const uint32_t ex = excl_scan_u32(nn);
+            const uint32_t tot = __reduce_add_sync(FULL, nn);
+            ex_fn = ex & 0xFFFFu;
+            ex_ln = ex >> 16;
+            tsum[2] = tot & 0xFFFFu;
+            tsum[3] = tot >> 16;
+        }
+        if (tsum[0] + tsum[1] + tsum[4] <= 0xFFFFFFFFull) {   // the usual case: 32-bit scans
+            ex_fe = excl_scan_u32(s_fe);
+            ex_le = excl_scan_u32(s_le);
+            ex_h = excl_scan_u32(s_h);
+        } else {
+            ex_fe = excl_scan_u64(s_fe, tsum[0]);
+            ex_le = excl_scan_u64(s_le, tsum[1]);
+            ex_h = excl_scan_u64(s_h, tsum[4]);
+        }
         {
             unsigned long long r[5] = {0, 0, 0, 0, 0};
             if (lane == 0) {
