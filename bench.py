@@ -190,13 +190,14 @@ def peaks():
 
 
 def measured_traffic(kernel, units):
-    """DRAM bytes (read + write) of `kernel` for `units` work units (triples
-    for k_rows, sweep entries for k_leaf), from the per-unit figure of its last
-    ncu capture (profiles/dram_per_unit.txt: `kernel bytes_per_unit sha1`).
-    None if there is no capture or the kernel's source changed since."""
+    """DRAM bytes (read + write) of `kernel` for `units` work units (DP
+    entries written by the trie levels for k_rows, sweep entries for k_leaf),
+    from the per-unit figure of its last ncu capture
+    (profiles/dram_per_unit.txt: `kernel bytes_per_unit sha1`).  None if there
+    is no capture or the kernel's source changed since."""
     import hashlib
     path = os.path.join(ROOT, "profiles", "dram_per_unit.txt")
-    src_of = {"k_rows": "ae_trie.cu", "k_leaf": "ae_kernels.cu"}
+    src_of = {"k_rows": "ae_rows_dna.cu", "k_leaf": "ae_kernels.cu"}
     if kernel not in src_of or not os.path.exists(path):
         return None
     for line in open(path):
@@ -467,7 +468,8 @@ def run_ours(args):
     # The row update's roofline is HBM: 20 algorithmic bytes against 6 integer
     # operations per DP entry (0.3 op/B, far below the GPU's ~5.5 op/B balance).
     sec = groups[dom] / 1000.0
-    launches_dom = {"k_rows": 2 * kstats["levels"], "k_leaf": max(1, kstats["leaf_sweeps"])}.get(dom, 1)
+    # one launch per trie level (DNA route; a level run again at exact sizes adds one)
+    launches_dom = {"k_rows": max(1, kstats["levels"]), "k_leaf": max(1, kstats["leaf_sweeps"])}.get(dom, 1)
     ent = {"k_rows": ent_trie, "k_leaf": ent_leaf}.get(dom, kstats["raw_hits"])
     gbs = BYTES_PER_ENTRY * ent / sec / 1e9 if sec > 0 else 0.0
     traffic = measured_traffic(dom, ent)

@@ -60,7 +60,7 @@ typedef struct {
 } ae_scoring;
 
 /* One result: the largest similarity `score` of any alignment ending at text
- * position text_end and query position query_end (Algorithm 1 line 11). */
+ * position text_end and query position query_end (a result of Algorithm 1). */
 typedef struct {
     int64_t text_end;
     int32_t query_end;

@@ -9,7 +9,7 @@ Contents (each follows the passage it cites):
 * ``sw_hits`` / ``sw_matrix`` — the plain full-matrix affine-gap
   Smith-Waterman of ``sw_oracle.c``: the local-alignment problem of Section
   2.1 (largest similarity of T[x..i] and P[y..j] for every end pair, results
-  >= H as in Algorithm 1 line 11). This is the oracle the GPU hits must match.
+  >= H as Algorithm 1 reports them). This is the oracle the GPU hits must match.
 * ``sw_hits_mt`` — the same recurrence on every host core: query column
   stripes computed as a wavefront over blocks of text rows, only the edge
   column's V and F crossing between stripes. Pinned bit for bit against

@@ -10,7 +10,7 @@
  * is the best score of a global alignment of them under the scheme
  * <s_a, s_b, s_g, s_s> (a run of r gap letters scores s_g + r*s_s).  For a
  * threshold H >= 1 the reported results are the cells whose largest
- * similarity is at least H (Algorithm 1, line 11).
+ * similarity is at least H (the hit report of Algorithm 1).
  *
  * The value is the textbook affine-gap Smith-Waterman cell (Gotoh's three
  * states), written out over the full n x m matrix with no index and no

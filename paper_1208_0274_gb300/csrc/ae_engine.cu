@@ -2,12 +2,13 @@
 //
 // ae_search_device runs, per batch of work items:
 //   seed (Theorem 3: the query's (q-1)-grams located by backward search) or
-//   the trie root;  then one trie level per iteration (count pass, scan, write
-//   pass) until the frontier is empty;  then the text-position sweep over the
+//   the trie root;  then one trie level per iteration (DNA: one launch that
+//   counts, reserves and writes; general route: count pass, scan, write pass)
+//   until the frontier is empty;  then the text-position sweep over the
 //   rows that reached a single occurrence;  then the located hits of the
 //   multi-occurrence nodes.  All hits of all batches are sorted by
 //   (query, text end, query end) and reduced to the per-cell maximum
-//   (Algorithm 1, lines 6-11).
+//   (Algorithm 1's per-cell maximum and hit report).
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <stdio.h>
@@ -810,7 +811,13 @@ void Search::dna_level(int64_t &F, int cur, int64_t &cur_ent, int64_t &lf_ent_ba
     const double in[5] = {(double)cur_ent, (double)cur_ent, (double)F, (double)F, (double)cur_ent};
     int64_t want[5];
     for (int q = 0; q < 5; ++q) {
-        const double r = dna_ratio_ok ? dna_ratio[q] * 1.2 : first_ratio[q];
+        double r = dna_ratio_ok ? dna_ratio[q] * 1.2 : first_ratio[q];
+        // a large level's output is guessed at most 1.5 times its input: the growth
+        // ratio peaks and falls within a few levels, and sizing every later level by
+        // the peak ratio would hold several times the memory the search needs (a
+        // short guess costs one more run of the level, and only until the buffers
+        // have grown)
+        if (r * in[q] > (double)(1 << 28)) r = std::min(r, 1.5);
         want[q] = (int64_t)(r * in[q]) + 256;
     }
     want[2] = std::min<int64_t>(want[2], 4 * F);   // a node has at most four children

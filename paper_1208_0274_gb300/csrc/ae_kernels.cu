@@ -802,18 +802,34 @@ __global__ void __launch_bounds__(128, AE_LEAF_MINB) k_leaf(LeafArgs a) {
                 // LEAF_E consecutive entries (a lane-local prefix, then one warp scan
                 // per quantity), so a wide row needs LEAF_E times fewer warp steps.
                 int32_t carry = AE_KNEG, prev_j = -2, prev_M = AE_NEG;
+                // the next chunk's entries are loaded while this chunk is computed
+                int32_t nj[LEAF_E], nM[LEAF_E], nG[LEAF_E];
+#pragma unroll
+                for (int e = 0; e < LEAF_E; ++e) {
+                    const int64_t x = (int64_t)lane * LEAF_E + e;
+                    const bool v = x < rlen;
+                    nj[e] = v ? R.j[x] : m;
+                    nM[e] = v ? R.M[x] : AE_NEG;
+                    nG[e] = v ? R.Ga[x] : AE_NEG;
+                }
                 for (int64_t base = 0; base < rlen; base += 32 * LEAF_E) {
                     const int64_t i0 = base + (int64_t)lane * LEAF_E;
                     int32_t jj[LEAF_E], MM[LEAF_E], GG[LEAF_E];
 #pragma unroll
                     for (int e = 0; e < LEAF_E; ++e) {
-                        const bool v = i0 + e < rlen;
-                        jj[e] = v ? R.j[i0 + e] : m;
-                        MM[e] = v ? R.M[i0 + e] : AE_NEG;
-                        GG[e] = v ? R.Ga[i0 + e] : AE_NEG;
+                        jj[e] = nj[e];
+                        MM[e] = nM[e];
+                        GG[e] = nG[e];
+                        const int64_t x = i0 + 32 * LEAF_E + e;
+                        const bool v = x < rlen;
+                        nj[e] = v ? R.j[x] : m;
+                        nM[e] = v ? R.M[x] : AE_NEG;
+                        nG[e] = v ? R.Ga[x] : AE_NEG;
                     }
+                    // the first entry of the next chunk (lane 0's next load), m past the row
                     int32_t jnext = __shfl_down_sync(FULL, jj[0], 1);
-                    if (lane == 31) jnext = (base + 32 * LEAF_E < rlen) ? R.j[base + 32 * LEAF_E] : m;
+                    const int32_t jfirst_next = __shfl_sync(FULL, nj[0], 0);
+                    if (lane == 31) jnext = jfirst_next;
                     int32_t pj0 = __shfl_up_sync(FULL, jj[LEAF_E - 1], 1), pM0 = __shfl_up_sync(FULL, MM[LEAF_E - 1], 1);
                     if (lane == 0) {
                         pj0 = prev_j;
