@@ -1760,9 +1760,8 @@ ae_status ae_plan(int64_t m, int32_t alphabet, const ae_scoring *scoring, int32_
 // ------------------------------------------------------------------ no-allocation search
 //
 // ae_search_device_static: the search of ae_search_device for callers that
-// must not allocate device memory (e.g. code running inside a CUDA graph
-// capture, where cudaMalloc is not allowed, or a host process whose device
-// memory is fully reserved by someone else).  Every working buffer of the
+// must not allocate device memory (e.g. a host process whose device memory is
+// fully reserved by another allocator).  Every working buffer of the
 // search -- level arenas, sort buffers, hit records and the per-warp rows of
 // the text-position sweep -- is carved from one file-scope device array of
 // AE_STATIC_SCRATCH_BYTES, which every GPU that loads this library holds
