@@ -122,6 +122,8 @@ typedef struct {
     int64_t reused;
     int64_t reroutes;         /* engine batches whose frontier left the int16x2 route for int32 (a
                                  state could pass the int16 range; nothing is recomputed) */
+    int64_t leaf_wide_walks;  /* walks of the text-position sweep continued on a thread block
+                                 (ae_options.leaf_wide_rows) */
 } ae_stats;
 
 /* Engine knobs (NULL = defaults).  None of them changes the result set. */
@@ -167,6 +169,10 @@ typedef struct {
      * or report it with a lower score.  Defaults: 1 and 0 (the whole search). */
     int32_t fork_parts;
     int32_t fork_part;
+    int32_t leaf_wide_rows;   /* a walk of the text-position sweep whose row grows past this many
+                                 entries continues on a whole thread block (each step spread over
+                                 its threads) instead of one warp; 0: never.  Default 256.  The
+                                 results are the same */
 } ae_options;
 
 /* Fill *opt with the defaults. */

@@ -46,7 +46,8 @@ class ae_options(ctypes.Structure):
                 ("hint_hits", ctypes.c_void_p), ("tier_stats", ctypes.c_int32),
                 ("workspace_limit", ctypes.c_int64), ("general_rows", ctypes.c_int32),
                 ("qprefix_domination", ctypes.c_int32), ("row_layout", ctypes.c_int32),
-                ("fork_parts", ctypes.c_int32), ("fork_part", ctypes.c_int32)]
+                ("fork_parts", ctypes.c_int32), ("fork_part", ctypes.c_int32),
+                ("leaf_wide_rows", ctypes.c_int32)]
 
 
 class ae_stats(ctypes.Structure):
@@ -66,7 +67,8 @@ class ae_stats(ctypes.Structure):
                 ("triples", ctypes.c_int64), ("batch_splits", ctypes.c_int64),
                 ("dominated", ctypes.c_int64), ("candidates", ctypes.c_int64),
                 ("pruned_nonpos", ctypes.c_int64), ("pruned_reach", ctypes.c_int64),
-                ("reused", ctypes.c_int64), ("reroutes", ctypes.c_int64)]
+                ("reused", ctypes.c_int64), ("reroutes", ctypes.c_int64),
+                ("leaf_wide_walks", ctypes.c_int64)]
 
 
 def _load():

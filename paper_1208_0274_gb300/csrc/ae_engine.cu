@@ -170,8 +170,8 @@ struct Workspace {
     DevBuf sk0, sv0, sk1, sv1, sort_tmp;
     // point hits of the whole search
     DevBuf hkey, hscore, hcount, hk1, hv1;
-    // leaf sweep scratch
-    DevBuf scratch, next_seg;
+    // leaf sweep scratch; walks handed on to blocks (state, count, row buffers)
+    DevBuf scratch, next_seg, esc, esc_count, esc_rows;
     // output
     DevBuf uniq, uflags, uoff, qcount;
     DevBuf stats, segs, ctr, seg_cnt, seg_hit, task_first, task_tot, task_off, task_tmp, task_sum, res, res_key;
@@ -196,7 +196,7 @@ struct Workspace {
                 &aM[1], &aGa[0], &aGa[1], &nodes[0], &nodes[1], &cnt[0], &cnt[1], &cnt[2], &cnt[3],
                 &cnt[4], &off[0], &off[1], &off[2], &off[3], &off[4], &totals, &scan_tmp, &lj, &lM,
                 &lGa, &inj, &rhits, &sk0, &sv0, &sk1, &sv1, &sort_tmp, &hkey, &hscore, &hcount, &hk1,
-                &hv1, &scratch, &next_seg, &uniq, &uflags, &uoff, &qcount, &stats, &segs, &ctr, &seg_cnt, &seg_hit,
+                &hv1, &scratch, &next_seg, &esc, &esc_count, &esc_rows, &uniq, &uflags, &uoff, &qcount, &stats, &segs, &ctr, &seg_cnt, &seg_hit,
                 &task_first, &task_tot, &task_off, &task_tmp, &task_sum, &res, &res_key};
     }
 
@@ -215,7 +215,8 @@ struct Workspace {
     void trim_batch() {
         DevBuf *drop[] = {&aj[0], &aj[1], &aM[0], &aM[1], &aGa[0], &aGa[1], &nodes[0], &nodes[1], &cnt[0], &cnt[1],
                           &cnt[2], &cnt[3], &cnt[4], &off[0], &off[1], &off[2], &off[3], &off[4], &scan_tmp, &lj,
-                          &lM, &lGa, &inj, &rhits, &sk0, &sv0, &sk1, &sv1, &sort_tmp, &hk1, &hv1, &scratch, &uniq,
+                          &lM, &lGa, &inj, &rhits, &sk0, &sv0, &sk1, &sv1, &sort_tmp, &hk1, &hv1, &scratch, &esc_rows,
+                          &uniq,
                           &uflags, &uoff, &segs, &seg_cnt, &seg_hit, &task_first, &task_tot, &task_off, &task_tmp,
                           &res, &res_key};
         for (DevBuf *b : drop)
@@ -781,6 +782,12 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
     stats.ms_reduce += ms_since(t2);
 }
 
+// Slots for sweep walks handed on to thread blocks (12 row buffers of the
+// sweep's row capacity each; a walk that finds no free slot stays on its warp)
+#ifndef AE_LEAF_WIDE_SLOTS
+#define AE_LEAF_WIDE_SLOTS 256
+#endif
+
 // Average parent-row length up to which a level's rows are walked one lane per
 // (node, child) rather than spread one entry per lane (per level on the 100 Mbp
 // text with queries of 10 kbp to 1 Mbp, the walk was the faster layout up to
@@ -1043,8 +1050,18 @@ void Search::leaf_phase(int64_t ninj) {
     ensure(w->hcount, 8, st);
     int64_t hit_cap = std::max<int64_t>(1 << 20, batch_hint >= 0 ? (int64_t)(1.25 * batch_hint) + 65536
                                                                  : (int64_t)(ninj * w->hit_ratio) + 4096);
+    // wide walks move to blocks (not inside the fixed arena of the no-allocation
+    // entry point, nor when entries are counted by tier, which only the warp walk does)
+    const int32_t esc_min = (g_arena || opt.tier_stats) ? 0 : opt.leaf_wide_rows;
+    const int32_t esc_max = esc_min > 0 ? AE_LEAF_WIDE_SLOTS : 0;
     for (int attempt = 0; attempt < 12; ++attempt) {
         ensure(w->scratch, (size_t)ae_leaf_scratch_words(w->leaf_cap, nwarps) * 4, st);
+        if (esc_max > 0) {
+            ensure(w->esc, (size_t)esc_max * sizeof(EscWalk), st);
+            ensure(w->esc_count, 8, st);
+            ensure(w->esc_rows, (size_t)esc_max * 12 * (size_t)w->leaf_cap * 4, st);
+            CU(cudaMemsetAsync(w->esc_count.p, 0, 8, st));
+        }
         hits_reserve(hit_cap);
         CU(cudaMemsetAsync(w->next_seg.p, 0, 8, st));
         unsigned long long base = (unsigned long long)nhits;
@@ -1080,20 +1097,29 @@ void Search::leaf_phase(int64_t ninj) {
         la.bj = bj;
         la.tiers = opt.tier_stats ? 1 : 0;
         la.stats = ptr<DevStats>(w->stats);
+        la.esc_min = esc_max > 0 ? esc_min : 0;
+        la.esc_max = esc_max;
+        if (esc_max > 0) {
+            la.esc_count = ptr<unsigned long long>(w->esc_count);
+            la.esc = ptr<EscWalk>(w->esc);
+            la.esc_rows = ptr<int32_t>(w->esc_rows);
+        }
         prof.mark(K_LEAF);
         ++stats.leaf_sweeps;
         const auto t_sweep = std::chrono::steady_clock::now();
         ae_leaf_sweep(la, blocks, threads, st);
         prof.mark(K_LEAF);
         CU(cudaGetLastError());
-        unsigned long long hdr[3];
+        unsigned long long hdr[4] = {0, 0, 0, 0};
         CU(cudaMemcpyAsync(tot(), w->hcount.p, 8, cudaMemcpyDeviceToHost, st));
         CU(cudaMemcpyAsync(tot() + 1, (char *)w->stats.p + offsetof(DevStats, leaf_overflow), 16,
                            cudaMemcpyDeviceToHost, st));
+        if (esc_max > 0) CU(cudaMemcpyAsync(tot() + 3, w->esc_count.p, 8, cudaMemcpyDeviceToHost, st));
         sync();
         hdr[0] = tot()[0];
         hdr[1] = tot()[1];
         hdr[2] = tot()[2];
+        if (esc_max > 0) hdr[3] = std::min<unsigned long long>(tot()[3], (unsigned long long)esc_max);
         if (trace())
             fprintf(stderr, "[ae leaf] injections %lld (tasks %lld of %d) attempt %d: %.2f ms, hits %llu (cap %lld), row overflow %llu, hit overflow %llu, cap %d\n",
                     (long long)ninj, (long long)la.nseg, la.seg, attempt, ms_since(t_sweep),
@@ -1117,6 +1143,7 @@ void Search::leaf_phase(int64_t ninj) {
         w->hit_ratio = std::max(w->hit_ratio,
                                 std::min(64.0, 1.3 * (double)((int64_t)hdr[0] - nhits) / (double)ninj + 0.01));
         stats.leaf_raw_hits += (int64_t)hdr[0] - nhits;
+        stats.leaf_wide_walks += (int64_t)hdr[3];
         nhits = (int64_t)hdr[0];
         return;
     }
@@ -1212,6 +1239,7 @@ ae_status search_core(const ae_index *idx, Workspace *w, const int64_t *offsets,
     ae_options_default(&s.opt);
     if (opt) s.opt = *opt;
     if (s.opt.fork_parts < 1 || s.opt.fork_part < 0 || s.opt.fork_part >= s.opt.fork_parts) return AE_EINVAL;
+    if (s.opt.leaf_wide_rows < 0) return AE_EINVAL;
     if (s.opt.item_columns < 1 || s.opt.batch_columns < 1 || s.opt.leaf_capacity < 64 || s.opt.leaf_segment < 0 ||
         s.opt.leaf_delay < 0 || s.opt.leaf_delay > 14 || s.opt.int16_limit < 0 || s.opt.int16_limit > 32000)
         return AE_EINVAL;
@@ -1418,6 +1446,7 @@ void ae_options_default(ae_options *opt) {
     opt->qprefix_domination = 1;
     opt->row_layout = 0;
     opt->fork_parts = 1;
+    opt->leaf_wide_rows = 256;
     opt->fork_part = 0;
 }
 

@@ -495,6 +495,125 @@ __device__ __forceinline__ void make_slots(const ScoreView &sc, const int8_t *sm
     s.next_col = jn;
 }
 
+// Merge the rows injected at (qid, p) into the walked row Rn (nlen entries).  They are finished rows, and
+// the union of two finished rows taken by maximum per column is again
+// finished (each is closed under the horizontal-gap recurrence), so the
+// merge needs no second finish.  Cells where an injected row brings a
+// new or larger value report their hits here.
+// Used by the warp walk of k_leaf and, run by one warp, by the block walk of
+// k_leaf_wide.
+__device__ __forceinline__ void leaf_merge(const LeafArgs &a, int lane, int32_t qid, int32_t p, int32_t H,
+                                           uint64_t jmask, int64_t &k, int64_t kend, Buf &Rn, Buf &Cb, Buf &C2,
+                                           int64_t &nlen, int64_t cap, bool &overflow, HitStage &hstage,
+                                           unsigned long long &st_ent, unsigned long long &st_reused,
+                                           unsigned long long &st_t0) {
+    while (k < kend) {
+        const Inject I = a.inj[a.order[k]];
+        if (I.qid != qid || I.e != p) break;
+        ++k;
+        const int32_t *ij = a.lj + I.off, *iM = a.lM + I.off, *iGa = a.lGa + I.off;
+        const int64_t icnt = I.cnt;
+        // an injected row whose every entry the walked row already has with
+        // M and G_a at least as large changes nothing (its hits were reported
+        // with the walked values): skip it.  Along a homologous region the row
+        // walked from earlier starts usually dominates the later forks.
+        bool dominated = nlen > 0;
+        for (int64_t base = 0; dominated && base < icnt; base += 32) {
+            const int64_t idx = base + lane;
+            bool ok = true;
+            if (idx < icnt) {
+                const int32_t y = ij[idx];
+                const int64_t q = lower_bound_g(Rn.j, nlen, y);
+                ok = q < nlen && Rn.j[q] == y && Rn.M[q] >= iM[idx] && Rn.Ga[q] >= iGa[idx];
+            }
+            dominated = __all_sync(FULL, ok);
+        }
+        if (dominated) {
+            st_reused += (unsigned long long)icnt;   // the whole row rides on the walked one
+            continue;
+        }
+        if (nlen + icnt > cap) {
+            overflow = true;
+            break;
+        }
+        for (int64_t base = 0; base < nlen; base += 32) {
+            const int64_t idx = base + lane;
+            if (idx < nlen) {
+                const int32_t x = Rn.j[idx];
+                const int64_t d = idx + lower_bound_g(ij, icnt, x);
+                C2.j[d] = x;
+                C2.M[d] = Rn.M[idx];
+                C2.Ga[d] = Rn.Ga[idx];
+            }
+        }
+        for (int64_t base = 0; base < icnt; base += 32) {
+            const int64_t idx = base + lane;
+            if (idx < icnt) {
+                const int32_t y = ij[idx];
+                const int64_t d = idx + upper_bound_g(Rn.j, nlen, y);
+                C2.j[d] = (int32_t)((uint32_t)y | 0x80000000u);   // tag: from the injected row
+                C2.M[d] = iM[idx];
+                C2.Ga[d] = iGa[idx];
+            }
+        }
+        __syncwarp();
+        // an equal column appears twice: the walked entry first, then the injected one
+        const int64_t len2 = nlen + icnt;
+        int64_t out = 0;
+        const uint64_t kq = ((uint64_t)qid << (a.be + a.bj)) | ((uint64_t)(uint32_t)p << a.bj);
+        for (int64_t base = 0; base < len2; base += 32) {
+            const int64_t idx = base + lane;
+            const bool valid = idx < len2;
+            int32_t j = 0, Mv = AE_NEG, Gv = AE_NEG;
+            bool keep = false, hit = false, fresh = false;
+            if (valid) {
+                const uint32_t raw = (uint32_t)C2.j[idx];
+                j = (int32_t)(raw & 0x7FFFFFFFu);
+                const bool from_inj = raw >> 31;
+                Mv = C2.M[idx];
+                Gv = C2.Ga[idx];
+                keep = !(idx > 0 && (int32_t)((uint32_t)C2.j[idx - 1] & 0x7FFFFFFFu) == j);
+                if (keep) {
+                    if (idx + 1 < len2 && (int32_t)((uint32_t)C2.j[idx + 1] & 0x7FFFFFFFu) == j) {
+                        const int32_t Mi = C2.M[idx + 1];
+                        hit = Mi > Mv && Mi >= H;
+                        Mv = max(Mv, Mi);
+                        Gv = max(Gv, C2.Ga[idx + 1]);
+                    } else {
+                        fresh = from_inj;
+                        hit = from_inj && Mv >= H;
+                    }
+                }
+            }
+            const uint32_t ci = warp_incl_sum(keep ? 1u : 0u);
+            const uint32_t tot = __shfl_sync(FULL, ci, 31);
+            const uint32_t hi = warp_incl_sum(hit ? 1u : 0u);
+            const uint32_t htot = __shfl_sync(FULL, hi, 31);
+            __syncwarp();
+            if (keep) {
+                const int64_t d = out + ci - 1;
+                Cb.j[d] = j;
+                Cb.M[d] = Mv;
+                Cb.Ga[d] = Gv;
+            }
+            if (htot) {
+                bool staged, hok;
+                const uint64_t hbase = stage_reserve(hstage, a, lane, htot, staged, hok);
+                if (hok && hit) hit_put(hstage, a, staged, hbase + hi - 1, kq | ((uint64_t)j & jmask), Mv);
+            }
+            if (a.tiers && fresh) ++st_t0;
+            out += tot;
+        }
+        __syncwarp();
+        st_ent += (unsigned long long)(out - nlen);
+        st_reused += (unsigned long long)(nlen + icnt - out);   // columns both rows had
+        Buf t = Rn;
+        Rn = Cb;
+        Cb = t;
+        nlen = out;
+    }
+}
+
 #ifndef AE_LEAF_E
 #define AE_LEAF_E 2
 #endif
@@ -562,7 +681,6 @@ __global__ void __launch_bounds__(128, AE_LEAF_MINB) k_leaf(LeafArgs a) {
             nk_e = In.e;
         }
         while (true) {
-            int64_t clen = 0;
             if (rlen == 0 && k < kend) {
                 // ---- jump to a lone injected row: it is already a finished row
                 const Inject I0 = a.inj[a.order[k]];
@@ -947,116 +1065,8 @@ __global__ void __launch_bounds__(128, AE_LEAF_MINB) k_leaf(LeafArgs a) {
                 if (overflow) break;
                 st_ent += (unsigned long long)nlen;
             }
-            // ---- merge the rows injected at (qid, p).  They are finished rows, and
-            // the union of two finished rows taken by maximum per column is again
-            // finished (each is closed under the horizontal-gap recurrence), so the
-            // merge needs no second finish.  Cells where an injected row brings a
-            // new or larger value report their hits here.
-            while (k < kend) {
-                const Inject I = a.inj[a.order[k]];
-                if (I.qid != qid || I.e != p) break;
-                ++k;
-                const int32_t *ij = a.lj + I.off, *iM = a.lM + I.off, *iGa = a.lGa + I.off;
-                const int64_t icnt = I.cnt;
-                // an injected row whose every entry the walked row already has with
-                // M and G_a at least as large changes nothing (its hits were reported
-                // with the walked values): skip it.  Along a homologous region the row
-                // walked from earlier starts usually dominates the later forks.
-                bool dominated = nlen > 0;
-                for (int64_t base = 0; dominated && base < icnt; base += 32) {
-                    const int64_t idx = base + lane;
-                    bool ok = true;
-                    if (idx < icnt) {
-                        const int32_t y = ij[idx];
-                        const int64_t q = lower_bound_g(Rn.j, nlen, y);
-                        ok = q < nlen && Rn.j[q] == y && Rn.M[q] >= iM[idx] && Rn.Ga[q] >= iGa[idx];
-                    }
-                    dominated = __all_sync(FULL, ok);
-                }
-                if (dominated) {
-                    st_reused += (unsigned long long)icnt;   // the whole row rides on the walked one
-                    continue;
-                }
-                if (nlen + icnt > cap) {
-                    overflow = true;
-                    break;
-                }
-                for (int64_t base = 0; base < nlen; base += 32) {
-                    const int64_t idx = base + lane;
-                    if (idx < nlen) {
-                        const int32_t x = Rn.j[idx];
-                        const int64_t d = idx + lower_bound_g(ij, icnt, x);
-                        C2.j[d] = x;
-                        C2.M[d] = Rn.M[idx];
-                        C2.Ga[d] = Rn.Ga[idx];
-                    }
-                }
-                for (int64_t base = 0; base < icnt; base += 32) {
-                    const int64_t idx = base + lane;
-                    if (idx < icnt) {
-                        const int32_t y = ij[idx];
-                        const int64_t d = idx + upper_bound_g(Rn.j, nlen, y);
-                        C2.j[d] = (int32_t)((uint32_t)y | 0x80000000u);   // tag: from the injected row
-                        C2.M[d] = iM[idx];
-                        C2.Ga[d] = iGa[idx];
-                    }
-                }
-                __syncwarp();
-                // an equal column appears twice: the walked entry first, then the injected one
-                const int64_t len2 = nlen + icnt;
-                int64_t out = 0;
-                const uint64_t kq = ((uint64_t)qid << (a.be + a.bj)) | ((uint64_t)(uint32_t)p << a.bj);
-                for (int64_t base = 0; base < len2; base += 32) {
-                    const int64_t idx = base + lane;
-                    const bool valid = idx < len2;
-                    int32_t j = 0, Mv = AE_NEG, Gv = AE_NEG;
-                    bool keep = false, hit = false, fresh = false;
-                    if (valid) {
-                        const uint32_t raw = (uint32_t)C2.j[idx];
-                        j = (int32_t)(raw & 0x7FFFFFFFu);
-                        const bool from_inj = raw >> 31;
-                        Mv = C2.M[idx];
-                        Gv = C2.Ga[idx];
-                        keep = !(idx > 0 && (int32_t)((uint32_t)C2.j[idx - 1] & 0x7FFFFFFFu) == j);
-                        if (keep) {
-                            if (idx + 1 < len2 && (int32_t)((uint32_t)C2.j[idx + 1] & 0x7FFFFFFFu) == j) {
-                                const int32_t Mi = C2.M[idx + 1];
-                                hit = Mi > Mv && Mi >= H;
-                                Mv = max(Mv, Mi);
-                                Gv = max(Gv, C2.Ga[idx + 1]);
-                            } else {
-                                fresh = from_inj;
-                                hit = from_inj && Mv >= H;
-                            }
-                        }
-                    }
-                    const uint32_t ci = warp_incl_sum(keep ? 1u : 0u);
-                    const uint32_t tot = __shfl_sync(FULL, ci, 31);
-                    const uint32_t hi = warp_incl_sum(hit ? 1u : 0u);
-                    const uint32_t htot = __shfl_sync(FULL, hi, 31);
-                    __syncwarp();
-                    if (keep) {
-                        const int64_t d = out + ci - 1;
-                        Cb.j[d] = j;
-                        Cb.M[d] = Mv;
-                        Cb.Ga[d] = Gv;
-                    }
-                    if (htot) {
-                        bool staged, hok;
-                        const uint64_t hbase = stage_reserve(hstage, a, lane, htot, staged, hok);
-                        if (hok && hit) hit_put(hstage, a, staged, hbase + hi - 1, kq | ((uint64_t)j & jmask), Mv);
-                    }
-                    if (a.tiers && fresh) ++st_t0;
-                    out += tot;
-                }
-                __syncwarp();
-                st_ent += (unsigned long long)(out - nlen);
-                st_reused += (unsigned long long)(nlen + icnt - out);   // columns both rows had
-                Buf t = Rn;
-                Rn = Cb;
-                Cb = t;
-                nlen = out;
-            }
+            leaf_merge(a, lane, qid, p, H, jmask, k, kend, Rn, Cb, C2, nlen, cap, overflow, hstage, st_ent, st_reused,
+                       st_t0);
             if (overflow) break;
             if (k < kend) {
                 const Inject In = a.inj[a.order[k]];
@@ -1072,6 +1082,34 @@ __global__ void __launch_bounds__(128, AE_LEAF_MINB) k_leaf(LeafArgs a) {
             ++st_rows;
             ++seg_steps;
             seg_width = max(seg_width, (unsigned long long)nlen);
+            if (a.esc_min > 0 && rlen > a.esc_min) {
+                // a wide row goes on on a whole block (k_leaf_wide), with the rest of
+                // this task's injections; the warp takes its next task
+                unsigned long long slot = 0;
+                if (lane == 0) slot = atomicAdd(a.esc_count, 1ull);
+                slot = __shfl_sync(FULL, slot, 0);
+                if (slot < (unsigned long long)a.esc_max) {
+                    int32_t *eb = a.esc_rows + (int64_t)slot * 12 * cap;
+                    for (int64_t i = lane; i < rlen; i += 32) {
+                        eb[i] = R.j[i];
+                        eb[cap + i] = R.M[i];
+                        eb[2 * cap + i] = R.Ga[i];
+                    }
+                    if (lane == 0) {
+                        EscWalk e;
+                        e.qid = qid;
+                        e.p = p;
+                        e.rlen = rlen;
+                        e.k = k;
+                        e.kend = kend;
+                        a.esc[slot] = e;
+                    }
+                    __syncwarp();
+                    rlen = 0;
+                    k = kend;
+                    continue;
+                }
+            }
             if (rlen <= 32) {
                 if (lane < rlen) {
                     rj = R.j[lane];
@@ -1105,6 +1143,271 @@ __global__ void __launch_bounds__(128, AE_LEAF_MINB) k_leaf(LeafArgs a) {
         if (t1) atomicAdd(&a.stats->tier[1], t1);
         if (t2) atomicAdd(&a.stats->tier[2], t2);
         if (st_reused) atomicAdd(&a.stats->reused, st_reused);
+    }
+}
+
+// ------------------------------------------------------------------ wide sweep walks
+//
+// A walk whose row has grown wide is continued by a whole block: each step's
+// entries are spread over LEAF_WIDE_THREADS threads (LEAF_E consecutive
+// entries each), the horizontal-gap keys and the output counts are block-wide
+// scans, and the merges of injected rows run on the first warp.  The values
+// are those of the warp walk of k_leaf (the same make_slots / slot_finish per
+// entry, the same merge); only the time per step differs.
+constexpr int LEAF_WIDE_THREADS = 256;
+constexpr int LEAF_WIDE_WARPS = LEAF_WIDE_THREADS / 32;
+
+__device__ __forceinline__ int32_t block_excl_max(int32_t v, int32_t *sw, int32_t &total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const int32_t incl = warp_incl_max(v);
+    if (lane == 31) sw[w] = incl;
+    __syncthreads();
+    int32_t pre = AE_KNEG, all = AE_KNEG;
+#pragma unroll
+    for (int x = 0; x < LEAF_WIDE_WARPS; ++x) {
+        const int32_t y = sw[x];
+        if (x < w) pre = max(pre, y);
+        all = max(all, y);
+    }
+    int32_t ex = __shfl_up_sync(FULL, incl, 1);
+    if (lane == 0) ex = AE_KNEG;
+    total = all;
+    __syncthreads();
+    return max(pre, ex);
+}
+
+__device__ __forceinline__ uint32_t block_excl_sum(uint32_t v, uint32_t *sw, uint32_t &total) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const uint32_t incl = warp_incl_sum(v);
+    if (lane == 31) sw[w] = incl;
+    __syncthreads();
+    uint32_t pre = 0, all = 0;
+#pragma unroll
+    for (int x = 0; x < LEAF_WIDE_WARPS; ++x) {
+        const uint32_t y = sw[x];
+        if (x < w) pre += y;
+        all += y;
+    }
+    total = all;
+    __syncthreads();
+    return pre + incl - v;
+}
+
+struct WideState {
+    int64_t rlen, k;
+    int32_t p, qid, m, H;
+    int32_t buf[4];   // the slot's buffers serving as R, Rn, Cb, C2
+    int32_t overflow;
+};
+
+__global__ void __launch_bounds__(LEAF_WIDE_THREADS) k_leaf_wide(LeafArgs a) {
+    __shared__ int8_t smat[AE_MAX_SIGMA * AE_MAX_SIGMA];
+    __shared__ uint64_t s_hkey[LEAF_WIDE_WARPS][LEAF_HS];
+    __shared__ int32_t s_hscore[LEAF_WIDE_WARPS][LEAF_HS];
+    __shared__ uint32_t s_scan[LEAF_WIDE_WARPS];
+    __shared__ WideState ws;
+    load_matrix(a.sc, smat);
+    const unsigned long long nesc = min(*(volatile unsigned long long *)a.esc_count, (unsigned long long)a.esc_max);
+    if ((unsigned long long)blockIdx.x >= nesc) return;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    HitStage hstage = {s_hkey[wid], s_hscore[wid], 0u};
+    const ScoreView &sc = a.sc;
+    const int32_t u = -sc.ss, oe = sc.sg + sc.ss, g = sc.gmax;
+    const int64_t cap = a.cap;
+    const uint64_t jmask = (1ull << a.bj) - 1ull;
+    int32_t *eb = a.esc_rows + (int64_t)blockIdx.x * 12 * cap;
+    Buf B[4];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) B[x] = Buf{eb + 3 * x * cap, eb + (3 * x + 1) * cap, eb + (3 * x + 2) * cap};
+    const EscWalk e0 = a.esc[blockIdx.x];
+    const int64_t kend = e0.kend;
+    if (threadIdx.x == 0) {
+        ws.rlen = e0.rlen;
+        ws.k = e0.k;
+        ws.p = e0.p;
+        ws.qid = e0.qid;
+        ws.m = a.qv.m[e0.qid];
+        ws.H = a.qv.H[e0.qid];
+        for (int x = 0; x < 4; ++x) ws.buf[x] = x;
+        ws.overflow = 0;
+    }
+    __syncthreads();
+    unsigned long long st_rows = 0, st_ent = 0, st_reused = 0, st_t0 = 0, steps = 0, width = 0;
+    const long long t_start = clock64();
+    while (true) {
+        const int64_t rlen = ws.rlen;
+        int64_t k = ws.k;
+        int32_t p = ws.p, qid = ws.qid, m = ws.m, H = ws.H;
+        const int ib[4] = {ws.buf[0], ws.buf[1], ws.buf[2], ws.buf[3]};
+        __syncthreads();   // every thread has the state before thread 0 changes it
+        Buf R = B[ib[0]], Rn = B[ib[1]], Cb = B[ib[2]], C2 = B[ib[3]];
+        int64_t nlen = 0;
+        if (rlen == 0) {
+            if (k >= kend) break;
+            // a new walk: the row at p is the union of the rows injected there
+            const Inject I0 = a.inj[a.order[k]];
+            p = I0.e;
+            qid = I0.qid;
+            m = a.qv.m[qid];
+            H = a.qv.H[qid];
+        } else {
+            if (p + 1 >= a.ix.n || seq_end(a.ix, p)) {   // the walk ends with the text or its sequence
+                if (threadIdx.x == 0) ws.rlen = 0;
+                __syncthreads();
+                continue;
+            }
+            ++p;
+            const int c = (int)a.ix.text[p];
+            const uint8_t *P = a.qv.codes + a.qv.off[qid];
+            int32_t carry = AE_KNEG;
+            bool ovf = false;
+            for (int64_t base = 0; base < rlen; base += (int64_t)LEAF_WIDE_THREADS * LEAF_E) {
+                const int64_t i0 = base + (int64_t)threadIdx.x * LEAF_E;
+                int32_t jj[LEAF_E], MM[LEAF_E], GG[LEAF_E];
+#pragma unroll
+                for (int e = 0; e < LEAF_E; ++e) {
+                    const bool v = i0 + e < rlen;
+                    jj[e] = v ? R.j[i0 + e] : m;
+                    MM[e] = v ? R.M[i0 + e] : AE_NEG;
+                    GG[e] = v ? R.Ga[i0 + e] : AE_NEG;
+                }
+                // the entries around this thread's: the next one's column, the previous one
+                const int32_t jnext = i0 + LEAF_E < rlen ? R.j[i0 + LEAF_E] : m;
+                int32_t pj0 = -2, pM0 = AE_NEG;
+                if (i0 > 0 && i0 - 1 < rlen) {
+                    pj0 = R.j[i0 - 1];
+                    pM0 = R.M[i0 - 1];
+                }
+                Slots sl[LEAF_E];
+                int32_t lk[LEAF_E];
+#pragma unroll
+                for (int e = 0; e < LEAF_E; ++e) {
+                    const bool v = i0 + e < rlen;
+                    int32_t jn = (e + 1 < LEAF_E) ? jj[e + 1] : jnext;
+                    if (i0 + e + 1 >= rlen) jn = m;
+                    const int32_t pj = e ? jj[e - 1] : pj0, pM = e ? MM[e - 1] : pM0;
+                    make_slots(sc, smat, c, P, m, H, g, oe, v, jj[e], MM[e], GG[e], pj, pM, jn, sl[e]);
+                    const int32_t keyA = sl[e].MpA > AE_NEG ? sl[e].MpA + sl[e].colA * u : AE_KNEG;
+                    const int32_t keyB = sl[e].MpB > AE_NEG ? sl[e].MpB + (sl[e].colA + 1) * u : AE_KNEG;
+                    lk[e] = max(e ? lk[e - 1] : AE_KNEG, max(keyA, keyB));
+                }
+                int32_t kall;
+                int32_t lexcl = block_excl_max(lk[LEAF_E - 1], (int32_t *)s_scan, kall);
+                lexcl = max(lexcl, carry);
+                carry = max(carry, kall);
+                SlotOut o[LEAF_E];
+                uint32_t cl = 0, hl = 0;
+                int32_t ik[LEAF_E];
+#pragma unroll
+                for (int e = 0; e < LEAF_E; ++e) {
+                    const int32_t ex = e ? max(lexcl, lk[e - 1]) : lexcl;
+                    ik[e] = max(lexcl, lk[e]);
+                    slot_finish(sl[e].colA, sl[e].MpA, sl[e].hasB, sl[e].MpB, sl[e].next_col, ex, ik[e], sc, m, H, u,
+                                i0 + e < rlen, o[e]);
+                    cl += (uint32_t)o[e].aliveA + (uint32_t)o[e].aliveB + (uint32_t)o[e].run_len;
+                    hl += (uint32_t)(o[e].aliveA && o[e].MA >= H) + (uint32_t)(o[e].aliveB && o[e].MB >= H) +
+                          (uint32_t)o[e].run_hits;
+                }
+                uint32_t ctot;
+                const uint32_t cex = block_excl_sum(cl, s_scan, ctot);
+                if (nlen + (int64_t)ctot > cap) {   // block-uniform
+                    ovf = true;
+                    break;
+                }
+                // hits: each warp reserves its own in its stage
+                const uint32_t hi = warp_incl_sum(hl);
+                const uint32_t htot = __shfl_sync(FULL, hi, 31);
+                bool staged = true, hok = true;
+                uint64_t hbase = 0;
+                if (htot) hbase = stage_reserve(hstage, a, lane, htot, staged, hok);
+                const uint64_t kq = ((uint64_t)qid << (a.be + a.bj)) | ((uint64_t)(uint32_t)p << a.bj);
+                int64_t eo = nlen + (int64_t)cex;
+                uint64_t ho = hbase + hi - hl;
+#pragma unroll
+                for (int e = 0; e < LEAF_E; ++e) {
+                    const int32_t colA = sl[e].colA;
+                    const bool hA = o[e].aliveA && o[e].MA >= H, hB = o[e].aliveB && o[e].MB >= H;
+                    if (o[e].aliveA) {
+                        Rn.j[eo] = colA;
+                        Rn.M[eo] = o[e].MA;
+                        Rn.Ga[eo] = sl[e].GaA;
+                        ++eo;
+                        if (hA && hok) hit_put(hstage, a, staged, ho, kq | ((uint64_t)colA & jmask), o[e].MA);
+                        ho += hA;
+                    }
+                    if (o[e].aliveB) {
+                        Rn.j[eo] = colA + 1;
+                        Rn.M[eo] = o[e].MB;
+                        Rn.Ga[eo] = AE_NEG;
+                        ++eo;
+                        if (hB && hok) hit_put(hstage, a, staged, ho, kq | ((uint64_t)(colA + 1) & jmask), o[e].MB);
+                        ho += hB;
+                    }
+                    for (int32_t r = 0; r < o[e].run_len; ++r) {
+                        const int32_t cc = o[e].run_start + r;
+                        const int32_t v = sc.sg - cc * u + ik[e];
+                        Rn.j[eo] = cc;
+                        Rn.M[eo] = v;
+                        Rn.Ga[eo] = AE_NEG;
+                        ++eo;
+                        if (r < o[e].run_hits) {
+                            if (hok) hit_put(hstage, a, staged, ho, kq | ((uint64_t)cc & jmask), v);
+                            ++ho;
+                        }
+                    }
+                }
+                nlen += (int64_t)ctot;
+            }
+            if (ovf) {
+                if (threadIdx.x == 0) ws.overflow = 1;
+                __syncthreads();
+                break;
+            }
+            st_ent += (unsigned long long)nlen;
+            __syncthreads();   // the step's row is complete before the merge reads it
+        }
+        // ---- the rows injected at (qid, p), merged by the first warp
+        if (wid == 0) {
+            bool ovf = false;
+            leaf_merge(a, lane, qid, p, H, jmask, k, kend, Rn, Cb, C2, nlen, cap, ovf, hstage, st_ent, st_reused,
+                       st_t0);
+            if (lane == 0) {
+                int nr = ib[1], nc = ib[2];   // the merge may have exchanged Rn and Cb
+                if (Rn.j != B[ib[1]].j) {
+                    nr = ib[2];
+                    nc = ib[1];
+                }
+                ws.buf[0] = nr;   // the finished row at p
+                ws.buf[1] = ib[0];
+                ws.buf[2] = nc;
+                ws.buf[3] = ib[3];
+                ws.rlen = nlen;
+                ws.k = k;
+                ws.p = p;
+                ws.qid = qid;
+                ws.m = m;
+                ws.H = H;
+                if (ovf) ws.overflow = 1;
+            }
+        }
+        __syncthreads();
+        if (ws.overflow) break;
+        ++st_rows;
+        ++steps;
+        width = max(width, (unsigned long long)ws.rlen);
+    }
+    stage_flush(hstage, a, lane);
+    if (threadIdx.x == 0) {
+        if (ws.overflow) atomicAdd(&a.stats->leaf_overflow, 1ull);
+        if (st_rows) atomicAdd(&a.stats->leaf_rows, st_rows);
+        if (st_ent) {
+            atomicAdd(&a.stats->entries, st_ent);
+            atomicAdd(&a.stats->entries_leaf, st_ent);
+        }
+        if (st_reused) atomicAdd(&a.stats->reused, st_reused);
+        atomicMax(&a.stats->leaf_max_steps, steps);
+        atomicMax(&a.stats->leaf_max_width, width);
+        atomicMax(&a.stats->leaf_max_cycles, (unsigned long long)(clock64() - t_start));
     }
 }
 
@@ -1297,6 +1600,10 @@ void ae_leaf_sweep(const LeafArgs &a, int blocks, int threads, cudaStream_t st) 
     if (a.nseg <= 0) return;
     ++g_launches;
     k_leaf<<<blocks, threads, 0, st>>>(a);
+    if (a.esc_min > 0 && a.esc_max > 0) {   // the walks handed on to blocks (a block per slot taken)
+        ++g_launches;
+        k_leaf_wide<<<a.esc_max, LEAF_WIDE_THREADS, 0, st>>>(a);
+    }
 }
 
 void ae_locate_counts(const RangeHit *rh, int64_t nrh, uint32_t *cnt, cudaStream_t st) {

@@ -210,6 +210,22 @@ struct LeafArgs {
     int32_t be, bj;               // key packing widths
     int32_t tiers;                // 1: count entries by cost tier
     DevStats *stats;
+    // walks whose row grows past esc_min entries (0: never) continue on a whole
+    // block (k_leaf_wide) with the rest of their task's injections, in one of
+    // esc_max slots: esc[slot] the walk's state, esc_rows + slot * 12 * cap its
+    // four row buffers; *esc_count counts the slots taken (it may pass esc_max:
+    // a walk that finds no free slot stays on its warp)
+    int32_t esc_min, esc_max;
+    unsigned long long *esc_count;
+    struct EscWalk *esc;
+    int32_t *esc_rows;
+};
+// A sweep walk handed from a warp to a block: its query, text position, the
+// row at that position (in the slot's first buffer) and its task's remaining
+// injections [k, kend) (indices into the sorted order).
+struct EscWalk {
+    int32_t qid, p;
+    int64_t rlen, k, kend;
 };
 void ae_inject_keys(const Inject *inj, int64_t ninj, uint64_t *keys, uint32_t *vals, cudaStream_t st);
 void ae_leaf_sweep(const LeafArgs &a, int blocks, int threads, cudaStream_t st);

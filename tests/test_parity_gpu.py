@@ -95,7 +95,9 @@ def test_dna_small_workload_full_parity(small):
                                   dict(item_columns=97), dict(item_columns=250, batch_columns=300),
                                   dict(leaf_capacity=64), dict(leaf_delay=0), dict(leaf_delay=3),
                                   dict(leaf_delay=14, leaf_segment=5), dict(int16_limit=0),
-                                  dict(int16_limit=6), dict(int16_limit=13, leaf_delay=14)])
+                                  dict(int16_limit=6), dict(int16_limit=13, leaf_delay=14),
+                                  dict(leaf_wide_rows=0), dict(leaf_wide_rows=8, leaf_delay=0),
+                                  dict(leaf_wide_rows=33, leaf_segment=3)])
 def test_dna_small_knobs_do_not_change_hits(small, opts):
     wl, idx = small
     want = want_hits(wl.text, wl.queries[0], wl.scheme, wl.H[0])
@@ -123,7 +125,8 @@ def test_random_planted_cases(si):
                                        leaf_delay=int(rng.integers(0, 15)),
                                        int16_limit=int(rng.choice([0, 5, 9, 32000])),
                                        general_rows=int(rng.integers(0, 2)),
-                                       row_layout=int(rng.integers(0, 3)))
+                                       row_layout=int(rng.integers(0, 3)),
+                                       leaf_wide_rows=int(rng.choice([0, 4, 33, 256])))
                 hits, _ = ae.ae_search(idx, [P], scheme, [H], options=opts)
                 assert_same(hits, want_hits(T, P, scheme, H), f"case {case} H {H} seed {seed_on}")
         idx.close()
@@ -164,6 +167,34 @@ def test_row_kernels_agree_entry_for_entry():
             assert np.array_equal(g[0], ref[0]) and np.array_equal(g[1], ref[1]), (delay, kind)
             assert g[2:] == ref[2:], (delay, kind, g[2:], ref[2:])
     idx.close()
+
+
+def test_wide_sweep_walks_on_blocks_keep_every_hit(small):
+    # walks whose rows grow past leaf_wide_rows entries continue on a whole block;
+    # with a low threshold most sweep walks do (and more than there are slots, so
+    # some stay on their warps): the hits equal the oracle's and the warp-only run's
+    wl, idx = small
+    want = want_hits(wl.text, wl.queries[0], wl.scheme, wl.H[0])
+    base, _ = ae.ae_search(idx, wl.queries, wl.scheme, wl.H, options=ae.make_options(leaf_wide_rows=0, leaf_delay=0))
+    assert ae.ae_last_stats()["leaf_wide_walks"] == 0
+    for thr in (2, 8, 40):
+        hits, _ = ae.ae_search(idx, wl.queries, wl.scheme, wl.H,
+                               options=ae.make_options(leaf_wide_rows=thr, leaf_delay=0, leaf_segment=2))
+        st = ae.ae_last_stats()
+        assert st["leaf_wide_walks"] > 0, thr
+        assert_same(hits, want, f"leaf_wide_rows {thr}")
+        assert np.array_equal(hits, base)
+    # protein rows in the block walk
+    rng = np.random.default_rng(77)
+    T = iid_text(6000, PROTEIN, [0.05] * 20, rng)
+    P = T[1000:1400].copy()
+    P[::9] = np.frombuffer(PROTEIN, dtype=np.uint8)[rng.integers(0, 20, size=P[::9].size)]
+    pidx = ae.ae_index_build(T, ae.AE_PROTEIN)
+    sc = Scheme(matrix=BLOSUM62, gap_open=-11, gap_extend=-1)
+    for thr in (0, 8):
+        hits, _ = ae.ae_search(pidx, [P], sc, [40], options=ae.make_options(leaf_wide_rows=thr, leaf_delay=0))
+        assert_same(hits, want_hits(T, P, sc, 40, alphabet=PROTEIN), f"protein, leaf_wide_rows {thr}")
+    pidx.close()
 
 
 def test_multi_query_batch_equals_single():
