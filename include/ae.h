@@ -171,7 +171,7 @@ typedef struct {
     int32_t fork_part;
     int32_t leaf_wide_rows;   /* a walk of the text-position sweep whose row grows past this many
                                  entries continues on a whole thread block (each step spread over
-                                 its threads) instead of one warp; 0: never.  Default 256.  The
+                                 its threads) instead of one warp; 0: never.  Default 128.  The
                                  results are the same */
 } ae_options;
 

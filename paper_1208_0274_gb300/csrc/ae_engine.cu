@@ -785,7 +785,7 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
 // Slots for sweep walks handed on to thread blocks (12 row buffers of the
 // sweep's row capacity each; a walk that finds no free slot stays on its warp)
 #ifndef AE_LEAF_WIDE_SLOTS
-#define AE_LEAF_WIDE_SLOTS 256
+#define AE_LEAF_WIDE_SLOTS 512
 #endif
 
 // Average parent-row length up to which a level's rows are walked one lane per
@@ -1446,7 +1446,7 @@ void ae_options_default(ae_options *opt) {
     opt->qprefix_domination = 1;
     opt->row_layout = 0;
     opt->fork_parts = 1;
-    opt->leaf_wide_rows = 256;
+    opt->leaf_wide_rows = 128;
     opt->fork_part = 0;
 }
 

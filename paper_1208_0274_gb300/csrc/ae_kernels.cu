@@ -409,7 +409,8 @@ constexpr int LEAF_WARPS = 4;   // k_leaf runs 128-thread blocks
 struct HitStage {
     uint64_t *key;
     int32_t *score;
-    uint32_t n;   // staged records (warp-uniform)
+    uint32_t n;     // staged records (warp-uniform)
+    uint32_t cap;   // records the stage holds
 };
 
 __device__ __forceinline__ void stage_flush(HitStage &hs, const LeafArgs &a, int lane) {
@@ -434,7 +435,7 @@ __device__ __forceinline__ void stage_flush(HitStage &hs, const LeafArgs &a, int
 // (staged) or in the global buffer (ok = within its capacity).
 __device__ __forceinline__ uint64_t stage_reserve(HitStage &hs, const LeafArgs &a, int lane, uint32_t htot,
                                                   bool &staged, bool &ok) {
-    if (htot > (uint32_t)LEAF_HS) {
+    if (htot > hs.cap) {
         unsigned long long g = 0;
         if (lane == 0) g = atomicAdd(a.hit_count, (unsigned long long)htot);
         g = __shfl_sync(FULL, g, 0);
@@ -443,7 +444,7 @@ __device__ __forceinline__ uint64_t stage_reserve(HitStage &hs, const LeafArgs &
         if (!ok && lane == 0) atomicAdd(&a.stats->hit_overflow, 1ull);
         return g;
     }
-    if (hs.n + htot > (uint32_t)LEAF_HS) stage_flush(hs, a, lane);
+    if (hs.n + htot > hs.cap) stage_flush(hs, a, lane);
     staged = true;
     ok = true;
     const uint64_t b = hs.n;
@@ -640,7 +641,8 @@ __global__ void __launch_bounds__(128, AE_LEAF_MINB) k_leaf(LeafArgs a) {
     const int lane = threadIdx.x & 31;
     const int gw = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
     if (gw >= a.nwarps) return;
-    HitStage hstage = {s_hkey[(threadIdx.x >> 5) & (LEAF_WARPS - 1)], s_hscore[(threadIdx.x >> 5) & (LEAF_WARPS - 1)], 0u};
+    HitStage hstage = {s_hkey[(threadIdx.x >> 5) & (LEAF_WARPS - 1)], s_hscore[(threadIdx.x >> 5) & (LEAF_WARPS - 1)], 0u,
+                       (uint32_t)LEAF_HS};
     const ScoreView &sc = a.sc;
     const int32_t u = -sc.ss, oe = sc.sg + sc.ss, g = sc.gmax;
     const int64_t cap = a.cap;
@@ -1154,8 +1156,9 @@ __global__ void __launch_bounds__(128, AE_LEAF_MINB) k_leaf(LeafArgs a) {
 // scans, and the merges of injected rows run on the first warp.  The values
 // are those of the warp walk of k_leaf (the same make_slots / slot_finish per
 // entry, the same merge); only the time per step differs.
-constexpr int LEAF_WIDE_THREADS = 256;
+constexpr int LEAF_WIDE_THREADS = 512;
 constexpr int LEAF_WIDE_WARPS = LEAF_WIDE_THREADS / 32;
+constexpr int LEAF_WIDE_HS = 128;   // hit records staged per warp of the block
 
 __device__ __forceinline__ int32_t block_excl_max(int32_t v, int32_t *sw, int32_t &total) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -1202,15 +1205,15 @@ struct WideState {
 
 __global__ void __launch_bounds__(LEAF_WIDE_THREADS) k_leaf_wide(LeafArgs a) {
     __shared__ int8_t smat[AE_MAX_SIGMA * AE_MAX_SIGMA];
-    __shared__ uint64_t s_hkey[LEAF_WIDE_WARPS][LEAF_HS];
-    __shared__ int32_t s_hscore[LEAF_WIDE_WARPS][LEAF_HS];
+    __shared__ uint64_t s_hkey[LEAF_WIDE_WARPS][LEAF_WIDE_HS];
+    __shared__ int32_t s_hscore[LEAF_WIDE_WARPS][LEAF_WIDE_HS];
     __shared__ uint32_t s_scan[LEAF_WIDE_WARPS];
     __shared__ WideState ws;
     load_matrix(a.sc, smat);
     const unsigned long long nesc = min(*(volatile unsigned long long *)a.esc_count, (unsigned long long)a.esc_max);
     if ((unsigned long long)blockIdx.x >= nesc) return;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    HitStage hstage = {s_hkey[wid], s_hscore[wid], 0u};
+    HitStage hstage = {s_hkey[wid], s_hscore[wid], 0u, (uint32_t)LEAF_WIDE_HS};
     const ScoreView &sc = a.sc;
     const int32_t u = -sc.ss, oe = sc.sg + sc.ss, g = sc.gmax;
     const int64_t cap = a.cap;
