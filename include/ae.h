@@ -160,7 +160,8 @@ typedef struct {
                                  depth); 0: keep every fork.  The results are the same */
     int32_t row_layout;       /* DNA int16x2 kernel: 0 (default) chooses per trie level, 1 walks each
                                  parent row in one lane per (node, child), 2 spreads each row over the
-                                 lanes one entry per lane.  The results are the same */
+                                 lanes one entry per lane, 3 gives each node a whole thread block.
+                                 The results are the same */
     /* A search split over ranks or devices: with fork_parts = R > 1 the search keeps only part
      * fork_part (0 <= fork_part < R) of the forks -- the seed subtrees whose gram hashes to the
      * part (q-prefix seeding), or the start columns j with j % R == fork_part (walks from the

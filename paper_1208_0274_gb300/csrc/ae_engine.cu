@@ -788,6 +788,15 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
 #define AE_LEAF_WIDE_SLOTS 512
 #endif
 
+// Levels of at most AE_WIDE_NODES nodes whose rows average AE_WIDE_ROW_AVG
+// entries or more give each node a whole block (k_rows_dna_wide)
+#ifndef AE_WIDE_NODES
+#define AE_WIDE_NODES 65536
+#endif
+#ifndef AE_WIDE_ROW_AVG
+#define AE_WIDE_ROW_AVG 512
+#endif
+
 // Average parent-row length up to which a level's rows are walked one lane per
 // (node, child) rather than spread one entry per lane (per level on the 100 Mbp
 // text with queries of 10 kbp to 1 Mbp, the walk was the faster layout up to
@@ -876,6 +885,9 @@ void Search::dna_level(int64_t &F, int cur, int64_t &cur_ent, int64_t &lf_ent_ba
     // short parent rows are walked one lane per (node, child); long rows spread
     // over the lanes (a lone long row would hold its warp alone)
     da.sequential = (opt.row_layout == 1) || (opt.row_layout == 0 && cur_ent <= AE_SEQ_ROW_AVG * F) ? 1 : 0;
+    // a level of few nodes with long rows: one block per node
+    if (opt.row_layout == 3 || (opt.row_layout == 0 && F <= AE_WIDE_NODES && cur_ent >= AE_WIDE_ROW_AVG * F))
+        da.sequential = 2;
     const auto t_level = std::chrono::steady_clock::now();
     LevelCounters hc;
     auto run = [&]() {
@@ -939,7 +951,8 @@ void Search::dna_level(int64_t &F, int cur, int64_t &cur_ent, int64_t &lf_ent_ba
     if (trace()) {
         fprintf(stderr, "[ae level] dna %s nodes %lld (per task %d) entries %lld triples %lld -> frontier %lld nodes %lld, "
                         "leaf %lld rows %lld%s; %.3f ms\n",
-                da.sequential ? "walk" : "spread", (long long)F, npt, (long long)cur_ent, (long long)hc.triples,
+                da.sequential == 2 ? "block" : da.sequential ? "walk" : "spread", (long long)F, npt, (long long)cur_ent,
+                (long long)hc.triples,
                 (long long)fr_ent, (long long)fr_node, (long long)lf_ent, (long long)lf_node,
                 retried ? " (run again at exact sizes)" : "", ms_since(t_level));
     }
@@ -1240,6 +1253,7 @@ ae_status search_core(const ae_index *idx, Workspace *w, const int64_t *offsets,
     if (opt) s.opt = *opt;
     if (s.opt.fork_parts < 1 || s.opt.fork_part < 0 || s.opt.fork_part >= s.opt.fork_parts) return AE_EINVAL;
     if (s.opt.leaf_wide_rows < 0) return AE_EINVAL;
+    if (s.opt.row_layout < 0 || s.opt.row_layout > 3) return AE_EINVAL;
     if (s.opt.item_columns < 1 || s.opt.batch_columns < 1 || s.opt.leaf_capacity < 64 || s.opt.leaf_segment < 0 ||
         s.opt.leaf_delay < 0 || s.opt.leaf_delay > 14 || s.opt.int16_limit < 0 || s.opt.int16_limit > 32000)
         return AE_EINVAL;

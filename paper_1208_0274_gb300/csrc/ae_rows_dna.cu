@@ -21,6 +21,8 @@
 // protein, the int32 route, root rows and cost-tier counting; both produce the
 // same nodes and arenas.
 #include <cuda_runtime.h>
+
+#include <algorithm>
 #include <stdint.h>
 
 #include "ae_device.cuh"
@@ -801,6 +803,339 @@ __global__ void __launch_bounds__(DW * 32, AE_DNA_MINB) k_rows_dna(DnaRowsArgs a
     if (lane == 0 && trip_mine) atomicAdd(&a.ctr->triples, (unsigned long long)trip_mine);
 }
 
+
+// ---- levels of few nodes with long rows: one block per node
+//
+// The spread layout gives a node one warp, which carries its row's
+// horizontal-gap scan from chunk to chunk; a level of a few hundred nodes with
+// rows of thousands of entries then runs on a few hundred warps.  Here a whole
+// block takes a node: each chunk of WB_T parent entries is spread one per
+// thread, and per child the keys are a block-wide max-scan carried from chunk
+// to chunk.  The count phase sums each child's outputs, thread 0 reserves the
+// node's ranges (as a task of k_rows_dna does), and the write phase computes
+// the chunks again and writes at block-wide exclusive sums of the counts.  The
+// values are those of the other layouts.
+constexpr int WB_T = 512;
+constexpr int WB_W = WB_T / 32;
+
+struct WideNode {
+    uint32_t clo[4], chi[4];
+    unsigned kmask, smask, wmask;
+    int32_t qid, m, H, full;
+    uint32_t pcnt, len, qoff;
+    uint64_t off;
+    uint64_t pos_e[4], pos_h[4];       // write: each child's next entry and hit positions
+    unsigned long long cn[4], ch[4];   // count: each child's entries and hits
+    int32_t sw[WB_W];                  // block scans: per-warp values
+    unsigned long long sw64[WB_W];
+};
+
+__device__ __forceinline__ int32_t wb_scan_max(int32_t v, WideNode &w, int32_t &excl, int32_t &total) {
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    int32_t incl = warp_incl_max(v);
+    if (lane == 31) w.sw[wi] = incl;
+    __syncthreads();
+    int32_t pre = AE_KNEG, all = AE_KNEG;
+#pragma unroll
+    for (int x = 0; x < WB_W; ++x) {
+        const int32_t y = w.sw[x];
+        if (x < wi) pre = max(pre, y);
+        all = max(all, y);
+    }
+    int32_t ex = __shfl_up_sync(FULL, incl, 1);
+    if (lane == 0) ex = AE_KNEG;
+    excl = max(pre, ex);
+    total = all;
+    __syncthreads();
+    return max(pre, incl);
+}
+
+__device__ __forceinline__ unsigned long long wb_scan_sum(unsigned long long v, WideNode &w, unsigned long long &total) {
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    unsigned long long incl = v;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+        const unsigned long long y = __shfl_up_sync(FULL, incl, d);
+        if (lane >= d) incl += y;
+    }
+    if (lane == 31) w.sw64[wi] = incl;
+    __syncthreads();
+    unsigned long long pre = 0, all = 0;
+#pragma unroll
+    for (int x = 0; x < WB_W; ++x) {
+        const unsigned long long y = w.sw64[x];
+        if (x < wi) pre += y;
+        all += y;
+    }
+    total = all;
+    __syncthreads();
+    return pre + incl - v;   // exclusive
+}
+
+__global__ void __launch_bounds__(WB_T) k_rows_dna_wide(DnaRowsArgs a) {
+    __shared__ WideNode w;
+    const ScoreView &sc = a.sc;
+    const int32_t u = -sc.ss, oe = sc.sg + sc.ss, g = sc.gmax, sa = sc.sa, sb = sc.sb;
+    const int32_t strong = -oe;
+    unsigned long long trip_mine = 0;
+    for (int64_t v = blockIdx.x; v < a.nnodes; v += gridDim.x) {
+        if (threadIdx.x == 0) {
+            const Node nd = a.nodes[v];
+            uint32_t clo[4] = {0, 0, 0, 0}, chi[4] = {0, 0, 0, 0};
+            unsigned kmask = kids4(a.ix, nd.lo, nd.hi, clo, chi);
+            if (!nd.cnt) kmask = 0;
+            const uint32_t pcnt = (uint32_t)nd.item >> 24;
+            unsigned smask = 0;
+            if (kmask) {
+                const bool young = (int)pcnt + 1 <= a.leaf_delay;
+                for (int c = 0; c < 4; ++c)
+                    if (((kmask >> c) & 1u) && (young || chi[c] - clo[c] >= 2)) smask |= 1u << c;
+            }
+            w.qid = nd.item & 0xFFFFFF;
+            w.pcnt = pcnt;
+            w.len = nd.cnt;
+            w.off = nd.off;
+            w.kmask = kmask;
+            w.smask = smask;
+            w.m = kmask ? a.qv.m[w.qid] : 1;
+            w.H = kmask ? a.qv.H[w.qid] : 1;
+            w.qoff = kmask ? (uint32_t)a.qv.off[w.qid] : 0u;
+            w.full = 0;
+            for (int c = 0; c < 4; ++c) {
+                w.clo[c] = clo[c];
+                w.chi[c] = chi[c];
+                w.cn[c] = 0;
+                w.ch[c] = 0;
+            }
+        }
+        __syncthreads();
+        const unsigned kmask = w.kmask, smask = w.smask;
+        const uint32_t len = w.len;
+        if (!kmask) {
+            __syncthreads();
+            continue;
+        }
+        const int32_t m = w.m, H = w.H, qid = w.qid;
+        const uint64_t off = w.off;
+        const int32_t tb0 = H - 1 - (m - 1) * g;   // thr(j) = max(tb0 + j g, 0), Theorem 2
+        const uint8_t *P = a.qv.codes + w.qoff;
+        trip_mine += (unsigned long long)__popc(kmask) * len;
+        for (int ph = 0; ph < 2; ++ph) {
+            const bool write = ph == 1;
+            const unsigned pmask = write ? w.wmask : kmask;
+            int32_t carry[4] = {AE_KNEG, AE_KNEG, AE_KNEG, AE_KNEG};   // by child index of the phase
+            for (uint32_t t0 = 0; t0 < len; t0 += WB_T) {
+                const uint32_t t = t0 + threadIdx.x;
+                const bool valid = t < len;
+                int32_t j = m, jn = m, pjv = -2, pMv = 0;
+                uint32_t mg = 0;
+                if (valid) {
+                    j = a.pj[off + t];
+                    mg = a.pmg[off + t];
+                    jn = t + 1 < len ? a.pj[off + t + 1] : m;
+                    if (t > 0) {
+                        pjv = a.pj[off + t - 1];
+                        pMv = (int32_t)(int16_t)(a.pmg[off + t - 1] & 0xFFFFu);
+                    }
+                }
+                const bool ok = valid && (uint32_t)j < (uint32_t)m && jn > j && jn <= m;   // a sorted row in [0, m)
+                if (valid && !ok) atomicExch(&a.ctr->overflow, 1ull);
+                const int32_t M = (int32_t)(int16_t)(mg & 0xFFFFu);
+                const bool adjA = ok && pjv + 1 == j && pMv > 0;
+                const bool hasB = ok && (j + 1 < m) && (j + 1 != jn);
+                const int pA = ok ? (int)P[j] : 255;
+                const int pB = hasB ? (int)P[j + 1] : 255;
+                const int32_t traw = tb0 + j * g;
+                const int32_t tA = max(traw, 0), tB = max(traw + g, 0);
+                int32_t Gap = ok ? gap_from_mg(mg, sc.ss, oe) : AE_NEG;
+                Gap = Gap > tA ? Gap : AE_NEG;
+                const int32_t ju = j * u;
+                unsigned rem = pmask;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {   // block-uniform
+                    if (!rem) break;
+                    const int c = __ffs(rem) - 1;
+                    rem &= rem - 1;
+                    int32_t MpA = AE_NEG, MpB = AE_NEG;
+                    if (ok) {
+                        int32_t DA = adjA ? pMv + (c == pA ? sa : sb) : AE_NEG;
+                        DA = DA > tA ? DA : AE_NEG;
+                        MpA = max(DA, Gap);
+                        const int32_t DB = M + (c == pB ? sa : sb);
+                        MpB = (hasB && DB > tB) ? DB : AE_NEG;
+                    }
+                    const int32_t keyA = MpA > strong ? MpA + ju : AE_KNEG;
+                    const int32_t keyB = MpB > strong ? MpB + ju + u : AE_KNEG;
+                    int32_t excl, tot;
+                    int32_t incl = wb_scan_max(max(keyA, keyB), w, excl, tot);
+                    excl = max(excl, carry[i]);
+                    incl = max(incl, carry[i]);
+                    carry[i] = max(carry[i], tot);
+                    const int32_t GbA = excl > AE_KNEG / 2 ? sc.sg - ju + excl : AE_NEG;
+                    const int32_t MA = max(MpA, GbA);
+                    const bool aliveA = ok && MA > tA;
+                    int32_t MB = AE_NEG;
+                    bool aliveB = false;
+                    if (hasB) {
+                        const int32_t KB = max(excl, keyA);
+                        const int32_t GbB = KB > AE_KNEG / 2 ? sc.sg - ju - u + KB : AE_NEG;
+                        MB = max(MpB, GbB);
+                        aliveB = MB > tB;
+                    }
+                    int32_t run_len = 0, run_hits = 0;
+                    const int32_t run_start = hasB ? j + 2 : j + 1;
+                    const int32_t V0 = sc.sg - run_start * u + incl;
+                    if (ok && incl > AE_KNEG / 2 && run_start < jn && V0 > 0) {
+                        const int32_t rl = min((int32_t)div_small((uint32_t)(V0 - 1), a.urec) + 1, jn - run_start);
+                        if (traw + (run_start + rl - 1) * g <= 0) {
+                            run_len = rl;
+                            if (V0 >= H) run_hits = min(rl, (int32_t)div_small((uint32_t)(V0 - H), a.urec) + 1);
+                        } else {
+                            run_of(run_start, jn, incl, sc, m, H, u, run_len, run_hits);
+                        }
+                    }
+                    const bool st = (smask >> c) & 1u;
+                    const bool hA = st && aliveA && MA >= H, hB = st && aliveB && MB >= H;
+                    const uint32_t cnt = (uint32_t)aliveA + (uint32_t)aliveB + (uint32_t)run_len;
+                    const uint32_t hcnt = (uint32_t)hA + (uint32_t)hB + (st ? (uint32_t)run_hits : 0u);
+                    if (!write) {
+                        // per-warp sums into the child's totals
+                        unsigned long long x = ((unsigned long long)cnt << 32) | hcnt;
+#pragma unroll
+                        for (int d = 16; d > 0; d >>= 1) x += __shfl_down_sync(FULL, x, d);
+                        if ((threadIdx.x & 31) == 0 && x) {
+                            atomicAdd(&w.cn[c], x >> 32);
+                            atomicAdd(&w.ch[c], x & 0xFFFFFFFFull);
+                        }
+                        continue;
+                    }
+                    // the child's positions are read before the scan: thread 0 moves them on after it
+                    const uint64_t pe = w.pos_e[c], ph = w.pos_h[c];
+                    unsigned long long ctot;
+                    const unsigned long long ex =
+                        wb_scan_sum(((unsigned long long)cnt << 32) | hcnt, w, ctot);
+                    uint64_t e0 = pe + (ex >> 32), h0 = ph + (ex & 0xFFFFFFFFull);
+                    const uint64_t ecap = st ? a.fr_ent_cap : a.lf_ent_cap;
+                    if (cnt && (e0 + cnt > ecap || h0 + hcnt > a.hit_cap)) {   // never past the arenas
+                        atomicExch(&a.ctr->overflow, 1ull);
+                    } else {
+                        const uint32_t clo = w.clo[c], chi = w.chi[c];
+                        if (aliveA) {
+                            if (st) {
+                                a.fj[e0] = j;
+                                a.fmg[e0] = pack_mg(MA, Gap);
+                            } else {
+                                a.lj[e0] = j;
+                                a.lM[e0] = MA;
+                                a.lGa[e0] = Gap;
+                            }
+                            ++e0;
+                            if (hA) a.rhits[h0++] = RangeHit{clo, chi, qid, j, MA, 0};
+                        }
+                        if (aliveB) {
+                            if (st) {
+                                a.fj[e0] = j + 1;
+                                a.fmg[e0] = pack_mg(MB, AE_NEG);
+                            } else {
+                                a.lj[e0] = j + 1;
+                                a.lM[e0] = MB;
+                                a.lGa[e0] = AE_NEG;
+                            }
+                            ++e0;
+                            if (hB) a.rhits[h0++] = RangeHit{clo, chi, qid, j + 1, MB, 0};
+                        }
+                        for (int32_t r = 0; r < run_len; ++r) {
+                            const int32_t col = run_start + r, val = V0 - r * u;
+                            if (st) {
+                                a.fj[e0 + r] = col;
+                                a.fmg[e0 + r] = pack_mg(val, AE_NEG);
+                            } else {
+                                a.lj[e0 + r] = col;
+                                a.lM[e0 + r] = val;
+                                a.lGa[e0 + r] = AE_NEG;
+                            }
+                            if (st && r < run_hits) a.rhits[h0 + r] = RangeHit{clo, chi, qid, col, val, 0};
+                        }
+                    }
+                    if (threadIdx.x == 0) {
+                        w.pos_e[c] += ctot >> 32;
+                        w.pos_h[c] += ctot & 0xFFFFFFFFull;
+                    }
+                    __syncthreads();
+                }
+            }
+            __syncthreads();
+            if (!write) {
+                // ---- reservation of the node's ranges, as a task of k_rows_dna does
+                if (threadIdx.x == 0) {
+                    unsigned long long s_fe = 0, s_le = 0, s_fn = 0, s_ln = 0, s_h = 0;
+                    unsigned wmask = kmask;
+                    for (int c = 0; c < 4; ++c) {
+                        if (!((kmask >> c) & 1u)) continue;
+                        if (w.cn[c] == 0 && w.ch[c] == 0) wmask &= ~(1u << c);
+                        if ((smask >> c) & 1u) {
+                            s_fe += w.cn[c];
+                            s_fn += w.cn[c] ? 1 : 0;
+                        } else {
+                            s_le += w.cn[c];
+                            s_ln += w.cn[c] ? 1 : 0;
+                        }
+                        s_h += w.ch[c];
+                    }
+                    w.wmask = wmask;
+                    const unsigned long long b0 = s_fe ? atomicAdd(&a.ctr->fr_ent, s_fe) : 0;
+                    const unsigned long long b1 = s_le ? atomicAdd(&a.ctr->lf_ent, s_le) : 0;
+                    const unsigned long long b2 = s_fn ? atomicAdd(&a.ctr->fr_node, s_fn) : 0;
+                    const unsigned long long b3 = s_ln ? atomicAdd(&a.ctr->lf_node, s_ln) : 0;
+                    const unsigned long long b4 = s_h ? atomicAdd(&a.ctr->hits, s_h) : 0;
+                    const bool full = (s_fe && b0 + s_fe > a.fr_ent_cap) || (s_le && b1 + s_le > a.lf_ent_cap) ||
+                                      (s_fn && b2 + s_fn > a.fr_node_cap) || (s_ln && b3 + s_ln > a.lf_node_cap) ||
+                                      (s_h && b4 + s_h > a.hit_cap);
+                    w.full = full ? 1 : 0;
+                    if (full) {
+                        atomicExch(&a.ctr->retry, 1ull);
+                    } else {
+                        uint64_t efr = b0, elf = b1, nfr = b2, nlf = b3, hh = b4;
+                        for (int c = 0; c < 4; ++c) {
+                            if (!((kmask >> c) & 1u)) continue;
+                            const bool st = (smask >> c) & 1u;
+                            w.pos_e[c] = st ? efr : elf;
+                            w.pos_h[c] = hh;
+                            const uint32_t cn = (uint32_t)w.cn[c];
+                            if (cn) {
+                                if (st) {
+                                    Node cn_;
+                                    cn_.lo = w.clo[c];
+                                    cn_.hi = w.chi[c];
+                                    const uint32_t uq = (w.chi[c] - w.clo[c] == 1) ? w.pcnt + 1u : 0u;
+                                    cn_.item = (int32_t)((uint32_t)qid | (uq << 24));
+                                    cn_.cnt = cn;
+                                    cn_.off = efr;
+                                    a.fnodes[nfr++] = cn_;
+                                } else {
+                                    Inject in;
+                                    in.qid = qid;
+                                    in.e = a.ix.tend[w.clo[c]];
+                                    in.cnt = cn;
+                                    in.pad = 0;
+                                    in.off = elf;
+                                    a.inj[nlf++] = in;
+                                }
+                            }
+                            if (st) efr += cn;
+                            else elf += cn;
+                            hh += w.ch[c];
+                        }
+                    }
+                }
+                __syncthreads();
+                if (w.full || !w.wmask) break;   // block-uniform
+            }
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0 && trip_mine) atomicAdd(&a.ctr->triples, trip_mine);
+}
 }  // namespace
 
 int ae_rows_dna_blocks_per_sm() { return AE_DNA_MINB; }
@@ -809,7 +1144,13 @@ int ae_rows_dna_warps_per_block() { return DW; }
 void ae_rows_dna(const DnaRowsArgs &a, int blocks, cudaStream_t st) {
     if (a.nnodes <= 0) return;
     ++g_launches;
-    if (a.sequential)
+    if (a.sequential == 2) {   // one block per node
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int64_t nb = std::min<int64_t>(a.nnodes, (int64_t)sms * 4);
+        k_rows_dna_wide<<<(unsigned)nb, WB_T, 0, st>>>(a);
+    } else if (a.sequential)
         k_rows_dna<true><<<blocks, DW * 32, 0, st>>>(a);
     else
         k_rows_dna<false><<<blocks, DW * 32, 0, st>>>(a);

@@ -125,7 +125,7 @@ def test_random_planted_cases(si):
                                        leaf_delay=int(rng.integers(0, 15)),
                                        int16_limit=int(rng.choice([0, 5, 9, 32000])),
                                        general_rows=int(rng.integers(0, 2)),
-                                       row_layout=int(rng.integers(0, 3)),
+                                       row_layout=int(rng.integers(0, 4)),
                                        leaf_wide_rows=int(rng.choice([0, 4, 33, 256])))
                 hits, _ = ae.ae_search(idx, [P], scheme, [H], options=opts)
                 assert_same(hits, want_hits(T, P, scheme, H), f"case {case} H {H} seed {seed_on}")
@@ -157,7 +157,8 @@ def test_row_kernels_agree_entry_for_entry():
     for delay in (0, 8, 14):
         got = {}
         for kind, opts in (("general", dict(general_rows=1)), ("auto", dict()),
-                           ("walk", dict(row_layout=1)), ("spread", dict(row_layout=2))):
+                           ("walk", dict(row_layout=1)), ("spread", dict(row_layout=2)),
+                           ("block", dict(row_layout=3))):
             hits, counts = ae.ae_search(idx, qs, scheme, Hs, options=ae.make_options(leaf_delay=delay, **opts))
             st = ae.ae_last_stats()
             got[kind] = (hits, counts, st["entries"], st["triples"], st["nodes"], st["injections"])
