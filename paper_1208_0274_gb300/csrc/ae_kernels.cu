@@ -1456,17 +1456,28 @@ __global__ void k_unique_flags(const uint64_t *key, int64_t N, uint32_t *flags) 
 __global__ void k_unique_write(const uint64_t *key, const int32_t *score, int64_t N, const uint64_t *off, int be,
                                int bj, ae_hit *out, unsigned long long *qcount) {
     const uint64_t jmask = (1ull << bj) - 1ull, emask = (1ull << be) - 1ull;
-    for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < N; t += (int64_t)gridDim.x * blockDim.x) {
-        const uint64_t k = key[t];
-        if (t > 0 && key[t - 1] == k) continue;
-        int32_t best = score[t];
-        for (int64_t u = t + 1; u < N && key[u] == k; ++u) best = max(best, score[u]);
-        ae_hit h;
-        h.text_end = (int64_t)((k >> bj) & emask);
-        h.query_end = (int32_t)(k & jmask);
-        h.score = best;
-        out[off[t]] = h;
-        atomicAdd(&qcount[k >> (be + bj)], 1ull);
+    const int lane = threadIdx.x & 31;
+    // the loop bound is uniform over a warp, so every lane reaches the per-query vote
+    for (int64_t t0 = blockIdx.x * (int64_t)blockDim.x; t0 < N; t0 += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t t = t0 + threadIdx.x;
+        uint32_t q = 0xFFFFFFFFu;   // the query of a cell's first record, else none
+        if (t < N) {
+            const uint64_t k = key[t];
+            if (!(t > 0 && key[t - 1] == k)) {
+                int32_t best = score[t];
+                for (int64_t u = t + 1; u < N && key[u] == k; ++u) best = max(best, score[u]);
+                ae_hit h;
+                h.text_end = (int64_t)((k >> bj) & emask);
+                h.query_end = (int32_t)(k & jmask);
+                h.score = best;
+                out[off[t]] = h;
+                q = (uint32_t)(k >> (be + bj));
+            }
+        }
+        // per-query counts: one atomic per query present in the warp (the records are
+        // sorted by query, so a warp usually holds one or two)
+        const unsigned grp = __match_any_sync(FULL, q);
+        if (q != 0xFFFFFFFFu && lane == __ffs(grp) - 1) atomicAdd(&qcount[q], (unsigned long long)__popc(grp));
     }
 }
 
