@@ -455,6 +455,10 @@ struct Search {
     int64_t dna_nodes = 0, dna_entries = 0, dna_retries = 0;   // DNA int16x2 route (counted on the host)
     double dna_ratio[5] = {0, 0, 0, 0, 0};   // the last DNA level's outputs per input, by arena kind
     bool dna_ratio_ok = false;
+    // every batch so far held whole queries, later than the previous batch's: the
+    // batches' compacted hits then already lie sorted by (query, text end, query end)
+    bool batches_ordered = true;
+    int32_t last_batch_q = -1;
     int num_sms = 152;
     Prof prof;
 
@@ -480,6 +484,11 @@ struct Search {
 };
 
 void Search::run_batch(const std::vector<WorkItem> &items) {
+    int32_t batch_max_q = last_batch_q;
+    for (const WorkItem &it : items) {
+        if (it.c0 != 0 || it.c1 != m[it.qid] || it.qid <= last_batch_q) batches_ordered = false;
+        batch_max_q = std::max(batch_max_q, it.qid);
+    }
     const int sigma = ix.sigma;
     const int64_t batch_hits0 = nhits;
     const int nitems = (int)items.size();
@@ -779,6 +788,7 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
     auto t2 = std::chrono::steady_clock::now();
     locate_phase(rh_base);
     compact_hits(batch_hits0);
+    last_batch_q = batch_max_q;
     stats.ms_reduce += ms_since(t2);
 }
 
@@ -1199,6 +1209,23 @@ int64_t Search::finish(ae_hit **out_dev, std::vector<int64_t> &counts) {
         *out_dev = nullptr;
         stats.ms_reduce += ms_since(t0);
         return 0;
+    }
+    if (batches_ordered) {
+        // each batch's hits are sorted and unique, and the batches follow each other in
+        // query order: the records are final as they lie
+        ensure(w->uniq, std::max<int64_t>(N, 1) * sizeof(ae_hit), st);
+        prof.mark(K_OTHER);
+        ae_unique_write(ptr<uint64_t>(w->hkey), ptr<int32_t>(w->hscore), N, nullptr, be, bj, ptr<ae_hit>(w->uniq),
+                        ptr<unsigned long long>(w->qcount), st);
+        prof.mark(K_OTHER);
+        std::vector<unsigned long long> qc(nq);
+        CU(cudaMemcpyAsync(qc.data(), w->qcount.p, sizeof(unsigned long long) * nq, cudaMemcpyDeviceToHost, st));
+        sync();
+        for (int q = 0; q < nq; ++q) counts[q] = (int64_t)qc[q];
+        *out_dev = ptr<ae_hit>(w->uniq);
+        stats.hits = N;
+        stats.ms_reduce += ms_since(t0);
+        return N;
     }
     ensure(w->hk1, N * 8, st);
     ensure(w->hv1, N * 4, st);

@@ -1470,7 +1470,7 @@ __global__ void k_unique_write(const uint64_t *key, const int32_t *score, int64_
                 h.text_end = (int64_t)((k >> bj) & emask);
                 h.query_end = (int32_t)(k & jmask);
                 h.score = best;
-                out[off[t]] = h;
+                out[off ? off[t] : t] = h;   // off NULL: the records are unique already
                 q = (uint32_t)(k >> (be + bj));
             }
         }
