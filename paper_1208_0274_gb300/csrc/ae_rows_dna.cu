@@ -221,35 +221,42 @@ __device__ __forceinline__ void rows_seq(const DnaRowsArgs &a, WarpSmem &sm, int
         uint32_t cnt = 0, hcnt = 0;
         bool bad = false;
         int32_t K = AE_KNEG, prev_j = -2, prev_M = 0;
+        const int32_t *pjr = a.pj + off;     // the parent row
+        const uint32_t *pmr = a.pmg + off;
         // loads run ahead of their use: the next entry and its query letters, and
         // the column of the entry after it
-        int32_t j_c = a.pj[off];
-        uint32_t mg_c = a.pmg[off];
-        int32_t j_n = nlen > 1 ? a.pj[off + 1] : m;
-        int pa_c = (uint32_t)j_c < (uint32_t)m ? (int)P[j_c] : 255;
-        int pb_c = (uint32_t)(j_c + 1) < (uint32_t)m ? (int)P[j_c + 1] : 255;
-        for (uint32_t k = 0; k < nlen; ++k) {
+        int32_t j_c = pjr[0];
+        uint32_t mg_c = pmr[0];
+        int32_t j_n = nlen > 1 ? pjr[1] : m;
+        // a parent row is sorted by column inside [0, m): its first column is checked
+        // here and every next one against the previous and m below; anything else is
+        // reported, and no column past the query is read
+        if ((uint32_t)j_c >= (uint32_t)m) bad = true;
+        int pa_c = !bad ? (int)P[j_c] : 255;
+        int pb_c = !bad && j_c + 1 < m ? (int)P[j_c + 1] : 255;
+        for (uint32_t k = 0; k < nlen && !bad; ++k) {
             const int32_t j = j_c, jn = j_n;
             const uint32_t mg = mg_c;
             const int pA = pa_c, pB = pb_c;
-            if (k + 1 < nlen) {
-                mg_c = a.pmg[off + k + 1];
-                j_c = jn;
-                j_n = (k + 2 < nlen) ? a.pj[off + k + 2] : m;
-                pa_c = (uint32_t)jn < (uint32_t)m ? (int)P[jn] : 255;
-                pb_c = (uint32_t)(jn + 1) < (uint32_t)m ? (int)P[jn + 1] : 255;
-            }
-            // a parent row is sorted by column inside [0, m); anything else is
-            // reported, and no column past the query is read
-            if ((uint32_t)j >= (uint32_t)m || jn <= j || jn > m) {
+            if (jn <= j || jn > m) {
                 bad = true;
                 break;
+            }
+            if (k + 1 < nlen) {
+                mg_c = pmr[k + 1];
+                j_c = jn;
+                j_n = (k + 2 < nlen) ? pjr[k + 2] : m;
+                // a next column at m is reported in its own step (no later column is above it)
+                pa_c = jn < m ? (int)P[jn] : 255;
+                pb_c = jn + 1 < m ? (int)P[jn + 1] : 255;
             }
             const int32_t M = (int32_t)(int16_t)(mg & 0xFFFFu);
             const int32_t traw = tb0 + j * g;
             const int32_t tA = max(traw, 0), tB = max(traw + g, 0);
             const int32_t ju = j * u;
-            int32_t Gap = gap_from_mg(mg, sc.ss, oe);
+            // the vertical gap, max(G_a + s_s, M + s_g + s_s); a dead state (stored as
+            // AE_DEAD16) stays far below the threshold, which is >= 0
+            int32_t Gap = max((int32_t)(int16_t)(mg >> 16) + sc.ss, M + oe);
             Gap = Gap > tA ? Gap : AE_NEG;
             int32_t DA = (prev_j + 1 == j && prev_M > 0) ? prev_M + (c == pA ? sa : sb) : AE_NEG;
             DA = DA > tA ? DA : AE_NEG;
