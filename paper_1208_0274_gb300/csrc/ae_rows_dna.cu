@@ -415,7 +415,7 @@ __device__ __forceinline__ void rows_spread(const DnaRowsArgs &a, WarpSmem &sm, 
         const int pB = hasB ? (int)P[j + 1] : 255;
         const int32_t traw = tb0 + j * g;
         const int32_t tA = max(traw, 0), tB = max(traw + g, 0);
-        int32_t Gap = valid ? gap_from_mg(mg, sc.ss, oe) : AE_NEG;
+        int32_t Gap = valid ? max((int32_t)(int16_t)(mg >> 16) + sc.ss, M + oe) : AE_NEG;   // dead stays below tA >= 0
         Gap = Gap > tA ? Gap : AE_NEG;
         const int32_t ju = j * u;
         // the node continuing from the previous chunk sits at lane 0
@@ -954,7 +954,7 @@ __global__ void __launch_bounds__(WB_T) k_rows_dna_wide(DnaRowsArgs a) {
                 const int pB = hasB ? (int)P[j + 1] : 255;
                 const int32_t traw = tb0 + j * g;
                 const int32_t tA = max(traw, 0), tB = max(traw + g, 0);
-                int32_t Gap = ok ? gap_from_mg(mg, sc.ss, oe) : AE_NEG;
+                int32_t Gap = ok ? max((int32_t)(int16_t)(mg >> 16) + sc.ss, M + oe) : AE_NEG;   // dead stays below tA
                 Gap = Gap > tA ? Gap : AE_NEG;
                 const int32_t ju = j * u;
                 unsigned rem = pmask;
