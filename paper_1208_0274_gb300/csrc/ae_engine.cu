@@ -172,6 +172,8 @@ struct Workspace {
     DevBuf hkey, hscore, hcount, hk1, hv1;
     // leaf sweep scratch; walks handed on to blocks (state, count, row buffers)
     DevBuf scratch, next_seg, esc, esc_count, esc_rows;
+    // walk layout of the DNA row kernel: per warp and lane, the count phase's child rows
+    DevBuf stage;
     // output
     DevBuf uniq, uflags, uoff, qcount;
     DevBuf stats, segs, ctr, seg_cnt, seg_hit, task_first, task_tot, task_off, task_tmp, task_sum, res, res_key;
@@ -196,7 +198,7 @@ struct Workspace {
                 &aM[1], &aGa[0], &aGa[1], &nodes[0], &nodes[1], &cnt[0], &cnt[1], &cnt[2], &cnt[3],
                 &cnt[4], &off[0], &off[1], &off[2], &off[3], &off[4], &totals, &scan_tmp, &lj, &lM,
                 &lGa, &inj, &rhits, &sk0, &sv0, &sk1, &sv1, &sort_tmp, &hkey, &hscore, &hcount, &hk1,
-                &hv1, &scratch, &next_seg, &esc, &esc_count, &esc_rows, &uniq, &uflags, &uoff, &qcount, &stats, &segs, &ctr, &seg_cnt, &seg_hit,
+                &hv1, &scratch, &next_seg, &esc, &esc_count, &esc_rows, &stage, &uniq, &uflags, &uoff, &qcount, &stats, &segs, &ctr, &seg_cnt, &seg_hit,
                 &task_first, &task_tot, &task_off, &task_tmp, &task_sum, &res, &res_key};
     }
 
@@ -792,6 +794,12 @@ void Search::run_batch(const std::vector<WorkItem> &items) {
     stats.ms_reduce += ms_since(t2);
 }
 
+// Row entries each lane of the DNA row kernel's walk layout can keep from its
+// count phase for the write phase (per task)
+#ifndef AE_STAGE_ROWS
+#define AE_STAGE_ROWS 256
+#endif
+
 // Slots for sweep walks handed on to thread blocks (12 row buffers of the
 // sweep's row capacity each; a walk that finds no free slot stays on its warp)
 #ifndef AE_LEAF_WIDE_SLOTS
@@ -898,6 +906,20 @@ void Search::dna_level(int64_t &F, int cur, int64_t &cur_ent, int64_t &lf_ent_ba
     // a level of few nodes with long rows: one block per node
     if (opt.row_layout == 3 || (opt.row_layout == 0 && F <= AE_WIDE_NODES && cur_ent >= AE_WIDE_ROW_AVG * F))
         da.sequential = 2;
+    // the walk layout keeps its count phase's rows for the write phase (outside the
+    // fixed arena of the no-allocation entry point; without room, rows are computed twice)
+    da.stage = nullptr;
+    da.stage_cap = 0;
+    if (da.sequential == 1 && !g_arena) {
+        const int64_t lanes = (int64_t)num_sms * ae_rows_dna_blocks_per_sm() * ae_rows_dna_warps_per_block() * 32;
+        try {
+            ensure(w->stage, (size_t)lanes * AE_STAGE_ROWS * sizeof(uint2), st);
+            da.stage = ptr<uint2>(w->stage);
+            da.stage_cap = AE_STAGE_ROWS;
+        } catch (const ae_error &e) {
+            if (e.st != AE_ENOMEM) throw;
+        }
+    }
     const auto t_level = std::chrono::steady_clock::now();
     LevelCounters hc;
     auto run = [&]() {

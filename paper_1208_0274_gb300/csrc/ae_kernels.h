@@ -185,6 +185,12 @@ struct DnaRowsArgs {
     RangeHit *rhits;
     uint64_t hit_cap;
     LevelCounters *ctr;
+    // walk layout: the count phase keeps each pair's child row here (per warp and
+    // lane, stage_cap entries of (column, packed M | G_a)); rows that fit are
+    // copied out after the reservation instead of being computed again.  NULL:
+    // every row is computed twice
+    uint2 *stage;
+    int32_t stage_cap;
 };
 void ae_rows_dna(const DnaRowsArgs &a, int blocks, cudaStream_t st);
 int ae_rows_dna_blocks_per_sm();

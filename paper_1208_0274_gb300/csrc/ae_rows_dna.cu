@@ -103,6 +103,7 @@ struct WarpSmem {
     uint32_t bh[128];   // write: the child's counted hits
     uint32_t lo[128];   // child SA range
     uint32_t hi[128];
+    uint32_t sinfo[128];   // walk layout: a staged child row: 1 << 31 | lane << 16 | first entry; 0: not staged
     int32_t carry[4];   // per child index: the G_b scan's carry into the next chunk
     uint64_t base[3];   // write: the task's first slot in the frontier, leaf and hit arenas
 };
@@ -183,6 +184,11 @@ __device__ __forceinline__ void rows_seq(const DnaRowsArgs &a, WarpSmem &sm, int
     }
     const uint32_t npairs = __shfl_sync(FULL, poff, 31);
     poff -= np;
+    // count phase: this lane's staging region (its pairs' rows one after another)
+    uint2 *stg = nullptr;
+    if (!WRITE && a.stage)
+        stg = a.stage + ((int64_t)(blockIdx.x * DW + (threadIdx.x >> 5)) * 32 + lane) * a.stage_cap;
+    uint32_t sf = 0;   // entries staged so far in this task
     for (uint32_t p0 = 0; p0 < npairs; p0 += 32) {
         const uint32_t p = p0 + lane;
         const bool valid = p < npairs;
@@ -220,6 +226,7 @@ __device__ __forceinline__ void rows_seq(const DnaRowsArgs &a, WarpSmem &sm, int
         }
         uint32_t cnt = 0, hcnt = 0;
         bool bad = false;
+        const uint32_t sf0 = sf;   // count phase: where this pair's row starts in the staging region
         int32_t K = AE_KNEG, prev_j = -2, prev_M = 0;
         const int32_t *pjr = a.pj + off;     // the parent row
         const uint32_t *pmr = a.pmg + off;
@@ -289,8 +296,19 @@ __device__ __forceinline__ void rows_seq(const DnaRowsArgs &a, WarpSmem &sm, int
             }
             const bool hA = st && aliveA && MA >= H, hB = st && aliveB && MB >= H;
             if (!WRITE) {
-                cnt += (uint32_t)aliveA + (uint32_t)aliveB + (uint32_t)run_len;
+                const uint32_t n = (uint32_t)aliveA + (uint32_t)aliveB + (uint32_t)run_len;
+                cnt += n;
                 hcnt += (uint32_t)hA + (uint32_t)hB + (st ? (uint32_t)run_hits : 0u);
+                if (stg && n) {
+                    if (sf + n > (uint32_t)a.stage_cap) {
+                        stg = nullptr;   // the region is full: this and the later pairs are computed again
+                    } else {
+                        if (aliveA) stg[sf++] = make_uint2((uint32_t)j, pack_mg(MA, Gap));
+                        if (aliveB) stg[sf++] = make_uint2((uint32_t)(j + 1), pack_mg(MB, AE_NEG));
+                        for (int32_t r = 0; r < run_len; ++r)
+                            stg[sf++] = make_uint2((uint32_t)(rs + r), pack_mg(V0 - r * u, AE_NEG));
+                    }
+                }
             } else if (!bad) {
                 // every write stays inside the child's own range, as the count phase sized it
                 if (cnt + (uint32_t)aliveA + (uint32_t)aliveB + (uint32_t)run_len > ebud ||
@@ -342,6 +360,7 @@ __device__ __forceinline__ void rows_seq(const DnaRowsArgs &a, WarpSmem &sm, int
         if (!WRITE) {
             sm.a[slot] = cnt;
             sm.h[slot] = hcnt;
+            sm.sinfo[slot] = (stg && !bad) ? (0x80000000u | ((uint32_t)lane << 16) | sf0) : 0u;
         }
         if (bad) atomicExch(&a.ctr->overflow, 1ull);
     }
@@ -685,6 +704,7 @@ __global__ void __launch_bounds__(DW * 32, AE_DNA_MINB) k_rows_dna(DnaRowsArgs a
             sm.h[lane * 4 + c] = 0;
             sm.lo[lane * 4 + c] = clo[c];
             sm.hi[lane * 4 + c] = chi[c];
+            sm.sinfo[lane * 4 + c] = 0;
         }
         __syncwarp();
 
@@ -803,8 +823,50 @@ __global__ void __launch_bounds__(DW * 32, AE_DNA_MINB) k_rows_dna(DnaRowsArgs a
         }
         __syncwarp();
 
-        // ---- write phase: the same rows again, written at the reserved positions
-        rows_phase<SEQ>(true, a, sm, lane, wmask, smask, len, nd.off, qm, qH, tbase, qoff, qid, woff, total);
+        // ---- write phase: staged rows are copied to their reserved positions (four
+        // slots per lane), the others computed again and written there
+        unsigned rmask = wmask;
+        if (SEQ && a.stage) {
+            const uint2 *wst = a.stage + (int64_t)(blockIdx.x * DW + (threadIdx.x >> 5)) * 32 * a.stage_cap;
+#pragma unroll 1
+            for (int s0 = 0; s0 < 128; s0 += 32) {
+                const int slot = s0 + lane, L = slot >> 2, c = slot & 3;
+                const int32_t HL = __shfl_sync(FULL, qH, L), qL = __shfl_sync(FULL, qid, L);
+                const unsigned smL = __shfl_sync(FULL, smask, L), wmL = __shfl_sync(FULL, wmask, L);
+                const uint32_t info = sm.sinfo[slot];
+                if (!((wmL >> c) & 1u) || !(info >> 31)) continue;
+                const bool st = (smL >> c) & 1u;
+                const uint32_t n = sm.be[slot], nh = sm.bh[slot];
+                const uint64_t e = sm.base[st ? 0 : 1] + sm.a[slot];
+                const uint64_t h0 = sm.base[2] + sm.h[slot];
+                const uint2 *src = wst + (int64_t)((info >> 16) & 31u) * a.stage_cap + (info & 0xFFFFu);
+                const uint32_t clo_ = sm.lo[slot], chi_ = sm.hi[slot];
+                uint32_t nhit = 0;
+                for (uint32_t k = 0; k < n; ++k) {
+                    const uint2 x = src[k];
+                    const int32_t j = (int32_t)x.x;
+                    const int32_t M = mg_lo(x.y);
+                    if (st) {
+                        a.fj[e + k] = j;
+                        a.fmg[e + k] = x.y;
+                        if (M >= HL) {   // a kept entry reaching H is a hit (Section 2.2)
+                            if (nhit < nh) a.rhits[h0 + nhit] = RangeHit{clo_, chi_, qL, j, M, 0};
+                            ++nhit;
+                        }
+                    } else {
+                        a.lj[e + k] = j;
+                        a.lM[e + k] = M;
+                        a.lGa[e + k] = mg_hi(x.y);
+                    }
+                }
+                if (st && nhit != nh) atomicExch(&a.ctr->overflow, 1ull);   // the phases disagree
+            }
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                if (sm.sinfo[lane * 4 + c] >> 31) rmask &= ~(1u << c);
+        }
+        if (__any_sync(FULL, rmask != 0))
+            rows_phase<SEQ>(true, a, sm, lane, rmask, smask, len, nd.off, qm, qH, tbase, qoff, qid, woff, total);
     }
     }
     if (lane == 0 && trip_mine) atomicAdd(&a.ctr->triples, (unsigned long long)trip_mine);
