@@ -164,14 +164,17 @@ __device__ __forceinline__ void rows_seq(const DnaRowsArgs &a, WarpSmem &sm, int
     // bitonic sort of the node lanes by length), so that the lanes of a round walk
     // rows of similar length
     uint32_t key = (kmask ? min(len, (1u << 26) - 1u) : 0u) << 5 | (uint32_t)(31 - lane);   // distinct per lane
+    // with at most 32 pairs there is a single round, whose length no order changes
+    if (__reduce_add_sync(FULL, (uint32_t)__popc(kmask)) > 32) {
 #pragma unroll
-    for (int k = 2; k <= 32; k <<= 1) {
+        for (int k = 2; k <= 32; k <<= 1) {
 #pragma unroll
-        for (int jj = k >> 1; jj > 0; jj >>= 1) {
-            const uint32_t other = __shfl_xor_sync(FULL, key, jj);
-            const bool up = ((lane & k) == 0);          // this block sorts descending
-            const bool low = (lane & jj) == 0;
-            key = (low == up) ? max(key, other) : min(key, other);
+            for (int jj = k >> 1; jj > 0; jj >>= 1) {
+                const uint32_t other = __shfl_xor_sync(FULL, key, jj);
+                const bool up = ((lane & k) == 0);          // this block sorts descending
+                const bool low = (lane & jj) == 0;
+                key = (low == up) ? max(key, other) : min(key, other);
+            }
         }
     }
     const int sorted_lane = 31 - (int)(key & 31u);      // the node lane at this sorted position
