@@ -97,13 +97,15 @@ def test_normalisation_is_applied_inside_the_model():
     m.set_params(p)
     Xr = (X * x_sd + x_mu).astype(np.float32)
     dy = torch.empty((B, 2), dtype=torch.float32, device="cuda")
-    m.forward(_dev(Xr).data_ptr(), B, dy.data_ptr())
+    dxr = _dev(Xr)
+    m.forward(dxr.data_ptr(), B, dy.data_ptr())
     Xn = ((Xr.astype(np.float64) - x_mu) / x_sd)
     y_or, _ = mo.forward(p.astype(np.float64), Xn, bf16=True)
     assert np.allclose(dy.cpu().numpy(), y_or * y_sd + y_mu, rtol=5e-3, atol=5e-3 * np.abs(y_or * y_sd).max())
     # the loss is taken against normalised targets
     Tr = (T * y_sd + y_mu).astype(np.float32)
-    loss, _ = m.loss_grad(_dev(Xr).data_ptr(), _dev(Tr).data_ptr(), B, want_grads=False)
+    dtr = _dev(Tr)
+    loss, _ = m.loss_grad(dxr.data_ptr(), dtr.data_ptr(), B, want_grads=False)
     L_or, _ = mo.loss_and_grads(p.astype(np.float64), Xn, T, bf16=True)
     assert abs(loss - L_or) <= 5e-3 * abs(L_or)
     m.close()
@@ -117,7 +119,8 @@ def test_one_adam_step_matches_oracle():
     m.set_params(p)
     lr = 1e-2
     wd = 0.3
-    m.train(_dev(X).data_ptr(), _dev(T).data_ptr(), B, epochs=1, batch=B, lr=lr, weight_decay=wd, seed=3)
+    dx, dt = _dev(X), _dev(T)  # held: a freed temporary's memory would be handed to the next tensor
+    m.train(dx.data_ptr(), dt.data_ptr(), B, epochs=1, batch=B, lr=lr, weight_decay=wd, seed=3)
     p1 = m.get_params()
     _, g_or = mo.loss_and_grads(p.astype(np.float64), X, T, bf16=True)
     z = np.zeros_like(g_or)
@@ -130,6 +133,59 @@ def test_one_adam_step_matches_oracle():
     assert sure.sum() > 0.2 * p.size
     assert np.abs(p1.astype(np.float64) - p).max() <= lr * (1 + wd * np.abs(p).max() + 1e-3)
     m.close()
+
+
+@pytest.mark.parametrize("B", [1, 32, 64])
+def test_fused_training_step_matches_oracle(B):
+    # mini-batches of at most 64 rows train in one fused launch (fp32 products):
+    # one Adam step from the oracle's exact gradients
+    p, X, T = _random_problem(B, seed=100 + B)
+    m = ae.Mlp(0)
+    _identity_norm(m)
+    m.set_params(p)
+    lr, wd = 1e-2, 0.3
+    dx, dt = _dev(X), _dev(T)  # held: a freed temporary's memory would be handed to the next tensor
+    m.train(dx.data_ptr(), dt.data_ptr(), B, epochs=1, batch=B, lr=lr, weight_decay=wd, seed=3)
+    p1 = m.get_params()
+    _, g_or = mo.loss_and_grads(p.astype(np.float64), X, T, bf16=False)
+    z = np.zeros_like(g_or)
+    want, _, _ = mo.adam(p.astype(np.float64), g_or, z, z, t=1, lr=lr, wd=wd)
+    # as for the tensor-core path: where |g| is near Adam's epsilon the first step's
+    # size depends on the last bits of g, so parameters with small gradients are
+    # only bounded
+    sure = np.abs(g_or) > 1e-2 * np.abs(g_or).max()
+    assert np.allclose(p1[sure], want[sure], atol=1e-3 * lr + 1e-6)
+    assert sure.sum() > 0.2 * p.size
+    assert np.abs(p1.astype(np.float64) - p).max() <= lr * (1 + wd * np.abs(p).max() + 1e-3)
+    m.close()
+
+
+def test_fused_training_over_epochs_reduces_the_loss_and_keeps_the_step_count():
+    rng = np.random.default_rng(12)
+    n = 1000
+    X = rng.normal(size=(n, 66)).astype(np.float32)
+    w = rng.normal(size=(66, 2))
+    T = (np.tanh(X @ w / 8.0) * 3.0 + 1.0).astype(np.float32)
+    m = ae.Mlp(2)
+    _identity_norm(m)
+    dx, dt = _dev(X), _dev(T)
+    l0, _ = m.loss_grad(dx.data_ptr(), dt.data_ptr(), n, want_grads=False)
+    l1 = m.train(dx.data_ptr(), dt.data_ptr(), n, epochs=20, batch=32, lr=3e-3, seed=1)
+    l2, _ = m.loss_grad(dx.data_ptr(), dt.data_ptr(), n, want_grads=False)
+    assert l2 < 0.1 * l0 and l1 < 0.2 * l0
+    # Adam's step count carries over between calls: with one mini-batch per epoch
+    # (whose gradient no row order changes beyond rounding), two calls of one epoch
+    # equal one call of two; a restarted count would take a first step twice
+    a, b = ae.Mlp(2), ae.Mlp(2)
+    for mm in (a, b):
+        _identity_norm(mm)
+    dxs, dts = _dev(X[:32]), _dev(T[:32])
+    a.train(dxs.data_ptr(), dts.data_ptr(), 32, epochs=2, batch=32, lr=3e-3, seed=1)
+    for _ in range(2):
+        b.train(dxs.data_ptr(), dts.data_ptr(), 32, epochs=1, batch=32, lr=3e-3, seed=1)
+    assert np.allclose(a.get_params(), b.get_params(), rtol=1e-4, atol=1e-6)
+    for mm in (m, a, b):
+        mm.close()
 
 
 def test_training_reduces_the_loss_on_a_learnable_target():
