@@ -252,170 +252,6 @@ __global__ void k_gather(const float *x, const float *t, const int32_t *perm, in
     }
 }
 
-
-// ------------------------------------------------------------------ fused training
-//
-// The whole of ae_mlp_train for mini-batches of at most MLP_FUSED_BATCH rows in
-// one launch of one block: per step the rows are gathered and standardised,
-// the forward pass, the loss, the backward pass and the Adam update run in
-// shared memory and the block's registers, separated by block barriers.  The
-// products of the tensor-core path (tiny shapes: at most 64 x 128 x 128) would
-// spend their time in launches; here a training run is one launch.  Products
-// are fp32 (the tensor-core path rounds operands to bf16).
-constexpr int MLP_FUSED_BATCH = 64;
-constexpr int MLP_FUSED_THREADS = 256;
-
-struct FusedTrainArgs {
-    const float *x, *t;          // n x NIN raw inputs, n x NOUT raw targets
-    const int32_t *perm;         // epochs x n row order
-    int32_t n, epochs, batch;
-    float lr, wd;
-    int64_t step0;               // Adam steps taken before this run
-    const float *norm;
-    float *p, *g, *m, *v;
-    float *loss;                 // per step of the last epoch
-};
-
-__global__ void __launch_bounds__(MLP_FUSED_THREADS) k_mlp_train(FusedTrainArgs a) {
-    extern __shared__ float sh[];
-    const int B = a.batch;
-    float *X = sh;                         // B x NIN, standardised
-    float *Z1 = X + B * NIN;               // B x NH: pre-activations, then dL/dZ1
-    float *Z2 = Z1 + B * NH;               // B x NH: pre-activations, then dL/dZ2
-    float *Y = Z2 + B * NH;                // B x NOUT
-    float *TN = Y + B * NOUT;              // B x NOUT normalised targets
-    float *DY = TN + B * NOUT;             // B x NOUT
-    float *red = DY + B * NOUT;            // MLP_FUSED_THREADS
-    const int tid = threadIdx.x, nt = blockDim.x;
-    const float *W1 = a.p + OFF_W1, *b1 = a.p + OFF_B1, *W2 = a.p + OFF_W2, *b2 = a.p + OFF_B2;
-    const float *W3 = a.p + OFF_W3, *b3 = a.p + OFF_B3;
-    const int steps = (a.n + B - 1) / B;
-    int64_t step = a.step0;
-    for (int e = 0; e < a.epochs; ++e) {
-        const int32_t *perm = a.perm + (int64_t)e * a.n;
-        for (int k = 0; k < steps; ++k) {
-            const int r0 = k * B, rows = min(B, a.n - r0);
-            const float inv_b = 1.f / (float)rows;
-            // ---- gather and standardise
-            for (int i = tid; i < rows * NIN; i += nt) {
-                const int r = i / NIN, c = i % NIN;
-                X[i] = (a.x[(int64_t)perm[r0 + r] * NIN + c] - a.norm[NORM_XMU + c]) * a.norm[NORM_XISD + c];
-            }
-            for (int i = tid; i < rows * NOUT; i += nt) {
-                const int r = i / NOUT, c = i % NOUT;
-                TN[i] = (a.t[(int64_t)perm[r0 + r] * NOUT + c] - a.norm[NORM_YMU + c]) / a.norm[NORM_YSD + c];
-            }
-            __syncthreads();
-            // ---- forward
-            for (int i = tid; i < rows * NH; i += nt) {
-                const int r = i / NH, h = i % NH;
-                float s = b1[h];
-                for (int c = 0; c < NIN; ++c) s = fmaf(X[r * NIN + c], W1[h * NIN + c], s);
-                Z1[i] = s;
-            }
-            __syncthreads();
-            for (int i = tid; i < rows * NH; i += nt) {
-                const int r = i / NH, h = i % NH;
-                float s = b2[h];
-                for (int q = 0; q < NH; ++q) s = fmaf(fmaxf(Z1[r * NH + q], 0.f), W2[h * NH + q], s);
-                Z2[i] = s;
-            }
-            __syncthreads();
-            for (int i = tid; i < rows * NOUT; i += nt) {
-                const int r = i / NOUT, o = i % NOUT;
-                float s = b3[o];
-                for (int q = 0; q < NH; ++q) s = fmaf(fmaxf(Z2[r * NH + q], 0.f), W3[o * NH + q], s);
-                Y[i] = s;
-            }
-            __syncthreads();
-            // ---- loss L = sum r^2 / (2B) and dL/dy = r / B
-            float part = 0.f;
-            for (int i = tid; i < rows * NOUT; i += nt) {
-                const float r = Y[i] - TN[i];
-                DY[i] = r * inv_b;
-                part += r * r;
-            }
-            red[tid] = part;
-            __syncthreads();
-            for (int w = nt / 2; w > 0; w >>= 1) {
-                if (tid < w) red[tid] += red[tid + w];
-                __syncthreads();
-            }
-            if (tid == 0 && e == a.epochs - 1) a.loss[k] = red[0] * 0.5f * inv_b;
-            // ---- backward: layer 3, then dL/dZ2 in place of Z2
-            for (int i = tid; i < NOUT * NH; i += nt) {
-                const int o = i / NH, q = i % NH;
-                float s = 0.f;
-                for (int r = 0; r < rows; ++r) s = fmaf(DY[r * NOUT + o], fmaxf(Z2[r * NH + q], 0.f), s);
-                a.g[OFF_W3 + i] = s;
-            }
-            if (tid < NOUT) {
-                float s = 0.f;
-                for (int r = 0; r < rows; ++r) s += DY[r * NOUT + tid];
-                a.g[OFF_B3 + tid] = s;
-            }
-            __syncthreads();
-            for (int i = tid; i < rows * NH; i += nt) {
-                const int r = i / NH, q = i % NH;
-                float s = 0.f;
-                for (int o = 0; o < NOUT; ++o) s = fmaf(DY[r * NOUT + o], W3[o * NH + q], s);
-                Z2[i] = Z2[i] > 0.f ? s : 0.f;
-            }
-            __syncthreads();
-            // ---- layer 2, then dL/dZ1 in place of Z1
-            for (int i = tid; i < NH * NH; i += nt) {
-                const int h = i / NH, q = i % NH;
-                float s = 0.f;
-                for (int r = 0; r < rows; ++r) s = fmaf(Z2[r * NH + h], fmaxf(Z1[r * NH + q], 0.f), s);
-                a.g[OFF_W2 + i] = s;
-            }
-            for (int h = tid; h < NH; h += nt) {
-                float s = 0.f;
-                for (int r = 0; r < rows; ++r) s += Z2[r * NH + h];
-                a.g[OFF_B2 + h] = s;
-            }
-            __syncthreads();
-            for (int i = tid; i < rows * NH; i += nt) {
-                const int r = i / NH, q = i % NH;
-                float s = 0.f;
-                for (int h = 0; h < NH; ++h) s = fmaf(Z2[r * NH + h], W2[h * NH + q], s);
-                Z1[i] = Z1[i] > 0.f ? s : 0.f;
-            }
-            __syncthreads();
-            // ---- layer 1
-            for (int i = tid; i < NH * NIN; i += nt) {
-                const int h = i / NIN, c = i % NIN;
-                float s = 0.f;
-                for (int r = 0; r < rows; ++r) s = fmaf(Z1[r * NH + h], X[r * NIN + c], s);
-                a.g[OFF_W1 + i] = s;
-            }
-            for (int h = tid; h < NH; h += nt) {
-                float s = 0.f;
-                for (int r = 0; r < rows; ++r) s += Z1[r * NH + h];
-                a.g[OFF_B1 + h] = s;
-            }
-            __syncthreads();
-            // ---- Adam with decoupled weight decay (as k_adam)
-            ++step;
-            const float bc1 = 1.f - powf(0.9f, (float)step), bc2 = 1.f - powf(0.999f, (float)step);
-            for (int i = tid; i < NPARAM; i += nt) {
-                const float gi = a.g[i];
-                const float mi = 0.9f * a.m[i] + 0.1f * gi;
-                const float vi = 0.999f * a.v[i] + 0.001f * gi * gi;
-                a.m[i] = mi;
-                a.v[i] = vi;
-                const float pi = a.p[i];
-                a.p[i] = pi - a.lr * ((mi / bc1) / (sqrtf(vi / bc2) + 1e-8f) + a.wd * pi);
-            }
-            __syncthreads();
-        }
-    }
-}
-
-size_t fused_train_smem(int batch) {
-    return sizeof(float) * ((size_t)batch * (NIN + 2 * NH + 3 * NOUT) + MLP_FUSED_THREADS);
-}
-
 // ------------------------------------------------------------------ features
 
 // Window length of the interval feature: ceil(log4(n + 1)) + 4 letters, long
@@ -818,55 +654,6 @@ ae_status ae_mlp_train(ae_mlp *mlp, const float *d_x, const float *d_t, int32_t 
         std::vector<int32_t> perm(n);
         std::vector<float> losses(steps, 0.f);
         uint64_t s = seed;
-        if (batch <= MLP_FUSED_BATCH && epochs > 0) {
-            // small mini-batches: every epoch's order up front, then the whole run as
-            // one launch of k_mlp_train
-            std::vector<int32_t> all((size_t)epochs * n);
-            for (int32_t e = 0; e < epochs; ++e) {
-                for (int32_t i = 0; i < n; ++i) perm[i] = i;
-                for (int32_t i = n - 1; i > 0; --i) {      // Fisher-Yates, as below
-                    const int32_t j = (int32_t)(splitmix64(s) % (uint64_t)(i + 1));
-                    std::swap(perm[i], perm[j]);
-                }
-                std::copy(perm.begin(), perm.end(), all.begin() + (size_t)e * n);
-            }
-            int32_t *d_all = nullptr;
-            MC(cudaMallocAsync(&d_all, sizeof(int32_t) * all.size(), st));
-            MC(cudaMemcpyAsync(d_all, all.data(), sizeof(int32_t) * all.size(), cudaMemcpyHostToDevice, st));
-            FusedTrainArgs fa;
-            fa.x = d_x;
-            fa.t = d_t;
-            fa.perm = d_all;
-            fa.n = n;
-            fa.epochs = epochs;
-            fa.batch = batch;
-            fa.lr = lr;
-            fa.wd = weight_decay;
-            fa.step0 = mlp->step;
-            fa.norm = mlp->norm;
-            fa.p = mlp->p;
-            fa.g = mlp->g;
-            fa.m = mlp->m;
-            fa.v = mlp->v;
-            fa.loss = mlp->loss;
-            const size_t smem = fused_train_smem(batch);
-            MC(cudaFuncSetAttribute(k_mlp_train, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-            ++g_launches;
-            k_mlp_train<<<1, MLP_FUSED_THREADS, smem, st>>>(fa);
-            MC(cudaGetLastError());
-            MC(cudaFreeAsync(d_all, st));
-            mlp->step += (int64_t)epochs * steps;
-            if (loss) {
-                MC(cudaMemcpyAsync(losses.data(), mlp->loss, sizeof(float) * steps, cudaMemcpyDeviceToHost, st));
-                MC(cudaStreamSynchronize(st));
-                double acc = 0;
-                for (float v : losses) acc += v;
-                *loss = (float)(acc / steps);
-            } else {
-                MC(cudaStreamSynchronize(st));
-            }
-            return AE_OK;
-        }
         for (int32_t e = 0; e < epochs; ++e) {
             for (int32_t i = 0; i < n; ++i) perm[i] = i;
             for (int32_t i = n - 1; i > 0; --i) {          // Fisher-Yates

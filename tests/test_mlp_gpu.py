@@ -135,10 +135,10 @@ def test_one_adam_step_matches_oracle():
     m.close()
 
 
-@pytest.mark.parametrize("B", [1, 32, 64])
-def test_fused_training_step_matches_oracle(B):
-    # mini-batches of at most 64 rows train in one fused launch (fp32 products):
-    # one Adam step from the oracle's exact gradients
+@pytest.mark.parametrize("B", [1, 31, 64])
+def test_small_and_ragged_training_step_matches_oracle(B):
+    # mini-batches ragged against the 16-row mma tile and the 16-deep K chunks of the
+    # weight gradients (1, 31), and whole tiles (64)
     p, X, T = _random_problem(B, seed=100 + B)
     m = ae.Mlp(0)
     _identity_norm(m)
@@ -147,12 +147,10 @@ def test_fused_training_step_matches_oracle(B):
     dx, dt = _dev(X), _dev(T)  # held: a freed temporary's memory would be handed to the next tensor
     m.train(dx.data_ptr(), dt.data_ptr(), B, epochs=1, batch=B, lr=lr, weight_decay=wd, seed=3)
     p1 = m.get_params()
-    _, g_or = mo.loss_and_grads(p.astype(np.float64), X, T, bf16=False)
+    _, g_or = mo.loss_and_grads(p.astype(np.float64), X, T, bf16=True)
     z = np.zeros_like(g_or)
     want, _, _ = mo.adam(p.astype(np.float64), g_or, z, z, t=1, lr=lr, wd=wd)
-    # as for the tensor-core path: where |g| is near Adam's epsilon the first step's
-    # size depends on the last bits of g, so parameters with small gradients are
-    # only bounded
+    # as in the 128-row step: parameters with small gradients are only bounded
     sure = np.abs(g_or) > 1e-2 * np.abs(g_or).max()
     assert np.allclose(p1[sure], want[sure], atol=1e-3 * lr + 1e-6)
     assert sure.sum() > 0.2 * p.size
@@ -160,7 +158,7 @@ def test_fused_training_step_matches_oracle(B):
     m.close()
 
 
-def test_fused_training_over_epochs_reduces_the_loss_and_keeps_the_step_count():
+def test_training_over_epochs_reduces_the_loss_and_keeps_the_step_count():
     rng = np.random.default_rng(12)
     n = 1000
     X = rng.normal(size=(n, 66)).astype(np.float32)
