@@ -224,6 +224,9 @@ ae_status ae_index_info(const ae_index *idx, int64_t *n, int32_t *alphabet, int6
  * a group; counts[k] (host, nq entries) is the number of results of query k.
  * Free *hits with ae_hits_free.  stream is a cudaStream_t (NULL = the legacy
  * default stream); the call returns after the results are on the host.
+ * Results past 32 MiB are copied out by up to 8 host threads through pinned
+ * chunks (8 MiB, two per thread, kept with the stream's workspace); the call
+ * returns after those threads have finished.
  * Errors: AE_EINVAL, AE_ENOMEM, AE_ECUDA, AE_EUNSUPPORTED. */
 ae_status ae_search(const ae_index *idx, const ae_query *queries, int32_t nq,
                     const ae_scoring *scoring, const int32_t *H, const ae_options *opt,

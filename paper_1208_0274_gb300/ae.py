@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import weakref
 
 import numpy as np
 
@@ -277,11 +278,14 @@ def ae_search(index, queries, scheme, H, options=None, stream=None):
                        ctypes.byref(out), counts.ctypes.data, _stream_handle(stream))
     _check(st, "ae_search")
     total = int(counts[:nq].sum())
-    hits = np.empty(total, dtype=HIT_DTYPE)
-    if total:
-        ctypes.memmove(hits.ctypes.data, out.value, total * HIT_DTYPE.itemsize)
-    lib.ae_hits_free(out)
-    return hits, counts[:nq].copy()
+    if not total:
+        lib.ae_hits_free(out)
+        return np.empty(0, dtype=HIT_DTYPE), counts[:nq].copy()
+    # the array is a view of the library's buffer, which is freed when the last
+    # array over it goes away (no second copy of the results)
+    buf = (ctypes.c_uint8 * (total * HIT_DTYPE.itemsize)).from_address(out.value)
+    weakref.finalize(buf, lib.ae_hits_free, ctypes.c_void_p(out.value))
+    return np.frombuffer(buf, dtype=HIT_DTYPE, count=total), counts[:nq].copy()
 
 
 def ae_search_device(index, d_seq_ptr, offsets, scheme, H, d_hits_ptr, capacity, options=None, stream=None):

@@ -20,6 +20,8 @@
 #include <atomic>
 #include <mutex>
 #include <new>
+#include <system_error>
+#include <thread>
 #include <vector>
 
 #include "ae_internal.h"
@@ -183,6 +185,13 @@ struct Workspace {
     bool h_tot_static = false;
     uint8_t *h_stage = nullptr;   // pinned copy of the ASCII queries of ae_search (grow-only)
     size_t h_stage_bytes = 0;
+    // the threaded result copy of ae_search: two pinned chunks, one stream and two
+    // events per copying thread, and the event that orders them after the search
+    uint8_t *h_out = nullptr;
+    size_t h_out_bytes = 0;
+    std::vector<cudaStream_t> out_st;
+    std::vector<cudaEvent_t> out_ev;
+    cudaEvent_t out_ready = nullptr;
     int32_t leaf_cap = 0;
     std::mutex busy;              // one search at a time per workspace (per stream)
 
@@ -210,6 +219,10 @@ struct Workspace {
             }
         if (h_tot && !h_tot_static) cudaFreeHost(h_tot);
         if (h_stage) cudaFreeHost(h_stage);
+        if (h_out) cudaFreeHost(h_out);
+        for (cudaStream_t s : out_st) cudaStreamDestroy(s);
+        for (cudaEvent_t e : out_ev) cudaEventDestroy(e);
+        if (out_ready) cudaEventDestroy(out_ready);
     }
 
     // Free the buffers of one batch's walk (kept: queries, counters and the point
@@ -1613,6 +1626,100 @@ ae_status ae_index_info(const ae_index *idx, int64_t *n, int32_t *alphabet, int6
     return AE_OK;
 }
 
+// The results of ae_search leave the device through pinned double buffers.  Up
+// to OUT_THREADS host threads each copy a contiguous share of the hits in
+// chunks of OUT_CHUNK bytes on their own stream, and move chunk k into the
+// caller's buffer while chunk k + 1 is in flight.  A single copy into pageable
+// memory goes through the driver's staging on one core and takes the fresh
+// buffer's first-touch page faults one after another; here they are spread
+// over the threads.  Small results take the single copy.
+constexpr size_t OUT_CHUNK = (size_t)8 << 20;
+constexpr int OUT_THREADS = 8;
+constexpr size_t OUT_THREADED_MIN = (size_t)32 << 20;
+
+static ae_status copy_hits_out(Workspace *w, ae_hit *h, const ae_hit *dev, int64_t total, cudaStream_t st) {
+    const size_t bytes = sizeof(ae_hit) * (size_t)total;
+    if (bytes < OUT_THREADED_MIN) {
+        if (cudaMemcpyAsync(h, dev, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaStreamSynchronize(st) != cudaSuccess)
+            return AE_ECUDA;
+        return AE_OK;
+    }
+    int nt = (int)std::max(1u, std::min<unsigned>(OUT_THREADS, std::thread::hardware_concurrency()));
+    nt = (int)std::min<size_t>((size_t)nt, (bytes + OUT_CHUNK - 1) / OUT_CHUNK);
+    int dev_id = 0;
+    if (cudaGetDevice(&dev_id) != cudaSuccess) return AE_ECUDA;
+    const size_t need = (size_t)nt * 2 * OUT_CHUNK;
+    if (w->h_out_bytes < need) {
+        if (cudaStreamSynchronize(st) != cudaSuccess) return AE_ECUDA;
+        if (w->h_out) cudaFreeHost(w->h_out);
+        w->h_out = nullptr;
+        w->h_out_bytes = 0;
+        if (cudaMallocHost(&w->h_out, need) != cudaSuccess) return AE_ENOMEM;
+        w->h_out_bytes = need;
+    }
+    while ((int)w->out_st.size() < nt) {
+        // a thread's stream and its two events are kept only together
+        cudaStream_t s = nullptr;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&e0, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&e1, cudaEventDisableTiming) != cudaSuccess) {
+            if (e0) cudaEventDestroy(e0);
+            if (s) cudaStreamDestroy(s);
+            return AE_ECUDA;
+        }
+        w->out_st.push_back(s);
+        w->out_ev.push_back(e0);
+        w->out_ev.push_back(e1);
+    }
+    if (!w->out_ready && cudaEventCreateWithFlags(&w->out_ready, cudaEventDisableTiming) != cudaSuccess)
+        return AE_ECUDA;
+    if (cudaEventRecord(w->out_ready, st) != cudaSuccess) return AE_ECUDA;
+    std::atomic<int> fail{0};
+    auto share = [&](int t) {
+        if (cudaSetDevice(dev_id) != cudaSuccess) {
+            fail = 1;
+            return;
+        }
+        cudaStream_t s = w->out_st[t];
+        const size_t lo = sizeof(ae_hit) * ((size_t)total * t / nt);
+        const size_t hi = sizeof(ae_hit) * ((size_t)total * (t + 1) / nt);
+        const size_t nch = (hi - lo + OUT_CHUNK - 1) / OUT_CHUNK;
+        uint8_t *buf[2] = {w->h_out + (size_t)(2 * t) * OUT_CHUNK, w->h_out + (size_t)(2 * t + 1) * OUT_CHUNK};
+        auto issue = [&](size_t c) {
+            const size_t o = lo + c * OUT_CHUNK, len = std::min(OUT_CHUNK, hi - o);
+            return cudaMemcpyAsync(buf[c & 1], reinterpret_cast<const uint8_t *>(dev) + o, len,
+                                   cudaMemcpyDeviceToHost, s) == cudaSuccess &&
+                   cudaEventRecord(w->out_ev[2 * t + (c & 1)], s) == cudaSuccess;
+        };
+        bool ok = cudaStreamWaitEvent(s, w->out_ready, 0) == cudaSuccess && (nch == 0 || issue(0));
+        for (size_t c = 0; ok && c < nch; ++c) {
+            // chunk c + 1 goes into the buffer whose chunk c - 1 was moved out last round
+            if (c + 1 < nch && !issue(c + 1)) ok = false;
+            if (ok && cudaEventSynchronize(w->out_ev[2 * t + (c & 1)]) != cudaSuccess) ok = false;
+            if (ok) {
+                const size_t o = lo + c * OUT_CHUNK;
+                memcpy(reinterpret_cast<uint8_t *>(h) + o, buf[c & 1], std::min(OUT_CHUNK, hi - o));
+            }
+        }
+        // nothing may still be writing into the pinned chunks once this returns
+        if (cudaStreamSynchronize(s) != cudaSuccess) ok = false;
+        if (!ok) fail = 1;
+    };
+    std::vector<std::thread> th;
+    int started = 1;
+    try {
+        for (; started < nt; ++started) th.emplace_back(share, started);
+    } catch (const std::system_error &) {
+        // no more threads: the shares not handed out are copied here
+    }
+    share(0);
+    for (int t = started; t < nt; ++t) share(t);
+    for (std::thread &x : th) x.join();
+    return fail ? AE_ECUDA : AE_OK;
+}
+
 ae_status ae_search(const ae_index *idx, const ae_query *queries, int32_t nq, const ae_scoring *scoring,
                     const int32_t *H, const ae_options *opt, ae_hit **hits, int64_t *counts, void *stream) {
     if (!idx || !hits || !counts || nq < 0 || (nq > 0 && (!queries || !H))) return AE_EINVAL;
@@ -1664,10 +1771,10 @@ ae_status ae_search(const ae_index *idx, const ae_query *queries, int32_t nq, co
         ae_hit *h = (ae_hit *)malloc(sizeof(ae_hit) * (size_t)std::max<int64_t>(total, 1));
         if (!h) return AE_ENOMEM;
         if (total > 0) {
-            if (cudaMemcpyAsync(h, dev, sizeof(ae_hit) * (size_t)total, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-                cudaStreamSynchronize(st) != cudaSuccess) {
+            const ae_status ce = copy_hits_out(w, h, dev, total, st);
+            if (ce != AE_OK) {
                 free(h);
-                return AE_ECUDA;
+                return ce;
             }
         }
         for (int q = 0; q < nq; ++q) counts[q] = cnt[q];

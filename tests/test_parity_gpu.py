@@ -292,6 +292,33 @@ def test_device_entry_point_and_overflow(small):
     assert st == ae.AE_EOVERFLOW and counts[0] == want.size
 
 
+def test_large_host_results_equal_the_device_results():
+    # results past 32 MB leave the device in shares copied by several host threads
+    # through pinned chunks: they must equal the device entry point's results byte
+    # for byte, and the returned array must keep its buffer alive on its own
+    # (an exact copy of L letters at H = 30 gives about 0.4 L^2 results: past the
+    # diagonal's score d, gapped extensions stay above H for gaps up to (d - H) / 2)
+    rng = np.random.default_rng(77)
+    T = iid_text(200_000, DNA, [0.25] * 4, rng)
+    qs = [T[x:x + L].copy() for x, L in ((10_000, 2_000), (80_000, 2_011), (150_000, 1_999))]
+    scheme, Hs = Scheme(), [30] * len(qs)
+    idx = ae.ae_index_build(T, ae.AE_DNA)
+    hits, counts = ae.ae_search(idx, qs, scheme, Hs)
+    assert 32 << 20 < hits.nbytes < 160 << 20 and hits.size == counts.sum()
+    d = torch.from_numpy(np.concatenate(qs)).cuda()
+    off = np.concatenate([[0], np.cumsum([q.size for q in qs])]).astype(np.int64)
+    out = torch.empty(hits.size * 16, dtype=torch.uint8, device="cuda")
+    st, c2 = ae.ae_search_device(idx, d.data_ptr(), off, scheme, Hs, out.data_ptr(), hits.size)
+    assert st == ae.AE_OK and np.array_equal(c2, counts)
+    assert np.array_equal(out.cpu().numpy().view(ae.HIT_DTYPE), hits)
+    tail = hits[-1000:]
+    want_tail = tail.copy()
+    del hits
+    again, _ = ae.ae_search(idx, qs[:2], scheme, Hs[:2])
+    assert again.size > 0 and np.array_equal(tail, want_tail)
+    idx.close()
+
+
 def test_bad_letters_rejected(small):
     wl, idx = small
     with pytest.raises(ae.AEError) as e:
