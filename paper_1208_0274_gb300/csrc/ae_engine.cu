@@ -1630,7 +1630,7 @@ ae_status ae_index_info(const ae_index *idx, int64_t *n, int32_t *alphabet, int6
 // to OUT_THREADS host threads each copy a contiguous share of the hits in
 // chunks of OUT_CHUNK bytes on their own stream, and move chunk k into the
 // caller's buffer while chunk k + 1 is in flight.  A single copy into pageable
-// memory goes through the driver's staging on one core and takes the fresh
+// memory goes through the CUDA runtime's own staging on one core and takes the fresh
 // buffer's first-touch page faults one after another; here they are spread
 // over the threads.  Small results take the single copy.
 constexpr size_t OUT_CHUNK = (size_t)8 << 20;
