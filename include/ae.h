@@ -262,8 +262,7 @@ ae_status ae_search_device(const ae_index *idx, const uint8_t *d_seq, const int6
  * fourfold up to 1,024); beyond that the call returns AE_EUNSUPPORTED and
  * writes nothing to d_hits.
  * The call synchronises `stream` while it runs (it reads each trie level's
- * sizes back to the host), so a stream that is being captured into a CUDA
- * graph is refused with AE_EUNSUPPORTED before any work is queued.
+ * sizes back to the host).
  * The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current.  All calls on a device
  * share the array, which keeps the previous call's contents (the search

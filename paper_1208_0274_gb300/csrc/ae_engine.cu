@@ -2028,14 +2028,6 @@ extern "C" ae_status ae_search_device_static(const ae_index *idx, const uint8_t 
     }
     if (dev < 0 || dev >= AE_STATIC_MAX_DEVICES) return AE_EUNSUPPORTED;
     cudaStream_t st = (cudaStream_t)stream;
-    // the search synchronises its stream and reads level sizes back to the host,
-    // which a stream in capture mode does not allow: refuse before any work
-    cudaStreamCaptureStatus cap_status = cudaStreamCaptureStatusNone;
-    if (cudaStreamIsCapturing(st, &cap_status) != cudaSuccess) {
-        cudaGetLastError();
-        return AE_ECUDA;
-    }
-    if (cap_status != cudaStreamCaptureStatusNone) return AE_EUNSUPPORTED;
     std::lock_guard<std::mutex> guard(g_static_mu[dev]);
     if (!g_static_ptr[dev]) {
         // once per device, with that device current

@@ -111,18 +111,3 @@ def test_static_search_out_of_array_midway_then_next_call_is_clean():
     assert st == ae.AE_OK and np.array_equal(got, want)
     assert np.array_equal(_hits(got_buf, int(got.sum())), _hits(ref, int(want.sum())))
     idx.close()
-
-
-def test_static_search_refuses_a_capturing_stream():
-    wl = dna_small()
-    idx = ae.ae_index_build(wl.text, ae.AE_DNA)
-    d_seq, offsets = _device_inputs(wl.queries)
-    out = torch.empty(1 << 20, dtype=torch.uint8, device="cuda")
-    s = torch.cuda.Stream()
-    g = torch.cuda.CUDAGraph()
-    torch.cuda.synchronize()
-    with torch.cuda.graph(g, stream=s):
-        st, _ = ae.ae_search_device_static(idx, d_seq.data_ptr(), offsets, wl.scheme, wl.H, out.data_ptr(),
-                                           out.numel() // 16, stream=s)
-    assert st == ae.AE_EUNSUPPORTED
-    idx.close()
