@@ -1708,6 +1708,7 @@ static ae_status copy_hits_out(Workspace *w, ae_hit *h, const ae_hit *dev, int64
         if (!ok) fail = 1;
     };
     std::vector<std::thread> th;
+    th.reserve((size_t)nt);   // no reallocation (and no throw) once a thread runs
     int started = 1;
     try {
         for (; started < nt; ++started) th.emplace_back(share, started);
