@@ -176,7 +176,11 @@ typedef struct {
                                  results are the same */
 } ae_options;
 
-/* Fill *opt with the defaults. */
+/* Fill *opt with the defaults: qprefix_seed 1, leaf_segment 0, item_columns
+ * 2^24, batch_columns 2^20, leaf_capacity 4096, profile 0, leaf_delay 8,
+ * int16_limit 32000, hint_hits NULL, tier_stats 0, workspace_limit 0,
+ * general_rows 0, qprefix_domination 1, row_layout 0, fork_parts 1,
+ * fork_part 0, leaf_wide_rows 128. */
 void ae_options_default(ae_options *opt);
 
 /* Build an index of text[0..n) (host ASCII) for `alphabet` (AE_DNA or

@@ -94,8 +94,13 @@ def test_argument_errors_without_device():
 
 
 def test_options_default():
+    # the defaults the header lists
     o = ae.ae_options_default()
-    assert o.qprefix_seed == 1 and o.leaf_segment >= 0 and o.item_columns > 0
+    want = dict(qprefix_seed=1, leaf_segment=0, item_columns=1 << 24, batch_columns=1 << 20, leaf_capacity=4096,
+                profile=0, leaf_delay=8, int16_limit=32000, tier_stats=0, workspace_limit=0, general_rows=0,
+                qprefix_domination=1, row_layout=0, fork_parts=1, fork_part=0, leaf_wide_rows=128)
+    assert {k: getattr(o, k) for k in want} == want
+    assert not o.hint_hits
 
 
 @pytest.mark.parametrize("kind", ["iid", "period5", "blocks", "protein"])
