@@ -11,15 +11,18 @@
 //   reserves  its ranges in the five output arenas (frontier rows, leaf rows,
 //             frontier nodes, leaf injections, range hits) with one atomic
 //             per arena on the level's cursors, and
-//   writes    the child node records, injections, row entries and range hits,
-//             computing the rows a second time.
+//   writes    the child node records, injections, row entries and range hits:
+//             in the walk layout the rows the count phase staged (up to
+//             stage_cap entries per lane, DnaRowsArgs) are copied, longer rows
+//             and the other layouts are computed a second time.
 //
-// Rows are computed in one of two layouts chosen per level: short parent rows
-// walked one lane per (node, child) in column order (the horizontal gap as a
-// running key), long rows spread one parent entry per lane with the horizontal
-// gap as a segmented max-plus scan.  The general kernel (ae_trie.cu) handles
-// protein, the int32 route, root rows and cost-tier counting; both produce the
-// same nodes and arenas.
+// Rows are computed in one of three layouts chosen per level: short parent
+// rows walked one lane per (node, child) in column order (the horizontal gap
+// as a running key), long rows spread one parent entry per lane with the
+// horizontal gap as a segmented max-plus scan, and levels of few nodes with
+// long rows one node per block of WB_T threads (k_rows_dna_wide).  The general
+// kernel (ae_trie.cu) handles protein, the int32 route, root rows and cost-tier
+// counting; all produce the same nodes and arenas.
 #include <cuda_runtime.h>
 
 #include <algorithm>
