@@ -628,8 +628,10 @@ constexpr int LEAF_E = AE_LEAF_E;   // row entries per lane in the wide sweep st
 // The walk jumps to the next injection when R has no live entry.  Rows live
 // in per-warp global scratch (cap entries per buffer); a row that outgrows it
 // sets leaf_overflow and the host reruns with a larger cap.
-// The sweep's time is set by its longest walks (one warp each), which run
-// fastest with registers to spare: 3 resident blocks per SM (measured).
+// A walk whose row grows past esc_min entries is handed on, with the rest of
+// its segment, to a slot of k_leaf_wide (a block of threads per walk); when
+// the slots are taken the warp carries on itself.  The remaining warp walks
+// run fastest with registers to spare: 3 resident blocks per SM (measured).
 #ifndef AE_LEAF_MINB
 #define AE_LEAF_MINB 3
 #endif
