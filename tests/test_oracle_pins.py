@@ -98,6 +98,20 @@ def test_fig1_matrices():
     assert (M[4, 3], Ga[4, 3], Gb[4, 3]) == (-4, -4, -14)
 
 
+def test_theorem5_example_fgoe_scores():
+    # Section 4.1's example for Theorem 5: X = GCTACCCCCTTTGGAA and two forks whose
+    # query segments GCTACACCCTTT and GCTACCTCCTTT each differ from X[1..12] in one
+    # letter; both first gap-open entries score 8 (11 matches, one mismatch), and the
+    # common substring GGAA after them carries both on to 8 + s
+    X = "GCTACCCCCTTTGGAA"
+    P = "GCTACACCCTTT" + "GGAA" + "GCTACCTCCTTT" + "GGAA"
+    M, _, _ = oracle.mx_matrices(X, P, Scheme(1, -3, -5, -2))
+    pi1, pi2 = 1, 17
+    assert M[12, pi1 + 11] == 8 and M[12, pi2 + 11] == 8
+    for s in range(5):
+        assert M[12 + s, pi1 + 11 + s] == M[12 + s, pi2 + 11 + s] == 8 + s
+
+
 def test_basic_alg1_matches_oracle():
     rng = np.random.default_rng(11)
     for scheme in SCHEMES[:4]:
